@@ -1,0 +1,121 @@
+"""Overlap operator (Sec. 1):
+
+  D(mu) = 1/2 (1 + mu + (1 - mu) gamma5 sign(K)),
+
+sign(K) either from its spectral definition (Sec. 1: sum_i psi_i psi_i^dag
+sign(lambda_i) over the eigenpairs of the Hermitian K; dense eigh, small
+lattices only) or from the Zolotarev rational of Sec. 3,
+
+  epsilon(K) v = sum_i omega_i K (K^2 + sigma_i)^-1 v,
+
+each shifted system solved by its own plain conjugate gradient (no multi-shift,
+no pole dropping). Test infrastructure only.
+"""
+import numpy as np
+
+from . import wilson
+
+
+# ---------------------------------------------------------------- dense forms
+def dense_sign(Kd):
+    """sign(K) = Q sign(Lambda) Q^dag for Hermitian dense K (Sec. 1)."""
+    w, Q = np.linalg.eigh(Kd)
+    return (Q * np.sign(w)) @ np.conj(Q.T), w
+
+
+def dense_zolotarev_sign(Kd, omega, sigma):
+    """epsilon(K) evaluated on the spectrum of dense Hermitian K."""
+    w, Q = np.linalg.eigh(Kd)
+    ew = sum(om * w / (w * w + s) for om, s in zip(omega, sigma))
+    return (Q * ew) @ np.conj(Q.T)
+
+
+def gamma5_matrix(nsites):
+    g5 = np.diag(np.real(np.diag(wilson.GAMMA5)))
+    return np.kron(np.eye(nsites), np.kron(g5, np.eye(3))).astype(np.complex128)
+
+
+def dense_overlap(Sd, mu, nsites):
+    """D(mu) = 1/2 (1 + mu + (1 - mu) gamma5 S) as a dense matrix."""
+    n = Sd.shape[0]
+    G5 = gamma5_matrix(nsites)
+    return 0.5 * (1.0 + mu) * np.eye(n) + 0.5 * (1.0 - mu) * (G5 @ Sd)
+
+
+# ---------------------------------------------------------------- matrix free
+def vdot(a, b):
+    return np.vdot(a.ravel(), b.ravel())
+
+
+def norm(a):
+    return float(np.sqrt(np.real(vdot(a, a))))
+
+
+def cg(apply, b, tol, maxiter=100000):
+    """Plain conjugate gradient for Hermitian positive definite apply(); stops at
+    ||r|| <= tol * ||b||. Returns (x, iterations)."""
+    x = np.zeros_like(b)
+    r = b.copy()
+    p = r.copy()
+    rr = np.real(vdot(r, r))
+    stop = (tol * norm(b)) ** 2
+    it = 0
+    while rr > stop and it < maxiter:
+        Ap = apply(p)
+        alpha = rr / np.real(vdot(p, Ap))
+        x = x + alpha * p
+        r = r - alpha * Ap
+        rr_new = np.real(vdot(r, r))
+        p = r + (rr_new / rr) * p
+        rr = rr_new
+        it += 1
+    return x, it
+
+
+def zolotarev_sign_apply(U, v, m0, omega, sigma, tol=1e-13, antiperiodic_t=False,
+                         return_solutions=False):
+    """epsilon(K) v = K sum_i omega_i (K^2 + sigma_i)^-1 v, every pole by its own CG."""
+    K = lambda x: wilson.apply_K(U, x, m0, antiperiodic_t)
+    y = np.zeros_like(v)
+    sols = []
+    for om, s in zip(omega, sigma):
+        xi, _ = cg(lambda p, s=s: K(K(p)) + s * p, v, tol)
+        sols.append(xi)
+        y = y + om * xi
+    out = K(y)
+    if return_solutions:
+        return out, sols
+    return out
+
+
+def overlap_apply(U, v, m0, mu, omega, sigma, tol=1e-13, antiperiodic_t=False):
+    """D(mu) v = 1/2 (1+mu) v + 1/2 (1-mu) gamma5 epsilon(K) v."""
+    s = zolotarev_sign_apply(U, v, m0, omega, sigma, tol, antiperiodic_t)
+    return 0.5 * (1.0 + mu) * v + 0.5 * (1.0 - mu) * wilson.apply_gamma5(s)
+
+
+def overlap_apply_dagger(U, v, m0, mu, omega, sigma, tol=1e-13, antiperiodic_t=False):
+    """D^dag = gamma5 D gamma5 (gamma5-hermiticity, Sec. 1)."""
+    g5 = wilson.apply_gamma5
+    return g5(overlap_apply(U, g5(v), m0, mu, omega, sigma, tol, antiperiodic_t))
+
+
+def free_field_overlap_spectrum(dims, m0, mu, antiperiodic_t=False):
+    """Eigenvalues of D(mu) at U = 1 in closed form.
+
+    With gamma5 K = 2 kappa (b + i gamma.s), sign(K) = gamma5 (b + i gamma.s)/sqrt(b^2+s^2),
+    so gamma5 sign(K) = (b + i gamma.s)/sqrt(b^2+s^2), whose eigenvalues are
+    (b +- i|s|)/sqrt(b^2+|s|^2), each 6-fold per momentum (spin pair x colour).
+    """
+    lx, ly, lz, lt = dims
+    ps = [2 * np.pi * np.arange(L) / L for L in (lx, ly, lz)]
+    pt = 2 * np.pi * (np.arange(lt) + (0.5 if antiperiodic_t else 0.0)) / lt
+    P = np.meshgrid(ps[0], ps[1], ps[2], pt, indexing="ij")
+    b = (sum(1 - np.cos(p) for p in P) - m0).ravel()
+    s = np.sqrt(sum(np.sin(p) ** 2 for p in P)).ravel()
+    r = np.sqrt(b * b + s * s)
+    ev = []
+    for sg in (+1, -1):
+        lam = 0.5 * (1 + mu) + 0.5 * (1 - mu) * (b + sg * 1j * s) / r
+        ev.append(np.repeat(lam, 6))
+    return np.concatenate(ev)

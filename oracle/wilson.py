@@ -1,0 +1,123 @@
+"""Wilson kernel of the overlap operator, written out from Sec. 1 (the equation
+for aK_xy):
+
+  K psi(x) = gamma5 [ psi(x) - kappa sum_mu ( (1-gamma_mu) U_mu(x) psi(x+mu)
+                                             + (1+gamma_mu) U_mu(x-mu)^dag psi(x-mu) ) ]
+
+with kappa = 1/(8-2m). The gamma matrices are the Hermitian chiral
+(DeGrand-Rossi) set; the paper fixes only "the standard Hermitian form" with
+gamma_mu^2 = 1, and every pin used here is basis independent.
+
+No spin projection, no link compression, no blocking: explicit 4x4 spin
+matrices and 3x3 colour matrices applied with einsum. Test infrastructure only.
+"""
+import numpy as np
+
+# site axes of the canonical array (Lt, Lz, Ly, Lx): direction mu -> numpy axis
+MU_AXIS = {0: 3, 1: 2, 2: 1, 3: 0}
+
+I4 = np.eye(4, dtype=np.complex128)
+
+
+def gamma_matrices():
+    """(gamma_1..gamma_4, gamma_5) in the DeGrand-Rossi chiral basis."""
+    g = np.zeros((4, 4, 4), dtype=np.complex128)
+    i = 1j
+    g[0] = [[0, 0, 0, i], [0, 0, i, 0], [0, -i, 0, 0], [-i, 0, 0, 0]]
+    g[1] = [[0, 0, 0, -1], [0, 0, 1, 0], [0, 1, 0, 0], [-1, 0, 0, 0]]
+    g[2] = [[0, 0, i, 0], [0, 0, 0, -i], [-i, 0, 0, 0], [0, i, 0, 0]]
+    g[3] = [[0, 0, 1, 0], [0, 0, 0, 1], [1, 0, 0, 0], [0, 1, 0, 0]]
+    g5 = g[0] @ g[1] @ g[2] @ g[3]
+    return g, g5
+
+
+GAMMA, GAMMA5 = gamma_matrices()
+
+
+def kappa_of_m(m0):
+    """kappa = 1/(8 - 2m), Sec. 1."""
+    return 1.0 / (8.0 - 2.0 * m0)
+
+
+def shift(psi, mu, sign, antiperiodic_t=False):
+    """Return psi(x + sign*mu) for psi with site axes (..., Lt, Lz, Ly, Lx, ...).
+
+    psi has shape (..., Lt, Lz, Ly, Lx, 4, 3) or links (..., Lt, Lz, Ly, Lx, 3, 3):
+    the site axes are found counting from the end (two internal axes).
+    """
+    ax = psi.ndim - 6 + MU_AXIS[mu]
+    out = np.roll(psi, -sign, axis=ax)
+    if antiperiodic_t and mu == 3:
+        n = psi.shape[ax]
+        idx = [slice(None)] * psi.ndim
+        # the wrapped slice: for +t it is the last time slice, for -t the first
+        idx[ax] = n - 1 if sign > 0 else 0
+        out[tuple(idx)] *= -1.0
+    return out
+
+
+def shift_links(U_mu, mu, sign):
+    """U_mu(x + sign*mu-hat) for one link direction with axes (Lt, Lz, Ly, Lx, 3, 3)."""
+    ax = MU_AXIS[mu]
+    return np.roll(U_mu, -sign, axis=ax)
+
+
+def hopping(U, psi, antiperiodic_t=False):
+    """sum_mu (1-g_mu) U_mu(x) psi(x+mu) + (1+g_mu) U_mu(x-mu)^dag psi(x-mu)."""
+    out = np.zeros_like(psi)
+    for mu in range(4):
+        Umu = U[..., mu, :, :]
+        fwd = np.einsum("...ab,...sb->...sa", Umu, shift(psi, mu, +1, antiperiodic_t))
+        out += np.einsum("st,...tb->...sb", I4 - GAMMA[mu], fwd)
+        Ub = shift_links(Umu, mu, -1)                       # U_mu(x - mu)
+        bwd = np.einsum("...ba,...sb->...sa", np.conj(Ub), shift(psi, mu, -1, antiperiodic_t))
+        out += np.einsum("st,...tb->...sb", I4 + GAMMA[mu], bwd)
+    return out
+
+
+def apply_gamma5(psi):
+    return np.einsum("st,...tb->...sb", GAMMA5, psi)
+
+
+def apply_K(U, psi, m0, antiperiodic_t=False):
+    """K psi = gamma5 [psi - kappa * hopping(psi)]   (Sec. 1, aK_xy)."""
+    kap = kappa_of_m(m0)
+    return apply_gamma5(psi - kap * hopping(U, psi, antiperiodic_t))
+
+
+def apply_DW(U, psi, m0, antiperiodic_t=False):
+    """gamma5 K = 1 - kappa*hopping (the Wilson operator up to the factor 2 kappa)."""
+    kap = kappa_of_m(m0)
+    return psi - kap * hopping(U, psi, antiperiodic_t)
+
+
+def dense_operator(apply, site_shape):
+    """Dense matrix of a linear map on spinors: column j = apply(e_j)."""
+    n = int(np.prod(site_shape)) * 12
+    eye = np.eye(n, dtype=np.complex128).reshape((n,) + tuple(site_shape) + (4, 3))
+    cols = apply(eye)                                   # batched over the leading axis
+    return cols.reshape(n, n).T.copy()
+
+
+def dense_K(U, m0, antiperiodic_t=False):
+    site_shape = U.shape[:4]
+    return dense_operator(lambda v: apply_K(U, v, m0, antiperiodic_t), site_shape)
+
+
+def free_field_K_abs_spectrum(dims, m0, antiperiodic_t=False):
+    """|lambda(K)| for U = 1, from the plane-wave closed form.
+
+    With psi = e^{ipx} u, the hopping term gives sum_mu [2cos p_mu - 2i gamma_mu sin p_mu],
+    so gamma5 K = 2 kappa [ b(p) + i gamma.s(p) ], b = sum_mu (1 - cos p_mu) - m0,
+    s_mu = sin p_mu, hence |lambda| = 2 kappa sqrt(b^2 + |s|^2), 12-fold per momentum
+    (4 spins x 3 colours; the sign splits 6/6).
+    """
+    lx, ly, lz, lt = dims
+    kap = kappa_of_m(m0)
+    ps = [2 * np.pi * np.arange(L) / L for L in (lx, ly, lz)]
+    pt = 2 * np.pi * (np.arange(lt) + (0.5 if antiperiodic_t else 0.0)) / lt
+    P = np.meshgrid(ps[0], ps[1], ps[2], pt, indexing="ij")
+    b = sum(1 - np.cos(p) for p in P) - m0
+    s2 = sum(np.sin(p) ** 2 for p in P)
+    lam = 2 * kap * np.sqrt(b ** 2 + s2)
+    return np.sort(np.repeat(lam.ravel(), 12))

@@ -1,0 +1,37 @@
+"""Pin of the oracle's gauge-link gradient: central finite differences of S along
+random Lie-algebra directions U -> exp(i h X) U, with S evaluated by dense
+linear algebra on the frozen Zolotarev rational (2^4 lattice)."""
+import numpy as np
+
+import synth
+from oracle import wilson, overlap, zolotarev as zo, force
+
+
+def _S_dense(U, phi, m0, mu, om, sg):
+    Kd = wilson.dense_K(U, m0)
+    E = overlap.dense_zolotarev_sign(Kd, om, sg)
+    ns = int(np.prod(U.shape[:4]))
+    D = overlap.dense_overlap(E, mu, ns)
+    x = np.linalg.solve(D.conj().T @ D, phi.ravel())
+    return float(np.real(np.vdot(phi.ravel(), x)))
+
+
+def test_force_finite_differences():
+    dims = (2, 2, 2, 2)
+    m0, mu = 1.4, 0.05
+    U = synth.gauge_links(dims, 0.3, 31)
+    phi = synth.gaussian_source(dims, 32)
+    om, sg, _ = zo.zolotarev(8, 0.15, 2.6)
+    G = force.gradient(U, phi, m0, mu, om, sg, tol=1e-13)
+    rng = np.random.Generator(np.random.PCG64(33))
+    lam = synth._gell_mann()
+    h = 1e-5
+    for _ in range(6):
+        X = np.einsum("...a,aij->...ij", rng.standard_normal(U.shape[:5] + (8,)), lam) * 0.5
+        w, v = np.linalg.eigh(X)
+        expo = lambda t: np.einsum("...ij,...j,...kj->...ik", v, np.exp(1j * t * w), np.conj(v))
+        Sp = _S_dense(expo(h) @ U, phi, m0, mu, om, sg)
+        Sm = _S_dense(expo(-h) @ U, phi, m0, mu, om, sg)
+        fd = (Sp - Sm) / (2 * h)
+        an = 2 * np.real(np.sum(np.conj(G) * (1j * X @ U)))
+        assert abs(fd - an) <= 1e-6 * max(1.0, abs(an))

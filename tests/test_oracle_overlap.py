@@ -1,0 +1,87 @@
+"""Pins of the oracle's overlap operator (Sec. 1) and sign function (Secs. 1, 3):
+sign(K)^2 = 1, the Zolotarev error bound against the spectral sign, per-pole CG
+against the dense rational, the Ginsparg-Wilson relation, gamma5-hermiticity,
+the circle spectrum, normality, [gamma5, D^dag D] = 0, the mass dependence of
+D^dag D, and the free-field overlap spectrum in closed form."""
+import numpy as np
+import pytest
+
+import synth
+from oracle import wilson, overlap, zolotarev as zo
+from tests.oracle_util import dense_setup
+
+DIMS = (2, 2, 2, 2)
+NS = 16
+
+
+def test_sign_squares_to_one():
+    U, Kd, S, w = dense_setup(DIMS)
+    assert np.allclose(S @ S, np.eye(S.shape[0]), atol=1e-12)
+    assert np.allclose(S, S.conj().T, atol=1e-13)
+
+
+def test_zolotarev_bound_and_per_pole_cg():
+    U, Kd, S, w = dense_setup(DIMS)
+    a, b = 0.99 * np.min(np.abs(w)), 1.01 * np.max(np.abs(w))
+    om, sg, delta = zo.zolotarev(6, a, b)
+    E = overlap.dense_zolotarev_sign(Kd, om, sg)
+    assert np.linalg.norm(E - S, 2) <= delta * (1 + 1e-8) + 1e-14
+    v = synth.gaussian_source(DIMS, 4)
+    got = overlap.zolotarev_sign_apply(U, v, 1.4, om, sg, tol=1e-14)
+    ref = (E @ v.ravel()).reshape(v.shape)
+    assert np.linalg.norm(got - ref) <= 1e-11 * np.linalg.norm(ref)
+
+
+def _D(S, mu):
+    return overlap.dense_overlap(S, mu, NS)
+
+
+def test_ginsparg_wilson():
+    _, _, S, _ = dense_setup(DIMS)
+    D0 = _D(S, 0.0)
+    G5 = overlap.gamma5_matrix(NS)
+    gw = D0 @ G5 @ (np.eye(D0.shape[0]) - 2 * D0) + G5 @ D0
+    assert np.max(np.abs(gw)) < 1e-12
+
+
+@pytest.mark.parametrize("mu", [0.0, 0.05, 0.3])
+def test_gamma5_hermiticity_circle_normality(mu):
+    _, _, S, _ = dense_setup(DIMS)
+    D = _D(S, mu)
+    G5 = overlap.gamma5_matrix(NS)
+    assert np.allclose(D.conj().T, G5 @ D @ G5, atol=1e-13)
+    assert np.allclose(D @ D.conj().T, D.conj().T @ D, atol=1e-12)
+    lam = np.linalg.eigvals(D)
+    assert np.allclose(np.abs(lam - (1 + mu) / 2), (1 - mu) / 2, atol=1e-12)
+    DD = D.conj().T @ D
+    assert np.allclose(G5 @ DD, DD @ G5, atol=1e-12)
+    D0 = _D(S, 0.0)
+    assert np.allclose(DD, mu ** 2 * np.eye(DD.shape[0]) + (1 - mu ** 2) * D0.conj().T @ D0, atol=1e-12)
+
+
+@pytest.mark.parametrize("dims,apt", [((2, 2, 2, 2), False), ((2, 2, 2, 4), True)])
+def test_free_field_overlap_spectrum(dims, apt):
+    mu = 0.05
+    U = synth.unit_links(dims)
+    Kd = wilson.dense_K(U, 1.4, apt)
+    S, _ = overlap.dense_sign(Kd)
+    ns = int(np.prod(dims))
+    lam = np.linalg.eigvals(overlap.dense_overlap(S, mu, ns))
+    ref = overlap.free_field_overlap_spectrum(dims, 1.4, mu, apt)
+    key = lambda z: (np.round(z.real, 9), np.round(z.imag, 9))
+    assert np.allclose(sorted(lam, key=key), sorted(ref, key=key), atol=1e-11)
+    if not apt:
+        # p = 0 gives lambda = mu, 12-fold (exact zero modes of D(0))
+        assert np.sum(np.abs(lam - mu) < 1e-10) == 12
+
+
+def test_matrix_free_overlap_matches_dense():
+    U, Kd, S, w = dense_setup(DIMS)
+    a, b = 0.99 * np.min(np.abs(w)), 1.01 * np.max(np.abs(w))
+    om, sg, delta = zo.zolotarev(12, a, b)
+    v = synth.gaussian_source(DIMS, 9)
+    got = overlap.overlap_apply(U, v, 1.4, 0.05, om, sg, tol=1e-14)
+    ref = (_D(S, 0.05) @ v.ravel()).reshape(v.shape)
+    assert np.linalg.norm(got - ref) <= 1e-11 * np.linalg.norm(ref)
+    gd = overlap.overlap_apply_dagger(U, v, 1.4, 0.05, om, sg, tol=1e-14)
+    assert np.linalg.norm(gd - (_D(S, 0.05).conj().T @ v.ravel()).reshape(v.shape)) <= 1e-11 * np.linalg.norm(ref)
