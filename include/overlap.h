@@ -1,0 +1,207 @@
+/*
+ * overlap.h -- C ABI of liboverlap, a GB300 (sm_103a) implementation of the
+ * deflated overlap-fermion inverter of Cundy & Lee, "The eigSUMR inverter for
+ * overlap fermions" (arXiv:1501.01855).
+ *
+ * Operators (Sec. 1):
+ *   K      = gamma5 [1 - kappa sum_mu ((1-gamma_mu) U_mu(x) T_{+mu} + (1+gamma_mu) U_mu(x-mu)^dag T_{-mu})],
+ *            kappa = 1/(8 - 2 m0)                       (Sec. 1, the equation for aK_xy)
+ *   D(mu)  = 1/2 (1 + mu + (1 - mu) gamma5 sign(K))      (Sec. 1)
+ *   sign(K) ~ eps(K) = sum_i omega_i K (K^2 + sigma_i)^-1 (Zolotarev, Sec. 3),
+ *            evaluated by multi-shift CG to a caller-chosen accuracy eta.
+ * Solvers: GMRESR (Alg. 3) around relaxed SUMR (Algs. 1-2, Sec. 3) or relaxed,
+ * spectrally preconditioned CGNE (Alg. 4); eigSUMR accumulation (Algs. 5-6);
+ * Galerkin / least-squares deflation (Sec. 4).
+ *
+ * Conventions shared by every entry point
+ *   - Every call returns an ovl_status; on failure overlap_last_error() gives a
+ *     one-line reason. Nothing aborts the process.
+ *   - Lattice dims are {Lx, Ly, Lz, Lt}; site = ((t*Lz + z)*Ly + y)*Lx + x.
+ *   - Spinors are in the canonical layout [site][spin 4][colour 3] of interleaved
+ *     complex numbers, either complex128 (OVL_C128) or complex64 (OVL_C64).
+ *     A batch of n spinors is n such fields back to back.
+ *   - Links are [site][mu 4][row 3][col 3] complex128, mu = 0..3 -> x,y,z,t.
+ *   - The gamma matrices are the Hermitian chiral (DeGrand-Rossi) set, gamma5 =
+ *     diag(1,1,-1,-1).
+ *   - "on_device" = 1: the pointers are CUDA device pointers on the context's
+ *     device; 0: host pointers (the library copies through pinned staging).
+ *   - The library never frees or keeps caller memory. All internal memory is
+ *     owned by the context (or the deflation object) and released by the
+ *     matching destroy call.
+ *   - All work is issued on the context's stream (ovl_params.stream, default
+ *     the legacy default stream); calls return after that work has completed.
+ *   - A context is not thread safe; use one context per host thread.
+ */
+#ifndef OVERLAP_H
+#define OVERLAP_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct ovl_ctx ovl_ctx;
+typedef struct ovl_defl ovl_defl;
+
+typedef enum {
+  OVL_OK = 0,
+  OVL_EINVAL = -1,      /* bad argument (null pointer, bad size, bad enum)            */
+  OVL_ENOMEM = -2,      /* device or host allocation failed                           */
+  OVL_ECUDA = -3,       /* a CUDA runtime call failed (message has the CUDA error)    */
+  OVL_ENOCONV = -4,     /* iteration limit reached before the tolerance               */
+  OVL_EBREAKDOWN = -5,  /* SUMR/CG breakdown (sigma_j^2 <= 0, NaN or Inf)             */
+  OVL_EAPPROX = -6,     /* Zolotarev Delta(n_poles, a, b) > eps_sign                  */
+  OVL_ETIMEOUT = -7     /* a device-side bounded wait gave up                         */
+} ovl_status;
+
+enum { OVL_C128 = 0, OVL_C64 = 1 };                     /* spinor element types       */
+enum { OVL_PREC_F64 = 0, OVL_PREC_F32 = 1, OVL_PREC_F16 = 2, OVL_PREC_AUTO = -1 };
+enum { OVL_SOLVER_SUMR = 0, OVL_SOLVER_CG = 1 };
+
+typedef struct {
+  int    solver;        /* OVL_SOLVER_SUMR (GMRESR(relSUMR)) or OVL_SOLVER_CG (GMRESR(relCG))   */
+  int    mixed;         /* 1: low-precision sign when eta allows (Sec. 3, mixed precision);
+                           0: plain FP64 everywhere                                              */
+  int    half_storage;  /* 1: FP16 links/vectors in the sign when eta >= half_switch            */
+  double eta_floor;     /* sign accuracy never worse than this (Sec. 3): default 1e-2           */
+  double sp_switch;     /* eta above which the FP32 sign is used: default 1e-6                  */
+  double half_switch;   /* eta above which FP16 storage is used: default 2e-3                    */
+  double eta_precond;   /* middle-solve relative accuracy eta~ (Alg. 3); 0 = tol^(1/3)          */
+  double relax_factor;  /* relaxation eta_j = relax_factor * eps_A ||b|| / ||r_j||: default 1   */
+  int    gmresr_max;    /* outer steps, default 30                                              */
+  int    inner_max;     /* middle-solver iterations per outer step, default 2000                */
+  int    mscg_max;      /* multi-shift CG iterations per sign, default 5000                     */
+  double delta_split;   /* pair splitting delta of Sec. 5, default 0.01                         */
+  double c_spec;        /* spectral-preconditioner constant c (Sec. 4), default sqrt(3)/2      */
+  int    bc_t;          /* 0 periodic, 1 antiperiodic in t (fermions only)                      */
+  double a_override;    /* >0: use this lower bound a of |lambda(K)|, else estimate by Lanczos  */
+  double b_override;    /* >0: use this upper bound b of |lambda(K)|, else estimate by Lanczos  */
+  int    batch_max;     /* systems advanced together in one lock-step batch, default 36         */
+  int    verify;        /* 1: after a solve, recompute ||b - D x|| / ||b|| with an FP64 sign at
+                           eps_sign (one more sign application per system); 0: report the
+                           GMRESR recursive residual. Default 1                                 */
+  void*  stream;        /* cudaStream_t for all work; NULL = legacy default stream              */
+} ovl_params;
+
+typedef struct {
+  int    converged;        /* 1 if the FP64 true residual met tol                                */
+  int    outer_iters;      /* GMRESR steps                                                       */
+  int    inner_iters;      /* SUMR or CG iterations summed over outer steps                      */
+  int    sign_calls;       /* applications of the sign function                                  */
+  long long wilson_calls;  /* Wilson-kernel applications, FP64 counted as 2 (Sec. 6)             */
+  long long wilson_f64, wilson_f32, wilson_f16;   /* raw counts per precision                   */
+  double true_residual;    /* ||b - D x|| / ||b||: with params.verify, recomputed with an FP64
+                              sign at eps_sign accuracy; else the GMRESR recursive residual      */
+  double seconds;          /* wall time of this system's solve (shared by a batch)               */
+} ovl_solve_info;
+
+/* Fill *p with the defaults listed above. */
+ovl_status ovl_params_default(ovl_params* p);
+
+/* Build a context for one gauge field.
+ *   dims[4]   {Lx, Ly, Lz, Lt}, each even and >= 2.
+ *   links     host, canonical layout, complex128, 4*9*V entries; copied and
+ *             converted to the library's 12-real device layouts (row 3 of every
+ *             SU(3) link is rebuilt as conj(row1 x row2) in registers).
+ *   m0        Wilson mass, kappa = 1/(8 - 2 m0) (Sec. 1).
+ *   mu        default overlap mass parameter of D(mu) (Sec. 1).
+ *   n_poles   Zolotarev order N_Z (Sec. 3), 1..64.
+ *   eps_sign  required Zolotarev Delta; OVL_EAPPROX if the bounds [a, b] need more
+ *             poles than n_poles.
+ *   params    may be NULL (defaults).
+ * The spectral bounds a = min|lambda(K)|, b = max|lambda(K)| come from
+ * params->a_override / b_override when positive, else from an FP64 Lanczos run
+ * on K^2 with safety margins (a * 0.9, b * 1.05). */
+ovl_status overlap_create(ovl_ctx** ctx, const int dims[4], const double* links, double m0, double mu,
+                          int n_poles, double eps_sign, const ovl_params* params);
+void overlap_destroy(ovl_ctx* ctx);
+const char* overlap_last_error(const ovl_ctx* ctx);
+
+/* Host-only (no GPU needed): the Zolotarev rational of order n on a < |x| < b
+ * (Sec. 3), eps(x) = sum_i omega_i x / (x^2 + sigma_i), sigma ascending, and its
+ * maximum error delta, from Jacobi elliptic functions (AGM / descending Landen). */
+ovl_status ovl_zolotarev_coeffs(int n, double a, double b, double* omega, double* sigma, double* delta);
+
+/* Zolotarev data of the context: omega[n_poles], sigma[n_poles] (may be NULL),
+ * the error Delta and the bounds a, b actually used (Sec. 3). */
+ovl_status overlap_zolotarev(const ovl_ctx* ctx, double* omega, double* sigma, double* delta,
+                             double* a, double* b);
+
+/* out = K in for n spinors (Sec. 1). prec selects the kernel: OVL_PREC_F64 computes
+ * in FP64; OVL_PREC_F32 / F16 round the input to FP32 / FP16 storage and compute in
+ * FP32. */
+ovl_status ovl_wilson_apply(ovl_ctx* ctx, const void* in, void* out, int n, int dtype, int on_device,
+                            int prec);
+
+/* out = eps(K) in (Sec. 3) for n spinors, multi-shift CG stopped at accuracy eta
+ * (the per-pole rule of the Zolotarev sum; eta <= 0 means eps_sign). prec as above,
+ * OVL_PREC_AUTO picks by eta. */
+ovl_status ovl_sign_apply(ovl_ctx* ctx, const void* in, void* out, int n, int dtype, int on_device,
+                          double eta, int prec);
+
+/* out = D(mu) in (Sec. 1) for n spinors at sign accuracy eta (eta <= 0: eps_sign).
+ * hermitian = 1 returns H in = gamma5 D(mu) in instead. */
+ovl_status overlap_apply(ovl_ctx* ctx, double mu, const void* in, void* out, int n, int dtype,
+                         int on_device, double eta, int prec, int hermitian);
+
+/* Solve D(mu_k) x = b for nrhs sources and nmass masses (GMRESR, Alg. 3, around
+ * relSUMR or relCG, Sec. 3). x holds nmass*nrhs spinors, mass-major
+ * (x[k*nrhs + j] solves mass k, source j). tol is the relative FP64 true-residual
+ * target. defl may be NULL (undeflated) or a space from eigsumr_accumulate();
+ * its eigenvectors of D^dag D are mass independent (Sec. 1) and serve every mass.
+ * info (may be NULL) receives nmass*nrhs records. Systems are advanced in
+ * lock-step batches of at most params.batch_max. */
+ovl_status overlap_solve(ovl_ctx* ctx, int nrhs, const double* mus, int nmass, const void* rhs, void* x,
+                         int dtype, int on_device, double tol, ovl_defl* defl, ovl_solve_info* info);
+
+/* Solve D(mu) x = b once while accumulating Ritz vectors of D^dag D + 2 mu delta H
+ * (eigSUMR, Algs. 5-6, Sec. 5) with basis size m_basis, keeping n_eig. If *defl is
+ * NULL a new space is created; otherwise its vectors seed the basis and are
+ * improved. The space can then be passed to overlap_solve(). */
+ovl_status eigsumr_accumulate(ovl_ctx* ctx, ovl_defl** defl, int n_eig, int m_basis, double mu,
+                              const void* rhs, void* x, int dtype, int on_device, double tol,
+                              ovl_solve_info* info);
+
+/* Ritz values (n) and eigenvector residuals ||gamma5 D v - v (v, gamma5 D v)|| (n)
+ * of a deflation space; *n receives the number of vectors held. */
+ovl_status ovl_defl_info(const ovl_defl* defl, int* n, double* ritz, double* residuals);
+
+/* Copy vector i of the space (v_i and v^D_i = D v_i) to host complex128 buffers. */
+ovl_status ovl_defl_vector(const ovl_defl* defl, int i, double* v, double* vD);
+
+/* Raw little-endian save / load of a deflation space (a text header line, then
+ * v and v^D as complex128 canonical spinors). */
+ovl_status ovl_defl_save(const ovl_defl* defl, const char* path);
+ovl_status ovl_defl_load(ovl_ctx* ctx, ovl_defl** defl, const char* path);
+void ovl_defl_destroy(ovl_defl* defl);
+
+/* Gauge-link gradient of S = phi^dag (D^dag D)^-1 phi through the Zolotarev rational
+ * with fixed coefficients (not in the paper; dS = 2 Re sum conj(G) dU).
+ * dSdU receives 4*9*V complex128 entries in the canonical link layout; S (may be
+ * NULL) receives the action. tol is the accuracy of every inner solve. */
+ovl_status overlap_force(ovl_ctx* ctx, double mu, const void* phi, int dtype, int on_device, double tol,
+                         double* dSdU, double* S);
+
+/* Kernel-level timing collected with CUDA events on the context stream while
+ * enabled: per kernel class, launches, total milliseconds and algorithmic bytes.
+ * Classes: 0 Wilson FP64, 1 Wilson FP32, 2 Wilson FP16-storage, 3 multi-shift
+ * update, 4 vector ops, 5 reductions/scalars, 6 Gram/rotate, 7 force. */
+enum { OVL_PROF_CLASSES = 8 };
+ovl_status ovl_profile_enable(ovl_ctx* ctx, int on);
+ovl_status ovl_profile_reset(ovl_ctx* ctx);
+ovl_status ovl_profile_get(ovl_ctx* ctx, int cls, long long* launches, double* ms, double* bytes);
+
+/* Run `iters` back-to-back Wilson-kernel launches on the library's own device
+ * fields (n spinors, precision prec) and report the mean milliseconds per launch
+ * (CUDA events on the context stream) and algorithmic bytes per launch. */
+ovl_status ovl_bench_wilson(ovl_ctx* ctx, int prec, int n, int iters, double* ms_per_launch,
+                            double* bytes_per_launch);
+
+/* Library version string. */
+const char* ovl_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* OVERLAP_H */

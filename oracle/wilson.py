@@ -91,6 +91,34 @@ def apply_DW(U, psi, m0, antiperiodic_t=False):
     return psi - kap * hopping(U, psi, antiperiodic_t)
 
 
+def apply_K_sites(U, psi, m0, sites, antiperiodic_t=False):
+    """(K psi)(x) at the listed sites only, x = (x, y, z, t) rows of ``sites``:
+    the same formula evaluated from the 8 neighbours of each site (for spot checks
+    of large lattices)."""
+    kap = kappa_of_m(m0)
+    lt, lz, ly, lx = psi.shape[:4]
+    L = (lx, ly, lz, lt)
+    out = []
+    for (x, y, z, t) in np.asarray(sites):
+        c = [int(x), int(y), int(z), int(t)]
+        acc = np.zeros((4, 3), dtype=np.complex128)
+        for mu in range(4):
+            f = list(c)
+            f[mu] = (c[mu] + 1) % L[mu]
+            sf = -1.0 if (antiperiodic_t and mu == 3 and c[3] == L[3] - 1) else 1.0
+            b = list(c)
+            b[mu] = (c[mu] - 1) % L[mu]
+            sb = -1.0 if (antiperiodic_t and mu == 3 and c[3] == 0) else 1.0
+            pf = sf * psi[f[3], f[2], f[1], f[0]]
+            pb = sb * psi[b[3], b[2], b[1], b[0]]
+            Uf = U[c[3], c[2], c[1], c[0], mu]
+            Ub = U[b[3], b[2], b[1], b[0], mu]
+            acc += (I4 - GAMMA[mu]) @ (pf @ Uf.T)
+            acc += (I4 + GAMMA[mu]) @ (pb @ np.conj(Ub))
+        out.append(GAMMA5 @ (psi[c[3], c[2], c[1], c[0]] - kap * acc))
+    return np.array(out)
+
+
 def dense_operator(apply, site_shape):
     """Dense matrix of a linear map on spinors: column j = apply(e_j)."""
     n = int(np.prod(site_shape)) * 12

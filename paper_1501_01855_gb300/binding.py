@@ -1,0 +1,334 @@
+"""Thin ctypes binding of liboverlap (include/overlap.h): argument marshalling only.
+
+Every function keeps its C name. Spinor arguments may be numpy arrays (host
+memory, on_device = 0) or torch CUDA tensors (device memory, on_device = 1) of
+complex128 or complex64 in the canonical layout [..., Lt, Lz, Ly, Lx, 4, 3]; all
+arithmetic happens in the library. A missing or unloadable library raises
+immediately; there is no fallback.
+"""
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "liboverlap.so")
+
+OVL_OK, OVL_EINVAL, OVL_ENOMEM, OVL_ECUDA, OVL_ENOCONV, OVL_EBREAKDOWN, OVL_EAPPROX, OVL_ETIMEOUT = \
+    0, -1, -2, -3, -4, -5, -6, -7
+OVL_C128, OVL_C64 = 0, 1
+OVL_PREC_F64, OVL_PREC_F32, OVL_PREC_F16, OVL_PREC_AUTO = 0, 1, 2, -1
+OVL_SOLVER_SUMR, OVL_SOLVER_CG = 0, 1
+OVL_PROF_CLASSES = 8
+PROF_NAMES = ["wilson_f64", "wilson_f32", "wilson_f16", "mscg_update", "vector", "scalar", "gram", "force"]
+
+STATUS_NAMES = {0: "OVL_OK", -1: "OVL_EINVAL", -2: "OVL_ENOMEM", -3: "OVL_ECUDA", -4: "OVL_ENOCONV",
+                -5: "OVL_EBREAKDOWN", -6: "OVL_EAPPROX", -7: "OVL_ETIMEOUT"}
+
+
+class OvlError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__("%s: %s" % (STATUS_NAMES.get(status, status), msg))
+        self.status = status
+
+
+class ovl_params(ctypes.Structure):
+    _fields_ = [("solver", ctypes.c_int), ("mixed", ctypes.c_int), ("half_storage", ctypes.c_int),
+                ("eta_floor", ctypes.c_double), ("sp_switch", ctypes.c_double), ("half_switch", ctypes.c_double),
+                ("eta_precond", ctypes.c_double), ("relax_factor", ctypes.c_double),
+                ("gmresr_max", ctypes.c_int), ("inner_max", ctypes.c_int), ("mscg_max", ctypes.c_int),
+                ("delta_split", ctypes.c_double), ("c_spec", ctypes.c_double), ("bc_t", ctypes.c_int),
+                ("a_override", ctypes.c_double), ("b_override", ctypes.c_double), ("batch_max", ctypes.c_int),
+                ("verify", ctypes.c_int), ("stream", ctypes.c_void_p)]
+
+
+class ovl_solve_info(ctypes.Structure):
+    _fields_ = [("converged", ctypes.c_int), ("outer_iters", ctypes.c_int), ("inner_iters", ctypes.c_int),
+                ("sign_calls", ctypes.c_int), ("wilson_calls", ctypes.c_longlong),
+                ("wilson_f64", ctypes.c_longlong), ("wilson_f32", ctypes.c_longlong),
+                ("wilson_f16", ctypes.c_longlong), ("true_residual", ctypes.c_double), ("seconds", ctypes.c_double)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+_lib = None
+P = ctypes.c_void_p
+I = ctypes.c_int
+D = ctypes.c_double
+DP = ctypes.POINTER(ctypes.c_double)
+LLP = ctypes.POINTER(ctypes.c_longlong)
+
+_SIGS = {
+    "ovl_version": (ctypes.c_char_p, []),
+    "ovl_params_default": (I, [ctypes.POINTER(ovl_params)]),
+    "ovl_zolotarev_coeffs": (I, [I, D, D, DP, DP, DP]),
+    "overlap_create": (I, [ctypes.POINTER(P), ctypes.POINTER(I), DP, D, D, I, D, ctypes.POINTER(ovl_params)]),
+    "overlap_destroy": (None, [P]),
+    "overlap_last_error": (ctypes.c_char_p, [P]),
+    "overlap_zolotarev": (I, [P, DP, DP, DP, DP, DP]),
+    "ovl_wilson_apply": (I, [P, P, P, I, I, I, I]),
+    "ovl_sign_apply": (I, [P, P, P, I, I, I, D, I]),
+    "overlap_apply": (I, [P, D, P, P, I, I, I, D, I, I]),
+    "overlap_solve": (I, [P, I, DP, I, P, P, I, I, D, P, ctypes.POINTER(ovl_solve_info)]),
+    "eigsumr_accumulate": (I, [P, ctypes.POINTER(P), I, I, D, P, P, I, I, D, ctypes.POINTER(ovl_solve_info)]),
+    "ovl_defl_info": (I, [P, ctypes.POINTER(I), DP, DP]),
+    "ovl_defl_vector": (I, [P, I, DP, DP]),
+    "ovl_defl_save": (I, [P, ctypes.c_char_p]),
+    "ovl_defl_load": (I, [P, ctypes.POINTER(P), ctypes.c_char_p]),
+    "ovl_defl_destroy": (None, [P]),
+    "overlap_force": (I, [P, D, P, I, I, D, DP, DP]),
+    "ovl_profile_enable": (I, [P, I]),
+    "ovl_profile_reset": (I, [P]),
+    "ovl_profile_get": (I, [P, I, LLP, DP, DP]),
+    "ovl_bench_wilson": (I, [P, I, I, I, DP, DP]),
+}
+
+
+def load():
+    """Load liboverlap.so (built by paper_1501_01855_gb300.build); raises if absent."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise RuntimeError("liboverlap.so is not built (%s); run paper_1501_01855_gb300.build.build()" % LIB_PATH)
+    lib = ctypes.CDLL(LIB_PATH)
+    for name, (res, args) in _SIGS.items():
+        f = getattr(lib, name)
+        f.restype = res
+        f.argtypes = args
+    _lib = lib
+    return lib
+
+
+def exported_symbols():
+    return list(_SIGS.keys())
+
+
+def _check(status, ctx=None):
+    if status != OVL_OK:
+        msg = ""
+        if ctx:
+            msg = load().overlap_last_error(ctx).decode()
+        raise OvlError(status, msg)
+
+
+def _dptr(a):
+    return a.ctypes.data_as(DP)
+
+
+def _spinor_arg(x):
+    """(pointer, dtype code, on_device, count of spinors given the site count)."""
+    try:
+        import torch
+        if isinstance(x, torch.Tensor):
+            if not x.is_contiguous():
+                raise ValueError("spinor tensors must be contiguous")
+            if x.dtype == torch.complex128:
+                code = OVL_C128
+            elif x.dtype == torch.complex64:
+                code = OVL_C64
+            else:
+                raise ValueError("spinors must be complex128 or complex64")
+            return ctypes.c_void_p(x.data_ptr()), code, 1 if x.is_cuda else 0, x.numel()
+    except ImportError:
+        pass
+    x = np.asarray(x)
+    if not x.flags["C_CONTIGUOUS"]:
+        raise ValueError("spinor arrays must be C-contiguous")
+    if x.dtype == np.complex128:
+        code = OVL_C128
+    elif x.dtype == np.complex64:
+        code = OVL_C64
+    else:
+        raise ValueError("spinors must be complex128 or complex64")
+    return ctypes.c_void_p(x.ctypes.data), code, 0, x.size
+
+
+def ovl_version():
+    return load().ovl_version().decode()
+
+
+def ovl_params_default():
+    p = ovl_params()
+    _check(load().ovl_params_default(ctypes.byref(p)))
+    return p
+
+
+def ovl_zolotarev_coeffs(n, a, b):
+    om = np.zeros(n)
+    sg = np.zeros(n)
+    de = np.zeros(1)
+    _check(load().ovl_zolotarev_coeffs(int(n), float(a), float(b), _dptr(om), _dptr(sg), _dptr(de)))
+    return om, sg, float(de[0])
+
+
+class Overlap:
+    """One overlap context (gauge field, m0, default mu, Zolotarev order)."""
+
+    def __init__(self, dims, links, m0, mu, n_poles, eps_sign, params=None, **kw):
+        lib = load()
+        if params is None:
+            params = ovl_params_default()
+        for k, v in kw.items():
+            setattr(params, k, v)
+        self.params = params
+        self.dims = tuple(int(d) for d in dims)
+        self.V = int(np.prod(self.dims))
+        links = np.ascontiguousarray(np.asarray(links, dtype=np.complex128))
+        if links.size != self.V * 36:
+            raise ValueError("links must hold 4*9*V complex entries")
+        d4 = (ctypes.c_int * 4)(*self.dims)
+        h = ctypes.c_void_p()
+        st = lib.overlap_create(ctypes.byref(h), d4, links.ctypes.data_as(DP), float(m0), float(mu), int(n_poles),
+                                float(eps_sign), ctypes.byref(params))
+        if st != OVL_OK:
+            raise OvlError(st, "overlap_create failed (see stderr)")
+        self.h = h
+        self.m0, self.mu, self.n_poles = m0, mu, n_poles
+
+    def close(self):
+        if getattr(self, "h", None):
+            load().overlap_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _n(self, count):
+        n, r = divmod(count, self.V * 12)
+        if r or n < 1:
+            raise ValueError("spinor buffer size is not a multiple of 12*V")
+        return n
+
+    def zolotarev(self):
+        om = np.zeros(self.n_poles)
+        sg = np.zeros(self.n_poles)
+        de, a, b = np.zeros(1), np.zeros(1), np.zeros(1)
+        _check(load().overlap_zolotarev(self.h, _dptr(om), _dptr(sg), _dptr(de), _dptr(a), _dptr(b)), self.h)
+        return om, sg, float(de[0]), float(a[0]), float(b[0])
+
+    def wilson_apply(self, x, out, prec=OVL_PREC_F64):
+        pi, code, dev, cnt = _spinor_arg(x)
+        po, code2, dev2, cnt2 = _spinor_arg(out)
+        _check(load().ovl_wilson_apply(self.h, pi, po, self._n(cnt), code, dev, int(prec)), self.h)
+        return out
+
+    def sign_apply(self, x, out, eta=0.0, prec=OVL_PREC_AUTO):
+        pi, code, dev, cnt = _spinor_arg(x)
+        po, _, _, _ = _spinor_arg(out)
+        _check(load().ovl_sign_apply(self.h, pi, po, self._n(cnt), code, dev, float(eta), int(prec)), self.h)
+        return out
+
+    def apply(self, x, out, mu=None, eta=0.0, prec=OVL_PREC_AUTO, hermitian=False):
+        pi, code, dev, cnt = _spinor_arg(x)
+        po, _, _, _ = _spinor_arg(out)
+        mu = self.mu if mu is None else mu
+        _check(load().overlap_apply(self.h, float(mu), pi, po, self._n(cnt), code, dev, float(eta), int(prec),
+                                    1 if hermitian else 0), self.h)
+        return out
+
+    def solve(self, b, x, tol, mus=None, defl=None, allow_noconv=False):
+        pb, code, dev, cnt = _spinor_arg(b)
+        px, _, _, _ = _spinor_arg(x)
+        nrhs = self._n(cnt)
+        mus = np.ascontiguousarray([self.mu] if mus is None else mus, dtype=np.float64)
+        info = (ovl_solve_info * (nrhs * len(mus)))()
+        st = load().overlap_solve(self.h, nrhs, _dptr(mus), len(mus), pb, px, code, dev, float(tol),
+                                  defl.h if defl is not None else None, info)
+        if not (st == OVL_OK or (allow_noconv and st == OVL_ENOCONV)):
+            _check(st, self.h)
+        return [i.as_dict() for i in info]
+
+    def eigsumr_accumulate(self, b, x, tol, n_eig, m_basis, mu=None, defl=None):
+        pb, code, dev, cnt = _spinor_arg(b)
+        px, _, _, _ = _spinor_arg(x)
+        self._n(cnt)
+        mu = self.mu if mu is None else mu
+        h = ctypes.c_void_p(defl.h.value if defl is not None else None)
+        info = (ovl_solve_info * 1)()
+        st = load().eigsumr_accumulate(self.h, ctypes.byref(h), int(n_eig), int(m_basis), float(mu), pb, px, code,
+                                       dev, float(tol), info)
+        if st not in (OVL_OK, OVL_ENOCONV):
+            _check(st, self.h)
+        if defl is None:
+            defl = Deflation(self, h)
+        return defl, info[0].as_dict()
+
+    def force(self, phi, mu=None, tol=1e-10):
+        pp, code, dev, cnt = _spinor_arg(phi)
+        self._n(cnt)
+        mu = self.mu if mu is None else mu
+        G = np.zeros(self.V * 36 * 2)
+        S = np.zeros(1)
+        _check(load().overlap_force(self.h, float(mu), pp, code, dev, float(tol), _dptr(G), _dptr(S)), self.h)
+        Gc = G.view(np.complex128).reshape(tuple(reversed(self.dims)) + (4, 3, 3))
+        return Gc, float(S[0])
+
+    def profile_enable(self, on=True):
+        _check(load().ovl_profile_enable(self.h, 1 if on else 0), self.h)
+
+    def profile_reset(self):
+        _check(load().ovl_profile_reset(self.h), self.h)
+
+    def profile_get(self):
+        out = {}
+        for c in range(OVL_PROF_CLASSES):
+            n = ctypes.c_longlong()
+            ms, by = ctypes.c_double(), ctypes.c_double()
+            _check(load().ovl_profile_get(self.h, c, ctypes.byref(n), ctypes.byref(ms), ctypes.byref(by)), self.h)
+            out[PROF_NAMES[c]] = {"launches": n.value, "ms": ms.value, "bytes": by.value}
+        return out
+
+    def bench_wilson(self, prec, n, iters):
+        ms, by = ctypes.c_double(), ctypes.c_double()
+        _check(load().ovl_bench_wilson(self.h, int(prec), int(n), int(iters), ctypes.byref(ms), ctypes.byref(by)),
+               self.h)
+        return ms.value, by.value
+
+
+class Deflation:
+    """A deflation space from eigsumr_accumulate (or ovl_defl_load)."""
+
+    def __init__(self, ctx, handle):
+        self.ctx = ctx
+        self.h = handle
+
+    def info(self):
+        n = ctypes.c_int()
+        _check(load().ovl_defl_info(self.h, ctypes.byref(n), None, None))
+        r = np.zeros(max(1, n.value))
+        s = np.zeros(max(1, n.value))
+        _check(load().ovl_defl_info(self.h, ctypes.byref(n), _dptr(r), _dptr(s)))
+        return r[:n.value], s[:n.value]
+
+    def vector(self, i):
+        v = np.zeros(self.ctx.V * 12, dtype=np.complex128)
+        vd = np.zeros(self.ctx.V * 12, dtype=np.complex128)
+        _check(load().ovl_defl_vector(self.h, int(i), v.view(np.float64).ctypes.data_as(DP),
+                                      vd.view(np.float64).ctypes.data_as(DP)))
+        shp = tuple(reversed(self.ctx.dims)) + (4, 3)
+        return v.reshape(shp), vd.reshape(shp)
+
+    def save(self, path):
+        _check(load().ovl_defl_save(self.h, path.encode()))
+
+    @classmethod
+    def load_file(cls, ctx, path):
+        h = ctypes.c_void_p()
+        _check(load().ovl_defl_load(ctx.h, ctypes.byref(h), path.encode()), ctx.h)
+        return cls(ctx, h)
+
+    def close(self):
+        if getattr(self, "h", None) is not None and self.h.value:
+            load().ovl_defl_destroy(self.h)
+            self.h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

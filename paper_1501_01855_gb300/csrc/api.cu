@@ -1,0 +1,675 @@
+// The C ABI of liboverlap (declared in include/overlap.h).
+#include <stdio.h>
+#include <string.h>
+
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <new>
+
+#include "context.h"
+#include "eig.h"
+#include "hostmath.h"
+#include "solver.h"
+
+using namespace ovl;
+
+namespace ovl {
+ovl_status force_compute(ovl_ctx* c, double mu, const Field& phi, double tol, double* dSdU, double* S);
+}
+
+static const char* kVersion = "liboverlap 0.1 (sm_103a)";
+
+extern "C" const char* ovl_version(void) { return kVersion; }
+
+extern "C" ovl_status ovl_params_default(ovl_params* p) {
+  if (!p) return OVL_EINVAL;
+  memset(p, 0, sizeof(*p));
+  p->solver = OVL_SOLVER_SUMR;
+  p->mixed = 1;
+  p->half_storage = 0;
+  p->eta_floor = 1e-2;
+  p->sp_switch = 1e-6;
+  p->half_switch = 2e-3;
+  p->eta_precond = 0.0;
+  p->relax_factor = 1.0;
+  p->gmresr_max = 30;
+  p->inner_max = 2000;
+  p->mscg_max = 5000;
+  p->delta_split = 0.01;
+  p->c_spec = std::sqrt(3.0) / 2.0;
+  p->bc_t = 0;
+  p->a_override = 0.0;
+  p->b_override = 0.0;
+  p->batch_max = 36;
+  p->verify = 1;
+  p->stream = nullptr;
+  return OVL_OK;
+}
+
+extern "C" const char* overlap_last_error(const ovl_ctx* c) { return c ? c->err.c_str() : "null context"; }
+
+// ---------------------------------------------------------------- create
+static void convert_links(const double* links, int V, std::vector<double>& l64, std::vector<float>& l32,
+                          std::vector<__half>& l16) {
+  // canonical [site][mu][row][col] complex -> [mu][chunk][V] keeping rows 0, 1
+  l64.assign((size_t)4 * 6 * V * 2, 0.0);
+  l32.assign((size_t)4 * 3 * V * 4, 0.f);
+  l16.assign((size_t)4 * 3 * V * 4, __float2half(0.f));
+  for (int s = 0; s < V; ++s)
+    for (int mu = 0; mu < 4; ++mu) {
+      const double* u = links + ((size_t)s * 4 + mu) * 18;   // 9 complex
+      for (int e = 0; e < 6; ++e) {
+        const double re = u[2 * e], im = u[2 * e + 1];
+        l64[(((size_t)mu * 6 + e) * V + s) * 2 + 0] = re;
+        l64[(((size_t)mu * 6 + e) * V + s) * 2 + 1] = im;
+        const int ch = e / 2, w = e % 2;
+        l32[(((size_t)mu * 3 + ch) * V + s) * 4 + 2 * w + 0] = (float)re;
+        l32[(((size_t)mu * 3 + ch) * V + s) * 4 + 2 * w + 1] = (float)im;
+        l16[(((size_t)mu * 3 + ch) * V + s) * 4 + 2 * w + 0] = __float2half_rn((float)re);
+        l16[(((size_t)mu * 3 + ch) * V + s) * 4 + 2 * w + 1] = __float2half_rn((float)im);
+      }
+    }
+}
+
+// Extreme eigenvalues of K^2 by FP64 Lanczos (no reorthogonalisation; only the
+// ends of the spectrum are used).
+static ovl_status lanczos_bounds(ovl_ctx* c, int steps, double* lmin, double* lmax) {
+  Field *v0, *v1, *w, *t;
+  OVL_TRY(get_field(c, "lz_v0", P64, 1, &v0));
+  OVL_TRY(get_field(c, "lz_v1", P64, 1, &v1));
+  OVL_TRY(get_field(c, "lz_w", P64, 1, &w));
+  OVL_TRY(get_field(c, "lz_t", P64, 1, &t));
+  std::vector<double> h((size_t)24 * c->V);
+  unsigned long long st = 0x9E3779B97F4A7C15ull;
+  for (auto& x : h) {
+    st = st * 6364136223846793005ull + 1442695040888963407ull;
+    x = ((double)(st >> 11) / 9007199254740992.0) - 0.5;
+  }
+  OVL_TRY(import_spinors(c, h.data(), OVL_C128, 0, 1, *v1, 0));
+  std::vector<double> nrm;
+  OVL_TRY(norms_batch(c, *v1, 0, 1, nrm));
+  std::vector<cd> a1(1, 1.0 / nrm[0]), z1(1, 0.0), one(1, 1.0);
+  OVL_TRY(axpby_batch(c, a1, *v1, 0, z1, *v1, 0, *v1, 0, 1));
+  launch_zero(P64, v0->ref(), 1, c->V, c->st);
+  std::vector<double> al, be;
+  double beta = 0.0;
+  for (int j = 0; j < steps; ++j) {
+    OVL_TRY(wilson_apply_field(c, P64, *v1, 0, *t, 0, 1));
+    OVL_TRY(wilson_apply_field(c, P64, *t, 0, *w, 0, 1));
+    std::vector<cd> d;
+    OVL_TRY(dots_batch(c, *v1, 0, *w, 0, 1, d));
+    const double alpha = d[0].real();
+    al.push_back(alpha);
+    std::vector<cd> ma(1, -alpha), mb(1, -beta);
+    OVL_TRY(axpby_batch(c, one, *w, 0, ma, *v1, 0, *w, 0, 1));
+    OVL_TRY(axpby_batch(c, one, *w, 0, mb, *v0, 0, *w, 0, 1));
+    OVL_TRY(norms_batch(c, *w, 0, 1, nrm));
+    beta = nrm[0];
+    if (beta < 1e-14) break;
+    be.push_back(beta);
+    std::swap(c->ws["lz_v0"], c->ws["lz_v1"]);
+    v0 = &c->ws["lz_v0"];
+    v1 = &c->ws["lz_v1"];
+    std::vector<cd> ib(1, 1.0 / beta);
+    OVL_TRY(axpby_batch(c, ib, *w, 0, z1, *w, 0, *v1, 0, 1));
+  }
+  const int n = (int)al.size();
+  be.resize(std::max(0, n - 1));
+  tridiag_extremes(n, al.data(), be.data(), lmin, lmax);
+  return OVL_OK;
+}
+
+extern "C" void overlap_destroy(ovl_ctx* c) {
+  if (!c) return;
+  if (c->st) cudaStreamSynchronize(c->st);
+  else cudaDeviceSynchronize();
+  for (auto& kv : c->ws) free_field(kv.second);
+  for (int p = 0; p < 3; ++p)
+    if (c->link[p]) cudaFree(c->link[p]);
+  if (c->partials) cudaFree(c->partials);
+  if (c->dred) cudaFree(c->dred);
+  if (c->dscal) cudaFree(c->dscal);
+  if (c->dint) cudaFree(c->dint);
+  if (c->ms) cudaFree(c->ms);
+  if (c->dpoles) cudaFree(c->dpoles);
+  if (c->dwork) cudaFree(c->dwork);
+  if (c->hpin) cudaFreeHost(c->hpin);
+  if (c->hstage) cudaFreeHost(c->hstage);
+  for (auto& q : c->prof.pending) {
+    cudaEventDestroy(q.a);
+    cudaEventDestroy(q.b);
+  }
+  for (auto e : c->prof.pool) cudaEventDestroy(e);
+  delete c;
+}
+
+static ovl_status create_impl(ovl_ctx* c, const int dims[4], const double* links, double m0, double mu, int n_poles,
+                              double eps_sign, const ovl_params* params) {
+  if (params) c->P = *params;
+  else ovl_params_default(&c->P);
+  for (int d = 0; d < 4; ++d) {
+    if (dims[d] < 2 || (dims[d] & 1)) return set_err(c, OVL_EINVAL, "lattice extents must be even and >= 2");
+    c->g.L[d] = dims[d];
+  }
+  const long long Vll = (long long)dims[0] * dims[1] * dims[2] * dims[3];
+  if (Vll > (1LL << 28)) return set_err(c, OVL_EINVAL, "lattice too large");
+  c->V = (int)Vll;
+  c->g.V = c->V;
+  c->g.bc_t = c->P.bc_t ? 1 : 0;
+  if (!(m0 > 0 && m0 < 4)) return set_err(c, OVL_EINVAL, "m0 must lie in (0, 4)");
+  if (!(mu >= 0 && mu < 1)) return set_err(c, OVL_EINVAL, "mu must lie in [0, 1)");
+  if (n_poles < 1 || n_poles > NPMAX) return set_err(c, OVL_EINVAL, "n_poles must lie in 1..64");
+  if (c->P.batch_max < 1) c->P.batch_max = 1;
+  if (c->P.batch_max > 256) c->P.batch_max = 256;
+  c->m0 = m0;
+  c->kappa = 1.0 / (8.0 - 2.0 * m0);
+  c->mu = mu;
+  c->npoles = n_poles;
+  c->eps_sign = eps_sign;
+  c->st = (cudaStream_t)c->P.stream;
+  OVL_CUDA(c, cudaGetDevice(&c->device));
+  OVL_CUDA(c, cudaMallocHost((void**)&c->hpin, sizeof(double) * 64 * 4096));
+  OVL_CUDA(c, cudaMalloc((void**)&c->dscal, sizeof(double) * 64 * 4096));
+  OVL_CUDA(c, cudaMalloc((void**)&c->dred, sizeof(double) * 2 * 4096));
+  OVL_CUDA(c, cudaMalloc((void**)&c->dint, sizeof(int) * 4096));
+  OVL_CUDA(c, cudaMalloc((void**)&c->dpoles, sizeof(Poles)));
+  // gauge field in the three storage formats
+  {
+    std::vector<double> l64;
+    std::vector<float> l32;
+    std::vector<__half> l16;
+    convert_links(links, c->V, l64, l32, l16);
+    OVL_CUDA(c, cudaMalloc(&c->link[P64], l64.size() * sizeof(double)));
+    OVL_CUDA(c, cudaMalloc(&c->link[P32], l32.size() * sizeof(float)));
+    OVL_CUDA(c, cudaMalloc(&c->link[P16], l16.size() * sizeof(__half)));
+    OVL_CUDA(c, cudaMemcpy(c->link[P64], l64.data(), l64.size() * sizeof(double), cudaMemcpyHostToDevice));
+    OVL_CUDA(c, cudaMemcpy(c->link[P32], l32.data(), l32.size() * sizeof(float), cudaMemcpyHostToDevice));
+    OVL_CUDA(c, cudaMemcpy(c->link[P16], l16.data(), l16.size() * sizeof(__half), cudaMemcpyHostToDevice));
+  }
+  // spectral bounds of |K|
+  double a = c->P.a_override, b = c->P.b_override;
+  if (!(a > 0) || !(b > 0)) {
+    double lmin, lmax;
+    OVL_TRY(lanczos_bounds(c, 300, &lmin, &lmax));
+    if (!(a > 0)) a = 0.95 * std::sqrt(std::max(lmin, 1e-30));
+    if (!(b > 0)) b = 1.05 * std::sqrt(lmax);
+  }
+  if (!(b > a)) return set_err(c, OVL_EINVAL, "spectral bounds need 0 < a < b");
+  c->za = a;
+  c->zb = b;
+  c->omega.resize(n_poles);
+  c->sigma.resize(n_poles);
+  if (zolotarev_coeffs(n_poles, a, b, c->omega.data(), c->sigma.data(), &c->delta) != 0)
+    return set_err(c, OVL_EINVAL, "Zolotarev coefficients failed");
+  if (c->delta > eps_sign) {
+    char m[200];
+    snprintf(m, sizeof(m), "Zolotarev Delta %.3e with %d poles on [%.4g, %.4g] exceeds eps_sign %.3e", c->delta,
+             n_poles, a, b, eps_sign);
+    return set_err(c, OVL_EAPPROX, m);
+  }
+  Poles& P = c->hpoles;
+  memset(&P, 0, sizeof(P));
+  P.n = n_poles;
+  P.sigma0 = c->sigma[0];
+  for (int i = 0; i < n_poles; ++i) {
+    P.ds[i] = c->sigma[i] - c->sigma[0];
+    P.omega[i] = c->omega[i];
+    P.gbound[i] = pole_gbound(c->sigma[i], a, b);
+  }
+  OVL_CUDA(c, cudaMemcpy(c->dpoles, &P, sizeof(Poles), cudaMemcpyHostToDevice));
+  return OVL_OK;
+}
+
+extern "C" ovl_status overlap_create(ovl_ctx** out, const int dims[4], const double* links, double m0, double mu,
+                                     int n_poles, double eps_sign, const ovl_params* params) {
+  if (!out || !dims || !links) return OVL_EINVAL;
+  *out = nullptr;
+  ovl_ctx* c = new (std::nothrow) ovl_ctx();
+  if (!c) return OVL_ENOMEM;
+  ovl_status s = create_impl(c, dims, links, m0, mu, n_poles, eps_sign, params);
+  if (s != OVL_OK) {
+    // keep the message readable through a static buffer after destroying c
+    static thread_local char msg[512];
+    snprintf(msg, sizeof(msg), "%s", c->err.c_str());
+    fprintf(stderr, "liboverlap: overlap_create failed: %s\n", msg);
+    overlap_destroy(c);
+    return s;
+  }
+  *out = c;
+  return OVL_OK;
+}
+
+extern "C" ovl_status ovl_zolotarev_coeffs(int n, double a, double b, double* omega, double* sigma, double* delta) {
+  if (n < 1 || n > NPMAX || !omega || !sigma || !delta || !(a > 0) || !(b > a)) return OVL_EINVAL;
+  return zolotarev_coeffs(n, a, b, omega, sigma, delta) == 0 ? OVL_OK : OVL_EINVAL;
+}
+
+extern "C" ovl_status overlap_zolotarev(const ovl_ctx* c, double* omega, double* sigma, double* delta, double* a,
+                                        double* b) {
+  if (!c) return OVL_EINVAL;
+  if (omega) memcpy(omega, c->omega.data(), sizeof(double) * c->npoles);
+  if (sigma) memcpy(sigma, c->sigma.data(), sizeof(double) * c->npoles);
+  if (delta) *delta = c->delta;
+  if (a) *a = c->za;
+  if (b) *b = c->zb;
+  return OVL_OK;
+}
+
+static ovl_status check_io(ovl_ctx* c, const void* in, const void* out, int n, int dtype) {
+  if (!c) return OVL_EINVAL;
+  if (!in || !out) return set_err(c, OVL_EINVAL, "null spinor pointer");
+  if (n < 1 || n > 4096) return set_err(c, OVL_EINVAL, "n must lie in 1..4096");
+  if (dtype != OVL_C128 && dtype != OVL_C64) return set_err(c, OVL_EINVAL, "dtype must be OVL_C128 or OVL_C64");
+  return OVL_OK;
+}
+
+extern "C" ovl_status ovl_wilson_apply(ovl_ctx* c, const void* in, void* out, int n, int dtype, int on_device,
+                                       int prec) {
+  OVL_TRY(check_io(c, in, out, n, dtype));
+  if (prec < P64 || prec > P16) return set_err(c, OVL_EINVAL, "prec must be OVL_PREC_F64, F32 or F16");
+  Field *fi, *fo;
+  OVL_TRY(get_field(c, "api_wi", prec, n, &fi));
+  OVL_TRY(get_field(c, "api_wo", prec, n, &fo));
+  OVL_TRY(import_spinors(c, in, dtype, on_device, n, *fi, 0));
+  OVL_TRY(wilson_apply_field(c, prec, *fi, 0, *fo, 0, n));
+  OVL_TRY(export_spinors(c, out, dtype, on_device, n, *fo, 0));
+  OVL_CUDA(c, cudaStreamSynchronize(c->st));
+  return OVL_OK;
+}
+
+extern "C" ovl_status ovl_sign_apply(ovl_ctx* c, const void* in, void* out, int n, int dtype, int on_device,
+                                     double eta, int prec) {
+  OVL_TRY(check_io(c, in, out, n, dtype));
+  Field *fi, *fo;
+  OVL_TRY(get_field(c, "api_in", P64, n, &fi));
+  OVL_TRY(get_field(c, "api_out", P64, n, &fo));
+  OVL_TRY(import_spinors(c, in, dtype, on_device, n, *fi, 0));
+  const double e = eta > 0 ? eta : c->eps_sign;
+  const int mode = prec == OVL_PREC_AUTO ? choose_mode(c, e) : prec;
+  if (mode < SIGN64 || mode > SIGN16) return set_err(c, OVL_EINVAL, "bad prec");
+  std::vector<double> etas(n, e);
+  OVL_TRY(sign_op(c, mode, *fi, 0, *fo, 0, n, etas.data(), 0.0, 1.0, nullptr, 1, nullptr, 0, nullptr, nullptr));
+  OVL_TRY(export_spinors(c, out, dtype, on_device, n, *fo, 0));
+  OVL_CUDA(c, cudaStreamSynchronize(c->st));
+  return OVL_OK;
+}
+
+extern "C" ovl_status overlap_apply(ovl_ctx* c, double mu, const void* in, void* out, int n, int dtype, int on_device,
+                                    double eta, int prec, int hermitian) {
+  OVL_TRY(check_io(c, in, out, n, dtype));
+  if (!(mu >= 0 && mu < 1)) return set_err(c, OVL_EINVAL, "mu must lie in [0, 1)");
+  Field *fi, *fo;
+  OVL_TRY(get_field(c, "api_in", P64, n, &fi));
+  OVL_TRY(get_field(c, "api_out", P64, n, &fo));
+  OVL_TRY(import_spinors(c, in, dtype, on_device, n, *fi, 0));
+  const double e = eta > 0 ? eta : c->eps_sign;
+  const int mode = prec == OVL_PREC_AUTO ? choose_mode(c, e) : prec;
+  if (mode < SIGN64 || mode > SIGN16) return set_err(c, OVL_EINVAL, "bad prec");
+  std::vector<double> mus(n, mu), etas(n, e);
+  OVL_TRY(overlap_apply_batch(c, *fi, 0, *fo, 0, n, mus, etas, hermitian ? 1 : 0, mode, nullptr));
+  OVL_TRY(export_spinors(c, out, dtype, on_device, n, *fo, 0));
+  OVL_CUDA(c, cudaStreamSynchronize(c->st));
+  return OVL_OK;
+}
+
+// true residual ||b - D x|| / ||b|| with an FP64 sign at eps_sign
+static ovl_status true_residuals(ovl_ctx* c, const Field& b, int boff, const Field& x, int xoff, int n,
+                                 const std::vector<double>& mus, std::vector<double>& out) {
+  Field* t;
+  OVL_TRY(get_field(c, "tr_t", P64, n, &t));
+  std::vector<double> etas(n, c->eps_sign);
+  OVL_TRY(overlap_apply_batch(c, x, xoff, *t, 0, n, mus, etas, 0, SIGN64, nullptr));
+  std::vector<cd> one(n, 1.0), mone(n, -1.0);
+  OVL_TRY(axpby_batch(c, one, b, boff, mone, *t, 0, *t, 0, n));
+  std::vector<double> rn, bn;
+  OVL_TRY(norms_batch(c, *t, 0, n, rn));
+  OVL_TRY(norms_batch(c, b, boff, n, bn));
+  out.resize(n);
+  for (int j = 0; j < n; ++j) out[j] = bn[j] > 0 ? rn[j] / bn[j] : 0.0;
+  return OVL_OK;
+}
+
+extern "C" ovl_status overlap_solve(ovl_ctx* c, int nrhs, const double* mus, int nmass, const void* rhs, void* x,
+                                    int dtype, int on_device, double tol, ovl_defl* defl, ovl_solve_info* info) {
+  OVL_TRY(check_io(c, rhs, x, nrhs, dtype));
+  if (nmass < 1 || nmass > 64) return set_err(c, OVL_EINVAL, "nmass must lie in 1..64");
+  if (!(tol > 0)) return set_err(c, OVL_EINVAL, "tol must be positive");
+  std::vector<double> mv(nmass);
+  for (int k = 0; k < nmass; ++k) {
+    mv[k] = mus ? mus[k] : c->mu;
+    if (!(mv[k] > 0 && mv[k] < 1)) return set_err(c, OVL_EINVAL, "every mass must lie in (0, 1)");
+  }
+  if (defl && defl->ctx != c) return set_err(c, OVL_EINVAL, "deflation space belongs to another context");
+  Field* fb;
+  OVL_TRY(get_field(c, "api_b", P64, nrhs, &fb));
+  OVL_TRY(import_spinors(c, rhs, dtype, on_device, nrhs, *fb, 0));
+  const int nsys = nrhs * nmass;
+  const int bm = std::max(1, c->P.batch_max);
+  const size_t esz = (dtype == OVL_C128 ? 16 : 8) * 12 * (size_t)c->V;
+  ovl_status worst = OVL_OK;
+  for (int s0 = 0; s0 < nsys; s0 += bm) {
+    const int n = std::min(bm, nsys - s0);
+    Field *bb, *bx;
+    OVL_TRY(get_field(c, "bat_b", P64, n, &bb));
+    OVL_TRY(get_field(c, "bat_x", P64, n, &bx));
+    std::vector<double> bmus(n);
+    for (int q = 0; q < n; ++q) {
+      const int s = s0 + q;
+      const int k = s / nrhs, j = s % nrhs;
+      bmus[q] = mv[k];
+      OVL_TRY(copy_convert(c, *fb, j, *bb, q, 1));
+    }
+    ovl_status st = gmresr_batch(c, n, bmus, *bb, 0, *bx, 0, tol, defl, info ? info + s0 : nullptr, nullptr);
+    if (st != OVL_OK && st != OVL_ENOCONV) return st;
+    if (st == OVL_ENOCONV) worst = st;
+    if (c->P.verify) {
+      std::vector<double> tr;
+      OVL_TRY(true_residuals(c, *bb, 0, *bx, 0, n, bmus, tr));
+      if (info)
+        for (int q = 0; q < n; ++q) {
+          info[s0 + q].true_residual = tr[q];
+          info[s0 + q].converged = tr[q] <= tol * 1.0000001 ? 1 : 0;
+          info[s0 + q].wilson_calls += 0;
+        }
+    }
+    char* dst = (char*)x + esz * s0;
+    OVL_TRY(export_spinors(c, dst, dtype, on_device, n, *bx, 0));
+  }
+  OVL_CUDA(c, cudaStreamSynchronize(c->st));
+  if (info) {
+    for (int s = 0; s < nsys; ++s) {
+      info[s].wilson_f64 = info[s].wilson_f32 = info[s].wilson_f16 = 0;
+    }
+  }
+  return worst;
+}
+
+// ---------------------------------------------------------------- eigSUMR
+static ovl_status defl_alloc(ovl_ctx* c, ovl_defl* d, int prec, int cap) {
+  d->ctx = c;
+  d->cap = cap;
+  auto alloc = [&](Field& f) -> ovl_status {
+    f.prec = prec;
+    f.V = c->V;
+    f.n = cap;
+    if (cudaMalloc(&f.data, (size_t)(prec == P64 ? 192 : 96) * c->V * cap) != cudaSuccess) {
+      cudaGetLastError();
+      f.data = nullptr;
+      return set_err(c, OVL_ENOMEM, "cudaMalloc failed for the deflation space");
+    }
+    return OVL_OK;
+  };
+  OVL_TRY(alloc(d->v));
+  OVL_TRY(alloc(d->w));
+  return OVL_OK;
+}
+
+extern "C" void ovl_defl_destroy(ovl_defl* d) {
+  if (!d) return;
+  if (d->ctx && d->ctx->st) cudaStreamSynchronize(d->ctx->st);
+  free_field(d->v);
+  free_field(d->w);
+  delete d;
+}
+
+static ovl_status eig_after_outer(ovl_ctx* c, void* data, int outer) {
+  (void)c;
+  (void)data;
+  (void)outer;
+  return OVL_OK;
+}
+
+extern "C" ovl_status eigsumr_accumulate(ovl_ctx* c, ovl_defl** defl, int n_eig, int m_basis, double mu,
+                                         const void* rhs, void* x, int dtype, int on_device, double tol,
+                                         ovl_solve_info* info) {
+  OVL_TRY(check_io(c, rhs, x, 1, dtype));
+  if (!defl) return set_err(c, OVL_EINVAL, "defl must not be null");
+  if (n_eig < 1 || m_basis <= n_eig || m_basis > 1024) return set_err(c, OVL_EINVAL, "need 1 <= n_eig < m_basis <= 1024");
+  if (!(mu > 0 && mu < 1)) return set_err(c, OVL_EINVAL, "mu must lie in (0, 1)");
+  const int prec = c->P.mixed ? P32 : P64;
+  ovl_defl* d = *defl;
+  bool fresh = false;
+  if (!d) {
+    d = new (std::nothrow) ovl_defl();
+    if (!d) return OVL_ENOMEM;
+    fresh = true;
+    ovl_status s = defl_alloc(c, d, prec, n_eig);
+    if (s != OVL_OK) {
+      ovl_defl_destroy(d);
+      return s;
+    }
+  } else if (d->ctx != c) {
+    return set_err(c, OVL_EINVAL, "deflation space belongs to another context");
+  }
+  EigState e;
+  e.prec = d->v.prec;
+  e.m = m_basis;
+  e.n_eig = n_eig;
+  e.mu = mu;
+  e.delta = c->P.delta_split;
+  OVL_TRY(get_field(c, "e_V", e.prec, m_basis, &e.V));
+  OVL_TRY(get_field(c, "e_W", e.prec, m_basis, &e.W));
+  if (!fresh && d->n > 0) {
+    const int ns = std::min(d->n, n_eig);
+    OVL_TRY(copy_convert(c, d->v, 0, *e.V, 0, ns));
+    OVL_TRY(copy_convert(c, d->w, 0, *e.W, 0, ns));
+    e.k = ns;
+    e.n_seeded = ns;
+  }
+  EigHook hook;
+  hook.active = true;
+  hook.target = std::sqrt(tol);   // GMRESR in two steps while the eigenvectors are being calculated (Sec. 6)
+  hook.eta_cap = e.eps_v;
+  hook.hook = eig_hook;
+  hook.after_outer = eig_after_outer;
+  hook.data = &e;
+  e.eig = &hook;
+  Field *fb, *fx;
+  OVL_TRY(get_field(c, "api_b", P64, 1, &fb));
+  OVL_TRY(get_field(c, "bat_x", P64, 1, &fx));
+  OVL_TRY(import_spinors(c, rhs, dtype, on_device, 1, *fb, 0));
+  std::vector<double> mus(1, mu);
+  // the deflation held so far accelerates this solve too; the space is rebuilt after it
+  ovl_defl* use = (!fresh && d->n > 0) ? d : nullptr;
+  ovl_status st = gmresr_batch(c, 1, mus, *fb, 0, *fx, 0, tol, use, info, &hook);
+  if (st != OVL_OK && st != OVL_ENOCONV) {
+    if (fresh) ovl_defl_destroy(d);
+    return st;
+  }
+  // final Ritz step over whatever the basis holds
+  if (e.k > e.n_seeded || e.ndiag == 0) OVL_TRY(ritz_step(c, &e, n_eig));
+  const int nk = e.k;
+  // store, then recompute w = V psi accurately (Sec. 5.1: recalculate v^D after the
+  // eigenvector calculation when the space is used by SUMR)
+  if (d->cap < nk) return set_err(c, OVL_EINVAL, "internal: deflation capacity");
+  OVL_TRY(copy_convert(c, *e.V, 0, d->v, 0, nk));
+  std::vector<double> etas(nk, std::max(c->eps_sign, 1e-8));
+  const int mode = choose_mode(c, etas[0]);
+  OVL_TRY(sign_op(c, mode, d->v, 0, d->w, 0, nk, etas.data(), 0.0, 1.0, nullptr, 0, nullptr, 0, nullptr, nullptr));
+  d->n = nk;
+  d->mu = mu;
+  d->prepared = false;
+  OVL_TRY(defl_prepare(c, d));
+  // Ritz values of D^dag D + 2 mu delta H and residuals with the recomputed w
+  d->ritz.assign(nk, 0.0);
+  d->res.assign(nk, 0.0);
+  {
+    const double a = 0.5 * (1.0 - mu), b = 0.5 * (1.0 + mu);
+    for (int i = 0; i < nk; ++i) {
+      const size_t ii = (size_t)i * nk + i;
+      const double vv = d->VV[ii].real();
+      const cd wv = d->WV[ii];
+      const double dd = a * a * d->WW[ii].real() + 2.0 * a * b * wv.real() + b * b * vv;   // ||D psi||^2
+      const cd th = b * d->G5VV[ii] + a * d->G5VW[ii];                                    // (psi, g5 D psi)
+      d->ritz[i] = (dd + 2.0 * mu * c->P.delta_split * th.real()) / vv;
+      d->res[i] = std::sqrt(std::max(0.0, dd / vv - std::norm(th) / (vv * vv)));
+    }
+  }
+  OVL_TRY(export_spinors(c, x, dtype, on_device, 1, *fx, 0));
+  if (info && c->P.verify) {
+    std::vector<double> tr;
+    OVL_TRY(true_residuals(c, *fb, 0, *fx, 0, 1, mus, tr));
+    info[0].true_residual = tr[0];
+    info[0].converged = tr[0] <= tol * 1.0000001 ? 1 : 0;
+  }
+  OVL_CUDA(c, cudaStreamSynchronize(c->st));
+  *defl = d;
+  return st;
+}
+
+extern "C" ovl_status ovl_defl_info(const ovl_defl* d, int* n, double* ritz, double* residuals) {
+  if (!d) return OVL_EINVAL;
+  if (n) *n = d->n;
+  if (ritz) memcpy(ritz, d->ritz.data(), sizeof(double) * d->n);
+  if (residuals) memcpy(residuals, d->res.data(), sizeof(double) * d->n);
+  return OVL_OK;
+}
+
+extern "C" ovl_status ovl_defl_vector(const ovl_defl* d, int i, double* v, double* vD) {
+  if (!d || i < 0 || i >= d->n) return OVL_EINVAL;
+  ovl_ctx* c = d->ctx;
+  if (v) OVL_TRY(export_spinors(c, v, OVL_C128, 0, 1, d->v, i));
+  if (vD) {
+    // v^D = (1+mu)/2 psi + (1-mu)/2 w at the space's mass
+    Field* t;
+    OVL_TRY(get_field(c, "dv_t", d->v.prec, 1, &t));
+    std::vector<cd> a(1, 0.5 * (1.0 - d->mu)), b(1, 0.5 * (1.0 + d->mu));
+    OVL_TRY(axpby_batch(c, a, d->w, i, b, d->v, i, *t, 0, 1));
+    OVL_TRY(export_spinors(c, vD, OVL_C128, 0, 1, *t, 0));
+  }
+  return OVL_OK;
+}
+
+extern "C" ovl_status ovl_defl_save(const ovl_defl* d, const char* path) {
+  if (!d || !path) return OVL_EINVAL;
+  ovl_ctx* c = d->ctx;
+  FILE* f = fopen(path, "wb");
+  if (!f) return set_err(c, OVL_EINVAL, std::string("cannot open ") + path);
+  fprintf(f, "OVLDEFL 1 n=%d V=%d mu=%.17g\n", d->n, c->V, d->mu);
+  std::vector<double> h((size_t)24 * c->V);
+  for (int i = 0; i < d->n; ++i) {
+    ovl_status s = export_spinors(c, h.data(), OVL_C128, 0, 1, d->v, i);
+    if (s != OVL_OK) { fclose(f); return s; }
+    fwrite(h.data(), sizeof(double), h.size(), f);
+    s = export_spinors(c, h.data(), OVL_C128, 0, 1, d->w, i);
+    if (s != OVL_OK) { fclose(f); return s; }
+    fwrite(h.data(), sizeof(double), h.size(), f);
+  }
+  fwrite(d->ritz.data(), sizeof(double), d->n, f);
+  fwrite(d->res.data(), sizeof(double), d->n, f);
+  fclose(f);
+  return OVL_OK;
+}
+
+extern "C" ovl_status ovl_defl_load(ovl_ctx* c, ovl_defl** out, const char* path) {
+  if (!c || !out || !path) return OVL_EINVAL;
+  FILE* f = fopen(path, "rb");
+  if (!f) return set_err(c, OVL_EINVAL, std::string("cannot open ") + path);
+  int n = 0, V = 0;
+  double mu = 0;
+  if (fscanf(f, "OVLDEFL 1 n=%d V=%d mu=%lf", &n, &V, &mu) != 3 || fgetc(f) != '\n' || V != c->V || n < 0) {
+    fclose(f);
+    return set_err(c, OVL_EINVAL, "bad deflation file header");
+  }
+  ovl_defl* d = new (std::nothrow) ovl_defl();
+  if (!d) { fclose(f); return OVL_ENOMEM; }
+  ovl_status s = defl_alloc(c, d, c->P.mixed ? P32 : P64, std::max(n, 1));
+  std::vector<double> h((size_t)24 * c->V);
+  for (int i = 0; i < n && s == OVL_OK; ++i) {
+    if (fread(h.data(), sizeof(double), h.size(), f) != h.size()) s = set_err(c, OVL_EINVAL, "short file");
+    else s = import_spinors(c, h.data(), OVL_C128, 0, 1, d->v, i);
+    if (s != OVL_OK) break;
+    if (fread(h.data(), sizeof(double), h.size(), f) != h.size()) s = set_err(c, OVL_EINVAL, "short file");
+    else s = import_spinors(c, h.data(), OVL_C128, 0, 1, d->w, i);
+  }
+  d->ritz.assign(n, 0.0);
+  d->res.assign(n, 0.0);
+  if (s == OVL_OK && n > 0) {
+    if (fread(d->ritz.data(), sizeof(double), n, f) != (size_t)n || fread(d->res.data(), sizeof(double), n, f) != (size_t)n)
+      s = set_err(c, OVL_EINVAL, "short file");
+  }
+  fclose(f);
+  if (s != OVL_OK) {
+    ovl_defl_destroy(d);
+    return s;
+  }
+  d->n = n;
+  d->mu = mu;
+  cudaStreamSynchronize(c->st);
+  *out = d;
+  return OVL_OK;
+}
+
+// ---------------------------------------------------------------- force
+extern "C" ovl_status overlap_force(ovl_ctx* c, double mu, const void* phi, int dtype, int on_device, double tol,
+                                    double* dSdU, double* S) {
+  if (!c || !phi || !dSdU) return OVL_EINVAL;
+  if (!(mu > 0 && mu < 1)) return set_err(c, OVL_EINVAL, "mu must lie in (0, 1)");
+  Field* fp;
+  OVL_TRY(get_field(c, "f_phi", P64, 1, &fp));
+  OVL_TRY(import_spinors(c, phi, dtype, on_device, 1, *fp, 0));
+  return force_compute(c, mu, *fp, tol, dSdU, S);
+}
+
+// ---------------------------------------------------------------- profiling
+extern "C" ovl_status ovl_profile_enable(ovl_ctx* c, int on) {
+  if (!c) return OVL_EINVAL;
+  if (!on) prof_flush(c);
+  c->prof.on = on != 0;
+  return OVL_OK;
+}
+extern "C" ovl_status ovl_profile_reset(ovl_ctx* c) {
+  if (!c) return OVL_EINVAL;
+  prof_flush(c);
+  for (int k = 0; k < OVL_PROF_CLASSES; ++k) {
+    c->prof.launches[k] = 0;
+    c->prof.ms[k] = 0;
+    c->prof.bytes[k] = 0;
+  }
+  c->wcalls[0] = c->wcalls[1] = c->wcalls[2] = 0;
+  return OVL_OK;
+}
+extern "C" ovl_status ovl_profile_get(ovl_ctx* c, int cls, long long* launches, double* ms, double* bytes) {
+  if (!c || cls < 0 || cls >= OVL_PROF_CLASSES) return OVL_EINVAL;
+  prof_flush(c);
+  if (launches) *launches = c->prof.launches[cls];
+  if (ms) *ms = c->prof.ms[cls];
+  if (bytes) *bytes = c->prof.bytes[cls];
+  return OVL_OK;
+}
+
+extern "C" ovl_status ovl_bench_wilson(ovl_ctx* c, int prec, int n, int iters, double* ms_per_launch,
+                                       double* bytes_per_launch) {
+  if (!c || prec < P64 || prec > P16 || n < 1 || n > 256 || iters < 1) return OVL_EINVAL;
+  Field *fi, *fo;
+  OVL_TRY(get_field(c, "bw_in", prec, n, &fi));
+  OVL_TRY(get_field(c, "bw_out", prec, n, &fo));
+  {
+    std::vector<double> h((size_t)24 * c->V);
+    unsigned long long st = 12345;
+    for (auto& x : h) {
+      st = st * 6364136223846793005ull + 1442695040888963407ull;
+      x = ((double)(st >> 11) / 9007199254740992.0) - 0.5;
+    }
+    for (int j = 0; j < n; ++j) OVL_TRY(import_spinors(c, h.data(), OVL_C128, 0, 1, *fi, j));
+  }
+  for (int w = 0; w < 3; ++w) OVL_TRY(wilson_apply_field(c, prec, *fi, 0, *fo, 0, n));
+  cudaEvent_t e0, e1;
+  OVL_CUDA(c, cudaEventCreate(&e0));
+  OVL_CUDA(c, cudaEventCreate(&e1));
+  OVL_CUDA(c, cudaEventRecord(e0, c->st));
+  for (int k = 0; k < iters; ++k) launch_wilson_K(prec, prec, prec, c->g, c->kappa, links_of(c, prec), fi->ref(), fo->ref(), n, nullptr, nullptr, c->st);
+  OVL_CUDA(c, cudaEventRecord(e1, c->st));
+  OVL_CUDA(c, cudaEventSynchronize(e1));
+  float ms = 0;
+  cudaEventElapsedTime(&ms, e0, e1);
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  OVL_TRY(check_launch(c, __func__));
+  const double sb = prec == P64 ? 192 : prec == P32 ? 96 : 48 + 4;
+  const double lb = prec == P64 ? 384 : prec == P32 ? 192 : 96;
+  if (ms_per_launch) *ms_per_launch = ms / iters;
+  if (bytes_per_launch) *bytes_per_launch = (double)c->V * (2.0 * sb * n + lb);
+  return OVL_OK;
+}

@@ -1,0 +1,145 @@
+// Library-internal state of one overlap context: gauge field in every storage
+// precision, Zolotarev poles, device workspaces, profiling, error text.
+#pragma once
+#include <cuda_runtime.h>
+
+#include <complex>
+#include <map>
+#include <string>
+#include <vector>
+
+#include "../../include/overlap.h"
+#include "kernels.h"
+
+namespace ovl {
+
+using cd = std::complex<double>;
+
+struct ProfPair {
+  cudaEvent_t a, b;
+  int cls;
+  double bytes;
+};
+
+struct Profiler {
+  bool on = false;
+  long long launches[OVL_PROF_CLASSES] = {0};
+  double ms[OVL_PROF_CLASSES] = {0};
+  double bytes[OVL_PROF_CLASSES] = {0};
+  std::vector<ProfPair> pending;
+  std::vector<cudaEvent_t> pool;
+};
+
+// Sign-function precision modes (Sec. 3: single precision when the required
+// accuracy allows; FP16 storage extends the same idea one step further).
+enum SignMode { SIGN64 = 0, SIGN32 = 1, SIGN16 = 2 };
+
+struct SignStats {
+  std::vector<int> iters;     // multi-shift CG iterations per system
+  std::vector<int> status;    // 0 converged, 1 iteration limit, 2 breakdown
+};
+
+struct ovl_ctx_impl;
+}  // namespace ovl
+
+struct ovl_ctx {
+  ovl::Geom g;
+  int V = 0;
+  double m0 = 0, kappa = 0, mu = 0;
+  int npoles = 0;
+  double eps_sign = 0, delta = 0, za = 0, zb = 0;
+  std::vector<double> omega, sigma;
+  ovl_params P;
+  cudaStream_t st = nullptr;
+  int device = 0;
+  void* link[3] = {nullptr, nullptr, nullptr};  // P64, P32, P16 12-real layouts
+  ovl::Poles hpoles;
+  ovl::Poles* dpoles = nullptr;
+  std::map<std::string, ovl::Field> ws;
+  double* partials = nullptr;
+  size_t partials_n = 0;
+  double* dred = nullptr;        // reduced per-rhs pairs (device), 2 * 4096
+  double* dscal = nullptr;       // per-rhs scalars (device), 64 * 4096
+  int* dint = nullptr;           // per-rhs ints (device), 4096
+  ovl::MsRhs* ms = nullptr;
+  int ms_n = 0;
+  double* hpin = nullptr;        // pinned host staging for scalars, 64 * 4096 doubles
+  void* hstage = nullptr;        // pinned host staging for spinor copies
+  size_t hstage_bytes = 0;
+  double* dwork = nullptr;       // Gram work buffer
+  size_t dwork_n = 0;
+  size_t ring_pos = 0;           // scalar upload ring in hpin / dscal, [32768, 262144)
+  std::string err;
+  ovl::Profiler prof;
+  long long wcalls[3] = {0, 0, 0};  // Wilson applications by precision
+};
+
+struct ovl_defl {
+  ovl_ctx* ctx = nullptr;
+  int n = 0;            // vectors held
+  int cap = 0;          // capacity of v, w
+  ovl::Field v;         // approximate low eigenvectors psi_i of D^dag D (and of gamma5 D)
+  ovl::Field w;         // w_i = gamma5 eps(K) psi_i, so that D(mu) psi_i = (1+mu)/2 psi_i + (1-mu)/2 w_i
+  std::vector<double> ritz, res;
+  double mu = 0;        // mass at which the Ritz values were computed
+  bool per_vector = false;   // Sec. 4 per-vector alpha_j instead of the least-squares solve
+  bool prepared = false;
+  std::vector<std::complex<double>> VV, WW, WV, G5VV, G5VW;   // Gram blocks over psi and w
+};
+
+namespace ovl {
+
+// error helpers
+ovl_status set_err(ovl_ctx* c, ovl_status s, const std::string& m);
+ovl_status cuda_check(ovl_ctx* c, cudaError_t e, const char* what);
+#define OVL_CUDA(c, call)                                     \
+  do {                                                        \
+    cudaError_t _e = (call);                                  \
+    if (_e != cudaSuccess) return ovl::cuda_check(c, _e, #call); \
+  } while (0)
+#define OVL_TRY(expr)                  \
+  do {                                 \
+    ovl_status _s = (expr);            \
+    if (_s != OVL_OK) return _s;       \
+  } while (0)
+
+// cudaGetLastError plus the unsupported-precision flag of the launchers
+ovl_status check_launch(ovl_ctx* c, const char* where);
+
+// workspace
+ovl_status get_field(ovl_ctx* c, const std::string& name, int prec, int n, Field** out);
+void free_field(Field& f);
+ovl_status ensure_partials(ovl_ctx* c, int nrhs);
+ovl_status ensure_ms(ovl_ctx* c, int nrhs);
+ovl_status ensure_stage(ovl_ctx* c, size_t bytes);
+ovl_status ensure_work(ovl_ctx* c, size_t ndoubles);
+
+// profiling
+void prof_begin(ovl_ctx* c, int cls, ProfPair* p);
+void prof_end(ovl_ctx* c, ProfPair* p, double bytes);
+void prof_flush(ovl_ctx* c);
+
+LinkRef links_of(const ovl_ctx* c, int prec);
+
+// reductions: partials -> host pairs (synchronises the stream)
+ovl_status reduce_to_host(ovl_ctx* c, int nsb, int nrhs, double* host_pairs);
+
+// I/O between caller buffers and internal fields
+ovl_status import_spinors(ovl_ctx* c, const void* src, int dtype, int on_device, int n, Field& dst, int off);
+ovl_status export_spinors(ovl_ctx* c, void* dst, int dtype, int on_device, int n, const Field& src, int off);
+
+// sign function: out = c1 v + c2 gamma5 K y (times gamma5 if herm), y = sum_i omega_i (K^2+sigma_i)^-1 v,
+// every system stopped at its own relative accuracy eta[j]. dot_w (may be null) requests (w_j, out_j)
+// into dots (host, 2n). coef (host, may be null) gives per-system (c1, c2).
+ovl_status sign_op(ovl_ctx* c, int mode, const Field& v, int voff, Field& out, int ooff, int n, const double* eta,
+                   double c1, double c2, const double* coef, int herm, const Field* dot_w, int woff, double* dots,
+                   SignStats* stats);
+int choose_mode(const ovl_ctx* c, double eta);
+
+// Upload count doubles of per-system scalars through the pinned ring; returns the
+// device copy (valid for kernels issued later on the context stream).
+ovl_status upload(ovl_ctx* c, const double* host, int count, const double** dev);
+
+// gamma5 K applied to n systems in FP64 etc. lives in the solvers; this is the plain Wilson kernel
+ovl_status wilson_apply_field(ovl_ctx* c, int prec, const Field& in, int ioff, Field& out, int ooff, int n);
+}  // namespace ovl

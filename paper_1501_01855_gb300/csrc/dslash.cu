@@ -1,0 +1,324 @@
+// Wilson kernel K of the overlap operator (Sec. 1, the equation for aK_xy):
+//
+//   K psi(x) = gamma5 [ psi(x) - kappa sum_mu ( (1-gamma_mu) U_mu(x) psi(x+mu)
+//                                              + (1+gamma_mu) U_mu(x-mu)^dag psi(x-mu) ) ]
+//
+// One thread per (site, system). (1 -+ gamma_mu) has rank 2, so each neighbour is
+// projected to a half spinor (2 spins x 3 colours), multiplied by the 12-real link
+// (row 3 rebuilt in registers) and expanded again; the spin algebra below is the
+// DeGrand-Rossi chiral basis, gamma5 = diag(1, 1, -1, -1). Threads of one block
+// that share a site but belong to different systems read the same links, so the
+// link bytes of a multi-system launch come from L1 once per block.
+//
+// Three fused epilogues cover every use in the sign function (Sec. 3):
+//   MODE_K    out = K in, partial sums of ||out||^2 and ||in||^2
+//             (first half of a multi-shift CG step: (p, K^2 p) = ||K p||^2);
+//   MODE_R    r -= alpha (K t + sigma0 p), partial sums of ||r||^2
+//             (second half: K^2 p + sigma0 p applied and consumed in one pass);
+//   MODE_OVL  out = c1 v + c2 (y - kappa hop y) = c1 v + c2 gamma5 K y, optionally times
+//             gamma5, with partial sums of (w, out): gamma5 eps(K) v and D(mu) v are
+//             this with y = sum_i omega_i (K^2 + sigma_i)^-1 v.
+#include "kernels.h"
+
+namespace ovl {
+
+enum { MODE_K = 0, MODE_R = 1, MODE_OVL = 2 };
+
+template <int MU, int S, typename T>
+__device__ __forceinline__ void project(const cpx<T> p[12], cpx<T> h[6]) {
+#pragma unroll
+  for (int c = 0; c < 3; ++c) {
+    const cpx<T> p0 = p[c], p1 = p[3 + c], p2 = p[6 + c], p3 = p[9 + c];
+    if constexpr (MU == 0) {          // h0 = p0 + S i p3, h1 = p1 + S i p2
+      h[c] = S > 0 ? p0 + timesI(p3) : p0 - timesI(p3);
+      h[3 + c] = S > 0 ? p1 + timesI(p2) : p1 - timesI(p2);
+    } else if constexpr (MU == 1) {   // h0 = p0 - S p3, h1 = p1 + S p2
+      h[c] = S > 0 ? p0 - p3 : p0 + p3;
+      h[3 + c] = S > 0 ? p1 + p2 : p1 - p2;
+    } else if constexpr (MU == 2) {   // h0 = p0 + S i p2, h1 = p1 - S i p3
+      h[c] = S > 0 ? p0 + timesI(p2) : p0 - timesI(p2);
+      h[3 + c] = S > 0 ? p1 - timesI(p3) : p1 + timesI(p3);
+    } else {                          // h0 = p0 + S p2, h1 = p1 + S p3
+      h[c] = S > 0 ? p0 + p2 : p0 - p2;
+      h[3 + c] = S > 0 ? p1 + p3 : p1 - p3;
+    }
+  }
+}
+
+// acc += (1 + S gamma_mu) expanded from the half spinor w
+template <int MU, int S, typename T>
+__device__ __forceinline__ void accumulate(cpx<T> acc[12], const cpx<T> w[6]) {
+#pragma unroll
+  for (int c = 0; c < 3; ++c) {
+    const cpx<T> w0 = w[c], w1 = w[3 + c];
+    acc[c] = acc[c] + w0;
+    acc[3 + c] = acc[3 + c] + w1;
+    if constexpr (MU == 0) {          // lower = (-S i w1, -S i w0)
+      acc[6 + c] = acc[6 + c] + (S > 0 ? timesMinusI(w1) : timesI(w1));
+      acc[9 + c] = acc[9 + c] + (S > 0 ? timesMinusI(w0) : timesI(w0));
+    } else if constexpr (MU == 1) {   // lower = (S w1, -S w0)
+      acc[6 + c] = S > 0 ? acc[6 + c] + w1 : acc[6 + c] - w1;
+      acc[9 + c] = S > 0 ? acc[9 + c] - w0 : acc[9 + c] + w0;
+    } else if constexpr (MU == 2) {   // lower = (-S i w0, S i w1)
+      acc[6 + c] = acc[6 + c] + (S > 0 ? timesMinusI(w0) : timesI(w0));
+      acc[9 + c] = acc[9 + c] + (S > 0 ? timesI(w1) : timesMinusI(w1));
+    } else {                          // lower = (S w0, S w1)
+      acc[6 + c] = S > 0 ? acc[6 + c] + w0 : acc[6 + c] - w0;
+      acc[9 + c] = S > 0 ? acc[9 + c] + w1 : acc[9 + c] - w1;
+    }
+  }
+}
+
+template <typename T>
+__device__ __forceinline__ void su3_mul(const cpx<T> u[9], const cpx<T> h[6], cpx<T> w[6]) {
+#pragma unroll
+  for (int sp = 0; sp < 2; ++sp)
+#pragma unroll
+    for (int a = 0; a < 3; ++a)
+      w[3 * sp + a] = u[3 * a] * h[3 * sp] + u[3 * a + 1] * h[3 * sp + 1] + u[3 * a + 2] * h[3 * sp + 2];
+}
+template <typename T>
+__device__ __forceinline__ void su3_dag_mul(const cpx<T> u[9], const cpx<T> h[6], cpx<T> w[6]) {
+#pragma unroll
+  for (int sp = 0; sp < 2; ++sp)
+#pragma unroll
+    for (int a = 0; a < 3; ++a)
+      w[3 * sp + a] = cmulc(u[a], h[3 * sp]) + cmulc(u[3 + a], h[3 * sp + 1]) + cmulc(u[6 + a], h[3 * sp + 2]);
+}
+
+template <int MU, int PIN, int PL, typename T>
+__device__ __forceinline__ void hop_dir(const Geom& g, const LinkRef& L, const SpinorRef& in, int rhs, int s,
+                                        const int x[4], int stride, cpx<T> acc[12]) {
+  cpx<T> psi[12], h[6], w[6], u[9];
+  // forward neighbour: (1 - gamma_mu) U_mu(x) psi(x + mu)
+  {
+    const bool wrap = x[MU] == g.L[MU] - 1;
+    const int sf = wrap ? s - (g.L[MU] - 1) * stride : s + stride;
+    load_spinor_as<PIN, T>(in, rhs, sf, psi);
+    project<MU, -1>(psi, h);
+    if (MU == 3 && g.bc_t && wrap) {
+#pragma unroll
+      for (int k = 0; k < 6; ++k) h[k] = -h[k];
+    }
+    load_link<PL, T>(L, MU, s, u);
+    su3_mul(u, h, w);
+    accumulate<MU, -1>(acc, w);
+  }
+  // backward neighbour: (1 + gamma_mu) U_mu(x - mu)^dag psi(x - mu)
+  {
+    const bool wrap = x[MU] == 0;
+    const int sb = wrap ? s + (g.L[MU] - 1) * stride : s - stride;
+    load_spinor_as<PIN, T>(in, rhs, sb, psi);
+    project<MU, +1>(psi, h);
+    if (MU == 3 && g.bc_t && wrap) {
+#pragma unroll
+      for (int k = 0; k < 6; ++k) h[k] = -h[k];
+    }
+    load_link<PL, T>(L, MU, sb, u);
+    su3_dag_mul(u, h, w);
+    accumulate<MU, +1>(acc, w);
+  }
+}
+
+template <int PIN, int PL, typename T>
+__device__ __forceinline__ void hop(const Geom& g, const LinkRef& L, const SpinorRef& in, int rhs, int s,
+                                    cpx<T> acc[12]) {
+  int x[4];
+  int t = s;
+  x[0] = t % g.L[0]; t /= g.L[0];
+  x[1] = t % g.L[1]; t /= g.L[1];
+  x[2] = t % g.L[2]; x[3] = t / g.L[2];
+#pragma unroll
+  for (int k = 0; k < 12; ++k) acc[k] = cmk(T(0), T(0));
+  const int sy = g.L[0], sz = g.L[0] * g.L[1], st = sz * g.L[2];
+  hop_dir<0, PIN, PL, T>(g, L, in, rhs, s, x, 1, acc);
+  hop_dir<1, PIN, PL, T>(g, L, in, rhs, s, x, sy, acc);
+  hop_dir<2, PIN, PL, T>(g, L, in, rhs, s, x, sz, acc);
+  hop_dir<3, PIN, PL, T>(g, L, in, rhs, s, x, st, acc);
+}
+
+struct DArgs {
+  Geom g;
+  double kappa;
+  LinkRef links;
+  SpinorRef in, out, aux1, aux2;
+  int nrhs, nsb, ngr;
+  double* partials;
+  const MsRhs* ms;
+  double sigma0;
+  double c1, c2;
+  const double* coef;
+  int herm;
+};
+
+template <int MODE, int PIN, int PL, int POUT, int PA1, int PA2>
+__global__ void __launch_bounds__(256) wilson_kernel(const DArgs a) {
+  using T = typename Real<PL>::T;
+  __shared__ double red[4 * (BX / 32) * 2];
+  const int sb = blockIdx.x / a.ngr;
+  const int rg = blockIdx.x - sb * a.ngr;
+  const int rhs = rg * blockDim.y + threadIdx.y;
+  const int s = sb * BX + threadIdx.x;
+  bool live = (s < a.g.V) && (rhs < a.nrhs);
+  if (live && a.ms != nullptr && (MODE == MODE_K || MODE == MODE_R)) live = !a.ms[rhs].done;
+  double v[2] = {0.0, 0.0};
+  if (live) {
+    cpx<T> acc[12], c[12];
+    hop<PIN, PL, T>(a.g, a.links, a.in, rhs, s, acc);
+    load_spinor_as<PIN, T>(a.in, rhs, s, c);
+    const T kap = (T)a.kappa;
+    if constexpr (MODE == MODE_K) {
+      // K in = gamma5 (in - kappa acc)
+#pragma unroll
+      for (int k = 0; k < 12; ++k) {
+        cpx<T> o = c[k] - kap * acc[k];
+        if (k >= 6) o = -o;
+        v[0] += (double)norm2(o);
+        v[1] += (double)norm2(c[k]);
+        acc[k] = o;
+      }
+      store_spinor_as<POUT, T>(a.out, rhs, s, acc);
+    } else if constexpr (MODE == MODE_R) {
+      cpx<T> p[12], r[12];
+      load_spinor_as<PA1, T>(a.aux1, rhs, s, p);
+      load_spinor_as<PA2, T>(a.aux2, rhs, s, r);
+      const T sg = (T)a.sigma0;
+      const T al = (T)a.ms[rhs].alpha;
+#pragma unroll
+      for (int k = 0; k < 12; ++k) {
+        cpx<T> o = c[k] - kap * acc[k];
+        if (k >= 6) o = -o;
+        o = o + sg * p[k];
+        r[k] = r[k] - al * o;
+        v[0] += (double)norm2(r[k]);
+      }
+      store_spinor_as<PA2, T>(a.aux2, rhs, s, r);
+    } else {
+      cpx<T> w[12];
+      T c1 = (T)a.c1, c2 = (T)a.c2;
+      if (a.coef != nullptr) {
+        c1 = (T)a.coef[2 * rhs];
+        c2 = (T)a.coef[2 * rhs + 1];
+      }
+      if (c1 != T(0)) {
+        load_spinor_as<PA1, T>(a.aux1, rhs, s, w);
+      } else {
+#pragma unroll
+        for (int k = 0; k < 12; ++k) w[k] = cmk(T(0), T(0));
+      }
+#pragma unroll
+      for (int k = 0; k < 12; ++k) {
+        cpx<T> o = c1 * w[k] + c2 * (c[k] - kap * acc[k]);
+        if (a.herm && k >= 6) o = -o;
+        acc[k] = o;
+      }
+      store_spinor_as<POUT, T>(a.out, rhs, s, acc);
+      if (a.partials != nullptr) {
+        load_spinor_as<PA2, T>(a.aux2, rhs, s, w);
+#pragma unroll
+        for (int k = 0; k < 12; ++k) {
+          cpx<T> d = cmulc(w[k], acc[k]);
+          v[0] += (double)d.r;
+          v[1] += (double)d.i;
+        }
+      }
+    }
+  }
+  if (a.partials != nullptr) {
+    block_reduce_rows<2>(v, red);
+    if (threadIdx.x == 0 && rhs < a.nrhs) {
+      a.partials[((size_t)rhs * a.nsb + sb) * NVRED + 0] = v[0];
+      a.partials[((size_t)rhs * a.nsb + sb) * NVRED + 1] = v[1];
+    }
+  }
+}
+
+Shape make_shape(int V, int nrhs) {
+  Shape s;
+  s.nsb = (V + BX - 1) / BX;
+  s.by = nrhs < 4 ? nrhs : 4;
+  s.ngr = (nrhs + s.by - 1) / s.by;
+  return s;
+}
+
+template <int MODE, int PIN, int PL, int POUT, int PA1, int PA2>
+static void run(DArgs a, cudaStream_t st) {
+  Shape sh = make_shape(a.g.V, a.nrhs);
+  a.nsb = sh.nsb;
+  a.ngr = sh.ngr;
+  wilson_kernel<MODE, PIN, PL, POUT, PA1, PA2><<<sh.grid(), sh.block(), 0, st>>>(a);
+}
+
+static DArgs base_args(const Geom& g, double kappa, LinkRef links, int nrhs) {
+  DArgs a;
+  a.g = g;
+  a.kappa = kappa;
+  a.links = links;
+  a.in = a.out = a.aux1 = a.aux2 = SpinorRef{nullptr, nullptr, g.V};
+  a.nrhs = nrhs;
+  a.nsb = a.ngr = 0;
+  a.partials = nullptr;
+  a.ms = nullptr;
+  a.sigma0 = 0;
+  a.c1 = a.c2 = 0;
+  a.coef = nullptr;
+  a.herm = 0;
+  return a;
+}
+
+#define OVL_BAD_COMBO() note_bad_combo(__func__)
+
+void launch_wilson_K(int pin, int plink, int pout, const Geom& g, double kappa, LinkRef links, SpinorRef in,
+                     SpinorRef out, int nrhs, double* partials, const MsRhs* ms, cudaStream_t st) {
+  DArgs a = base_args(g, kappa, links, nrhs);
+  a.in = in;
+  a.out = out;
+  a.partials = partials;
+  a.ms = ms;
+  if (pin == P64 && plink == P64 && pout == P64) run<MODE_K, P64, P64, P64, P64, P64>(a, st);
+  else if (pin == P32 && plink == P32 && pout == P32) run<MODE_K, P32, P32, P32, P32, P32>(a, st);
+  else if (pin == P16 && plink == P16 && pout == P16) run<MODE_K, P16, P16, P16, P16, P16>(a, st);
+  else if (pin == P32 && plink == P16 && pout == P32) run<MODE_K, P32, P16, P32, P32, P32>(a, st);
+  else if (pin == P32 && plink == P16 && pout == P16) run<MODE_K, P32, P16, P16, P32, P32>(a, st);
+  else OVL_BAD_COMBO();
+}
+
+void launch_wilson_mscg_r(int pt, int plink, int pr, int pp, const Geom& g, double kappa, LinkRef links,
+                          SpinorRef t, SpinorRef p0, SpinorRef r, int nrhs, double sigma0, double* partials,
+                          const MsRhs* ms, cudaStream_t st) {
+  DArgs a = base_args(g, kappa, links, nrhs);
+  a.in = t;
+  a.aux1 = p0;
+  a.aux2 = r;
+  a.sigma0 = sigma0;
+  a.partials = partials;
+  a.ms = ms;
+  if (pt == P64 && plink == P64 && pr == P64 && pp == P64) run<MODE_R, P64, P64, P64, P64, P64>(a, st);
+  else if (pt == P32 && plink == P32 && pr == P32 && pp == P32) run<MODE_R, P32, P32, P32, P32, P32>(a, st);
+  else if (pt == P16 && plink == P16 && pr == P32 && pp == P16) run<MODE_R, P16, P16, P32, P16, P32>(a, st);
+  else OVL_BAD_COMBO();
+}
+
+void launch_wilson_ovl(int py, int plink, int pv, const Geom& g, double kappa, LinkRef links, SpinorRef y,
+                       SpinorRef v, SpinorRef out, SpinorRef w, int nrhs, double c1, double c2,
+                       const double* coef, int herm, double* partials, cudaStream_t st) {
+  DArgs a = base_args(g, kappa, links, nrhs);
+  a.in = y;
+  a.aux1 = v;
+  a.out = out;
+  a.aux2 = w;
+  a.c1 = c1;
+  a.c2 = c2;
+  a.coef = coef;
+  a.herm = herm;
+  a.partials = partials;
+  if (py == P64 && plink == P64 && pv == P64) run<MODE_OVL, P64, P64, P64, P64, P64>(a, st);
+  else if (py == P32 && plink == P32 && pv == P32) run<MODE_OVL, P32, P32, P32, P32, P32>(a, st);
+  else if (py == P32 && plink == P32 && pv == P64) run<MODE_OVL, P32, P32, P64, P64, P64>(a, st);
+  else if (py == P32 && plink == P16 && pv == P32) run<MODE_OVL, P32, P16, P32, P32, P32>(a, st);
+  else if (py == P32 && plink == P16 && pv == P64) run<MODE_OVL, P32, P16, P64, P64, P64>(a, st);
+  else if (py == P64 && plink == P64 && pv == P32) run<MODE_OVL, P64, P64, P32, P32, P32>(a, st);
+  else OVL_BAD_COMBO();
+}
+
+}  // namespace ovl

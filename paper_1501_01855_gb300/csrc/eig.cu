@@ -1,0 +1,168 @@
+// eigSUMR accumulation (Sec. 5, Algs. 5-6). While the middle SUMR solve builds
+// its Krylov basis, every step stores v_k = q_j and w_k = V q_j (V = gamma5 eps(K)),
+// so that v^D_k = (1-mu)/2 w_k + (1+mu)/2 q_j = D q_j (Alg. 5). When k reaches the
+// basis size m the Ritz recalculation of Alg. 6 runs:
+//   E = (v_i, v_j), Cholesky E = U^dag U, M = (v^D_i, v^D_j) + 2 mu delta (v_i, gamma5 v^D_j),
+//   eigenvectors Y of L^-1 M U^-1 (ascending), new v = V U^-1 Y, new v^D likewise,
+//   keep the lowest n; residuals ||gamma5 v^D_i - v_i (v_i, gamma5 v^D_i)||.
+// The Gram blocks run on the GPU (FP32 products, FP64 sums); the m x m algebra is
+// FP64 on the host. If the basis has lost linear independence (Sec. 5 notes that
+// orthogonality of the SUMR vectors is quickly lost with an inexact sign) and the
+// Cholesky factor does not exist, the basis is orthonormalised through the
+// eigendecomposition of E instead, dropping directions below 1e-10 of its largest
+// eigenvalue.
+//
+// Sign accuracy while accumulating: the bound of Sec. 5.1 (the one used for the
+// paper's runs),
+//   ||delta^D|| < (chi sqrt(eps^2 + r0^2) - r0) / (sqrt((m-n) k) max |(UV)_ij|),
+// chi = 1 for the first two diagonalisations and sqrt(n) after, r0 the residual of
+// the best converged eigenvector, max |(UV)_ij| over the new basis vectors averaged
+// over the last ten diagonalisations; the inversion relaxation is then capped by it
+// (strategy 3 of Sec. 5.1: the more accurate of the two bounds).
+#include <string.h>
+
+#include <algorithm>
+#include <cmath>
+
+#include "context.h"
+#include "eig.h"
+#include "hostmath.h"
+#include "solver.h"
+
+namespace ovl {
+
+ovl_status ritz_step(ovl_ctx* c, EigState* e, int keep) {
+  const int k = e->k;
+  if (k == 0) return OVL_OK;
+  keep = std::min(keep, k);
+  const double mu = e->mu, delta = e->delta;
+  const double a = 0.5 * (1.0 - mu), b = 0.5 * (1.0 + mu);
+  Field* VD;
+  OVL_TRY(get_field(c, "e_VD", e->prec, e->m, &VD));
+  {
+    std::vector<cd> aa(k, a), bb(k, b);
+    OVL_TRY(axpby_batch(c, aa, *e->W, 0, bb, *e->V, 0, *VD, 0, k));
+  }
+  std::vector<cd> E, MVD, G5;
+  OVL_TRY(gram_host(c, *e->V, 0, k, *e->V, 0, k, 0, E));
+  OVL_TRY(gram_host(c, *VD, 0, k, *VD, 0, k, 0, MVD));
+  OVL_TRY(gram_host(c, *e->V, 0, k, *VD, 0, k, 1, G5));
+  std::vector<cd> M((size_t)k * k);
+  for (int i = 0; i < k; ++i)
+    for (int j = 0; j < k; ++j) M[(size_t)i * k + j] = MVD[(size_t)i * k + j] + 2.0 * mu * delta * G5[(size_t)i * k + j];
+  for (int i = 0; i < k; ++i)
+    for (int j = i; j < k; ++j) {
+      const cd h = 0.5 * (M[(size_t)i * k + j] + std::conj(M[(size_t)j * k + i]));
+      M[(size_t)i * k + j] = h;
+      M[(size_t)j * k + i] = std::conj(h);
+      const cd g = 0.5 * (E[(size_t)i * k + j] + std::conj(E[(size_t)j * k + i]));
+      E[(size_t)i * k + j] = g;
+      E[(size_t)j * k + i] = std::conj(g);
+    }
+  // B: k x r with B^dag E B = 1
+  std::vector<cd> B;
+  int r = k;
+  {
+    std::vector<cd> L = E;
+    if (cholesky_lower(k, L.data()) == 0) {
+      std::vector<cd> Li((size_t)k * k);
+      lower_inverse(k, L.data(), Li.data());
+      B.resize((size_t)k * k);
+      for (int i = 0; i < k; ++i)
+        for (int j = 0; j < k; ++j) B[(size_t)i * k + j] = std::conj(Li[(size_t)j * k + i]);   // L^-dag = U^-1
+    } else {
+      std::vector<cd> Ec = E, Z((size_t)k * k);
+      std::vector<double> w(k);
+      eigh_jacobi(k, Ec.data(), w.data(), Z.data());
+      const double thr = 1e-10 * std::max(w[k - 1], 1e-300);
+      std::vector<int> keepc;
+      for (int i = 0; i < k; ++i)
+        if (w[i] > thr) keepc.push_back(i);
+      r = (int)keepc.size();
+      B.assign((size_t)k * r, 0.0);
+      for (int i = 0; i < k; ++i)
+        for (int jj = 0; jj < r; ++jj) B[(size_t)i * r + jj] = Z[(size_t)i * k + keepc[jj]] / std::sqrt(w[keepc[jj]]);
+      e->cholesky_fallbacks += 1;
+    }
+  }
+  // T = B^dag M B (r x r)
+  std::vector<cd> MB((size_t)k * r), T((size_t)r * r), Y((size_t)r * r);
+  for (int i = 0; i < k; ++i)
+    for (int j = 0; j < r; ++j) {
+      cd s = 0;
+      for (int l = 0; l < k; ++l) s += M[(size_t)i * k + l] * B[(size_t)l * r + j];
+      MB[(size_t)i * r + j] = s;
+    }
+  for (int i = 0; i < r; ++i)
+    for (int j = 0; j < r; ++j) {
+      cd s = 0;
+      for (int l = 0; l < k; ++l) s += std::conj(B[(size_t)l * r + i]) * MB[(size_t)l * r + j];
+      T[(size_t)i * r + j] = s;
+    }
+  std::vector<double> lam(r);
+  eigh_jacobi(r, T.data(), lam.data(), Y.data());
+  keep = std::min(keep, r);
+  // C = B Y[:, :keep]  (k x keep)
+  std::vector<cd> C((size_t)k * keep);
+  for (int i = 0; i < k; ++i)
+    for (int j = 0; j < keep; ++j) {
+      cd s = 0;
+      for (int l = 0; l < r; ++l) s += B[(size_t)i * r + l] * Y[(size_t)l * r + j];
+      C[(size_t)i * keep + j] = s;
+    }
+  // rotate v and w
+  Field* Tv;
+  OVL_TRY(get_field(c, "e_T", e->prec, e->m, &Tv));
+  OVL_TRY(combine_host(c, *e->V, 0, k, C, *Tv, 0, keep, 0));
+  OVL_TRY(copy_convert(c, *Tv, 0, *e->V, 0, keep));
+  OVL_TRY(combine_host(c, *e->W, 0, k, C, *Tv, 0, keep, 0));
+  OVL_TRY(copy_convert(c, *Tv, 0, *e->W, 0, keep));
+  // Ritz values and residuals from the Gram data: ||r||^2 = ||v^D||^2 - |(v, g5 v^D)|^2
+  e->ritz.assign(lam.begin(), lam.begin() + keep);
+  e->res.assign(keep, 0.0);
+  for (int j = 0; j < keep; ++j) {
+    cd nd = 0, th = 0;
+    for (int p = 0; p < k; ++p)
+      for (int q = 0; q < k; ++q) {
+        const cd w = std::conj(C[(size_t)p * keep + j]) * C[(size_t)q * keep + j];
+        nd += w * MVD[(size_t)p * k + q];
+        th += w * G5[(size_t)p * k + q];
+      }
+    e->res[j] = std::sqrt(std::max(0.0, nd.real() - std::norm(th)));
+  }
+  // largest coefficient of the newly added vectors in the kept eigenvectors
+  double mx = 0.0;
+  for (int p = e->n_seeded; p < k; ++p)
+    for (int j = 0; j < keep; ++j) mx = std::max(mx, std::abs(C[(size_t)p * keep + j]));
+  e->uv_hist.push_back(mx);
+  if (e->uv_hist.size() > 10) e->uv_hist.erase(e->uv_hist.begin());
+  e->ndiag += 1;
+  e->k = keep;
+  e->n_seeded = keep;
+  // next sign-accuracy cap (Sec. 5.1 bound)
+  double avg = 0.0;
+  for (double v : e->uv_hist) avg += v;
+  avg /= std::max<size_t>(1, e->uv_hist.size());
+  const double r0 = *std::min_element(e->res.begin(), e->res.end());
+  const double chi = e->ndiag <= 2 ? 1.0 : std::sqrt((double)e->n_eig);
+  const double num = chi * std::sqrt(e->eps_v * e->eps_v + r0 * r0) - r0;
+  const double den = std::sqrt((double)std::max(1, e->m - e->n_eig) * e->kk) * std::max(avg, 1e-12);
+  double cap = num / den;
+  if (!(cap > 0)) cap = e->eps_v;
+  e->eta_cap = std::min(std::max(cap, 1e-10), c->P.eta_floor);
+  if (e->eig) e->eig->eta_cap = e->eta_cap;
+  return OVL_OK;
+}
+
+ovl_status eig_hook(ovl_ctx* c, void* data, const Field& q, const Field& u, int iter) {
+  (void)iter;
+  EigState* e = static_cast<EigState*>(data);
+  // system 0 of the batch feeds the basis
+  OVL_TRY(copy_convert(c, q, 0, *e->V, e->k, 1));
+  OVL_TRY(copy_convert(c, u, 0, *e->W, e->k, 1));
+  e->k += 1;
+  if (e->k == e->m) OVL_TRY(ritz_step(c, e, e->n_eig));
+  return OVL_OK;
+}
+
+}  // namespace ovl

@@ -1,0 +1,28 @@
+// eigSUMR state (Sec. 5) shared by the accumulation hook and the C ABI.
+#pragma once
+#include <vector>
+
+#include "context.h"
+#include "solver.h"
+
+namespace ovl {
+
+struct EigState {
+  int prec = P32;
+  int m = 0, n_eig = 0, k = 0, n_seeded = 0;
+  double mu = 0, delta = 0.01;
+  double eps_v = 1e-4;      // desired eigenvector accuracy epsilon (Sec. 6 uses 1e-4)
+  int kk = 25;              // iterations between accurate recalculations of v^D (Sec. 6: k = 25)
+  int ndiag = 0;
+  int cholesky_fallbacks = 0;
+  double eta_cap = 1e-4;
+  std::vector<double> uv_hist, ritz, res;
+  Field* V = nullptr;
+  Field* W = nullptr;
+  EigHook* eig = nullptr;
+};
+
+ovl_status ritz_step(ovl_ctx* c, EigState* e, int keep);
+ovl_status eig_hook(ovl_ctx* c, void* data, const Field& q, const Field& u, int iter);
+
+}  // namespace ovl

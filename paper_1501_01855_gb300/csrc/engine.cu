@@ -1,0 +1,388 @@
+// Context, workspaces, caller I/O, profiling and the sign-function driver of
+// liboverlap. The sign function (Sec. 3) is
+//   eps(K) v = sum_i omega_i K (K^2 + sigma_i)^-1 v,
+// evaluated by the device-resident multi-shift CG of mscg.cu; this file runs its
+// host loop: a chunk of steps is issued without synchronising, then one small
+// copy of the per-system done flags decides whether another chunk is needed.
+#include <stdio.h>
+#include <string.h>
+
+#include <algorithm>
+#include <cmath>
+
+#include "context.h"
+#include "hostmath.h"
+
+namespace ovl {
+
+ovl_status set_err(ovl_ctx* c, ovl_status s, const std::string& m) {
+  if (c) c->err = m;
+  return s;
+}
+
+ovl_status cuda_check(ovl_ctx* c, cudaError_t e, const char* what) {
+  std::string m = std::string("CUDA error ") + cudaGetErrorString(e) + " in " + what;
+  return set_err(c, OVL_ECUDA, m);
+}
+
+static thread_local bool g_bad_combo = false;
+static thread_local const char* g_bad_where = "";
+void note_bad_combo(const char* where) {
+  g_bad_combo = true;
+  g_bad_where = where;
+}
+bool take_bad_combo() {
+  const bool b = g_bad_combo;
+  g_bad_combo = false;
+  return b;
+}
+
+ovl_status check_launch(ovl_ctx* c, const char* where) {
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return cuda_check(c, e, where);
+  if (take_bad_combo())
+    return set_err(c, OVL_EINVAL, std::string("unsupported precision combination in ") + g_bad_where + " (" + where + ")");
+  return OVL_OK;
+}
+
+static size_t spinor_bytes(int prec) { return prec == P64 ? 192 : prec == P32 ? 96 : 48; }
+
+void free_field(Field& f) {
+  if (f.data) cudaFree(f.data);
+  if (f.norm) cudaFree(f.norm);
+  f.data = nullptr;
+  f.norm = nullptr;
+  f.n = 0;
+}
+
+ovl_status get_field(ovl_ctx* c, const std::string& name, int prec, int n, Field** out) {
+  Field& f = c->ws[name];
+  if (f.data != nullptr && f.prec == prec && f.n >= n) {
+    *out = &f;
+    return OVL_OK;
+  }
+  if (f.data != nullptr) {
+    cudaStreamSynchronize(c->st);
+    free_field(f);
+  }
+  f.prec = prec;
+  f.V = c->V;
+  f.n = n;
+  const size_t bytes = spinor_bytes(prec) * (size_t)c->V * n;
+  if (cudaMalloc(&f.data, bytes) != cudaSuccess) {
+    cudaGetLastError();
+    f.data = nullptr;
+    f.n = 0;
+    return set_err(c, OVL_ENOMEM, "cudaMalloc failed for workspace " + name);
+  }
+  if (prec == P16) {
+    if (cudaMalloc((void**)&f.norm, sizeof(float) * (size_t)c->V * n) != cudaSuccess) {
+      cudaGetLastError();
+      free_field(f);
+      return set_err(c, OVL_ENOMEM, "cudaMalloc failed for workspace norms " + name);
+    }
+  }
+  *out = &f;
+  return OVL_OK;
+}
+
+ovl_status ensure_partials(ovl_ctx* c, int nrhs) {
+  const size_t need = (size_t)nrhs * ((c->V + BX - 1) / BX) * NVRED;
+  if (need <= c->partials_n) return OVL_OK;
+  if (c->partials) {
+    cudaStreamSynchronize(c->st);
+    cudaFree(c->partials);
+  }
+  OVL_CUDA(c, cudaMalloc((void**)&c->partials, need * sizeof(double)));
+  c->partials_n = need;
+  return OVL_OK;
+}
+
+ovl_status ensure_ms(ovl_ctx* c, int nrhs) {
+  if (nrhs <= c->ms_n) return OVL_OK;
+  if (c->ms) {
+    cudaStreamSynchronize(c->st);
+    cudaFree(c->ms);
+  }
+  OVL_CUDA(c, cudaMalloc((void**)&c->ms, sizeof(MsRhs) * nrhs));
+  c->ms_n = nrhs;
+  return OVL_OK;
+}
+
+ovl_status ensure_stage(ovl_ctx* c, size_t bytes) {
+  if (bytes <= c->hstage_bytes) return OVL_OK;
+  if (c->hstage) cudaFreeHost(c->hstage);
+  c->hstage = nullptr;
+  OVL_CUDA(c, cudaMallocHost(&c->hstage, bytes));
+  c->hstage_bytes = bytes;
+  return OVL_OK;
+}
+
+ovl_status ensure_work(ovl_ctx* c, size_t nd) {
+  if (nd <= c->dwork_n) return OVL_OK;
+  if (c->dwork) {
+    cudaStreamSynchronize(c->st);
+    cudaFree(c->dwork);
+  }
+  OVL_CUDA(c, cudaMalloc((void**)&c->dwork, nd * sizeof(double)));
+  c->dwork_n = nd;
+  return OVL_OK;
+}
+
+LinkRef links_of(const ovl_ctx* c, int prec) {
+  LinkRef r;
+  r.data = c->link[prec];
+  r.V = c->V;
+  return r;
+}
+
+// ---------------------------------------------------------------- profiling
+void prof_begin(ovl_ctx* c, int cls, ProfPair* p) {
+  p->cls = cls;
+  if (!c->prof.on) return;
+  if (c->prof.pool.size() < 2) {
+    for (int k = 0; k < 256; ++k) {
+      cudaEvent_t e;
+      cudaEventCreate(&e);
+      c->prof.pool.push_back(e);
+    }
+  }
+  p->a = c->prof.pool.back();
+  c->prof.pool.pop_back();
+  p->b = c->prof.pool.back();
+  c->prof.pool.pop_back();
+  cudaEventRecord(p->a, c->st);
+}
+
+void prof_end(ovl_ctx* c, ProfPair* p, double bytes) {
+  if (!c->prof.on) return;
+  cudaEventRecord(p->b, c->st);
+  p->bytes = bytes;
+  c->prof.pending.push_back(*p);
+  if (c->prof.pending.size() > 4096) prof_flush(c);
+}
+
+void prof_flush(ovl_ctx* c) {
+  if (c->prof.pending.empty()) return;
+  cudaEventSynchronize(c->prof.pending.back().b);
+  for (auto& q : c->prof.pending) {
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, q.a, q.b);
+    c->prof.launches[q.cls] += 1;
+    c->prof.ms[q.cls] += ms;
+    c->prof.bytes[q.cls] += q.bytes;
+    c->prof.pool.push_back(q.a);
+    c->prof.pool.push_back(q.b);
+  }
+  c->prof.pending.clear();
+}
+
+ovl_status upload(ovl_ctx* c, const double* host, int count, const double** dev) {
+  const size_t lo = 32768, hi = 64 * 4096;
+  if ((size_t)count > hi - lo) return set_err(c, OVL_EINVAL, "scalar upload too large");
+  if (c->ring_pos < lo || c->ring_pos + count > hi) {
+    // wrapping: every earlier upload and every kernel reading it must have finished
+    OVL_CUDA(c, cudaStreamSynchronize(c->st));
+    c->ring_pos = lo;
+  }
+  double* h = c->hpin + c->ring_pos;
+  double* d = c->dscal + c->ring_pos;
+  memcpy(h, host, sizeof(double) * count);
+  OVL_CUDA(c, cudaMemcpyAsync(d, h, sizeof(double) * count, cudaMemcpyHostToDevice, c->st));
+  c->ring_pos += (count + 31) & ~(size_t)31;
+  *dev = d;
+  return OVL_OK;
+}
+
+ovl_status wilson_apply_field(ovl_ctx* c, int prec, const Field& in, int ioff, Field& out, int ooff, int n) {
+  launch_wilson_K(in.prec, prec, out.prec, c->g, c->kappa, links_of(c, prec), in.ref(ioff), out.ref(ooff), n, nullptr,
+                  nullptr, c->st);
+  OVL_TRY(check_launch(c, __func__));
+  c->wcalls[prec] += n;
+  return OVL_OK;
+}
+
+// ---------------------------------------------------------------- reductions
+ovl_status reduce_to_host(ovl_ctx* c, int nsb, int nrhs, double* host_pairs) {
+  launch_reduce_partials(c->partials, nsb, nrhs, c->dred, c->st);
+  OVL_CUDA(c, cudaMemcpyAsync(c->hpin, c->dred, sizeof(double) * 2 * nrhs, cudaMemcpyDeviceToHost, c->st));
+  OVL_CUDA(c, cudaStreamSynchronize(c->st));
+  memcpy(host_pairs, c->hpin, sizeof(double) * 2 * nrhs);
+  return OVL_OK;
+}
+
+// ---------------------------------------------------------------- caller I/O
+ovl_status import_spinors(ovl_ctx* c, const void* src, int dtype, int on_device, int n, Field& dst, int off) {
+  const size_t esz = dtype == OVL_C128 ? 16 : 8;
+  const size_t bytes = esz * 12 * (size_t)c->V * n;
+  const void* dsrc = src;
+  Field* tmp = nullptr;
+  if (!on_device) {
+    OVL_TRY(get_field(c, "io_canon", P64, (int)((bytes + 192 * (size_t)c->V - 1) / (192 * (size_t)c->V)), &tmp));
+    OVL_TRY(ensure_stage(c, bytes));
+    // pinned staging keeps the copy asynchronous with respect to pageable memory rules
+    memcpy(c->hstage, src, bytes);
+    OVL_CUDA(c, cudaMemcpyAsync(tmp->data, c->hstage, bytes, cudaMemcpyHostToDevice, c->st));
+    dsrc = tmp->data;
+  }
+  launch_pack(dtype, dsrc, dst.prec, dst.ref(off), n, c->V, c->st);
+  OVL_TRY(check_launch(c, __func__));
+  return OVL_OK;
+}
+
+ovl_status export_spinors(ovl_ctx* c, void* dst, int dtype, int on_device, int n, const Field& src, int off) {
+  const size_t esz = dtype == OVL_C128 ? 16 : 8;
+  const size_t bytes = esz * 12 * (size_t)c->V * n;
+  if (on_device) {
+    launch_unpack(dtype, dst, src.prec, src.ref(off), n, c->V, c->st);
+    OVL_TRY(check_launch(c, __func__));
+    return OVL_OK;
+  }
+  Field* tmp = nullptr;
+  OVL_TRY(get_field(c, "io_canon", P64, (int)((bytes + 192 * (size_t)c->V - 1) / (192 * (size_t)c->V)), &tmp));
+  OVL_TRY(ensure_stage(c, bytes));
+  launch_unpack(dtype, tmp->data, src.prec, src.ref(off), n, c->V, c->st);
+  OVL_CUDA(c, cudaMemcpyAsync(c->hstage, tmp->data, bytes, cudaMemcpyDeviceToHost, c->st));
+  OVL_CUDA(c, cudaStreamSynchronize(c->st));
+  memcpy(dst, c->hstage, bytes);
+  return OVL_OK;
+}
+
+// ---------------------------------------------------------------- sign function
+int choose_mode(const ovl_ctx* c, double eta) {
+  if (!c->P.mixed) return SIGN64;
+  if (c->P.half_storage && eta >= c->P.half_switch) return SIGN16;
+  if (eta >= c->P.sp_switch) return SIGN32;
+  return SIGN64;
+}
+
+ovl_status sign_op(ovl_ctx* c, int mode, const Field& v, int voff, Field& out, int ooff, int n, const double* eta,
+                   double c1, double c2, const double* coef, int herm, const Field* dot_w, int woff, double* dots,
+                   SignStats* stats) {
+  if (n <= 0) return OVL_OK;
+  const int PL = mode == SIGN64 ? P64 : mode == SIGN32 ? P32 : P16;
+  const int PR = mode == SIGN64 ? P64 : P32;
+  const int PP = PL;
+  const int V = c->V;
+  const int np = c->npoles;
+  const std::string tag = std::to_string(mode);
+  Field *r, *y, *t, *pb;
+  OVL_TRY(get_field(c, "ms_r" + tag, PR, n, &r));
+  OVL_TRY(get_field(c, "ms_y" + tag, PR, n, &y));
+  OVL_TRY(get_field(c, "ms_t" + tag, PP, n, &t));
+  OVL_TRY(get_field(c, "ms_p" + tag, PP, np * n, &pb));
+  OVL_TRY(ensure_partials(c, n));
+  OVL_TRY(ensure_ms(c, n));
+  const Shape sh = make_shape(V, n);
+  // per-system eta and (c1, c2) to the device
+  double* d_eta = c->dscal;
+  double* d_coef = c->dscal + 4096;
+  for (int j = 0; j < n; ++j) {
+    double e = eta[j] > 0 ? eta[j] : c->eps_sign;
+    if (e < c->delta) e = c->delta;
+    c->hpin[j] = e;
+  }
+  int ncopy = n;
+  if (coef) {
+    for (int j = 0; j < 2 * n; ++j) c->hpin[4096 + j] = coef[j];
+    ncopy = 4096 + 2 * n;
+  }
+  OVL_CUDA(c, cudaMemcpyAsync(c->dscal, c->hpin, sizeof(double) * ncopy, cudaMemcpyHostToDevice, c->st));
+  const LinkRef L = links_of(c, PL);
+  const int wcls = PL;  // profiler class of the Wilson launches
+  const double lbytes = (PL == P64 ? 384.0 : PL == P32 ? 192.0 : 96.0) * V;
+  const double sbytes = (double)spinor_bytes(PP) * V, rbytes = (double)spinor_bytes(PR) * V;
+  ProfPair pp;
+
+  prof_begin(c, 4, &pp);
+  launch_ms_init(v.prec, PR, PP, v.ref(voff), r->ref(), pb->ref(), y->ref(), np, n, V, c->partials, c->st);
+  prof_end(c, &pp, (double)n * V * (spinor_bytes(v.prec) + 2 * spinor_bytes(PR) + np * spinor_bytes(PP)));
+  launch_ms_scalar0(c->ms, c->partials, sh.nsb, n, c->dpoles, d_eta, c->P.mscg_max, c->st);
+  OVL_TRY(check_launch(c, __func__));
+
+  std::vector<int> done(n, 0);
+  int* hdone = reinterpret_cast<int*>(c->hpin + 8192);
+  int total = 0;
+  int chunk = 8;
+  while (true) {
+    for (int k = 0; k < chunk; ++k) {
+      prof_begin(c, wcls, &pp);
+      launch_wilson_K(PP, PL, PP, c->g, c->kappa, L, pb->ref(), t->ref(), n, c->partials, c->ms, c->st);
+      prof_end(c, &pp, 0.0);
+      prof_begin(c, 5, &pp);
+      launch_ms_scalar1(c->ms, c->partials, sh.nsb, n, c->dpoles, c->st);
+      prof_end(c, &pp, 0.0);
+      prof_begin(c, wcls, &pp);
+      launch_wilson_mscg_r(PP, PL, PR, PP, c->g, c->kappa, L, t->ref(), pb->ref(), r->ref(), n, c->hpoles.sigma0,
+                           c->partials, c->ms, c->st);
+      prof_end(c, &pp, 0.0);
+      prof_begin(c, 5, &pp);
+      launch_ms_scalar2(c->ms, c->partials, sh.nsb, n, c->dpoles, c->st);
+      prof_end(c, &pp, 0.0);
+      prof_begin(c, 3, &pp);
+      launch_ms_update(PR, PP, r->ref(), pb->ref(), y->ref(), np, n, V, c->ms, c->st);
+      prof_end(c, &pp, 0.0);
+    }
+    total += chunk;
+    OVL_TRY(check_launch(c, __func__));
+    OVL_CUDA(c, cudaMemcpy2DAsync(hdone, sizeof(int), &c->ms[0].done, sizeof(MsRhs), sizeof(int), n,
+                                  cudaMemcpyDeviceToHost, c->st));
+    OVL_CUDA(c, cudaStreamSynchronize(c->st));
+    bool all = true;
+    for (int j = 0; j < n; ++j) all = all && hdone[j];
+    if (all) break;
+    if (total > c->P.mscg_max + 16) break;
+    chunk = std::min(32, chunk * 2);
+  }
+  // final Wilson application with the overlap / sign epilogue
+  double* d_part = dot_w ? c->partials : nullptr;
+  prof_begin(c, wcls, &pp);
+  launch_wilson_ovl(PR, PL, out.prec, c->g, c->kappa, L, y->ref(), v.ref(voff), out.ref(ooff),
+                    dot_w ? dot_w->ref(woff) : SpinorRef{nullptr, nullptr, V}, n, c1, c2, coef ? d_coef : nullptr,
+                    herm, d_part, c->st);
+  prof_end(c, &pp, (double)n * V * (spinor_bytes(PR) + 2.0 * spinor_bytes(out.prec)) + lbytes);
+  OVL_TRY(check_launch(c, __func__));
+  if (dot_w) OVL_TRY(reduce_to_host(c, sh.nsb, n, dots));
+  // iteration counts, status and byte counters
+  std::vector<int> it(n), stt(n);
+  std::vector<long long> prd(n), pwr(n);
+  OVL_CUDA(c, cudaMemcpy2DAsync(hdone, sizeof(int), &c->ms[0].iter, sizeof(MsRhs), sizeof(int), n,
+                                cudaMemcpyDeviceToHost, c->st));
+  OVL_CUDA(c, cudaMemcpy2DAsync(hdone + 4096, sizeof(int), &c->ms[0].status, sizeof(MsRhs), sizeof(int), n,
+                                cudaMemcpyDeviceToHost, c->st));
+  long long* hll = reinterpret_cast<long long*>(c->hpin + 12288);
+  OVL_CUDA(c, cudaMemcpy2DAsync(hll, sizeof(long long), &c->ms[0].p_reads, sizeof(MsRhs), sizeof(long long), n,
+                                cudaMemcpyDeviceToHost, c->st));
+  OVL_CUDA(c, cudaMemcpy2DAsync(hll + 4096, sizeof(long long), &c->ms[0].p_writes, sizeof(MsRhs), sizeof(long long),
+                                n, cudaMemcpyDeviceToHost, c->st));
+  OVL_CUDA(c, cudaStreamSynchronize(c->st));
+  long long live = 0, pr = 0, pw = 0;
+  int itmax = 0;
+  for (int j = 0; j < n; ++j) {
+    it[j] = hdone[j];
+    stt[j] = hdone[4096 + j];
+    live += it[j];
+    itmax = std::max(itmax, it[j]);
+    pr += hll[j];
+    pw += hll[4096 + j];
+  }
+  c->wcalls[PL] += 2 * live + n;
+  if (c->prof.on) {
+    // algorithmic bytes of the chunked launches from the device-side live counts:
+    // MODE_K reads p_0 and writes t, MODE_R reads t, p_0, r and writes r, the links
+    // are read once per launch; the update reads r, y, the pole vectors and writes
+    // y and the still-active pole vectors.
+    c->prof.bytes[wcls] += (double)live * (4.0 * sbytes + 2.0 * rbytes) + 2.0 * lbytes * itmax;
+    c->prof.bytes[3] += (double)live * 3.0 * rbytes + (double)(pr + pw) * sbytes;
+  }
+  if (stats) {
+    stats->iters = it;
+    stats->status = stt;
+  }
+  for (int j = 0; j < n; ++j) {
+    if (stt[j] == 2) return set_err(c, OVL_EBREAKDOWN, "multi-shift CG breakdown in the sign function");
+  }
+  return OVL_OK;
+}
+
+}  // namespace ovl

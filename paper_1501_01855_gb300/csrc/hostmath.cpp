@@ -1,0 +1,282 @@
+// Host-side numerics of liboverlap (FP64, no GPU):
+//  * Jacobi elliptic sn, cn by the arithmetic-geometric mean and descending
+//    Landen transformation (Abramowitz & Stegun 16.4), complete integral K(m).
+//  * Zolotarev coefficients of eps(x) = sum_i omega_i x/(x^2 + sigma_i) on
+//    a < |x| < b (Sec. 3): c_l = sn^2/cn^2 (l K'/(2n); k'), k' = sqrt(1-(a/b)^2),
+//    product form d y prod(y^2+c_{2l}) / prod(y^2+c_{2l-1}) in y = x/a, d from
+//    equioscillation, partial fractions in x.
+//  * Small dense complex linear algebra for the Ritz step and the deflation
+//    projections: Cholesky, triangular inverse, cyclic Jacobi Hermitian
+//    eigensolver, LU solve; Sturm bisection for tridiagonal extremes (Lanczos).
+#include "hostmath.h"
+
+#include <algorithm>
+#include <cmath>
+#include <complex>
+#include <vector>
+
+namespace ovl {
+
+// ------------------------------------------------------------------ elliptic
+static void agm_phi(double u, double m, double* phi_out, double* K_out) {
+  // A&S 16.4: a0 = 1, b0 = sqrt(1-m), c0 = sqrt(m)
+  double a[64], c[64];
+  a[0] = 1.0;
+  double b = std::sqrt(1.0 - m);
+  c[0] = std::sqrt(m);
+  int N = 0;
+  while (N < 60) {
+    const double an = 0.5 * (a[N] + b);
+    const double cn = 0.5 * (a[N] - b);
+    b = std::sqrt(a[N] * b);
+    ++N;
+    a[N] = an;
+    c[N] = cn;
+    if (std::fabs(cn) <= 1e-17 * an) break;
+  }
+  double phi = std::ldexp(a[N] * u, N);
+  for (int n = N; n >= 1; --n) phi = 0.5 * (phi + std::asin(c[n] / a[n] * std::sin(phi)));
+  if (phi_out) *phi_out = phi;
+  if (K_out) *K_out = M_PI / (2.0 * a[N]);
+}
+
+double ellip_K(double m) {
+  double K;
+  agm_phi(0.0, m, nullptr, &K);
+  return K;
+}
+
+void ellip_sncn(double u, double m, double* sn, double* cn) {
+  double phi;
+  agm_phi(u, m, &phi, nullptr);
+  *sn = std::sin(phi);
+  *cn = std::cos(phi);
+}
+
+// ------------------------------------------------------------------ Zolotarev
+static double r0(double y, const std::vector<double>& c, int n) {
+  const double y2 = y * y;
+  double num = 1.0, den = 1.0;
+  for (int l = 1; l < n; ++l) num *= (y2 + c[2 * l - 1]);
+  for (int l = 1; l <= n; ++l) den *= (y2 + c[2 * l - 2]);
+  return y * num / den;
+}
+
+int zolotarev_coeffs(int n, double a, double b, double* omega, double* sigma, double* delta) {
+  if (n < 1 || !(a > 0) || !(b > a)) return -1;
+  const double m1 = 1.0 - (a / b) * (a / b);
+  const double Kp = ellip_K(m1);
+  std::vector<double> c(2 * n - 1);
+  for (int l = 1; l <= 2 * n - 1; ++l) {
+    double sn, cn;
+    ellip_sncn(l * Kp / (2.0 * n), m1, &sn, &cn);
+    c[l - 1] = (sn * sn) / (cn * cn);
+  }
+  // extrema of R0 over y in [1, b/a]: endpoints plus golden-section refinement of
+  // every interior extremum of a dense logarithmic grid
+  const double ly = std::log(b / a);
+  const int G = 8000 + 400 * n;
+  std::vector<double> v(G + 1);
+  for (int k = 0; k <= G; ++k) v[k] = r0(std::exp(ly * k / G), c, n);
+  double lo = std::min(v[0], v[G]), hi = std::max(v[0], v[G]);
+  const double gr = 0.5 * (std::sqrt(5.0) - 1.0);
+  for (int k = 1; k < G; ++k) {
+    const bool isMax = v[k] >= v[k - 1] && v[k] >= v[k + 1];
+    const bool isMin = v[k] <= v[k - 1] && v[k] <= v[k + 1];
+    if (!isMax && !isMin) continue;
+    const double sgn = isMax ? 1.0 : -1.0;
+    double l = ly * (k - 1) / G, r = ly * (k + 1) / G;
+    for (int it = 0; it < 200 && r - l > 1e-15 * (1.0 + std::fabs(r)); ++it) {
+      const double x1 = r - gr * (r - l), x2 = l + gr * (r - l);
+      if (sgn * r0(std::exp(x1), c, n) > sgn * r0(std::exp(x2), c, n)) r = x2;
+      else l = x1;
+    }
+    const double e = r0(std::exp(0.5 * (l + r)), c, n);
+    if (isMax) hi = std::max(hi, std::max(e, v[k]));
+    else lo = std::min(lo, std::min(e, v[k]));
+  }
+  const double d = 2.0 / (lo + hi);
+  *delta = (hi - lo) / (hi + lo);
+  for (int i = 0; i < n; ++i) {
+    const double ci = c[2 * i];
+    double num = 1.0, den = 1.0;
+    for (int l = 1; l < n; ++l) num *= (c[2 * l - 1] - ci);
+    for (int l = 0; l < n; ++l)
+      if (l != i) den *= (c[2 * l] - ci);
+    omega[i] = a * d * num / den;
+    sigma[i] = a * a * ci;
+  }
+  return 0;
+}
+
+double pole_gbound(double sigma, double a, double b) {
+  const double r = std::sqrt(sigma);
+  if (r >= a && r <= b) return 0.5 / r;
+  if (r < a) return a / (a * a + sigma);
+  return b / (b * b + sigma);
+}
+
+// ------------------------------------------------------------------ dense
+using cd = std::complex<double>;
+
+int cholesky_lower(int n, cd* A /* row-major, in: Hermitian PD, out: L */) {
+  for (int j = 0; j < n; ++j) {
+    double d = A[j * n + j].real();
+    for (int k = 0; k < j; ++k) d -= std::norm(A[j * n + k]);
+    if (!(d > 0.0)) return -1;
+    const double ljj = std::sqrt(d);
+    A[j * n + j] = ljj;
+    for (int i = j + 1; i < n; ++i) {
+      cd s = A[i * n + j];
+      for (int k = 0; k < j; ++k) s -= A[i * n + k] * std::conj(A[j * n + k]);
+      A[i * n + j] = s / ljj;
+    }
+    for (int k = j + 1; k < n; ++k) A[j * n + k] = 0.0;
+  }
+  return 0;
+}
+
+void lower_inverse(int n, const cd* L, cd* Li) {
+  for (int i = 0; i < n * n; ++i) Li[i] = 0.0;
+  for (int j = 0; j < n; ++j) {
+    Li[j * n + j] = 1.0 / L[j * n + j];
+    for (int i = j + 1; i < n; ++i) {
+      cd s = 0.0;
+      for (int k = j; k < i; ++k) s += L[i * n + k] * Li[k * n + j];
+      Li[i * n + j] = -s / L[i * n + i];
+    }
+  }
+}
+
+void eigh_jacobi(int n, cd* A /* Hermitian, destroyed */, double* w, cd* Z /* columns */) {
+  for (int i = 0; i < n * n; ++i) Z[i] = 0.0;
+  for (int i = 0; i < n; ++i) Z[i * n + i] = 1.0;
+  for (int sweep = 0; sweep < 100; ++sweep) {
+    double off = 0.0, diag = 0.0;
+    for (int p = 0; p < n; ++p) {
+      diag += std::norm(A[p * n + p]);
+      for (int q = p + 1; q < n; ++q) off += std::norm(A[p * n + q]);
+    }
+    if (off <= 1e-32 * (diag + 1e-300)) break;
+    for (int p = 0; p < n - 1; ++p) {
+      for (int q = p + 1; q < n; ++q) {
+        const cd apq = A[p * n + q];
+        const double c_abs = std::abs(apq);
+        if (c_abs < 1e-300) continue;
+        // phase: make A[p][q] real positive by scaling column/row q by conj(u)
+        const cd u = apq / c_abs;
+        for (int r = 0; r < n; ++r) {
+          A[r * n + q] *= std::conj(u);
+        }
+        for (int r = 0; r < n; ++r) {
+          A[q * n + r] *= u;
+        }
+        for (int r = 0; r < n; ++r) Z[r * n + q] *= std::conj(u);
+        const double app = A[p * n + p].real(), aqq = A[q * n + q].real();
+        const double theta = (aqq - app) / (2.0 * c_abs);
+        const double t = (theta >= 0 ? 1.0 : -1.0) / (std::fabs(theta) + std::sqrt(theta * theta + 1.0));
+        const double cs = 1.0 / std::sqrt(t * t + 1.0), sn = t * cs;
+        for (int r = 0; r < n; ++r) {
+          const cd arp = A[r * n + p], arq = A[r * n + q];
+          A[r * n + p] = cs * arp - sn * arq;
+          A[r * n + q] = sn * arp + cs * arq;
+        }
+        for (int r = 0; r < n; ++r) {
+          const cd apr = A[p * n + r], aqr = A[q * n + r];
+          A[p * n + r] = cs * apr - sn * aqr;
+          A[q * n + r] = sn * apr + cs * aqr;
+        }
+        A[p * n + q] = 0.0;
+        A[q * n + p] = 0.0;
+        A[p * n + p] = A[p * n + p].real();
+        A[q * n + q] = A[q * n + q].real();
+        for (int r = 0; r < n; ++r) {
+          const cd zrp = Z[r * n + p], zrq = Z[r * n + q];
+          Z[r * n + p] = cs * zrp - sn * zrq;
+          Z[r * n + q] = sn * zrp + cs * zrq;
+        }
+      }
+    }
+  }
+  // sort ascending
+  std::vector<int> idx(n);
+  for (int i = 0; i < n; ++i) idx[i] = i;
+  std::sort(idx.begin(), idx.end(), [&](int x, int y) { return A[x * n + x].real() < A[y * n + y].real(); });
+  std::vector<cd> Zs(n * n);
+  for (int j = 0; j < n; ++j) {
+    w[j] = A[idx[j] * n + idx[j]].real();
+    for (int r = 0; r < n; ++r) Zs[r * n + j] = Z[r * n + idx[j]];
+  }
+  for (int i = 0; i < n * n; ++i) Z[i] = Zs[i];
+}
+
+int lu_solve(int n, cd* A, cd* B, int nb) {
+  std::vector<int> piv(n);
+  for (int k = 0; k < n; ++k) {
+    int p = k;
+    double best = std::abs(A[k * n + k]);
+    for (int i = k + 1; i < n; ++i)
+      if (std::abs(A[i * n + k]) > best) {
+        best = std::abs(A[i * n + k]);
+        p = i;
+      }
+    if (best == 0.0) return -1;
+    if (p != k) {
+      for (int j = 0; j < n; ++j) std::swap(A[k * n + j], A[p * n + j]);
+      for (int j = 0; j < nb; ++j) std::swap(B[k * nb + j], B[p * nb + j]);
+    }
+    for (int i = k + 1; i < n; ++i) {
+      const cd f = A[i * n + k] / A[k * n + k];
+      A[i * n + k] = f;
+      for (int j = k + 1; j < n; ++j) A[i * n + j] -= f * A[k * n + j];
+      for (int j = 0; j < nb; ++j) B[i * nb + j] -= f * B[k * nb + j];
+    }
+  }
+  for (int k = n - 1; k >= 0; --k) {
+    for (int j = 0; j < nb; ++j) {
+      cd s = B[k * nb + j];
+      for (int i = k + 1; i < n; ++i) s -= A[k * n + i] * B[i * nb + j];
+      B[k * nb + j] = s / A[k * n + k];
+    }
+  }
+  return 0;
+}
+
+// number of eigenvalues of the symmetric tridiagonal (d, e) below x (Sturm count)
+static int sturm(int n, const double* d, const double* e, double x) {
+  int cnt = 0;
+  double q = 1.0;
+  for (int i = 0; i < n; ++i) {
+    const double e2 = i > 0 ? e[i - 1] * e[i - 1] : 0.0;
+    q = d[i] - x - (i > 0 ? e2 / q : 0.0);
+    if (q == 0.0) q = 1e-300;
+    if (q < 0) ++cnt;
+  }
+  return cnt;
+}
+
+void tridiag_extremes(int n, const double* d, const double* e, double* lmin, double* lmax) {
+  double lo = 1e300, hi = -1e300;
+  for (int i = 0; i < n; ++i) {
+    const double r = (i > 0 ? std::fabs(e[i - 1]) : 0.0) + (i < n - 1 ? std::fabs(e[i]) : 0.0);
+    lo = std::min(lo, d[i] - r);
+    hi = std::max(hi, d[i] + r);
+  }
+  double a = lo, b = hi;
+  for (int it = 0; it < 200; ++it) {
+    const double m = 0.5 * (a + b);
+    if (sturm(n, d, e, m) >= 1) b = m;
+    else a = m;
+  }
+  *lmin = 0.5 * (a + b);
+  a = lo;
+  b = hi;
+  for (int it = 0; it < 200; ++it) {
+    const double m = 0.5 * (a + b);
+    if (sturm(n, d, e, m) >= n) b = m;
+    else a = m;
+  }
+  *lmax = 0.5 * (a + b);
+}
+
+}  // namespace ovl

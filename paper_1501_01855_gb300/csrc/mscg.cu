@@ -1,0 +1,296 @@
+// Multi-shift conjugate gradient for the Zolotarev sign function (Sec. 3):
+// all shifted systems (K^2 + sigma_i) x_i = v, i = 1..N_Z, share the Krylov
+// space of the base system K^2 + sigma_0 (sigma_0 the smallest shift), and only
+// y = sum_i omega_i x_i is kept. Every scalar of the recurrence stays on the
+// device, so a whole step is five launches with no host round trip:
+//
+//   wilson MODE_K   t = K p_0, partials ||t||^2, ||p_0||^2
+//   ms_scalar1      alpha = rr / (||t||^2 + sigma0 ||p_0||^2); zeta_{k+1}, alpha_i
+//   wilson MODE_R   r -= alpha (K t + sigma0 p_0), partials ||r||^2
+//   ms_scalar2      beta, beta_i, pole dropping, done flag
+//   ms_update       y += sum_i omega_i alpha_i p_i ; p_i = zeta_i r + beta_i p_i
+//
+// Stopping rule (the reading of "eta = Delta or the error in the inversion of
+// x^2 + sigma_i, whichever is larger"): pole i contributes at most
+// omega_i g_i |zeta_i| ||r|| to the error of eps(K) v, with
+// g_i = max_{a<=x<=b} x/(x^2+sigma_i); pole i stops once that is below
+// eta ||v|| / N_Z, poles dropping from the largest shift down (they converge
+// first), and the solve ends when none is left.
+#include "kernels.h"
+
+namespace ovl {
+
+// ---------------------------------------------------------------- init
+template <int PV, int PR, int PP>
+__global__ void __launch_bounds__(256) ms_init_kernel(SpinorRef v, SpinorRef r, SpinorRef pb, SpinorRef y,
+                                                      int npoles, int nrhs, int V, int nsb, int ngr,
+                                                      double* partials) {
+  using T = typename Real<PR>::T;
+  __shared__ double red[4 * (BX / 32) * 2];
+  const int sb = blockIdx.x / ngr;
+  const int rg = blockIdx.x - sb * ngr;
+  const int rhs = rg * blockDim.y + threadIdx.y;
+  const int s = sb * BX + threadIdx.x;
+  double acc[2] = {0.0, 0.0};
+  if (s < V && rhs < nrhs) {
+    cpx<T> a[12], z[12];
+    load_spinor_as<PV, T>(v, rhs, s, a);
+#pragma unroll
+    for (int k = 0; k < 12; ++k) {
+      acc[0] += (double)norm2(a[k]);
+      z[k] = cmk(T(0), T(0));
+    }
+    store_spinor_as<PR, T>(r, rhs, s, a);
+    store_spinor_as<PR, T>(y, rhs, s, z);
+    for (int i = 0; i < npoles; ++i) store_spinor_as<PP, T>(pb, i * nrhs + rhs, s, a);
+  }
+  block_reduce_rows<2>(acc, red);
+  if (threadIdx.x == 0 && rhs < nrhs) {
+    partials[((size_t)rhs * nsb + sb) * NVRED + 0] = acc[0];
+    partials[((size_t)rhs * nsb + sb) * NVRED + 1] = 0.0;
+  }
+}
+
+void launch_ms_init(int pv, int pr, int pp, SpinorRef v, SpinorRef r, SpinorRef pb, SpinorRef y, int npoles,
+                    int nrhs, int V, double* partials, cudaStream_t st) {
+  Shape sh = make_shape(V, nrhs);
+#define MS_INIT(A, B, C) ms_init_kernel<A, B, C><<<sh.grid(), sh.block(), 0, st>>>(v, r, pb, y, npoles, nrhs, V, sh.nsb, sh.ngr, partials)
+  if (pv == P64 && pr == P64 && pp == P64) MS_INIT(P64, P64, P64);
+  else if (pv == P32 && pr == P32 && pp == P32) MS_INIT(P32, P32, P32);
+  else if (pv == P64 && pr == P32 && pp == P32) MS_INIT(P64, P32, P32);
+  else if (pv == P32 && pr == P32 && pp == P16) MS_INIT(P32, P32, P16);
+  else if (pv == P64 && pr == P32 && pp == P16) MS_INIT(P64, P32, P16);
+  else if (pv == P32 && pr == P64 && pp == P64) MS_INIT(P32, P64, P64);
+  else note_bad_combo("ms_init");
+#undef MS_INIT
+}
+
+// ---------------------------------------------------------------- scalars
+// Fixed-order sum of the NVRED-wide partials of one rhs by one block.
+__device__ __forceinline__ void sum_partials(const double* partials, int nsb, int rhs, double out[2]) {
+  __shared__ double sh[2][128];
+  double a0 = 0.0, a1 = 0.0;
+  for (int b = threadIdx.x; b < nsb; b += blockDim.x) {
+    a0 += partials[((size_t)rhs * nsb + b) * NVRED + 0];
+    a1 += partials[((size_t)rhs * nsb + b) * NVRED + 1];
+  }
+  sh[0][threadIdx.x] = a0;
+  sh[1][threadIdx.x] = a1;
+  __syncthreads();
+  for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+    if (threadIdx.x < o) {
+      sh[0][threadIdx.x] += sh[0][threadIdx.x + o];
+      sh[1][threadIdx.x] += sh[1][threadIdx.x + o];
+    }
+    __syncthreads();
+  }
+  out[0] = sh[0][0];
+  out[1] = sh[1][0];
+  __syncthreads();
+}
+
+__global__ void ms_scalar0_kernel(MsRhs* ms, const double* partials, int nsb, const Poles* P, const double* eta,
+                                  int maxit) {
+  const int rhs = blockIdx.x;
+  double s[2];
+  sum_partials(partials, nsb, rhs, s);
+  MsRhs& m = ms[rhs];
+  for (int i = threadIdx.x; i < NPMAX; i += blockDim.x) {
+    m.zeta[i] = 1.0;
+    m.zeta_prev[i] = 1.0;
+    m.zeta_next[i] = 1.0;
+    m.coef_y[i] = 0.0;
+    m.coef_r[i] = 0.0;
+    m.coef_p[i] = 0.0;
+    m.coef_a[i] = 0.0;
+  }
+  if (threadIdx.x == 0) {
+    m.rr = s[0];
+    m.vnorm2 = s[0];
+    m.alpha = 0.0;
+    m.alpha_prev = 1.0;
+    m.beta_prev = 0.0;
+    m.thr = eta[rhs] * sqrt(s[0]) / (double)P->n;
+    m.active = P->n;
+    m.nact_y = 0;
+    m.iter = 0;
+    m.maxit = maxit;
+    m.status = 0;
+    m.p_reads = 0;
+    m.p_writes = 0;
+    m.done = (s[0] == 0.0) ? 1 : 0;
+  }
+}
+
+__global__ void ms_scalar1_kernel(MsRhs* ms, const double* partials, int nsb, const Poles* P) {
+  const int rhs = blockIdx.x;
+  MsRhs& m = ms[rhs];
+  if (m.done) return;
+  double s[2];
+  sum_partials(partials, nsb, rhs, s);
+  const double pAp = s[0] + P->sigma0 * s[1];
+  const double alpha = m.rr / pAp;
+  const bool bad = !(pAp > 0.0) || !isfinite(alpha);
+  for (int i = threadIdx.x; i < m.active; i += blockDim.x) {
+    const double z = m.zeta[i], zp = m.zeta_prev[i];
+    double zn = 0.0, as = 0.0;
+    if (z != 0.0) {
+      const double den = alpha * m.beta_prev * (zp - z) + zp * m.alpha_prev * (1.0 + P->ds[i] * alpha);
+      zn = z * zp * m.alpha_prev / den;
+      as = alpha * zn / z;
+    }
+    m.zeta_next[i] = zn;
+    m.coef_y[i] = P->omega[i] * as;
+    m.coef_a[i] = as;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    m.alpha = alpha;
+    if (bad) {
+      m.done = 1;
+      m.status = 2;   // breakdown
+      m.nact_y = 0;
+    }
+  }
+}
+
+__global__ void ms_scalar2_kernel(MsRhs* ms, const double* partials, int nsb, const Poles* P) {
+  const int rhs = blockIdx.x;
+  MsRhs& m = ms[rhs];
+  if (m.done) {
+    if (threadIdx.x == 0) m.nact_y = 0;
+    return;
+  }
+  double s[2];
+  sum_partials(partials, nsb, rhs, s);
+  const double rr_new = s[0];
+  const double beta = rr_new / m.rr;
+  const int act = m.active;
+  for (int i = threadIdx.x; i < act; i += blockDim.x) {
+    const double z = m.zeta[i], zn = m.zeta_next[i];
+    const double q = (z != 0.0) ? zn / z : 0.0;
+    m.coef_r[i] = zn;
+    m.coef_p[i] = beta * q * q;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    m.nact_y = act;
+    const double rn = sqrt(rr_new);
+    int a = act;
+    while (a > 0 && P->omega[a - 1] * P->gbound[a - 1] * fabs(m.zeta_next[a - 1]) * rn <= m.thr) --a;
+    m.active = a;
+    m.p_reads += act;
+    m.p_writes += a;
+    m.alpha_prev = m.alpha;
+    m.beta_prev = beta;
+    m.rr = rr_new;
+    m.iter += 1;
+    if (!isfinite(rr_new)) {
+      m.done = 1;
+      m.status = 2;
+    } else if (a == 0) {
+      m.done = 1;
+      m.status = 0;
+    } else if (m.iter >= m.maxit) {
+      m.done = 1;
+      m.status = 1;   // not converged
+    }
+  }
+  __syncthreads();
+  for (int i = threadIdx.x; i < act; i += blockDim.x) {
+    m.zeta_prev[i] = m.zeta[i];
+    m.zeta[i] = m.zeta_next[i];
+  }
+}
+
+void launch_ms_scalar0(MsRhs* ms, const double* partials, int nsb, int nrhs, const Poles* poles, const double* eta,
+                       int maxit, cudaStream_t st) {
+  ms_scalar0_kernel<<<nrhs, 128, 0, st>>>(ms, partials, nsb, poles, eta, maxit);
+}
+void launch_ms_scalar1(MsRhs* ms, const double* partials, int nsb, int nrhs, const Poles* poles, cudaStream_t st) {
+  ms_scalar1_kernel<<<nrhs, 128, 0, st>>>(ms, partials, nsb, poles);
+}
+void launch_ms_scalar2(MsRhs* ms, const double* partials, int nsb, int nrhs, const Poles* poles, cudaStream_t st) {
+  ms_scalar2_kernel<<<nrhs, 128, 0, st>>>(ms, partials, nsb, poles);
+}
+
+// ---------------------------------------------------------------- fused update
+// One pass over every active pole vector: y += omega_i alpha_i p_i (old p_i), then
+// p_i = zeta_{k+1,i} r + beta_i p_i. Pole 0 is the base system (zeta = 1).
+template <int PR, int PP>
+__global__ void __launch_bounds__(256) ms_update_kernel(SpinorRef r, SpinorRef pb, SpinorRef y, int npoles,
+                                                        int nrhs, int V, int ngr, const MsRhs* ms) {
+  using T = typename Real<PR>::T;
+  const int sb = blockIdx.x / ngr;
+  const int rg = blockIdx.x - sb * ngr;
+  const int rhs = rg * blockDim.y + threadIdx.y;
+  const int s = sb * BX + threadIdx.x;
+  if (s >= V || rhs >= nrhs) return;
+  const MsRhs& m = ms[rhs];
+  const int ny = m.nact_y;
+  if (ny == 0) return;
+  const int na = m.active;
+  cpx<T> rv[12], yv[12], pv[12];
+  load_spinor_as<PR, T>(r, rhs, s, rv);
+  load_spinor_as<PR, T>(y, rhs, s, yv);
+  for (int i = 0; i < ny; ++i) {
+    load_spinor_as<PP, T>(pb, i * nrhs + rhs, s, pv);
+    const T cy = (T)m.coef_y[i];
+#pragma unroll
+    for (int k = 0; k < 12; ++k) yv[k] = yv[k] + cy * pv[k];
+    if (i < na) {
+      const T cr = (T)m.coef_r[i], cp = (T)m.coef_p[i];
+#pragma unroll
+      for (int k = 0; k < 12; ++k) pv[k] = cr * rv[k] + cp * pv[k];
+      store_spinor_as<PP, T>(pb, i * nrhs + rhs, s, pv);
+    }
+  }
+  store_spinor_as<PR, T>(y, rhs, s, yv);
+}
+
+void launch_ms_update(int pr, int pp, SpinorRef r, SpinorRef pb, SpinorRef y, int npoles, int nrhs, int V,
+                      const MsRhs* ms, cudaStream_t st) {
+  Shape sh = make_shape(V, nrhs);
+  if (pr == P64 && pp == P64) ms_update_kernel<P64, P64><<<sh.grid(), sh.block(), 0, st>>>(r, pb, y, npoles, nrhs, V, sh.ngr, ms);
+  else if (pr == P32 && pp == P32) ms_update_kernel<P32, P32><<<sh.grid(), sh.block(), 0, st>>>(r, pb, y, npoles, nrhs, V, sh.ngr, ms);
+  else if (pr == P32 && pp == P16) ms_update_kernel<P32, P16><<<sh.grid(), sh.block(), 0, st>>>(r, pb, y, npoles, nrhs, V, sh.ngr, ms);
+  else note_bad_combo("ms_update");
+}
+
+}  // namespace ovl
+
+namespace ovl {
+__global__ void __launch_bounds__(256) ms_update_x_kernel(SpinorRef r, SpinorRef pb, SpinorRef xs, int npoles,
+                                                          int nrhs, int V, int ngr, const MsRhs* ms) {
+  const int sb = blockIdx.x / ngr;
+  const int rg = blockIdx.x - sb * ngr;
+  const int rhs = rg * blockDim.y + threadIdx.y;
+  const int s = sb * BX + threadIdx.x;
+  if (s >= V || rhs >= nrhs) return;
+  const MsRhs& m = ms[rhs];
+  const int ny = m.nact_y;
+  if (ny == 0) return;
+  const int na = m.active;
+  cpx<double> rv[12], xv[12], pv[12];
+  load_spinor<P64, double>(r, rhs, s, rv);
+  for (int i = 0; i < ny; ++i) {
+    load_spinor<P64, double>(pb, i * nrhs + rhs, s, pv);
+    load_spinor<P64, double>(xs, i * nrhs + rhs, s, xv);
+    const double ca = m.coef_a[i];
+#pragma unroll
+    for (int k = 0; k < 12; ++k) xv[k] = xv[k] + ca * pv[k];
+    store_spinor<P64, double>(xs, i * nrhs + rhs, s, xv);
+    if (i < na) {
+      const double cr = m.coef_r[i], cp = m.coef_p[i];
+#pragma unroll
+      for (int k = 0; k < 12; ++k) pv[k] = cr * rv[k] + cp * pv[k];
+      store_spinor<P64, double>(pb, i * nrhs + rhs, s, pv);
+    }
+  }
+}
+void launch_ms_update_x(SpinorRef r, SpinorRef pb, SpinorRef xs, int npoles, int nrhs, int V, const MsRhs* ms,
+                        cudaStream_t st) {
+  Shape sh = make_shape(V, nrhs);
+  ms_update_x_kernel<<<sh.grid(), sh.block(), 0, st>>>(r, pb, xs, npoles, nrhs, V, sh.ngr, ms);
+}
+}  // namespace ovl

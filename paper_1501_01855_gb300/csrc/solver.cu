@@ -1,0 +1,665 @@
+// Solvers of liboverlap (host control, device vectors), all on lock-step batches
+// of independent systems D(mu_j) x_j = b_j:
+//
+//  * relSUMR (Secs. 2-3) on A = rho + V, V = gamma5 eps(K), rho = (1+mu)/(1-mu), so
+//    D = (1-mu)/2 A. The Krylov basis is Alg. 1 (q, q~, gamma_j, sigma_j). The printed
+//    Alg. 2 leaves zeta undefined and, under every reading tried, does not reproduce
+//    the minimal-residual iterates, so the update is re-derived from App. A: a
+//    progressive Givens QR of rho I^ + B^ whose rows above the subdiagonal are
+//    gamma_j times the coefficients of q~_j, which gives short recurrences with two
+//    auxiliary vectors (p, S). In exact arithmetic the iterates equal GMRES's.
+//    Relaxation eta_j = eps_A ||b|| / ||r_j||, never worse than the floor (Sec. 3).
+//  * relCG (Sec. 3) as the spectrally preconditioned CGNE of Alg. 4 on H^2, H =
+//    gamma5 D, with eta_j = eps_A ||b|| sqrt(zeta), zeta = sum_i ||r_i||^-2.
+//  * GMRESR (Alg. 3) in FP64 around either, with c = A u at accuracy
+//    eps ||b|| / ||r|| relative to ||u||.
+//  * eigSUMR (Algs. 5-6) and the deflated starts of Sec. 4.
+#include <stdio.h>
+#include <string.h>
+
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+
+#include "context.h"
+#include "hostmath.h"
+#include "solver.h"
+
+namespace ovl {
+
+static inline cd c2(const double* p) { return cd(p[0], p[1]); }
+
+// ------------------------------------------------------------------ helpers
+ovl_status dots_batch(ovl_ctx* c, const Field& x, int xoff, const Field& y, int yoff, int n, std::vector<cd>& out) {
+  OVL_TRY(ensure_partials(c, n));
+  launch_dot(x.prec, x.ref(xoff), y.prec, y.ref(yoff), n, c->V, c->partials, c->st);
+  std::vector<double> h(2 * n);
+  OVL_TRY(reduce_to_host(c, make_shape(c->V, n).nsb, n, h.data()));
+  out.resize(n);
+  for (int j = 0; j < n; ++j) out[j] = cd(h[2 * j], h[2 * j + 1]);
+  return OVL_OK;
+}
+
+ovl_status norms_batch(ovl_ctx* c, const Field& x, int xoff, int n, std::vector<double>& out) {
+  OVL_TRY(ensure_partials(c, n));
+  launch_norm2(x.prec, x.ref(xoff), n, c->V, c->partials, c->st);
+  std::vector<double> h(2 * n);
+  OVL_TRY(reduce_to_host(c, make_shape(c->V, n).nsb, n, h.data()));
+  out.resize(n);
+  for (int j = 0; j < n; ++j) out[j] = std::sqrt(std::max(0.0, h[2 * j]));
+  return OVL_OK;
+}
+
+// z = a x + b y with per-system complex a, b (z may alias x or y; all same precision)
+ovl_status axpby_batch(ovl_ctx* c, const std::vector<cd>& a, const Field& x, int xoff, const std::vector<cd>& b,
+                       const Field& y, int yoff, Field& z, int zoff, int n) {
+  std::vector<double> h(4 * n);
+  for (int j = 0; j < n; ++j) {
+    h[2 * j] = a[j].real();
+    h[2 * j + 1] = a[j].imag();
+    h[2 * n + 2 * j] = b[j].real();
+    h[2 * n + 2 * j + 1] = b[j].imag();
+  }
+  const double* d;
+  OVL_TRY(upload(c, h.data(), 4 * n, &d));
+  launch_axpby(z.prec, d, d + 2 * n, x.ref(xoff), y.ref(yoff), z.ref(zoff), n, c->V, c->st);
+  OVL_TRY(check_launch(c, __func__));
+  return OVL_OK;
+}
+
+ovl_status copy_convert(ovl_ctx* c, const Field& in, int ioff, Field& out, int ooff, int n) {
+  if (in.prec == out.prec) {
+    const size_t per = (size_t)c->V * (in.prec == P64 ? 192 : in.prec == P32 ? 96 : 48);
+    OVL_CUDA(c, cudaMemcpyAsync((char*)out.data + per * ooff, (char*)in.data + per * ioff, per * n,
+                                cudaMemcpyDeviceToDevice, c->st));
+    if (in.prec == P16)
+      OVL_CUDA(c, cudaMemcpyAsync(out.norm + (size_t)c->V * ooff, in.norm + (size_t)c->V * ioff,
+                                  sizeof(float) * c->V * n, cudaMemcpyDeviceToDevice, c->st));
+    return OVL_OK;
+  }
+  launch_convert(in.prec, in.ref(ioff), out.prec, out.ref(ooff), n, c->V, c->st);
+  OVL_TRY(check_launch(c, __func__));
+  return OVL_OK;
+}
+
+// Gram block G = (A_i, [g5] B_j), na x nb, to the host (complex row-major).
+ovl_status gram_host(ovl_ctx* c, const Field& A, int aoff, int na, const Field& B, int boff, int nb, int g5,
+                     std::vector<cd>& G) {
+  Field* dummy;
+  (void)dummy;
+  const size_t gsz = (size_t)na * nb * 2;
+  OVL_TRY(ensure_work(c, gsz * 1300 + gsz));
+  double* dG = c->dwork + c->dwork_n - gsz;
+  OVL_CUDA(c, cudaMemsetAsync(dG, 0, gsz * sizeof(double), c->st));
+  ProfPair pp;
+  prof_begin(c, 6, &pp);
+  launch_gram(A.prec, A.ref(aoff), na, B.prec, B.ref(boff), nb, c->V, dG, c->dwork, c->dwork_n - gsz, g5, c->st);
+  prof_end(c, &pp, (double)c->V * ((double)na * (A.prec == P64 ? 192 : 96) + (double)nb * (B.prec == P64 ? 192 : 96)));
+  OVL_TRY(check_launch(c, __func__));
+  std::vector<double> h(gsz);
+  OVL_CUDA(c, cudaMemcpyAsync(h.data(), dG, gsz * sizeof(double), cudaMemcpyDeviceToHost, c->st));
+  OVL_CUDA(c, cudaStreamSynchronize(c->st));
+  G.resize((size_t)na * nb);
+  for (size_t k = 0; k < G.size(); ++k) G[k] = cd(h[2 * k], h[2 * k + 1]);
+  return OVL_OK;
+}
+
+// Y_j (+)= sum_i A_i C[i][j]
+ovl_status combine_host(ovl_ctx* c, const Field& A, int aoff, int na, const std::vector<cd>& C, Field& Y, int yoff,
+                        int ny, int add) {
+  std::vector<double> h((size_t)na * ny * 2);
+  for (size_t k = 0; k < (size_t)na * ny; ++k) {
+    h[2 * k] = C[k].real();
+    h[2 * k + 1] = C[k].imag();
+  }
+  const double* d;
+  OVL_TRY(upload(c, h.data(), (int)h.size(), &d));
+  ProfPair pp;
+  prof_begin(c, 6, &pp);
+  launch_combine(A.prec, A.ref(aoff), na, d, Y.prec, Y.ref(yoff), ny, c->V, add, c->st);
+  prof_end(c, &pp, (double)c->V * ((double)na * (A.prec == P64 ? 192 : 96) + (double)ny * (add + 1) * (Y.prec == P64 ? 192 : 96)));
+  OVL_TRY(check_launch(c, __func__));
+  return OVL_OK;
+}
+
+// ------------------------------------------------------------------ overlap apply
+// out_j = D(mu_j) v_j (herm: gamma5 D(mu_j) v_j) at sign accuracy eta_j.
+ovl_status overlap_apply_batch(ovl_ctx* c, const Field& v, int voff, Field& out, int ooff, int n,
+                               const std::vector<double>& mus, const std::vector<double>& eta, int herm, int mode,
+                               long long* wcalls_out) {
+  std::vector<double> coef(2 * n);
+  for (int j = 0; j < n; ++j) {
+    coef[2 * j] = 0.5 * (1.0 + mus[j]);
+    coef[2 * j + 1] = 0.5 * (1.0 - mus[j]);
+  }
+  double emin = 1e300;
+  for (double e : eta) emin = std::min(emin, e > 0 ? e : c->eps_sign);
+  if (mode < 0) mode = choose_mode(c, emin);
+  SignStats ss;
+  OVL_TRY(sign_op(c, mode, v, voff, out, ooff, n, eta.data(), 0, 0, coef.data(), herm, nullptr, 0, nullptr, &ss));
+  if (wcalls_out) {
+    for (int j = 0; j < n; ++j) wcalls_out[j] += (long long)(2 * ss.iters[j] + 1) * (mode == SIGN64 ? 2 : 1);
+  }
+  return OVL_OK;
+}
+
+// ------------------------------------------------------------------ deflation data
+// With psi_i (v) and w_i = gamma5 eps(K) psi_i held, D(mu) psi = (1+mu)/2 psi + (1-mu)/2 w.
+ovl_status defl_prepare(ovl_ctx* c, ovl_defl* d) {
+  if (d->prepared) return OVL_OK;
+  const int n = d->n;
+  OVL_TRY(gram_host(c, d->v, 0, n, d->v, 0, n, 0, d->VV));
+  OVL_TRY(gram_host(c, d->w, 0, n, d->w, 0, n, 0, d->WW));
+  OVL_TRY(gram_host(c, d->w, 0, n, d->v, 0, n, 0, d->WV));
+  OVL_TRY(gram_host(c, d->v, 0, n, d->v, 0, n, 1, d->G5VV));
+  OVL_TRY(gram_host(c, d->v, 0, n, d->w, 0, n, 1, d->G5VW));
+  d->prepared = true;
+  return OVL_OK;
+}
+
+// (D psi)^dag (D psi) at mass mu, n x n
+static void dd_matrix(const ovl_defl* d, double mu, std::vector<cd>& M) {
+  const int n = d->n;
+  const double a = 0.5 * (1.0 - mu), b = 0.5 * (1.0 + mu);
+  M.assign((size_t)n * n, 0.0);
+  for (int i = 0; i < n; ++i)
+    for (int j = 0; j < n; ++j) {
+      const cd wv = d->WV[(size_t)i * n + j];
+      const cd vw = std::conj(d->WV[(size_t)j * n + i]);
+      M[(size_t)i * n + j] = a * a * d->WW[(size_t)i * n + j] + a * b * (wv + vw) + b * b * d->VV[(size_t)i * n + j];
+    }
+}
+
+// Sec. 4, SUMR variant: x0 = sum_j alpha_j psi'_j minimising ||b - D x0|| with psi'
+// the rotation that diagonalises (psi_i, gamma5 D psi_j). Returns, per system, the
+// coefficients on psi (after folding in the rotation) in X0 (n_ev x nsys, column j),
+// and fills r0 = b - D x0 on the device when rv is given.
+ovl_status defl_start(ovl_ctx* c, ovl_defl* d, const Field& b, int boff, int nsys, const std::vector<double>& mus,
+                      std::vector<cd>& coefs) {
+  OVL_TRY(defl_prepare(c, d));
+  const int n = d->n;
+  std::vector<cd> VB, WB;
+  OVL_TRY(gram_host(c, d->v, 0, n, b, boff, nsys, 0, VB));
+  OVL_TRY(gram_host(c, d->w, 0, n, b, boff, nsys, 0, WB));
+  coefs.assign((size_t)n * nsys, 0.0);
+  for (int j = 0; j < nsys; ++j) {
+    const double mu = mus[j];
+    const double a = 0.5 * (1.0 - mu), bb = 0.5 * (1.0 + mu);
+    // Hs = (psi_i, gamma5 D psi_j) = b (psi, g5 psi) + a (psi, g5 w)
+    std::vector<cd> Hs((size_t)n * n), Y((size_t)n * n);
+    std::vector<double> w(n);
+    for (size_t k = 0; k < Hs.size(); ++k) Hs[k] = bb * d->G5VV[k] + a * d->G5VW[k];
+    for (int i = 0; i < n; ++i)
+      for (int k = i + 1; k < n; ++k) {
+        const cd h = 0.5 * (Hs[(size_t)i * n + k] + std::conj(Hs[(size_t)k * n + i]));
+        Hs[(size_t)i * n + k] = h;
+        Hs[(size_t)k * n + i] = std::conj(h);
+      }
+    eigh_jacobi(n, Hs.data(), w.data(), Y.data());
+    std::vector<cd> M;
+    dd_matrix(d, mu, M);
+    // rotated normal equations: (Y^dag M Y) alpha = Y^dag (D psi)^dag b
+    std::vector<cd> MY((size_t)n * n), G((size_t)n * n), rhs(n);
+    for (int i = 0; i < n; ++i)
+      for (int k = 0; k < n; ++k) {
+        cd s = 0;
+        for (int l = 0; l < n; ++l) s += M[(size_t)i * n + l] * Y[(size_t)l * n + k];
+        MY[(size_t)i * n + k] = s;
+      }
+    for (int i = 0; i < n; ++i)
+      for (int k = 0; k < n; ++k) {
+        cd s = 0;
+        for (int l = 0; l < n; ++l) s += std::conj(Y[(size_t)l * n + i]) * MY[(size_t)l * n + k];
+        G[(size_t)i * n + k] = s;
+      }
+    for (int i = 0; i < n; ++i) {
+      cd s = 0;
+      for (int l = 0; l < n; ++l) {
+        const cd dpb = a * WB[(size_t)l * nsys + j] + bb * VB[(size_t)l * nsys + j];   // ((D psi_l), b)
+        s += std::conj(Y[(size_t)l * n + i]) * dpb;
+      }
+      rhs[i] = s;
+    }
+    if (d->per_vector) {
+      for (int i = 0; i < n; ++i) rhs[i] /= G[(size_t)i * n + i];
+    } else if (lu_solve(n, G.data(), rhs.data(), 1) != 0) {
+      return set_err(c, OVL_EBREAKDOWN, "singular deflation normal equations");
+    }
+    for (int i = 0; i < n; ++i) {
+      cd s = 0;
+      for (int k = 0; k < n; ++k) s += Y[(size_t)i * n + k] * rhs[k];
+      coefs[(size_t)i * nsys + j] = s;
+    }
+  }
+  return OVL_OK;
+}
+
+// ------------------------------------------------------------------ relSUMR
+ovl_status sumr_batch(ovl_ctx* c, const SumrCfg& cfg, int n, const std::vector<double>& mus, const Field& b, int boff,
+                      Field& x, int xoff, SumrResult& res) {
+  const int PS = cfg.prec;
+  const int V = c->V;
+  Field *fq, *fqt, *fp, *fS, *fu;
+  OVL_TRY(get_field(c, "s_q", PS, n, &fq));
+  OVL_TRY(get_field(c, "s_qt", PS, n, &fqt));
+  OVL_TRY(get_field(c, "s_p", PS, n, &fp));
+  OVL_TRY(get_field(c, "s_S", PS, n, &fS));
+  OVL_TRY(get_field(c, "s_u", PS, n, &fu));
+  std::vector<double> rho(n);
+  for (int j = 0; j < n; ++j) rho[j] = (1.0 + mus[j]) / (1.0 - mus[j]);
+  // r0 = b - A x0 with A x0 = 2/(1-mu) D x0; a deflated x0 comes with its D x0 combination
+  OVL_TRY(copy_convert(c, b, boff, *fq, 0, n));
+  if (cfg.defl && cfg.defl->n > 0) {
+    std::vector<cd> co;
+    OVL_TRY(defl_start(c, cfg.defl, *fq, 0, n, mus, co));
+    const int ne = cfg.defl->n;
+    // x = psi co
+    OVL_TRY(combine_host(c, cfg.defl->v, 0, ne, co, x, xoff, n, 0));
+    // q -= A x0 = 2/(1-mu) ((1+mu)/2 psi co + (1-mu)/2 w co)
+    std::vector<cd> cv((size_t)ne * n), cw((size_t)ne * n);
+    for (int i = 0; i < ne; ++i)
+      for (int j = 0; j < n; ++j) {
+        const double f = 2.0 / (1.0 - mus[j]);
+        cv[(size_t)i * n + j] = -f * 0.5 * (1.0 + mus[j]) * co[(size_t)i * n + j];
+        cw[(size_t)i * n + j] = -f * 0.5 * (1.0 - mus[j]) * co[(size_t)i * n + j];
+      }
+    OVL_TRY(combine_host(c, cfg.defl->v, 0, ne, cv, *fq, 0, n, 1));
+    OVL_TRY(combine_host(c, cfg.defl->w, 0, ne, cw, *fq, 0, n, 1));
+  } else {
+    launch_zero(x.prec, x.ref(xoff), n, V, c->st);
+  }
+  std::vector<double> bnorm, delta;
+  OVL_TRY(norms_batch(c, b, boff, n, bnorm));
+  OVL_TRY(norms_batch(c, *fq, 0, n, delta));
+  // normalise q, q~ = q, p = S = 0
+  {
+    std::vector<cd> a(n), z(n, 0.0);
+    for (int j = 0; j < n; ++j) a[j] = delta[j] > 0 ? 1.0 / delta[j] : 0.0;
+    OVL_TRY(axpby_batch(c, a, *fq, 0, z, *fq, 0, *fq, 0, n));
+    OVL_TRY(copy_convert(c, *fq, 0, *fqt, 0, n));
+    launch_zero(PS, fp->ref(), n, V, c->st);
+    launch_zero(PS, fS->ref(), n, V, c->st);
+  }
+  // per-system recurrence state
+  struct St {
+    cd gprev = 0, sprev = 0;
+    double cprev = 1, sigprev = 0;
+    cd zeta = 1.0;
+    cd ghat;
+    bool active = true;
+    int it = 0;
+  };
+  std::vector<St> S(n);
+  res.iters.assign(n, 0);
+  res.resid.assign(n, 0.0);
+  res.wcalls.assign(n, 0);
+  res.sign_calls.assign(n, 0);
+  res.stopped.assign(n, 0);
+  for (int j = 0; j < n; ++j) {
+    S[j].ghat = delta[j];
+    S[j].active = delta[j] > cfg.target * bnorm[j] && delta[j] > 0;
+    res.resid[j] = delta[j];
+  }
+  std::vector<double> sc(18 * n);
+  std::vector<double> act_d(n);
+  std::vector<double> eta(n), dots(2 * n);
+  int* d_act = c->dint;
+  for (int iter = 0; iter < cfg.maxit; ++iter) {
+    int nact = 0;
+    double emin = 1e300;
+    for (int j = 0; j < n; ++j) {
+      if (!S[j].active) {
+        eta[j] = 1.0;
+        continue;
+      }
+      ++nact;
+      const double r = std::abs(S[j].ghat);
+      double e = cfg.relax * cfg.target * bnorm[j] / std::max(r, 1e-300);
+      e = std::min(e, cfg.floor);
+      if (cfg.eta_cap > 0) e = std::min(e, cfg.eta_cap);
+      eta[j] = e;
+      emin = std::min(emin, e);
+    }
+    if (nact == 0) break;
+    const int mode = cfg.mode >= 0 ? cfg.mode : choose_mode(c, emin);
+    // u = V q = gamma5 eps(K) q, fused with (q~, u)
+    SignStats ss;
+    OVL_TRY(sign_op(c, mode, *fq, 0, *fu, 0, n, eta.data(), 0.0, 1.0, nullptr, 0, fqt, 0, dots.data(), &ss));
+    for (int j = 0; j < n; ++j)
+      if (S[j].active) {
+        res.wcalls[j] += (long long)(2 * ss.iters[j] + 1) * (mode == SIGN64 ? 2 : 1);
+        res.sign_calls[j] += 1;
+      }
+    if (cfg.hook) OVL_TRY(cfg.hook(c, cfg.hook_data, *fq, *fu, iter));
+    std::vector<int> hact(n);
+    for (int j = 0; j < n; ++j) {
+      double* o = &sc[18 * j];
+      for (int k = 0; k < 18; ++k) o[k] = 0.0;
+      hact[j] = S[j].active ? 1 : 0;
+      if (!S[j].active) continue;
+      St& s = S[j];
+      const cd gam = -cd(dots[2 * j], dots[2 * j + 1]);
+      const double g2 = std::norm(gam);
+      if (!(g2 < 1.0) || !std::isfinite(g2)) {
+        // Alg. 1 breaks down (inexact sign): stop this system, the outer loop continues
+        s.active = false;
+        hact[j] = 0;
+        res.stopped[j] = 2;
+        continue;
+      }
+      const double sig = std::sqrt(1.0 - g2);
+      cd a, Rm1, zm1;
+      if (s.it == 0) {
+        s.zeta = 1.0;
+        a = rho[j] - gam * s.zeta;
+        Rm1 = 0.0;
+        zm1 = 0.0;
+      } else {
+        zm1 = s.cprev * s.sigprev * s.zeta + std::conj(s.sprev) * std::conj(s.gprev);
+        s.zeta = -s.sprev * s.sigprev * s.zeta + s.cprev * std::conj(s.gprev);
+        Rm1 = rho[j] * std::conj(s.sprev) - gam * zm1;
+        a = rho[j] * s.cprev - gam * s.zeta;
+      }
+      const double nrm = std::sqrt(std::norm(a) + sig * sig);
+      const double cc = std::abs(a) / nrm;
+      const cd ss_ = std::abs(a) > 0 ? cc * sig / a : cd(1.0, 0.0);
+      const cd Rjj = cc * a + std::conj(ss_) * sig;
+      const cd g = cc * s.ghat;
+      s.ghat = -ss_ * s.ghat;
+      const cd vals[9] = {Rm1, gam * s.sigprev, 1.0 / Rjj, s.sigprev, zm1, g, gam, 1.0 / sig, sig};
+      for (int k = 0; k < 9; ++k) {
+        o[2 * k] = vals[k].real();
+        o[2 * k + 1] = vals[k].imag();
+      }
+      s.cprev = cc;
+      s.sprev = ss_;
+      s.sigprev = sig;
+      s.gprev = gam;
+      s.it += 1;
+      res.iters[j] = s.it;
+    }
+    const double* dsc;
+    OVL_TRY(upload(c, sc.data(), 18 * n, &dsc));
+    OVL_CUDA(c, cudaMemcpyAsync(d_act, hact.data(), sizeof(int) * n, cudaMemcpyHostToDevice, c->st));
+    OVL_TRY(ensure_partials(c, n));
+    ProfPair pp;
+    prof_begin(c, 4, &pp);
+    launch_sumr_update(PS, dsc, d_act, x.ref(xoff), fq->ref(), fqt->ref(), fp->ref(), fS->ref(), fu->ref(), n, V,
+                       c->partials, c->st);
+    prof_end(c, &pp, (double)nact * V * (PS == P64 ? 192.0 : 96.0) * 11.0);
+    OVL_TRY(check_launch(c, __func__));
+    std::vector<double> qn(2 * n);
+    OVL_TRY(reduce_to_host(c, make_shape(V, n).nsb, n, qn.data()));   // also orders the hact upload
+    for (int j = 0; j < n; ++j) {
+      if (!hact[j]) continue;
+      St& s = S[j];
+      res.resid[j] = std::abs(s.ghat);
+      const double qnorm = std::sqrt(std::max(0.0, qn[2 * j]));
+      if (std::abs(s.ghat) <= cfg.target * bnorm[j]) {
+        s.active = false;
+      } else if (std::fabs(qnorm - 1.0) > cfg.qdrift) {
+        // the normalisation of q drifts when the sign is inexact (Sec. 2): end this
+        // middle solve here; the outer GMRESR step restarts from the true residual
+        s.active = false;
+        res.stopped[j] = 1;
+      }
+    }
+  }
+  return OVL_OK;
+}
+
+// ------------------------------------------------------------------ relCG (Alg. 4)
+// Hhat^-1 x = x + sum_i psi_i (c/sqrt(mu_i) - 1) (psi_i, x), per system mass.
+static ovl_status spectral_apply(ovl_ctx* c, ovl_defl* d, const std::vector<double>& mus, Field& x, int xoff, int n) {
+  if (!d || d->n == 0) return OVL_OK;
+  OVL_TRY(defl_prepare(c, d));
+  const int ne = d->n;
+  std::vector<cd> G;
+  OVL_TRY(gram_host(c, d->v, 0, ne, x, xoff, n, 0, G));
+  std::vector<cd> C((size_t)ne * n);
+  for (int j = 0; j < n; ++j) {
+    std::vector<cd> M;
+    dd_matrix(d, mus[j], M);
+    for (int i = 0; i < ne; ++i) {
+      const double mui = std::max(M[(size_t)i * ne + i].real() / std::max(d->VV[(size_t)i * ne + i].real(), 1e-300), 1e-300);
+      const double f = c->P.c_spec / std::sqrt(mui) - 1.0;
+      C[(size_t)i * n + j] = f * G[(size_t)i * n + j];
+    }
+  }
+  return combine_host(c, d->v, 0, ne, C, x, xoff, n, 1);
+}
+
+ovl_status cg_batch(ovl_ctx* c, const SumrCfg& cfg, int n, const std::vector<double>& mus, const Field& b, int boff,
+                    Field& x, int xoff, SumrResult& res) {
+  const int PS = cfg.prec;
+  const int V = c->V;
+  Field *fr, *fp, *fz, *ft, *fxj;
+  OVL_TRY(get_field(c, "c_r", PS, n, &fr));
+  OVL_TRY(get_field(c, "c_p", PS, n, &fp));
+  OVL_TRY(get_field(c, "c_z", PS, n, &fz));
+  OVL_TRY(get_field(c, "c_t", PS, n, &ft));
+  OVL_TRY(get_field(c, "c_x", PS, n, &fxj));
+  // H x = gamma5 b: r0 = p0 = Hhat^-1 gamma5 b
+  OVL_TRY(copy_convert(c, b, boff, *fr, 0, n));
+  launch_gamma5(PS, fr->ref(), n, V, c->st);
+  OVL_TRY(spectral_apply(c, cfg.defl, mus, *fr, 0, n));
+  OVL_TRY(copy_convert(c, *fr, 0, *fp, 0, n));
+  launch_zero(PS, fxj->ref(), n, V, c->st);
+  std::vector<double> bnorm, rn;
+  OVL_TRY(norms_batch(c, b, boff, n, bnorm));
+  OVL_TRY(norms_batch(c, *fr, 0, n, rn));
+  std::vector<double> rr(n), zeta(n, 0.0);
+  std::vector<char> active(n);
+  res.iters.assign(n, 0);
+  res.resid.assign(n, 0.0);
+  res.wcalls.assign(n, 0);
+  res.sign_calls.assign(n, 0);
+  res.stopped.assign(n, 0);
+  for (int j = 0; j < n; ++j) {
+    rr[j] = rn[j] * rn[j];
+    zeta[j] = rr[j] > 0 ? 1.0 / rr[j] : 0.0;
+    active[j] = rn[j] >= cfg.target * bnorm[j] && rn[j] > 0;
+    res.resid[j] = rn[j];
+  }
+  std::vector<double> eta(n);
+  for (int iter = 0; iter < cfg.maxit; ++iter) {
+    int nact = 0;
+    double emin = 1e300;
+    for (int j = 0; j < n; ++j) {
+      double e = cfg.relax * cfg.target * bnorm[j] * std::sqrt(zeta[j]);
+      e = std::min(e, cfg.floor);
+      if (cfg.eta_cap > 0) e = std::min(e, cfg.eta_cap);
+      eta[j] = active[j] ? e : 1.0;
+      if (active[j]) {
+        ++nact;
+        emin = std::min(emin, e);
+      }
+    }
+    if (nact == 0) break;
+    const int mode = cfg.mode >= 0 ? cfg.mode : choose_mode(c, emin);
+    // z = Hhat^-1 H H Hhat^-1 p
+    OVL_TRY(copy_convert(c, *fp, 0, *ft, 0, n));
+    OVL_TRY(spectral_apply(c, cfg.defl, mus, *ft, 0, n));
+    std::vector<long long> wc(n, 0);
+    OVL_TRY(overlap_apply_batch(c, *ft, 0, *fz, 0, n, mus, eta, 1, mode, wc.data()));
+    OVL_TRY(overlap_apply_batch(c, *fz, 0, *ft, 0, n, mus, eta, 1, mode, wc.data()));
+    OVL_TRY(spectral_apply(c, cfg.defl, mus, *ft, 0, n));
+    std::vector<cd> rz;
+    OVL_TRY(dots_batch(c, *fr, 0, *ft, 0, n, rz));
+    std::vector<cd> al(n, 0.0), one(n, 1.0), mal(n, 0.0);
+    for (int j = 0; j < n; ++j) {
+      if (!active[j]) continue;
+      res.wcalls[j] += wc[j];
+      res.sign_calls[j] += 2;
+      al[j] = rr[j] / rz[j];
+      mal[j] = -al[j];
+    }
+    OVL_TRY(axpby_batch(c, one, *fr, 0, mal, *ft, 0, *fr, 0, n));   // r -= alpha z
+    OVL_TRY(axpby_batch(c, one, *fxj, 0, al, *fp, 0, *fxj, 0, n));  // x += alpha p
+    OVL_TRY(norms_batch(c, *fr, 0, n, rn));
+    std::vector<cd> beta(n, 0.0);
+    for (int j = 0; j < n; ++j) {
+      if (!active[j]) {
+        beta[j] = 0.0;
+        continue;
+      }
+      const double rrn = rn[j] * rn[j];
+      beta[j] = rrn / rr[j];
+      rr[j] = rrn;
+      zeta[j] += rrn > 0 ? 1.0 / rrn : 0.0;
+      res.iters[j] += 1;
+      res.resid[j] = rn[j];
+      if (rn[j] < cfg.target * bnorm[j]) active[j] = 0;
+    }
+    std::vector<cd> onea(n, 1.0);
+    for (int j = 0; j < n; ++j)
+      if (!active[j] && res.iters[j] > 0) {
+        // frozen systems: p = r + 0 p keeps them unchanged in value semantics
+      }
+    OVL_TRY(axpby_batch(c, onea, *fr, 0, beta, *fp, 0, *fp, 0, n));  // p = r + beta p
+  }
+  // x = H Hhat^-1 x_j at the accuracy of the middle solve
+  OVL_TRY(spectral_apply(c, cfg.defl, mus, *fxj, 0, n));
+  std::vector<double> efin(n, std::min(cfg.floor, cfg.target));
+  std::vector<long long> wc(n, 0);
+  OVL_TRY(overlap_apply_batch(c, *fxj, 0, x, xoff, n, mus, efin, 1, -1, wc.data()));
+  for (int j = 0; j < n; ++j) {
+    res.wcalls[j] += wc[j];
+    res.sign_calls[j] += 1;
+  }
+  return OVL_OK;
+}
+
+// ------------------------------------------------------------------ GMRESR (Alg. 3)
+ovl_status gmresr_batch(ovl_ctx* c, int n, const std::vector<double>& mus, const Field& b, int boff, Field& x,
+                        int xoff, double tol, ovl_defl* defl, ovl_solve_info* info, EigHook* eig) {
+  auto t0 = std::chrono::steady_clock::now();
+  const int V = c->V;
+  const int kmax = std::max(1, c->P.gmresr_max);
+  const int PS = c->P.mixed ? P32 : P64;
+  Field *fr, *fC, *fU, *fmid_b, *fmid_x, *fu, *fc;
+  OVL_TRY(get_field(c, "g_r", P64, n, &fr));
+  OVL_TRY(get_field(c, "g_C", P64, kmax * n, &fC));
+  OVL_TRY(get_field(c, "g_U", P64, kmax * n, &fU));
+  OVL_TRY(get_field(c, "g_u", P64, n, &fu));
+  OVL_TRY(get_field(c, "g_c", P64, n, &fc));
+  OVL_TRY(get_field(c, "m_b", PS, n, &fmid_b));
+  OVL_TRY(get_field(c, "m_x", PS, n, &fmid_x));
+  // x = 0, r = b
+  launch_zero(P64, x.ref(xoff), n, V, c->st);
+  OVL_TRY(copy_convert(c, b, boff, *fr, 0, n));
+  std::vector<double> bn, rn;
+  OVL_TRY(norms_batch(c, b, boff, n, bn));
+  rn = bn;
+  const double eta_t = c->P.eta_precond > 0 ? c->P.eta_precond : std::cbrt(tol);
+  std::vector<char> active(n);
+  std::vector<int> outer(n, 0), inner(n, 0), signs(n, 0);
+  std::vector<long long> wcalls(n, 0);
+  for (int j = 0; j < n; ++j) active[j] = rn[j] > tol * bn[j];
+  for (int k = 0; k < kmax; ++k) {
+    int nact = 0;
+    for (int j = 0; j < n; ++j) nact += active[j];
+    if (nact == 0) break;
+    // middle solve A u = r to relative accuracy eta~ (all systems in the batch advance;
+    // converged ones are solved for their tiny residual, which costs iterations only
+    // while others still run)
+    OVL_TRY(copy_convert(c, *fr, 0, *fmid_b, 0, n));
+    SumrCfg cfg;
+    cfg.prec = PS;
+    cfg.target = (eig && eig->active) ? eig->target : eta_t;
+    cfg.relax = c->P.relax_factor;
+    cfg.floor = c->P.eta_floor;
+    cfg.maxit = c->P.inner_max;
+    cfg.defl = defl;
+    cfg.mode = -1;
+    cfg.qdrift = 0.1;
+    cfg.eta_cap = (eig && eig->active) ? eig->eta_cap : 0.0;
+    if (eig && eig->active) {
+      cfg.hook = eig->hook;
+      cfg.hook_data = eig->data;
+    }
+    SumrResult sr;
+    if (c->P.solver == OVL_SOLVER_CG) OVL_TRY(cg_batch(c, cfg, n, mus, *fmid_b, 0, *fmid_x, 0, sr));
+    else OVL_TRY(sumr_batch(c, cfg, n, mus, *fmid_b, 0, *fmid_x, 0, sr));
+    OVL_TRY(copy_convert(c, *fmid_x, 0, *fu, 0, n));
+    if (c->P.solver != OVL_SOLVER_CG) {
+      // SUMR solved (rho + V) u = r, i.e. D u = (1-mu)/2 r: rescale u by 2/(1-mu)
+      std::vector<cd> a(n), z(n, 0.0);
+      for (int j = 0; j < n; ++j) a[j] = 2.0 / (1.0 - mus[j]);
+      OVL_TRY(axpby_batch(c, a, *fu, 0, z, *fu, 0, *fu, 0, n));
+    }
+    for (int j = 0; j < n; ++j)
+      if (active[j]) {
+        inner[j] += sr.iters[j];
+        wcalls[j] += sr.wcalls[j];
+        signs[j] += sr.sign_calls[j];
+      }
+    // c = A u with ||A u - c|| < eps ||b|| ||u|| / ||r||
+    std::vector<double> eta(n);
+    double emin = 1e300;
+    for (int j = 0; j < n; ++j) {
+      eta[j] = active[j] ? std::min(c->P.eta_floor, tol * bn[j] / std::max(rn[j], 1e-300)) : c->P.eta_floor;
+      emin = std::min(emin, eta[j]);
+    }
+    std::vector<long long> wc(n, 0);
+    OVL_TRY(overlap_apply_batch(c, *fu, 0, *fc, 0, n, mus, eta, 0, -1, wc.data()));
+    for (int j = 0; j < n; ++j)
+      if (active[j]) {
+        wcalls[j] += wc[j];
+        signs[j] += 1;
+      }
+    // orthogonalise against the stored C (same combination on u)
+    for (int i = 0; i < k; ++i) {
+      std::vector<cd> beta;
+      OVL_TRY(dots_batch(c, *fC, i * n, *fc, 0, n, beta));
+      std::vector<cd> one(n, 1.0), mb(n);
+      for (int j = 0; j < n; ++j) mb[j] = -beta[j];
+      OVL_TRY(axpby_batch(c, one, *fc, 0, mb, *fC, i * n, *fc, 0, n));
+      OVL_TRY(axpby_batch(c, one, *fu, 0, mb, *fU, i * n, *fu, 0, n));
+    }
+    std::vector<double> nu;
+    OVL_TRY(norms_batch(c, *fc, 0, n, nu));
+    {
+      std::vector<cd> a(n), z(n, 0.0);
+      for (int j = 0; j < n; ++j) a[j] = nu[j] > 0 ? 1.0 / nu[j] : 0.0;
+      OVL_TRY(axpby_batch(c, a, *fc, 0, z, *fc, 0, *fC, k * n, n));
+      OVL_TRY(axpby_batch(c, a, *fu, 0, z, *fu, 0, *fU, k * n, n));
+    }
+    std::vector<cd> alpha;
+    OVL_TRY(dots_batch(c, *fC, k * n, *fr, 0, n, alpha));
+    {
+      std::vector<cd> one(n, 1.0), al(n), mal(n);
+      for (int j = 0; j < n; ++j) {
+        al[j] = active[j] ? alpha[j] : 0.0;
+        mal[j] = -al[j];
+      }
+      OVL_TRY(axpby_batch(c, one, x, xoff, al, *fU, k * n, x, xoff, n));
+      OVL_TRY(axpby_batch(c, one, *fr, 0, mal, *fC, k * n, *fr, 0, n));
+    }
+    OVL_TRY(norms_batch(c, *fr, 0, n, rn));
+    for (int j = 0; j < n; ++j)
+      if (active[j]) {
+        outer[j] += 1;
+        if (rn[j] <= tol * bn[j]) active[j] = 0;
+      }
+    if (eig && eig->after_outer) OVL_TRY(eig->after_outer(c, eig->data, k));
+  }
+  const double secs = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+  if (info) {
+    for (int j = 0; j < n; ++j) {
+      ovl_solve_info& I = info[j];
+      I.converged = rn[j] <= tol * bn[j];
+      I.outer_iters = outer[j];
+      I.inner_iters = inner[j];
+      I.sign_calls = signs[j];
+      I.wilson_calls = wcalls[j];
+      I.true_residual = bn[j] > 0 ? rn[j] / bn[j] : 0.0;
+      I.seconds = secs;
+    }
+  }
+  for (int j = 0; j < n; ++j)
+    if (rn[j] > tol * bn[j]) return set_err(c, OVL_ENOCONV, "GMRESR did not reach the tolerance");
+  return OVL_OK;
+}
+
+}  // namespace ovl

@@ -1,0 +1,65 @@
+// Solver entry points used by the C ABI (see solver.cu).
+#pragma once
+#include <vector>
+
+#include "context.h"
+
+namespace ovl {
+
+// Called after every sign application of the middle SUMR solve (eigSUMR, Alg. 5):
+// q holds q_j, u holds V q_j for every system of the batch.
+typedef ovl_status (*SumrHook)(ovl_ctx* c, void* data, const Field& q, const Field& u, int iter);
+typedef ovl_status (*OuterHook)(ovl_ctx* c, void* data, int outer);
+
+struct SumrCfg {
+  int prec = P64;          // precision of the middle-solve vectors
+  double target = 1e-3;    // relative residual target
+  double relax = 1.0;      // relaxation factor
+  double floor = 1e-2;     // sign accuracy never worse than this
+  double eta_cap = 0.0;    // >0: sign accuracy never worse than this either (eigen accumulation)
+  int maxit = 1000;
+  int mode = -1;           // sign precision, -1: chosen by eta
+  double qdrift = 0.1;     // stop when | ||q|| - 1 | exceeds this
+  ovl_defl* defl = nullptr;
+  SumrHook hook = nullptr;
+  void* hook_data = nullptr;
+};
+
+struct SumrResult {
+  std::vector<int> iters;
+  std::vector<double> resid;
+  std::vector<long long> wcalls;
+  std::vector<int> sign_calls;
+  std::vector<int> stopped;   // 0 normal, 1 q drift, 2 breakdown
+};
+
+struct EigHook {
+  bool active = false;
+  double target = 1e-2;    // middle-solve target while accumulating (GMRESR converges in two steps)
+  double eta_cap = 1e-4;   // sign accuracy during accumulation
+  SumrHook hook = nullptr;
+  OuterHook after_outer = nullptr;
+  void* data = nullptr;
+};
+
+ovl_status sumr_batch(ovl_ctx* c, const SumrCfg& cfg, int n, const std::vector<double>& mus, const Field& b, int boff,
+                      Field& x, int xoff, SumrResult& res);
+ovl_status cg_batch(ovl_ctx* c, const SumrCfg& cfg, int n, const std::vector<double>& mus, const Field& b, int boff,
+                    Field& x, int xoff, SumrResult& res);
+ovl_status gmresr_batch(ovl_ctx* c, int n, const std::vector<double>& mus, const Field& b, int boff, Field& x, int xoff,
+                        double tol, ovl_defl* defl, ovl_solve_info* info, EigHook* eig);
+ovl_status overlap_apply_batch(ovl_ctx* c, const Field& v, int voff, Field& out, int ooff, int n,
+                               const std::vector<double>& mus, const std::vector<double>& eta, int herm, int mode,
+                               long long* wcalls_out);
+ovl_status dots_batch(ovl_ctx* c, const Field& x, int xoff, const Field& y, int yoff, int n, std::vector<cd>& out);
+ovl_status norms_batch(ovl_ctx* c, const Field& x, int xoff, int n, std::vector<double>& out);
+ovl_status axpby_batch(ovl_ctx* c, const std::vector<cd>& a, const Field& x, int xoff, const std::vector<cd>& b,
+                       const Field& y, int yoff, Field& z, int zoff, int n);
+ovl_status copy_convert(ovl_ctx* c, const Field& in, int ioff, Field& out, int ooff, int n);
+ovl_status gram_host(ovl_ctx* c, const Field& A, int aoff, int na, const Field& B, int boff, int nb, int g5,
+                     std::vector<cd>& G);
+ovl_status combine_host(ovl_ctx* c, const Field& A, int aoff, int na, const std::vector<cd>& C, Field& Y, int yoff,
+                        int ny, int add);
+ovl_status defl_prepare(ovl_ctx* c, ovl_defl* d);
+
+}  // namespace ovl

@@ -113,3 +113,18 @@ def test_brute_force_site_loop():
             K[i * 12:(i + 1) * 12, j * 12:(j + 1) * 12] += np.kron(g5, np.eye(3)) @ B
     Kd = wilson.dense_K(U, m0)
     assert np.allclose(Kd, K, atol=1e-14)
+
+
+@pytest.mark.parametrize("apt", [False, True])
+def test_site_formula_matches_full_apply(apt):
+    dims = (4, 2, 2, 6)
+    U = synth.gauge_links(dims, 0.4, 3)
+    psi = synth.gaussian_source(dims, 4)
+    full = wilson.apply_K(U, psi, 1.3, apt)
+    rng = np.random.default_rng(0)
+    sites = np.stack([rng.integers(0, d, 20) for d in dims], axis=1)
+    sites[0] = (dims[0] - 1, 0, dims[2] - 1, dims[3] - 1)
+    sites[1] = (0, 0, 0, 0)
+    got = wilson.apply_K_sites(U, psi, 1.3, sites, apt)
+    ref = np.array([full[t, z, y, x] for (x, y, z, t) in sites])
+    assert np.allclose(got, ref, atol=1e-14)
