@@ -145,6 +145,15 @@ ovl_status ovl_sign_apply(ovl_ctx* ctx, const void* in, void* out, int n, int dt
 ovl_status overlap_apply(ovl_ctx* ctx, double mu, const void* in, void* out, int n, int dtype,
                          int on_device, double eta, int prec, int hermitian);
 
+/* The middle solver alone: relaxed SUMR (Algs. 1-2, Sec. 3) for D(mu) x = b, n systems,
+ * stopped at the relative residual estimate tol or after maxit iterations. eta_fixed > 0
+ * applies the sign at that accuracy every iteration; eta_fixed <= 0 relaxes it as
+ * eta_j = tol ||b|| / ||r_j|| (never worse than params.eta_floor). hist (may be NULL)
+ * receives maxit * n residual estimates ||r_j|| / ||b|| (system-major, 0 after the
+ * last iteration); iters (may be NULL) the iteration count per system. */
+ovl_status overlap_sumr(ovl_ctx* ctx, double mu, const void* b, void* x, int n, int dtype, int on_device, double tol,
+                        double eta_fixed, int maxit, double* hist, int* iters);
+
 /* Solve D(mu_k) x = b for nrhs sources and nmass masses (GMRESR, Alg. 3, around
  * relSUMR or relCG, Sec. 3). x holds nmass*nrhs spinors, mass-major
  * (x[k*nrhs + j] solves mass k, source j). tol is the relative FP64 true-residual

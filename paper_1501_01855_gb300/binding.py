@@ -70,6 +70,7 @@ _SIGS = {
     "ovl_wilson_apply": (I, [P, P, P, I, I, I, I]),
     "ovl_sign_apply": (I, [P, P, P, I, I, I, D, I]),
     "overlap_apply": (I, [P, D, P, P, I, I, I, D, I, I]),
+    "overlap_sumr": (I, [P, D, P, P, I, I, I, D, D, I, DP, ctypes.POINTER(I)]),
     "overlap_solve": (I, [P, I, DP, I, P, P, I, I, D, P, ctypes.POINTER(ovl_solve_info)]),
     "eigsumr_accumulate": (I, [P, ctypes.POINTER(P), I, I, D, P, P, I, I, D, ctypes.POINTER(ovl_solve_info)]),
     "ovl_defl_info": (I, [P, ctypes.POINTER(I), DP, DP]),
@@ -230,6 +231,18 @@ class Overlap:
         _check(load().overlap_apply(self.h, float(mu), pi, po, self._n(cnt), code, dev, float(eta), int(prec),
                                     1 if hermitian else 0), self.h)
         return out
+
+    def sumr(self, b, x, tol, eta_fixed=0.0, maxit=200, mu=None):
+        pb, code, dev, cnt = _spinor_arg(b)
+        px, _, _, _ = _spinor_arg(x)
+        n = self._n(cnt)
+        mu = self.mu if mu is None else mu
+        hist = np.zeros(n * maxit)
+        its = (ctypes.c_int * n)()
+        _check(load().overlap_sumr(self.h, float(mu), pb, px, n, code, dev, float(tol), float(eta_fixed), int(maxit),
+                                   _dptr(hist), its), self.h)
+        its = list(its)
+        return [hist[j * maxit:j * maxit + its[j]] for j in range(n)], its
 
     def solve(self, b, x, tol, mus=None, defl=None, allow_noconv=False):
         pb, code, dev, cnt = _spinor_arg(b)

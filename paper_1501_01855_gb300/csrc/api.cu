@@ -171,7 +171,7 @@ static ovl_status create_impl(ovl_ctx* c, const int dims[4], const double* links
   OVL_CUDA(c, cudaGetDevice(&c->device));
   OVL_CUDA(c, cudaMallocHost((void**)&c->hpin, sizeof(double) * 64 * 4096));
   OVL_CUDA(c, cudaMalloc((void**)&c->dscal, sizeof(double) * 64 * 4096));
-  OVL_CUDA(c, cudaMalloc((void**)&c->dred, sizeof(double) * 2 * 4096));
+  OVL_CUDA(c, cudaMalloc((void**)&c->dred, sizeof(double) * NVRED * 4096));
   OVL_CUDA(c, cudaMalloc((void**)&c->dint, sizeof(int) * 4096));
   OVL_CUDA(c, cudaMalloc((void**)&c->dpoles, sizeof(Poles)));
   // gauge field in the three storage formats
@@ -309,6 +309,46 @@ extern "C" ovl_status overlap_apply(ovl_ctx* c, double mu, const void* in, void*
   std::vector<double> mus(n, mu), etas(n, e);
   OVL_TRY(overlap_apply_batch(c, *fi, 0, *fo, 0, n, mus, etas, hermitian ? 1 : 0, mode, nullptr));
   OVL_TRY(export_spinors(c, out, dtype, on_device, n, *fo, 0));
+  OVL_CUDA(c, cudaStreamSynchronize(c->st));
+  return OVL_OK;
+}
+
+extern "C" ovl_status overlap_sumr(ovl_ctx* c, double mu, const void* b, void* x, int n, int dtype, int on_device,
+                                   double tol, double eta_fixed, int maxit, double* hist, int* iters) {
+  OVL_TRY(check_io(c, b, x, n, dtype));
+  if (!(mu > 0 && mu < 1)) return set_err(c, OVL_EINVAL, "mu must lie in (0, 1)");
+  if (maxit < 1 || !(tol > 0)) return set_err(c, OVL_EINVAL, "need maxit >= 1 and tol > 0");
+  const int PS = c->P.mixed ? P32 : P64;
+  Field *fb, *fx, *fo;
+  OVL_TRY(get_field(c, "api_in", P64, n, &fb));
+  OVL_TRY(get_field(c, "sm_b", PS, n, &fx));
+  OVL_TRY(get_field(c, "sm_x", PS, n, &fo));
+  OVL_TRY(import_spinors(c, b, dtype, on_device, n, *fb, 0));
+  OVL_TRY(copy_convert(c, *fb, 0, *fx, 0, n));
+  SumrCfg cfg;
+  cfg.prec = PS;
+  cfg.target = tol;
+  cfg.relax = c->P.relax_factor;
+  cfg.floor = c->P.eta_floor;
+  cfg.maxit = maxit;
+  cfg.eta_fixed = eta_fixed;
+  std::vector<std::vector<double>> h(n);
+  cfg.hist = h.data();
+  std::vector<double> mus(n, mu);
+  SumrResult sr;
+  OVL_TRY(sumr_batch(c, cfg, n, mus, *fx, 0, *fo, 0, sr));
+  // (rho + V) x' = b  ->  D x = b with x = 2 x' / (1 - mu)
+  Field* fr;
+  OVL_TRY(get_field(c, "api_out", P64, n, &fr));
+  OVL_TRY(copy_convert(c, *fo, 0, *fr, 0, n));
+  std::vector<cd> a(n, 2.0 / (1.0 - mu)), z(n, 0.0);
+  OVL_TRY(axpby_batch(c, a, *fr, 0, z, *fr, 0, *fr, 0, n));
+  OVL_TRY(export_spinors(c, x, dtype, on_device, n, *fr, 0));
+  for (int j = 0; j < n; ++j) {
+    if (iters) iters[j] = sr.iters[j];
+    if (hist)
+      for (int k = 0; k < maxit; ++k) hist[(size_t)j * maxit + k] = k < (int)h[j].size() ? h[j][k] : 0.0;
+  }
   OVL_CUDA(c, cudaStreamSynchronize(c->st));
   return OVL_OK;
 }

@@ -159,26 +159,28 @@ void launch_norm2(int px, SpinorRef x, int nrhs, int V, double* partials, cudaSt
 }
 
 __global__ void reduce_partials_kernel(const double* partials, int nsb, double* out) {
-  __shared__ double sh[2][128];
+  __shared__ double sh[NVRED][128];
   const int rhs = blockIdx.x;
-  double a0 = 0.0, a1 = 0.0;
+  double a[NVRED];
+#pragma unroll
+  for (int j = 0; j < NVRED; ++j) a[j] = 0.0;
   for (int b = threadIdx.x; b < nsb; b += blockDim.x) {
-    a0 += partials[((size_t)rhs * nsb + b) * NVRED + 0];
-    a1 += partials[((size_t)rhs * nsb + b) * NVRED + 1];
+#pragma unroll
+    for (int j = 0; j < NVRED; ++j) a[j] += partials[((size_t)rhs * nsb + b) * NVRED + j];
   }
-  sh[0][threadIdx.x] = a0;
-  sh[1][threadIdx.x] = a1;
+#pragma unroll
+  for (int j = 0; j < NVRED; ++j) sh[j][threadIdx.x] = a[j];
   __syncthreads();
   for (int o = blockDim.x / 2; o > 0; o >>= 1) {
     if (threadIdx.x < o) {
-      sh[0][threadIdx.x] += sh[0][threadIdx.x + o];
-      sh[1][threadIdx.x] += sh[1][threadIdx.x + o];
+#pragma unroll
+      for (int j = 0; j < NVRED; ++j) sh[j][threadIdx.x] += sh[j][threadIdx.x + o];
     }
     __syncthreads();
   }
   if (threadIdx.x == 0) {
-    out[2 * rhs] = sh[0][0];
-    out[2 * rhs + 1] = sh[1][0];
+#pragma unroll
+    for (int j = 0; j < NVRED; ++j) out[NVRED * rhs + j] = sh[j][0];
   }
 }
 void launch_reduce_partials(const double* partials, int nsb, int nrhs, double* out, cudaStream_t st) {

@@ -63,42 +63,68 @@ struct SpinorRef {
   int V;
 };
 
-template <int P, typename T>
-__device__ __forceinline__ void load_spinor(const SpinorRef& f, int rhs, int s, cpx<T> v[12]);
+// Chunk load: RO = true goes through the read-only (non-coherent) data path, which
+// is only valid for fields that no thread of the same kernel writes; every
+// in-place update (x = a x + ..., r -= alpha A p, the SUMR step) uses RO = false,
+// otherwise the compiler may legally re-load a value after the kernel's own store.
+template <bool RO, typename V>
+__device__ __forceinline__ V ldc(const V* p) {
+  if constexpr (RO) return __ldg(p);
+  else return *p;
+}
 
-template <>
-__device__ __forceinline__ void load_spinor<P64, double>(const SpinorRef& f, int rhs, int s, cpx<double> v[12]) {
-  const double2* p = reinterpret_cast<const double2*>(f.data) + (size_t)rhs * 12 * f.V + s;
+template <int P, typename T, bool RO = false>
+struct SpinorLoad;
+
+template <bool RO>
+struct SpinorLoad<P64, double, RO> {
+  static __device__ __forceinline__ void run(const SpinorRef& f, int rhs, int s, cpx<double> v[12]) {
+    const double2* p = reinterpret_cast<const double2*>(f.data) + (size_t)rhs * 12 * f.V + s;
 #pragma unroll
-  for (int c = 0; c < 12; ++c) {
-    double2 w = __ldg(p + (size_t)c * f.V);
-    v[c] = cmk(w.x, w.y);
-  }
-}
-template <>
-__device__ __forceinline__ void load_spinor<P32, float>(const SpinorRef& f, int rhs, int s, cpx<float> v[12]) {
-  const float4* p = reinterpret_cast<const float4*>(f.data) + (size_t)rhs * 6 * f.V + s;
-#pragma unroll
-  for (int c = 0; c < 6; ++c) {
-    float4 w = __ldg(p + (size_t)c * f.V);
-    v[2 * c] = cmk(w.x, w.y);
-    v[2 * c + 1] = cmk(w.z, w.w);
-  }
-}
-template <>
-__device__ __forceinline__ void load_spinor<P16, float>(const SpinorRef& f, int rhs, int s, cpx<float> v[12]) {
-  const uint4* p = reinterpret_cast<const uint4*>(f.data) + (size_t)rhs * 3 * f.V + s;
-  const float sc = __ldg(f.norm + (size_t)rhs * f.V + s);
-#pragma unroll
-  for (int c = 0; c < 3; ++c) {
-    uint4 w = __ldg(p + (size_t)c * f.V);
-    const __half2* h = reinterpret_cast<const __half2*>(&w);
-#pragma unroll
-    for (int k = 0; k < 4; ++k) {
-      float2 q = __half22float2(h[k]);
-      v[4 * c + k] = cmk(q.x * sc, q.y * sc);
+    for (int c = 0; c < 12; ++c) {
+      double2 w = ldc<RO>(p + (size_t)c * f.V);
+      v[c] = cmk(w.x, w.y);
     }
   }
+};
+template <bool RO>
+struct SpinorLoad<P32, float, RO> {
+  static __device__ __forceinline__ void run(const SpinorRef& f, int rhs, int s, cpx<float> v[12]) {
+    const float4* p = reinterpret_cast<const float4*>(f.data) + (size_t)rhs * 6 * f.V + s;
+#pragma unroll
+    for (int c = 0; c < 6; ++c) {
+      float4 w = ldc<RO>(p + (size_t)c * f.V);
+      v[2 * c] = cmk(w.x, w.y);
+      v[2 * c + 1] = cmk(w.z, w.w);
+    }
+  }
+};
+template <bool RO>
+struct SpinorLoad<P16, float, RO> {
+  static __device__ __forceinline__ void run(const SpinorRef& f, int rhs, int s, cpx<float> v[12]) {
+    const uint4* p = reinterpret_cast<const uint4*>(f.data) + (size_t)rhs * 3 * f.V + s;
+    const float sc = ldc<RO>(f.norm + (size_t)rhs * f.V + s);
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      uint4 w = ldc<RO>(p + (size_t)c * f.V);
+      const __half2* h = reinterpret_cast<const __half2*>(&w);
+#pragma unroll
+      for (int k = 0; k < 4; ++k) {
+        float2 q = __half22float2(h[k]);
+        v[4 * c + k] = cmk(q.x * sc, q.y * sc);
+      }
+    }
+  }
+};
+
+template <int P, typename T>
+__device__ __forceinline__ void load_spinor(const SpinorRef& f, int rhs, int s, cpx<T> v[12]) {
+  SpinorLoad<P, T, false>::run(f, rhs, s, v);
+}
+// read-only path: only for fields that the kernel does not write
+template <int P, typename T>
+__device__ __forceinline__ void load_spinor_ro(const SpinorRef& f, int rhs, int s, cpx<T> v[12]) {
+  SpinorLoad<P, T, true>::run(f, rhs, s, v);
 }
 
 template <int P, typename T>
@@ -171,6 +197,16 @@ __device__ __forceinline__ void load_spinor_as(const SpinorRef& f, int rhs, int 
     for (int k = 0; k < 12; ++k) v[k] = cmk((float)w[k].r, (float)w[k].i);
   }
 }
+// read-only variant of load_spinor_as (Wilson-kernel input, never written by that kernel)
+template <int P, typename T>
+__device__ __forceinline__ void load_spinor_as_ro(const SpinorRef& f, int rhs, int s, cpx<T> v[12]) {
+  if constexpr ((P == P64) == (sizeof(T) == 8)) {
+    load_spinor_ro<P, T>(f, rhs, s, v);
+  } else {
+    load_spinor_as<P, T>(f, rhs, s, v);
+  }
+}
+
 template <int P, typename T>
 __device__ __forceinline__ void store_spinor_as(const SpinorRef& f, int rhs, int s, const cpx<T> v[12]) {
   if constexpr ((P == P64) == (sizeof(T) == 8)) {

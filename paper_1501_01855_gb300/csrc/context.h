@@ -123,14 +123,17 @@ LinkRef links_of(const ovl_ctx* c, int prec);
 
 // reductions: partials -> host pairs (synchronises the stream)
 ovl_status reduce_to_host(ovl_ctx* c, int nsb, int nrhs, double* host_pairs);
+// the first nv of the NVRED partial sums per system
+ovl_status reduce_to_host_nv(ovl_ctx* c, int nsb, int nrhs, double* out, int nv);
 
 // I/O between caller buffers and internal fields
 ovl_status import_spinors(ovl_ctx* c, const void* src, int dtype, int on_device, int n, Field& dst, int off);
 ovl_status export_spinors(ovl_ctx* c, void* dst, int dtype, int on_device, int n, const Field& src, int off);
 
 // sign function: out = c1 v + c2 gamma5 K y (times gamma5 if herm), y = sum_i omega_i (K^2+sigma_i)^-1 v,
-// every system stopped at its own relative accuracy eta[j]. dot_w (may be null) requests (w_j, out_j)
-// into dots (host, 2n). coef (host, may be null) gives per-system (c1, c2).
+// every system stopped at its own relative accuracy eta[j]. dot_w (may be null) requests
+// {Re (w_j, out_j), Im (w_j, out_j), ||out_j||^2, ||w_j||^2} into dots (host, 4n). coef (host,
+// may be null) gives per-system (c1, c2).
 ovl_status sign_op(ovl_ctx* c, int mode, const Field& v, int voff, Field& out, int ooff, int n, const double* eta,
                    double c1, double c2, const double* coef, int herm, const Field* dot_w, int woff, double* dots,
                    SignStats* stats);

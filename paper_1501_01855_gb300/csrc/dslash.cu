@@ -94,7 +94,7 @@ __device__ __forceinline__ void hop_dir(const Geom& g, const LinkRef& L, const S
   {
     const bool wrap = x[MU] == g.L[MU] - 1;
     const int sf = wrap ? s - (g.L[MU] - 1) * stride : s + stride;
-    load_spinor_as<PIN, T>(in, rhs, sf, psi);
+    load_spinor_as_ro<PIN, T>(in, rhs, sf, psi);
     project<MU, -1>(psi, h);
     if (MU == 3 && g.bc_t && wrap) {
 #pragma unroll
@@ -108,7 +108,7 @@ __device__ __forceinline__ void hop_dir(const Geom& g, const LinkRef& L, const S
   {
     const bool wrap = x[MU] == 0;
     const int sb = wrap ? s + (g.L[MU] - 1) * stride : s - stride;
-    load_spinor_as<PIN, T>(in, rhs, sb, psi);
+    load_spinor_as_ro<PIN, T>(in, rhs, sb, psi);
     project<MU, +1>(psi, h);
     if (MU == 3 && g.bc_t && wrap) {
 #pragma unroll
@@ -154,18 +154,18 @@ struct DArgs {
 template <int MODE, int PIN, int PL, int POUT, int PA1, int PA2>
 __global__ void __launch_bounds__(256) wilson_kernel(const DArgs a) {
   using T = typename Real<PL>::T;
-  __shared__ double red[4 * (BX / 32) * 2];
+  __shared__ double red[4 * (BX / 32) * NVRED];
   const int sb = blockIdx.x / a.ngr;
   const int rg = blockIdx.x - sb * a.ngr;
   const int rhs = rg * blockDim.y + threadIdx.y;
   const int s = sb * BX + threadIdx.x;
   bool live = (s < a.g.V) && (rhs < a.nrhs);
   if (live && a.ms != nullptr && (MODE == MODE_K || MODE == MODE_R)) live = !a.ms[rhs].done;
-  double v[2] = {0.0, 0.0};
+  double v[NVRED] = {0.0, 0.0, 0.0, 0.0};
   if (live) {
     cpx<T> acc[12], c[12];
     hop<PIN, PL, T>(a.g, a.links, a.in, rhs, s, acc);
-    load_spinor_as<PIN, T>(a.in, rhs, s, c);
+    load_spinor_as_ro<PIN, T>(a.in, rhs, s, c);
     const T kap = (T)a.kappa;
     if constexpr (MODE == MODE_K) {
       // K in = gamma5 (in - kappa acc)
@@ -220,15 +220,17 @@ __global__ void __launch_bounds__(256) wilson_kernel(const DArgs a) {
           cpx<T> d = cmulc(w[k], acc[k]);
           v[0] += (double)d.r;
           v[1] += (double)d.i;
+          v[2] += (double)norm2(acc[k]);
+          v[3] += (double)norm2(w[k]);
         }
       }
     }
   }
   if (a.partials != nullptr) {
-    block_reduce_rows<2>(v, red);
+    block_reduce_rows<NVRED>(v, red);
     if (threadIdx.x == 0 && rhs < a.nrhs) {
-      a.partials[((size_t)rhs * a.nsb + sb) * NVRED + 0] = v[0];
-      a.partials[((size_t)rhs * a.nsb + sb) * NVRED + 1] = v[1];
+#pragma unroll
+      for (int j = 0; j < NVRED; ++j) a.partials[((size_t)rhs * a.nsb + sb) * NVRED + j] = v[j];
     }
   }
 }

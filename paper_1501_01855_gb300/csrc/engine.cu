@@ -203,12 +203,18 @@ ovl_status wilson_apply_field(ovl_ctx* c, int prec, const Field& in, int ioff, F
 }
 
 // ---------------------------------------------------------------- reductions
-ovl_status reduce_to_host(ovl_ctx* c, int nsb, int nrhs, double* host_pairs) {
+ovl_status reduce_to_host_nv(ovl_ctx* c, int nsb, int nrhs, double* out, int nv) {
   launch_reduce_partials(c->partials, nsb, nrhs, c->dred, c->st);
-  OVL_CUDA(c, cudaMemcpyAsync(c->hpin, c->dred, sizeof(double) * 2 * nrhs, cudaMemcpyDeviceToHost, c->st));
+  double* h = c->hpin + 16384;   // NVRED * 4096 doubles
+  OVL_CUDA(c, cudaMemcpyAsync(h, c->dred, sizeof(double) * NVRED * nrhs, cudaMemcpyDeviceToHost, c->st));
   OVL_CUDA(c, cudaStreamSynchronize(c->st));
-  memcpy(host_pairs, c->hpin, sizeof(double) * 2 * nrhs);
+  for (int j = 0; j < nrhs; ++j)
+    for (int k = 0; k < nv; ++k) out[nv * j + k] = h[NVRED * j + k];
   return OVL_OK;
+}
+
+ovl_status reduce_to_host(ovl_ctx* c, int nsb, int nrhs, double* host_pairs) {
+  return reduce_to_host_nv(c, nsb, nrhs, host_pairs, 2);
 }
 
 // ---------------------------------------------------------------- caller I/O
@@ -342,7 +348,7 @@ ovl_status sign_op(ovl_ctx* c, int mode, const Field& v, int voff, Field& out, i
                     herm, d_part, c->st);
   prof_end(c, &pp, (double)n * V * (spinor_bytes(PR) + 2.0 * spinor_bytes(out.prec)) + lbytes);
   OVL_TRY(check_launch(c, __func__));
-  if (dot_w) OVL_TRY(reduce_to_host(c, sh.nsb, n, dots));
+  if (dot_w) OVL_TRY(reduce_to_host_nv(c, sh.nsb, n, dots, 4));
   // iteration counts, status and byte counters
   std::vector<int> it(n), stt(n);
   std::vector<long long> prd(n), pwr(n);

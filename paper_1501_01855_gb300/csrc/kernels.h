@@ -16,7 +16,7 @@ bool take_bad_combo();
 
 constexpr int NPMAX = 64;       // maximum Zolotarev poles
 constexpr int BX = 64;          // sites per block (x dimension of every site kernel)
-constexpr int NVRED = 2;        // doubles per (rhs, block) reduction partial
+constexpr int NVRED = 4;        // doubles per (rhs, block) reduction partial
 
 // A batch of spinor fields owned by the library.
 struct Field {
@@ -76,8 +76,8 @@ void launch_wilson_mscg_r(int pt, int plink, int pr, int pp, const Geom& g, doub
                           SpinorRef t, SpinorRef p0, SpinorRef r, int nrhs, double sigma0,
                           double* partials, const MsRhs* ms, cudaStream_t st);
 // out = c1 v + c2 (y - kappa hop y)  [= c1 v + c2 gamma5 K y], optionally times gamma5,
-// with optional partials {Re, Im} of (w, out). coef (device, may be null) holds per-rhs
-// (c1, c2) pairs that replace c1, c2.
+// with optional partials {Re (w, out), Im (w, out), ||out||^2, ||w||^2}. coef (device,
+// may be null) holds per-rhs (c1, c2) pairs that replace c1, c2.
 void launch_wilson_ovl(int py, int plink, int pv, const Geom& g, double kappa, LinkRef links, SpinorRef y,
                        SpinorRef v, SpinorRef out, SpinorRef w, int nrhs, double c1, double c2,
                        const double* coef, int herm, double* partials, cudaStream_t st);
@@ -112,7 +112,7 @@ void launch_axpby(int p, const double* a, const double* b, SpinorRef x, SpinorRe
 void launch_dot(int px, SpinorRef x, int py, SpinorRef y, int nrhs, int V, double* partials, cudaStream_t st);
 // partials {||x||^2, 0}
 void launch_norm2(int px, SpinorRef x, int nrhs, int V, double* partials, cudaStream_t st);
-// Sum partials over blocks per rhs in a fixed order: out[rhs*NVRED + j].
+// Sum partials over blocks per rhs in a fixed order: out[rhs*NVRED + j], j < NVRED.
 void launch_reduce_partials(const double* partials, int nsb, int nrhs, double* out, cudaStream_t st);
 // x = gamma5 x
 void launch_gamma5(int p, SpinorRef x, int nrhs, int V, cudaStream_t st);

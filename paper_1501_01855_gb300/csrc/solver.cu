@@ -15,6 +15,7 @@
 //    eps ||b|| / ||r|| relative to ||u||.
 //  * eigSUMR (Algs. 5-6) and the deflated starts of Sec. 4.
 #include <stdio.h>
+#include <stdlib.h>
 #include <string.h>
 
 #include <algorithm>
@@ -27,7 +28,15 @@
 
 namespace ovl {
 
-static inline cd c2(const double* p) { return cd(p[0], p[1]); }
+// OVL_LOG=1 in the environment prints one line per outer step and per middle-solve step.
+static int log_level() {
+  static int lv = -1;
+  if (lv < 0) {
+    const char* e = getenv("OVL_LOG");
+    lv = e ? atoi(e) : 0;
+  }
+  return lv;
+}
 
 // ------------------------------------------------------------------ helpers
 ovl_status dots_batch(ovl_ctx* c, const Field& x, int xoff, const Field& y, int yoff, int n, std::vector<cd>& out) {
@@ -302,7 +311,7 @@ ovl_status sumr_batch(ovl_ctx* c, const SumrCfg& cfg, int n, const std::vector<d
   }
   std::vector<double> sc(18 * n);
   std::vector<double> act_d(n);
-  std::vector<double> eta(n), dots(2 * n);
+  std::vector<double> eta(n), dots(4 * n);
   int* d_act = c->dint;
   for (int iter = 0; iter < cfg.maxit; ++iter) {
     int nact = 0;
@@ -317,12 +326,13 @@ ovl_status sumr_batch(ovl_ctx* c, const SumrCfg& cfg, int n, const std::vector<d
       double e = cfg.relax * cfg.target * bnorm[j] / std::max(r, 1e-300);
       e = std::min(e, cfg.floor);
       if (cfg.eta_cap > 0) e = std::min(e, cfg.eta_cap);
+      if (cfg.eta_fixed > 0) e = cfg.eta_fixed;
       eta[j] = e;
       emin = std::min(emin, e);
     }
     if (nact == 0) break;
     const int mode = cfg.mode >= 0 ? cfg.mode : choose_mode(c, emin);
-    // u = V q = gamma5 eps(K) q, fused with (q~, u)
+    // u = V q = gamma5 eps(K) q, fused with (q~, u), ||u||^2, ||q~||^2
     SignStats ss;
     OVL_TRY(sign_op(c, mode, *fq, 0, *fu, 0, n, eta.data(), 0.0, 1.0, nullptr, 0, fqt, 0, dots.data(), &ss));
     for (int j = 0; j < n; ++j)
@@ -338,16 +348,22 @@ ovl_status sumr_batch(ovl_ctx* c, const SumrCfg& cfg, int n, const std::vector<d
       hact[j] = S[j].active ? 1 : 0;
       if (!S[j].active) continue;
       St& s = S[j];
-      const cd gam = -cd(dots[2 * j], dots[2 * j + 1]);
-      const double g2 = std::norm(gam);
-      if (!(g2 < 1.0) || !std::isfinite(g2)) {
-        // Alg. 1 breaks down (inexact sign): stop this system, the outer loop continues
+      // Alg. 1 with the sign applied inexactly: gamma_j is the projection coefficient of
+      // u on q~_j and sigma_j = ||u + gamma_j q~_j||, so that V q_j = sigma_j q_{j+1} - gamma_j q~_j
+      // holds for the computed vectors; with an exact (unitary) sign this is
+      // gamma_j = -(q~_j, u) and sigma_j = sqrt(1 - |gamma_j|^2) of Alg. 1.
+      const cd qtu(dots[4 * j], dots[4 * j + 1]);
+      const double uu = dots[4 * j + 2], tt = dots[4 * j + 3];
+      const cd gam = tt > 0 ? -qtu / tt : cd(0.0);
+      const double s2 = uu - std::norm(qtu) / std::max(tt, 1e-300);
+      if (!(s2 > 1e-24 * std::max(uu, 1e-300)) || !std::isfinite(s2)) {
+        // Krylov space exhausted or a non-finite sign: stop this system here
         s.active = false;
         hact[j] = 0;
         res.stopped[j] = 2;
         continue;
       }
-      const double sig = std::sqrt(1.0 - g2);
+      const double sig = std::sqrt(s2);
       cd a, Rm1, zm1;
       if (s.it == 0) {
         s.zeta = 1.0;
@@ -370,6 +386,11 @@ ovl_status sumr_batch(ovl_ctx* c, const SumrCfg& cfg, int n, const std::vector<d
       for (int k = 0; k < 9; ++k) {
         o[2 * k] = vals[k].real();
         o[2 * k + 1] = vals[k].imag();
+      }
+      if (log_level() >= 3) {
+        fprintf(stderr, "  sumr sys %d it %d vals", j, s.it + 1);
+        for (int k = 0; k < 9; ++k) fprintf(stderr, " (%.6f,%.6f)", vals[k].real(), vals[k].imag());
+        fprintf(stderr, "\n");
       }
       s.cprev = cc;
       s.sprev = ss_;
@@ -394,7 +415,11 @@ ovl_status sumr_batch(ovl_ctx* c, const SumrCfg& cfg, int n, const std::vector<d
       if (!hact[j]) continue;
       St& s = S[j];
       res.resid[j] = std::abs(s.ghat);
+      if (cfg.hist) cfg.hist[j].push_back(std::abs(s.ghat) / bnorm[j]);
       const double qnorm = std::sqrt(std::max(0.0, qn[2 * j]));
+      if (log_level() >= 2)
+        fprintf(stderr, "  sumr sys %d it %d |r|/|b| %.3e eta %.2e mode %d |q| %.6f gamma %.4f%+.4fi\n", j, s.it,
+                std::abs(s.ghat) / bnorm[j], eta[j], mode, qnorm, s.gprev.real(), s.gprev.imag());
       if (std::abs(s.ghat) <= cfg.target * bnorm[j]) {
         s.active = false;
       } else if (std::fabs(qnorm - 1.0) > cfg.qdrift) {
@@ -637,6 +662,10 @@ ovl_status gmresr_batch(ovl_ctx* c, int n, const std::vector<double>& mus, const
       OVL_TRY(axpby_batch(c, one, *fr, 0, mal, *fC, k * n, *fr, 0, n));
     }
     OVL_TRY(norms_batch(c, *fr, 0, n, rn));
+    if (log_level() >= 1)
+      for (int j = 0; j < n; ++j)
+        fprintf(stderr, "gmresr step %d sys %d |r|/|b| %.3e middle iters %d stopped %d |u| nu %.3e alpha %.3e%+.3ei\n",
+                k, j, rn[j] / bn[j], sr.iters[j], sr.stopped[j], nu[j], alpha[j].real(), alpha[j].imag());
     for (int j = 0; j < n; ++j)
       if (active[j]) {
         outer[j] += 1;

@@ -20,6 +20,8 @@ struct SumrCfg {
   int maxit = 1000;
   int mode = -1;           // sign precision, -1: chosen by eta
   double qdrift = 0.1;     // stop when | ||q|| - 1 | exceeds this
+  double eta_fixed = 0.0;  // >0: apply the sign at this accuracy every iteration (no relaxation)
+  std::vector<double>* hist = nullptr;   // residual estimates ||r_j|| / ||b||, appended per iteration
   ovl_defl* defl = nullptr;
   SumrHook hook = nullptr;
   void* hook_data = nullptr;
