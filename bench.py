@@ -1,0 +1,405 @@
+#!/usr/bin/env python
+"""Benchmark of the overlap hot path on GB300.
+
+Workload (the overlap-apply configuration): D(mu) v = 1/2 (1 + mu + (1 - mu) gamma5 sign(K)) v
+on a 16^3 x 32 lattice with smooth random SU(3) links (eps = 0.3, seed 1002), m0 = 1.4,
+mu = 0.05, 20 Zolotarev poles with Delta <= 1e-10, applied to 16 Gaussian vectors per
+step with the sign function evaluated to eta = 1e-10 (the FP64 multi-shift CG, because an
+FP32 sign cannot reach 1e-10). Inputs are resident in HBM when the timed region starts;
+16 input vectors plus 20 x 16 pole vectors (8 GB) exceed the 126 MB L2.
+
+One JSON line on rank 0:
+  value      applies/s over all ranks (device-resident inputs, CUDA events)
+  e2e        the same through the C ABI with host buffers (copies inside the timed region)
+  roofline   the dominant kernel of the timed region, from CUDA events recorded by the
+             library around every launch while the step runs
+  cpu_baseline  the oracle (plain NumPy, per-pole CG) on this host, extrapolated from a
+             bounded sample
+  extras     FP32 / FP16-storage applies with their error against the FP64 result,
+             Wilson-kernel bandwidth on 24^3 x 48, and one right-hand-side solve to 1e-10
+             (mixed GMRESR(relSUMR) and plain FP64)
+
+python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+Under torchrun each rank runs an independent replica on its own GPU (the path
+shards by right-hand sides; weak scaling, no collective on the data path).
+"""
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import numpy as np
+
+DIMS = (16, 16, 16, 32)
+M0, MU, NPOLES, EPS = 1.4, 0.05, 20, 1e-10
+NVEC = 16
+LINK_SEED, SRC_SEED = 1002, 2002
+WILSON_FLOPS_PER_SITE = 1320          # conventional count of the hopping term
+FP64_NOMINAL_TFLOPS = 1.25            # GB300 FP64 (nominal; the ALU roofline of the FP64 kernel)
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            p = json.load(f)
+        return float(p["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+# ------------------------------------------------------------------ distributed
+def dist_setup():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if ws > 1:
+        import torch
+        import torch.distributed as dist
+        backend = "nccl" if torch.cuda.is_available() else "gloo"
+        if torch.cuda.is_available():
+            torch.cuda.set_device(local)
+        dist.init_process_group(backend=backend)
+    return ws, rank, local
+
+
+def barrier(ws):
+    if ws > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def max_over_ranks(x, ws):
+    if ws == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device="cuda" if torch.cuda.is_available() else "cpu")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+# ------------------------------------------------------------------ clocks
+class Clocks:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.FIELDS,
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax.append(float(f[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        os.unlink(self.path)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ------------------------------------------------------------------ oracle baseline
+def oracle_baseline(budget_s=20.0):
+    """The oracle (per-pole plain CG, NumPy) timed on this host on a bounded sample:
+    a fixed number of CG iterations of one pole on the 16^3x32 workload gives the cost
+    of one K application; the number of K applications of a full apply at the same
+    accuracy is counted by running the oracle's per-pole CG to completion on a 4^4
+    lattice of the same ensemble type (spectral bounds from ARPACK on its K^2)."""
+    import synth
+    from oracle import wilson, zolotarev as zo, overlap
+    try:
+        cores = len(os.sched_getaffinity(0))
+    except Exception:
+        cores = os.cpu_count() or 1
+    from scipy.sparse.linalg import LinearOperator, eigsh
+    # iteration counts of a full oracle apply at eta = 1e-10 (small lattice, same ensemble);
+    # spectral bounds of |K| from ARPACK on the oracle's K^2, with the library's margins
+    dims_s = (4, 4, 4, 4)
+    Us = synth.gauge_links(dims_s, 0.3, LINK_SEED)
+    vs = synth.gaussian_source(dims_s, SRC_SEED)
+    K = lambda v: wilson.apply_K(Us, v, M0)
+    shp = vs.shape
+    n = vs.size
+    K2 = LinearOperator((n, n), matvec=lambda x: K(K(x.reshape(shp))).ravel(), dtype=np.complex128)
+    lmax = eigsh(K2, k=1, which="LA", tol=1e-6, return_eigenvectors=False)[0]
+    c0 = 1.05 * lmax
+    Ksh = LinearOperator((n, n), matvec=lambda x: c0 * x - K(K(x.reshape(shp))).ravel(), dtype=np.complex128)
+    lmin = c0 - eigsh(Ksh, k=1, which="LA", tol=1e-6, return_eigenvectors=False)[0]
+    a, b = 0.95 * np.sqrt(max(lmin, 1e-6)), 1.05 * np.sqrt(lmax)
+    om, sg, _ = zo.zolotarev(NPOLES, a, b)
+    iters = []
+    for s in sg:
+        _, it = overlap.cg(lambda p, s=s: K(K(p)) + s * p, vs, 1e-11)
+        iters.append(it)
+    n_k_full = 2 * sum(iters) + 1
+    # cost of one K application (plus its CG vector work) on the 16^3x32 workload
+    U = synth.gauge_links(DIMS, 0.3, LINK_SEED)
+    v = synth.gaussian_source(DIMS, SRC_SEED)
+    t0 = time.perf_counter()
+    n_k = 0
+    x = np.zeros_like(v)
+    r = v.copy()
+    p = r.copy()
+    rr = np.vdot(r, r).real
+    K16 = lambda w: wilson.apply_K(U, w, M0)
+    while time.perf_counter() - t0 < budget_s or n_k < 4:
+        Ap = K16(K16(p)) + sg[0] * p      # one CG step of the base pole
+        alpha = rr / np.vdot(p, Ap).real
+        x += alpha * p
+        r -= alpha * Ap
+        rr2 = np.vdot(r, r).real
+        p = r + (rr2 / rr) * p
+        rr = rr2
+        n_k += 2
+    dt = time.perf_counter() - t0
+    t_apply = dt / n_k * n_k_full
+    return {"value": NVEC / (NVEC * t_apply), "unit": "applies/s", "cores": 1,
+            "kind": "oracle",
+            "sample": "%d K applications of the per-pole CG on 16^3x32 in %.1f s; a full apply at "
+                      "eta=1e-10 needs %d (per-pole CG iteration counts of the oracle on 4^4 of the same ensemble); "
+                      "NumPy einsum runs on one core (host has %d)" % (n_k, dt, n_k_full, cores),
+            "seconds_per_apply": t_apply}
+
+
+# ------------------------------------------------------------------ ours
+def run_ours(args, ws, rank, local):
+    import torch
+    import synth
+    from paper_1501_01855_gb300 import build, binding as B
+
+    build.build()
+    dev = torch.device("cuda", local)
+    torch.cuda.set_device(dev)
+    stream = torch.cuda.current_stream(dev)
+    U = synth.gauge_links(DIMS, 0.3, LINK_SEED)
+    vecs = synth.gaussian_source(DIMS, SRC_SEED + rank, nvec=NVEC)
+    p = B.ovl_params_default()
+    p.stream = stream.cuda_stream
+    ctx = B.Overlap(DIMS, U, M0, MU, NPOLES, EPS, params=p)
+    om, sg, delta, a, b = ctx.zolotarev()
+    dv = torch.from_numpy(vecs).to(dev)
+    dout = torch.empty_like(dv)
+    step = lambda: ctx.apply(dv, dout, eta=EPS, prec=B.OVL_PREC_F64)
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    barrier(ws)
+    clk = Clocks(local)
+    clk.start()
+    ctx.profile_reset()
+    ctx.profile_enable(True)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for _ in range(args.steps):
+        step()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ctx.profile_enable(False)
+    clocks = clk.stop()
+    ms_total = e0.elapsed_time(e1)
+    prof = ctx.profile_get()
+    barrier(ws)
+    ms_total = max_over_ranks(ms_total, ws)
+    value = ws * NVEC * args.steps / (ms_total * 1e-3)
+
+    # end to end through the C ABI with host buffers
+    hv = np.ascontiguousarray(vecs)
+    hout = np.empty_like(hv)
+    torch.cuda.synchronize()
+    barrier(ws)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        ctx.apply(hv, hout, eta=EPS, prec=B.OVL_PREC_F64)
+    torch.cuda.synchronize()
+    te = max_over_ranks(time.perf_counter() - t0, ws)
+    nbytes = hv.nbytes
+    e2e = {"value": ws * NVEC * args.steps / te, "unit": "applies/s", "h2d_bytes_per_step": nbytes,
+           "d2h_bytes_per_step": nbytes}
+
+    # roofline of the dominant kernel class of the timed region
+    hbm, hbm_src = peaks()
+    dom = max(prof, key=lambda k: prof[k]["ms"])
+    d = prof[dom]
+    if dom == "wilson_f64":
+        ach = d["units"] * WILSON_FLOPS_PER_SITE / (d["ms"] * 1e-3) / 1e12
+        roof = {"kernel": "wilson_kernel (FP64, msCG steps + final sign/overlap epilogue)", "bound": "alu",
+                "achieved": ach, "peak": FP64_NOMINAL_TFLOPS, "unit": "TFLOP/s", "frac": ach / FP64_NOMINAL_TFLOPS,
+                "traffic": None, "peak_source": "GB300 nominal FP64 (1.25 TFLOP/s)",
+                "launches": d["launches"], "avg_launch_ms": d["ms"] / max(1, d["launches"]),
+                "share_of_step": d["ms"] / ms_total if ws == 1 else None}
+    else:
+        ach = d["bytes"] / (d["ms"] * 1e-3) / 1e9
+        roof = {"kernel": dom, "bound": "hbm", "achieved": ach, "peak": hbm, "unit": "GB/s", "frac": ach / hbm,
+                "traffic": None, "peak_source": hbm_src, "launches": d["launches"],
+                "avg_launch_ms": d["ms"] / max(1, d["launches"])}
+    launches = int(sum(v["launches"] for v in prof.values()))
+
+    line = {
+        "metric": "overlap D applies/s & RHS solves/s at 1e-10; Dslash HBM GB/s vs plain FP64",
+        "value": value, "unit": "applies/s", "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": ms_total / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": "overlap D(mu) apply, 16^3x32, m0=1.4, mu=0.05, 20 Zolotarev poles, eta=1e-10, "
+                               "16 Gaussian vectors per step",
+                   "lattice": "16x16x16x32", "links": "proj_SU3(exp(i 0.3 H)), seed 1002", "n_poles": NPOLES,
+                   "zolotarev_delta": delta, "bounds": [a, b], "sign_precision": "fp64", "nvec": NVEC,
+                   "l2": "inputs larger than L2 (16 x 25 MB vectors, 8 GB pole vectors per step)",
+                   "parallelism": "replicas" if ws > 1 else "single GPU"},
+        "e2e": e2e, "roofline": roof, "gpu_launches": launches, "clocks": clocks,
+        "profile": {k: {"launches": v["launches"], "ms": round(v["ms"], 3)} for k, v in prof.items() if v["launches"]},
+    }
+    ref_out = dout.cpu().numpy()
+
+    if rank == 0 and not args.no_extras:
+        line["extras"] = extras(args, ctx, dv, dout, ref_out, B, torch, stream, hbm)
+    ctx.close()
+    if rank == 0 and ws == 1 and not args.no_cpu:
+        line["cpu_baseline"] = oracle_baseline(args.cpu_budget)
+    return line
+
+
+def extras(args, ctx, dv, dout, ref_out, B, torch, stream, hbm):
+    import synth
+    out = {}
+    # mixed-precision applies: FP32 sign at eta=1e-6, FP16 storage at eta=1e-2
+    for name, prec, eta in (("fp32_eta1e-6", B.OVL_PREC_F32, 1e-6), ("fp16_eta1e-2", B.OVL_PREC_F16, 1e-2)):
+        ctx.apply(dv, dout, eta=eta, prec=prec)
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        reps = 3
+        for _ in range(reps):
+            ctx.apply(dv, dout, eta=eta, prec=prec)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / reps
+        got = dout.cpu().numpy()
+        err = max(np.linalg.norm(got[j] - ref_out[j]) / np.linalg.norm(ref_out[j]) for j in range(NVEC))
+        out[name] = {"applies_per_s": NVEC / (ms * 1e-3), "max_rel_error_vs_fp64": err}
+    # Wilson kernel bandwidth on 24^3x48 (working set larger than L2)
+    dims = (24, 24, 24, 48)
+    p = B.ovl_params_default()
+    p.a_override, p.b_override = 0.2, 2.6
+    p.stream = stream.cuda_stream
+    cw = B.Overlap(dims, synth.unit_links(dims), M0, MU, 8, 1e-3, params=p)
+    ds = {}
+    for prec, nm in ((0, "f64"), (1, "f32"), (2, "f16")):
+        for n in (1, 12):
+            ms, by = cw.bench_wilson(prec, n, 40 if n == 1 else 8)
+            gbs = by / (ms * 1e-3) / 1e9
+            ds["%s_n%d" % (nm, n)] = {"ms": ms, "GB/s": gbs, "frac_hbm": gbs / hbm,
+                                     "Gsites/s": 663552 * n / (ms * 1e-3) / 1e9}
+    cw.close()
+    out["wilson_24x24x24x48"] = ds
+    # one RHS solve to 1e-10: mixed GMRESR(relSUMR) vs plain FP64
+    U = synth.gauge_links(DIMS, 0.3, LINK_SEED)
+    b = synth.gaussian_source(DIMS, 3002)
+    sol = {}
+    for nm, mixed in (("mixed_relSUMR", 1), ("plain_fp64_relSUMR", 0)):
+        p = B.ovl_params_default()
+        p.mixed = mixed
+        p.stream = stream.cuda_stream
+        cs = B.Overlap(DIMS, U, M0, MU, NPOLES, EPS, params=p)
+        x = np.zeros_like(b)
+        cs.solve(b, x, 1e-10)             # warm-up (allocations)
+        t0 = time.perf_counter()
+        info = cs.solve(b, x, 1e-10)[0]
+        dt = time.perf_counter() - t0
+        sol[nm] = {"seconds": dt, "solves_per_s": 1.0 / dt, "true_residual": info["true_residual"],
+                   "outer": info["outer_iters"], "inner": info["inner_iters"],
+                   "wilson_calls_dp2": info["wilson_calls"]}
+        cs.close()
+    out["solve_16x16x16x32_mu0.05"] = sol
+    return out
+
+
+def run_reference(args, ws, rank):
+    if rank != 0:
+        return None
+    samples = []
+    for i in range(args.warmup + args.steps):
+        r = oracle_baseline(budget_s=args.cpu_budget / 4)
+        if i >= args.warmup:
+            samples.append(r)
+    t = sum(s["seconds_per_apply"] for s in samples) / len(samples)
+    value = 1.0 / t
+    cpu = dict(samples[-1])
+    cpu["value"] = value
+    cpu.pop("seconds_per_apply", None)
+    return {"metric": "overlap D applies/s & RHS solves/s at 1e-10; Dslash HBM GB/s vs plain FP64",
+            "impl": "reference", "value": value, "unit": "applies/s", "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": t * 1e3, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": "overlap D(mu) apply, 16^3x32, m0=1.4, mu=0.05, 20 Zolotarev poles, eta=1e-10",
+                       "implementation": "oracle (NumPy, per-pole plain CG) on the host cores, bounded sample "
+                                         "per step, extrapolated to one full apply"},
+            "cpu_baseline": cpu,
+            "e2e": {"value": value, "unit": "applies/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-extras", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--cpu-budget", type=float, default=20.0)
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    ws, rank, local = dist_setup()
+    if args.impl == "reference":
+        line = run_reference(args, ws, rank)
+    else:
+        line = run_ours(args, ws, rank, local)
+    if rank == 0 and line is not None:
+        print(json.dumps(line), flush=True)
+    if ws > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -200,6 +200,9 @@ enum { OVL_PROF_CLASSES = 8 };
 ovl_status ovl_profile_enable(ovl_ctx* ctx, int on);
 ovl_status ovl_profile_reset(ovl_ctx* ctx);
 ovl_status ovl_profile_get(ovl_ctx* ctx, int cls, long long* launches, double* ms, double* bytes);
+/* Work units of a class since the last reset: site applications for the Wilson
+ * classes (one site of one system through K), site passes for the multi-shift update. */
+ovl_status ovl_profile_units(ovl_ctx* ctx, int cls, double* units);
 
 /* Run `iters` back-to-back Wilson-kernel launches on the library's own device
  * fields (n spinors, precision prec) and report the mean milliseconds per launch

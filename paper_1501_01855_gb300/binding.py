@@ -82,6 +82,7 @@ _SIGS = {
     "ovl_profile_enable": (I, [P, I]),
     "ovl_profile_reset": (I, [P]),
     "ovl_profile_get": (I, [P, I, LLP, DP, DP]),
+    "ovl_profile_units": (I, [P, I, DP]),
     "ovl_bench_wilson": (I, [P, I, I, I, DP, DP]),
 }
 
@@ -293,7 +294,9 @@ class Overlap:
             n = ctypes.c_longlong()
             ms, by = ctypes.c_double(), ctypes.c_double()
             _check(load().ovl_profile_get(self.h, c, ctypes.byref(n), ctypes.byref(ms), ctypes.byref(by)), self.h)
-            out[PROF_NAMES[c]] = {"launches": n.value, "ms": ms.value, "bytes": by.value}
+            u = ctypes.c_double()
+            _check(load().ovl_profile_units(self.h, c, ctypes.byref(u)), self.h)
+            out[PROF_NAMES[c]] = {"launches": n.value, "ms": ms.value, "bytes": by.value, "units": u.value}
         return out
 
     def bench_wilson(self, prec, n, iters):

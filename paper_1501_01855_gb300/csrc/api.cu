@@ -666,6 +666,7 @@ extern "C" ovl_status ovl_profile_reset(ovl_ctx* c) {
     c->prof.launches[k] = 0;
     c->prof.ms[k] = 0;
     c->prof.bytes[k] = 0;
+    c->prof.units[k] = 0;
   }
   c->wcalls[0] = c->wcalls[1] = c->wcalls[2] = 0;
   return OVL_OK;
@@ -676,6 +677,13 @@ extern "C" ovl_status ovl_profile_get(ovl_ctx* c, int cls, long long* launches, 
   if (launches) *launches = c->prof.launches[cls];
   if (ms) *ms = c->prof.ms[cls];
   if (bytes) *bytes = c->prof.bytes[cls];
+  return OVL_OK;
+}
+
+extern "C" ovl_status ovl_profile_units(ovl_ctx* c, int cls, double* units) {
+  if (!c || cls < 0 || cls >= OVL_PROF_CLASSES || !units) return OVL_EINVAL;
+  prof_flush(c);
+  *units = c->prof.units[cls];
   return OVL_OK;
 }
 

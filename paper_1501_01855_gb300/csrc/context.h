@@ -26,6 +26,7 @@ struct Profiler {
   long long launches[OVL_PROF_CLASSES] = {0};
   double ms[OVL_PROF_CLASSES] = {0};
   double bytes[OVL_PROF_CLASSES] = {0};
+  double units[OVL_PROF_CLASSES] = {0};
   std::vector<ProfPair> pending;
   std::vector<cudaEvent_t> pool;
 };

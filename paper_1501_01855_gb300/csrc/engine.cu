@@ -231,7 +231,10 @@ ovl_status import_spinors(ovl_ctx* c, const void* src, int dtype, int on_device,
     OVL_CUDA(c, cudaMemcpyAsync(tmp->data, c->hstage, bytes, cudaMemcpyHostToDevice, c->st));
     dsrc = tmp->data;
   }
+  ProfPair pp;
+  prof_begin(c, 4, &pp);
   launch_pack(dtype, dsrc, dst.prec, dst.ref(off), n, c->V, c->st);
+  prof_end(c, &pp, (double)bytes + (double)n * c->V * spinor_bytes(dst.prec));
   OVL_TRY(check_launch(c, __func__));
   return OVL_OK;
 }
@@ -240,14 +243,20 @@ ovl_status export_spinors(ovl_ctx* c, void* dst, int dtype, int on_device, int n
   const size_t esz = dtype == OVL_C128 ? 16 : 8;
   const size_t bytes = esz * 12 * (size_t)c->V * n;
   if (on_device) {
+    ProfPair pp;
+    prof_begin(c, 4, &pp);
     launch_unpack(dtype, dst, src.prec, src.ref(off), n, c->V, c->st);
+    prof_end(c, &pp, (double)bytes + (double)n * c->V * spinor_bytes(src.prec));
     OVL_TRY(check_launch(c, __func__));
     return OVL_OK;
   }
   Field* tmp = nullptr;
   OVL_TRY(get_field(c, "io_canon", P64, (int)((bytes + 192 * (size_t)c->V - 1) / (192 * (size_t)c->V)), &tmp));
   OVL_TRY(ensure_stage(c, bytes));
+  ProfPair pp;
+  prof_begin(c, 4, &pp);
   launch_unpack(dtype, tmp->data, src.prec, src.ref(off), n, c->V, c->st);
+  prof_end(c, &pp, (double)bytes + (double)n * c->V * spinor_bytes(src.prec));
   OVL_CUDA(c, cudaMemcpyAsync(c->hstage, tmp->data, bytes, cudaMemcpyDeviceToHost, c->st));
   OVL_CUDA(c, cudaStreamSynchronize(c->st));
   memcpy(dst, c->hstage, bytes);
@@ -303,7 +312,9 @@ ovl_status sign_op(ovl_ctx* c, int mode, const Field& v, int voff, Field& out, i
   prof_begin(c, 4, &pp);
   launch_ms_init(v.prec, PR, PP, v.ref(voff), r->ref(), pb->ref(), y->ref(), np, n, V, c->partials, c->st);
   prof_end(c, &pp, (double)n * V * (spinor_bytes(v.prec) + 2 * spinor_bytes(PR) + np * spinor_bytes(PP)));
+  prof_begin(c, 5, &pp);
   launch_ms_scalar0(c->ms, c->partials, sh.nsb, n, c->dpoles, d_eta, c->P.mscg_max, c->st);
+  prof_end(c, &pp, 0.0);
   OVL_TRY(check_launch(c, __func__));
 
   std::vector<int> done(n, 0);
@@ -380,6 +391,9 @@ ovl_status sign_op(ovl_ctx* c, int mode, const Field& v, int voff, Field& out, i
     // y and the still-active pole vectors.
     c->prof.bytes[wcls] += (double)live * (4.0 * sbytes + 2.0 * rbytes) + 2.0 * lbytes * itmax;
     c->prof.bytes[3] += (double)live * 3.0 * rbytes + (double)(pr + pw) * sbytes;
+    // work units: site applications of the Wilson kernel, site passes of the update
+    c->prof.units[wcls] += (2.0 * (double)live + n) * V;
+    c->prof.units[3] += (double)live * V;
   }
   if (stats) {
     stats->iters = it;
