@@ -56,7 +56,9 @@ typedef enum {
 } ovl_status;
 
 enum { OVL_C128 = 0, OVL_C64 = 1 };                     /* spinor element types       */
-enum { OVL_PREC_F64 = 0, OVL_PREC_F32 = 1, OVL_PREC_F16 = 2, OVL_PREC_AUTO = -1 };
+/* OVL_PREC_F64E: FP64-accurate double-float ("hi + lo" of two floats, ~47-bit significand)
+ * computed on the FP32 pipes; storage the size of FP64. */
+enum { OVL_PREC_F64 = 0, OVL_PREC_F32 = 1, OVL_PREC_F16 = 2, OVL_PREC_F64E = 3, OVL_PREC_AUTO = -1 };
 enum { OVL_SOLVER_SUMR = 0, OVL_SOLVER_CG = 1 };
 
 typedef struct {
@@ -64,6 +66,8 @@ typedef struct {
   int    mixed;         /* 1: low-precision sign when eta allows (Sec. 3, mixed precision);
                            0: plain FP64 everywhere                                              */
   int    half_storage;  /* 1: FP16 links/vectors in the sign when eta >= half_switch            */
+  int    emulate_fp64;  /* 1: accurate signs (eta < sp_switch, or mixed = 0) in double-float on
+                           the FP32 pipes (OVL_PREC_F64E); 0: native FP64. Default 0          */
   double eta_floor;     /* sign accuracy never worse than this (Sec. 3): default 1e-2           */
   double sp_switch;     /* eta above which the FP32 sign is used: default 1e-6                  */
   double half_switch;   /* eta above which FP16 storage is used: default 2e-3                    */
@@ -196,7 +200,7 @@ ovl_status overlap_force(ovl_ctx* ctx, double mu, const void* phi, int dtype, in
  * enabled: per kernel class, launches, total milliseconds and algorithmic bytes.
  * Classes: 0 Wilson FP64, 1 Wilson FP32, 2 Wilson FP16-storage, 3 multi-shift
  * update, 4 vector ops, 5 reductions/scalars, 6 Gram/rotate, 7 force. */
-enum { OVL_PROF_CLASSES = 8 };
+enum { OVL_PROF_CLASSES = 9 };
 ovl_status ovl_profile_enable(ovl_ctx* ctx, int on);
 ovl_status ovl_profile_reset(ovl_ctx* ctx);
 ovl_status ovl_profile_get(ovl_ctx* ctx, int cls, long long* launches, double* ms, double* bytes);

@@ -17,10 +17,11 @@ LIB_PATH = os.path.join(_HERE, "liboverlap.so")
 OVL_OK, OVL_EINVAL, OVL_ENOMEM, OVL_ECUDA, OVL_ENOCONV, OVL_EBREAKDOWN, OVL_EAPPROX, OVL_ETIMEOUT = \
     0, -1, -2, -3, -4, -5, -6, -7
 OVL_C128, OVL_C64 = 0, 1
-OVL_PREC_F64, OVL_PREC_F32, OVL_PREC_F16, OVL_PREC_AUTO = 0, 1, 2, -1
+OVL_PREC_F64, OVL_PREC_F32, OVL_PREC_F16, OVL_PREC_F64E, OVL_PREC_AUTO = 0, 1, 2, 3, -1
 OVL_SOLVER_SUMR, OVL_SOLVER_CG = 0, 1
-OVL_PROF_CLASSES = 8
-PROF_NAMES = ["wilson_f64", "wilson_f32", "wilson_f16", "mscg_update", "vector", "scalar", "gram", "force"]
+OVL_PROF_CLASSES = 9
+PROF_NAMES = ["wilson_f64", "wilson_f32", "wilson_f16", "mscg_update", "vector", "scalar", "gram", "force",
+              "wilson_f64e"]
 
 STATUS_NAMES = {0: "OVL_OK", -1: "OVL_EINVAL", -2: "OVL_ENOMEM", -3: "OVL_ECUDA", -4: "OVL_ENOCONV",
                 -5: "OVL_EBREAKDOWN", -6: "OVL_EAPPROX", -7: "OVL_ETIMEOUT"}
@@ -34,6 +35,7 @@ class OvlError(RuntimeError):
 
 class ovl_params(ctypes.Structure):
     _fields_ = [("solver", ctypes.c_int), ("mixed", ctypes.c_int), ("half_storage", ctypes.c_int),
+                ("emulate_fp64", ctypes.c_int),
                 ("eta_floor", ctypes.c_double), ("sp_switch", ctypes.c_double), ("half_switch", ctypes.c_double),
                 ("eta_precond", ctypes.c_double), ("relax_factor", ctypes.c_double),
                 ("gmresr_max", ctypes.c_int), ("inner_max", ctypes.c_int), ("mscg_max", ctypes.c_int),

@@ -28,6 +28,7 @@ extern "C" ovl_status ovl_params_default(ovl_params* p) {
   p->solver = OVL_SOLVER_SUMR;
   p->mixed = 1;
   p->half_storage = 0;
+  p->emulate_fp64 = 0;
   p->eta_floor = 1e-2;
   p->sp_switch = 1e-6;
   p->half_switch = 2e-3;
@@ -51,11 +52,12 @@ extern "C" const char* overlap_last_error(const ovl_ctx* c) { return c ? c->err.
 
 // ---------------------------------------------------------------- create
 static void convert_links(const double* links, int V, std::vector<double>& l64, std::vector<float>& l32,
-                          std::vector<__half>& l16) {
+                          std::vector<__half>& l16, std::vector<float>& l64e) {
   // canonical [site][mu][row][col] complex -> [mu][chunk][V] keeping rows 0, 1
   l64.assign((size_t)4 * 6 * V * 2, 0.0);
   l32.assign((size_t)4 * 3 * V * 4, 0.f);
   l16.assign((size_t)4 * 3 * V * 4, __float2half(0.f));
+  l64e.assign((size_t)4 * 6 * V * 4, 0.f);
   for (int s = 0; s < V; ++s)
     for (int mu = 0; mu < 4; ++mu) {
       const double* u = links + ((size_t)s * 4 + mu) * 18;   // 9 complex
@@ -63,6 +65,11 @@ static void convert_links(const double* links, int V, std::vector<double>& l64, 
         const double re = u[2 * e], im = u[2 * e + 1];
         l64[(((size_t)mu * 6 + e) * V + s) * 2 + 0] = re;
         l64[(((size_t)mu * 6 + e) * V + s) * 2 + 1] = im;
+        const float rh = (float)re, ih = (float)im;
+        l64e[(((size_t)mu * 6 + e) * V + s) * 4 + 0] = rh;
+        l64e[(((size_t)mu * 6 + e) * V + s) * 4 + 1] = (float)(re - (double)rh);
+        l64e[(((size_t)mu * 6 + e) * V + s) * 4 + 2] = ih;
+        l64e[(((size_t)mu * 6 + e) * V + s) * 4 + 3] = (float)(im - (double)ih);
         const int ch = e / 2, w = e % 2;
         l32[(((size_t)mu * 3 + ch) * V + s) * 4 + 2 * w + 0] = (float)re;
         l32[(((size_t)mu * 3 + ch) * V + s) * 4 + 2 * w + 1] = (float)im;
@@ -125,7 +132,7 @@ extern "C" void overlap_destroy(ovl_ctx* c) {
   if (c->st) cudaStreamSynchronize(c->st);
   else cudaDeviceSynchronize();
   for (auto& kv : c->ws) free_field(kv.second);
-  for (int p = 0; p < 3; ++p)
+  for (int p = 0; p < 4; ++p)
     if (c->link[p]) cudaFree(c->link[p]);
   if (c->partials) cudaFree(c->partials);
   if (c->dred) cudaFree(c->dred);
@@ -157,6 +164,14 @@ static ovl_status create_impl(ovl_ctx* c, const int dims[4], const double* links
   c->V = (int)Vll;
   c->g.V = c->V;
   c->g.bc_t = c->P.bc_t ? 1 : 0;
+  // multiply-shift constants for site -> coordinate division (see common.cuh)
+  for (int d = 0; d < 3; ++d) {
+    int l = 0;
+    while ((1 << l) < dims[d]) ++l;
+    const int k = 31 + l;
+    c->g.dk[d] = k;
+    c->g.dm[d] = (((unsigned long long)1 << k) + (unsigned long long)dims[d] - 1) / (unsigned long long)dims[d];
+  }
   if (!(m0 > 0 && m0 < 4)) return set_err(c, OVL_EINVAL, "m0 must lie in (0, 4)");
   if (!(mu >= 0 && mu < 1)) return set_err(c, OVL_EINVAL, "mu must lie in [0, 1)");
   if (n_poles < 1 || n_poles > NPMAX) return set_err(c, OVL_EINVAL, "n_poles must lie in 1..64");
@@ -179,7 +194,10 @@ static ovl_status create_impl(ovl_ctx* c, const int dims[4], const double* links
     std::vector<double> l64;
     std::vector<float> l32;
     std::vector<__half> l16;
-    convert_links(links, c->V, l64, l32, l16);
+    std::vector<float> l64e;
+    convert_links(links, c->V, l64, l32, l16, l64e);
+    OVL_CUDA(c, cudaMalloc(&c->link[P64E], l64e.size() * sizeof(float)));
+    OVL_CUDA(c, cudaMemcpy(c->link[P64E], l64e.data(), l64e.size() * sizeof(float), cudaMemcpyHostToDevice));
     OVL_CUDA(c, cudaMalloc(&c->link[P64], l64.size() * sizeof(double)));
     OVL_CUDA(c, cudaMalloc(&c->link[P32], l32.size() * sizeof(float)));
     OVL_CUDA(c, cudaMalloc(&c->link[P16], l16.size() * sizeof(__half)));
@@ -267,7 +285,7 @@ static ovl_status check_io(ovl_ctx* c, const void* in, const void* out, int n, i
 extern "C" ovl_status ovl_wilson_apply(ovl_ctx* c, const void* in, void* out, int n, int dtype, int on_device,
                                        int prec) {
   OVL_TRY(check_io(c, in, out, n, dtype));
-  if (prec < P64 || prec > P16) return set_err(c, OVL_EINVAL, "prec must be OVL_PREC_F64, F32 or F16");
+  if (prec < P64 || prec > P64E) return set_err(c, OVL_EINVAL, "prec must be OVL_PREC_F64, F32, F16 or F64E");
   Field *fi, *fo;
   OVL_TRY(get_field(c, "api_wi", prec, n, &fi));
   OVL_TRY(get_field(c, "api_wo", prec, n, &fo));
@@ -287,7 +305,7 @@ extern "C" ovl_status ovl_sign_apply(ovl_ctx* c, const void* in, void* out, int 
   OVL_TRY(import_spinors(c, in, dtype, on_device, n, *fi, 0));
   const double e = eta > 0 ? eta : c->eps_sign;
   const int mode = prec == OVL_PREC_AUTO ? choose_mode(c, e) : prec;
-  if (mode < SIGN64 || mode > SIGN16) return set_err(c, OVL_EINVAL, "bad prec");
+  if (mode < SIGN64 || mode > SIGN64E) return set_err(c, OVL_EINVAL, "bad prec");
   std::vector<double> etas(n, e);
   OVL_TRY(sign_op(c, mode, *fi, 0, *fo, 0, n, etas.data(), 0.0, 1.0, nullptr, 1, nullptr, 0, nullptr, nullptr));
   OVL_TRY(export_spinors(c, out, dtype, on_device, n, *fo, 0));
@@ -305,7 +323,7 @@ extern "C" ovl_status overlap_apply(ovl_ctx* c, double mu, const void* in, void*
   OVL_TRY(import_spinors(c, in, dtype, on_device, n, *fi, 0));
   const double e = eta > 0 ? eta : c->eps_sign;
   const int mode = prec == OVL_PREC_AUTO ? choose_mode(c, e) : prec;
-  if (mode < SIGN64 || mode > SIGN16) return set_err(c, OVL_EINVAL, "bad prec");
+  if (mode < SIGN64 || mode > SIGN64E) return set_err(c, OVL_EINVAL, "bad prec");
   std::vector<double> mus(n, mu), etas(n, e);
   OVL_TRY(overlap_apply_batch(c, *fi, 0, *fo, 0, n, mus, etas, hermitian ? 1 : 0, mode, nullptr));
   OVL_TRY(export_spinors(c, out, dtype, on_device, n, *fo, 0));
@@ -433,7 +451,7 @@ static ovl_status defl_alloc(ovl_ctx* c, ovl_defl* d, int prec, int cap) {
     f.prec = prec;
     f.V = c->V;
     f.n = cap;
-    if (cudaMalloc(&f.data, (size_t)(prec == P64 ? 192 : 96) * c->V * cap) != cudaSuccess) {
+    if (cudaMalloc(&f.data, (size_t)spinor_site_bytes(prec) * c->V * cap) != cudaSuccess) {
       cudaGetLastError();
       f.data = nullptr;
       return set_err(c, OVL_ENOMEM, "cudaMalloc failed for the deflation space");
@@ -512,7 +530,12 @@ extern "C" ovl_status eigsumr_accumulate(ovl_ctx* c, ovl_defl** defl, int n_eig,
   std::vector<double> mus(1, mu);
   // the deflation held so far accelerates this solve too; the space is rebuilt after it
   ovl_defl* use = (!fresh && d->n > 0) ? d : nullptr;
+  // the accumulation rides on SUMR's Krylov basis (Alg. 5), whatever middle solver the
+  // context uses for ordinary solves; the space itself (eigenvectors of D^dag D) serves both
+  const int solver_keep = c->P.solver;
+  c->P.solver = OVL_SOLVER_SUMR;
   ovl_status st = gmresr_batch(c, 1, mus, *fb, 0, *fx, 0, tol, use, info, &hook);
+  c->P.solver = solver_keep;
   if (st != OVL_OK && st != OVL_ENOCONV) {
     if (fresh) ovl_defl_destroy(d);
     return st;
@@ -520,6 +543,10 @@ extern "C" ovl_status eigsumr_accumulate(ovl_ctx* c, ovl_defl** defl, int n_eig,
   // final Ritz step over whatever the basis holds
   if (e.k > e.n_seeded || e.ndiag == 0) OVL_TRY(ritz_step(c, &e, n_eig));
   const int nk = e.k;
+  if (nk < 1) {
+    if (fresh) ovl_defl_destroy(d);
+    return set_err(c, OVL_ENOCONV, "eigSUMR collected no basis vectors (the solve needed no SUMR step)");
+  }
   // store, then recompute w = V psi accurately (Sec. 5.1: recalculate v^D after the
   // eigenvector calculation when the space is used by SUMR)
   if (d->cap < nk) return set_err(c, OVL_EINVAL, "internal: deflation capacity");
@@ -689,7 +716,7 @@ extern "C" ovl_status ovl_profile_units(ovl_ctx* c, int cls, double* units) {
 
 extern "C" ovl_status ovl_bench_wilson(ovl_ctx* c, int prec, int n, int iters, double* ms_per_launch,
                                        double* bytes_per_launch) {
-  if (!c || prec < P64 || prec > P16 || n < 1 || n > 256 || iters < 1) return OVL_EINVAL;
+  if (!c || prec < P64 || prec > P64E || n < 1 || n > 256 || iters < 1) return OVL_EINVAL;
   Field *fi, *fo;
   OVL_TRY(get_field(c, "bw_in", prec, n, &fi));
   OVL_TRY(get_field(c, "bw_out", prec, n, &fo));
@@ -715,8 +742,8 @@ extern "C" ovl_status ovl_bench_wilson(ovl_ctx* c, int prec, int n, int iters, d
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   OVL_TRY(check_launch(c, __func__));
-  const double sb = prec == P64 ? 192 : prec == P32 ? 96 : 48 + 4;
-  const double lb = prec == P64 ? 384 : prec == P32 ? 192 : 96;
+  const double sb = prec == P16 ? 52 : spinor_site_bytes(prec);
+  const double lb = (prec == P64 || prec == P64E) ? 384 : prec == P32 ? 192 : 96;
   if (ms_per_launch) *ms_per_launch = ms / iters;
   if (bytes_per_launch) *bytes_per_launch = (double)c->V * (2.0 * sb * n + lb);
   return OVL_OK;

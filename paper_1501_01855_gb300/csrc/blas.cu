@@ -43,6 +43,7 @@ template <typename CT>
 static void pack_t(const CT* canon, int p, SpinorRef out, int nrhs, int V, cudaStream_t st) {
   Shape sh = make_shape(V, nrhs);
   if (p == P64) pack_kernel<CT, P64><<<sh.grid(), sh.block(), 0, st>>>(canon, out, nrhs, V, sh.ngr);
+  else if (p == P64E) pack_kernel<CT, P64E><<<sh.grid(), sh.block(), 0, st>>>(canon, out, nrhs, V, sh.ngr);
   else if (p == P32) pack_kernel<CT, P32><<<sh.grid(), sh.block(), 0, st>>>(canon, out, nrhs, V, sh.ngr);
   else pack_kernel<CT, P16><<<sh.grid(), sh.block(), 0, st>>>(canon, out, nrhs, V, sh.ngr);
 }
@@ -50,6 +51,7 @@ template <typename CT>
 static void unpack_t(CT* canon, int p, SpinorRef in, int nrhs, int V, cudaStream_t st) {
   Shape sh = make_shape(V, nrhs);
   if (p == P64) unpack_kernel<CT, P64><<<sh.grid(), sh.block(), 0, st>>>(canon, in, nrhs, V, sh.ngr);
+  else if (p == P64E) unpack_kernel<CT, P64E><<<sh.grid(), sh.block(), 0, st>>>(canon, in, nrhs, V, sh.ngr);
   else if (p == P32) unpack_kernel<CT, P32><<<sh.grid(), sh.block(), 0, st>>>(canon, in, nrhs, V, sh.ngr);
   else unpack_kernel<CT, P16><<<sh.grid(), sh.block(), 0, st>>>(canon, in, nrhs, V, sh.ngr);
 }
@@ -83,6 +85,11 @@ void launch_convert(int pin, SpinorRef in, int pout, SpinorRef out, int nrhs, in
   else if (pin == P32 && pout == P16) CONV(P32, P16);
   else if (pin == P16 && pout == P32) CONV(P16, P32);
   else if (pin == P16 && pout == P64) CONV(P16, P64);
+  else if (pin == P64 && pout == P64E) CONV(P64, P64E);
+  else if (pin == P64E && pout == P64) CONV(P64E, P64);
+  else if (pin == P32 && pout == P64E) CONV(P32, P64E);
+  else if (pin == P64E && pout == P32) CONV(P64E, P32);
+  else if (pin == P64E && pout == P64E) CONV(P64E, P64E);
   else CONV(P16, P16);
 #undef CONV
 }
@@ -108,6 +115,7 @@ void launch_axpby(int p, const double* a, const double* b, SpinorRef x, SpinorRe
   Shape sh = make_shape(V, nrhs);
   if (p == P64) axpby_kernel<P64><<<sh.grid(), sh.block(), 0, st>>>(a, b, x, y, z, nrhs, V, sh.ngr);
   else if (p == P32) axpby_kernel<P32><<<sh.grid(), sh.block(), 0, st>>>(a, b, x, y, z, nrhs, V, sh.ngr);
+  else if (p == P64E) axpby_kernel<P64E><<<sh.grid(), sh.block(), 0, st>>>(a, b, x, y, z, nrhs, V, sh.ngr);
   else axpby_kernel<P16><<<sh.grid(), sh.block(), 0, st>>>(a, b, x, y, z, nrhs, V, sh.ngr);
 }
 
@@ -148,6 +156,9 @@ void launch_dot(int px, SpinorRef x, int py, SpinorRef y, int nrhs, int V, doubl
   else if (px == P32 && py == P32) DOT(P32, P32);
   else if (px == P64 && py == P32) DOT(P64, P32);
   else if (px == P32 && py == P64) DOT(P32, P64);
+  else if (px == P64E && py == P64E) DOT(P64E, P64E);
+  else if (px == P64 && py == P64E) DOT(P64, P64E);
+  else if (px == P64E && py == P64) DOT(P64E, P64);
   else DOT(P16, P16);
 #undef DOT
 }
@@ -155,6 +166,7 @@ void launch_norm2(int px, SpinorRef x, int nrhs, int V, double* partials, cudaSt
   Shape sh = make_shape(V, nrhs);
   if (px == P64) dot_kernel<P64, P64, true><<<sh.grid(), sh.block(), 0, st>>>(x, x, nrhs, V, sh.nsb, sh.ngr, partials);
   else if (px == P32) dot_kernel<P32, P32, true><<<sh.grid(), sh.block(), 0, st>>>(x, x, nrhs, V, sh.nsb, sh.ngr, partials);
+  else if (px == P64E) dot_kernel<P64E, P64E, true><<<sh.grid(), sh.block(), 0, st>>>(x, x, nrhs, V, sh.nsb, sh.ngr, partials);
   else dot_kernel<P16, P16, true><<<sh.grid(), sh.block(), 0, st>>>(x, x, nrhs, V, sh.nsb, sh.ngr, partials);
 }
 
@@ -203,10 +215,11 @@ void launch_gamma5(int p, SpinorRef x, int nrhs, int V, cudaStream_t st) {
   Shape sh = make_shape(V, nrhs);
   if (p == P64) gamma5_kernel<P64><<<sh.grid(), sh.block(), 0, st>>>(x, nrhs, V, sh.ngr);
   else if (p == P32) gamma5_kernel<P32><<<sh.grid(), sh.block(), 0, st>>>(x, nrhs, V, sh.ngr);
+  else if (p == P64E) gamma5_kernel<P64E><<<sh.grid(), sh.block(), 0, st>>>(x, nrhs, V, sh.ngr);
   else gamma5_kernel<P16><<<sh.grid(), sh.block(), 0, st>>>(x, nrhs, V, sh.ngr);
 }
 void launch_zero(int p, SpinorRef x, int nrhs, int V, cudaStream_t st) {
-  const size_t per = (size_t)V * (p == P64 ? 192 : p == P32 ? 96 : 48);
+  const size_t per = (size_t)V * spinor_site_bytes(p);
   cudaMemsetAsync(x.data, 0, per * nrhs, st);
   if (p == P16 && x.norm) cudaMemsetAsync(x.norm, 0, sizeof(float) * V * nrhs, st);
 }

@@ -33,7 +33,8 @@ struct Profiler {
 
 // Sign-function precision modes (Sec. 3: single precision when the required
 // accuracy allows; FP16 storage extends the same idea one step further).
-enum SignMode { SIGN64 = 0, SIGN32 = 1, SIGN16 = 2 };
+// SIGN64E: FP64-accurate sign computed in double-float on the FP32 pipes.
+enum SignMode { SIGN64 = 0, SIGN32 = 1, SIGN16 = 2, SIGN64E = 3 };
 
 struct SignStats {
   std::vector<int> iters;     // multi-shift CG iterations per system
@@ -53,7 +54,7 @@ struct ovl_ctx {
   ovl_params P;
   cudaStream_t st = nullptr;
   int device = 0;
-  void* link[3] = {nullptr, nullptr, nullptr};  // P64, P32, P16 12-real layouts
+  void* link[4] = {nullptr, nullptr, nullptr, nullptr};  // P64, P32, P16, P64E 12-real layouts
   ovl::Poles hpoles;
   ovl::Poles* dpoles = nullptr;
   std::map<std::string, ovl::Field> ws;
@@ -72,7 +73,7 @@ struct ovl_ctx {
   size_t ring_pos = 0;           // scalar upload ring in hpin / dscal, [32768, 262144)
   std::string err;
   ovl::Profiler prof;
-  long long wcalls[3] = {0, 0, 0};  // Wilson applications by precision
+  long long wcalls[4] = {0, 0, 0, 0};  // Wilson applications by precision
 };
 
 struct ovl_defl {

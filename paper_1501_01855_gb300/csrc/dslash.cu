@@ -124,10 +124,7 @@ template <int PIN, int PL, typename T>
 __device__ __forceinline__ void hop(const Geom& g, const LinkRef& L, const SpinorRef& in, int rhs, int s,
                                     cpx<T> acc[12]) {
   int x[4];
-  int t = s;
-  x[0] = t % g.L[0]; t /= g.L[0];
-  x[1] = t % g.L[1]; t /= g.L[1];
-  x[2] = t % g.L[2]; x[3] = t / g.L[2];
+  site_coords(g, s, x);
 #pragma unroll
   for (int k = 0; k < 12; ++k) acc[k] = cmk(T(0), T(0));
   const int sy = g.L[0], sz = g.L[0] * g.L[1], st = sz * g.L[2];
@@ -282,6 +279,7 @@ void launch_wilson_K(int pin, int plink, int pout, const Geom& g, double kappa, 
   else if (pin == P16 && plink == P16 && pout == P16) run<MODE_K, P16, P16, P16, P16, P16>(a, st);
   else if (pin == P32 && plink == P16 && pout == P32) run<MODE_K, P32, P16, P32, P32, P32>(a, st);
   else if (pin == P32 && plink == P16 && pout == P16) run<MODE_K, P32, P16, P16, P32, P32>(a, st);
+  else if (pin == P64E && plink == P64E && pout == P64E) run<MODE_K, P64E, P64E, P64E, P64E, P64E>(a, st);
   else OVL_BAD_COMBO();
 }
 
@@ -298,6 +296,7 @@ void launch_wilson_mscg_r(int pt, int plink, int pr, int pp, const Geom& g, doub
   if (pt == P64 && plink == P64 && pr == P64 && pp == P64) run<MODE_R, P64, P64, P64, P64, P64>(a, st);
   else if (pt == P32 && plink == P32 && pr == P32 && pp == P32) run<MODE_R, P32, P32, P32, P32, P32>(a, st);
   else if (pt == P16 && plink == P16 && pr == P32 && pp == P16) run<MODE_R, P16, P16, P32, P16, P32>(a, st);
+  else if (pt == P64E && plink == P64E && pr == P64E && pp == P64E) run<MODE_R, P64E, P64E, P64E, P64E, P64E>(a, st);
   else OVL_BAD_COMBO();
 }
 
@@ -320,6 +319,8 @@ void launch_wilson_ovl(int py, int plink, int pv, const Geom& g, double kappa, L
   else if (py == P32 && plink == P16 && pv == P32) run<MODE_OVL, P32, P16, P32, P32, P32>(a, st);
   else if (py == P32 && plink == P16 && pv == P64) run<MODE_OVL, P32, P16, P64, P64, P64>(a, st);
   else if (py == P64 && plink == P64 && pv == P32) run<MODE_OVL, P64, P64, P32, P32, P32>(a, st);
+  else if (py == P64E && plink == P64E && pv == P64) run<MODE_OVL, P64E, P64E, P64, P64, P64>(a, st);
+  else if (py == P64E && plink == P64E && pv == P32) run<MODE_OVL, P64E, P64E, P32, P32, P32>(a, st);
   else OVL_BAD_COMBO();
 }
 

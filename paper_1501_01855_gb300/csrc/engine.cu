@@ -45,7 +45,7 @@ ovl_status check_launch(ovl_ctx* c, const char* where) {
   return OVL_OK;
 }
 
-static size_t spinor_bytes(int prec) { return prec == P64 ? 192 : prec == P32 ? 96 : 48; }
+static size_t spinor_bytes(int prec) { return (size_t)spinor_site_bytes(prec); }
 
 void free_field(Field& f) {
   if (f.data) cudaFree(f.data);
@@ -265,18 +265,19 @@ ovl_status export_spinors(ovl_ctx* c, void* dst, int dtype, int on_device, int n
 
 // ---------------------------------------------------------------- sign function
 int choose_mode(const ovl_ctx* c, double eta) {
-  if (!c->P.mixed) return SIGN64;
+  const int accurate = c->P.emulate_fp64 ? SIGN64E : SIGN64;
+  if (!c->P.mixed) return accurate;
   if (c->P.half_storage && eta >= c->P.half_switch) return SIGN16;
   if (eta >= c->P.sp_switch) return SIGN32;
-  return SIGN64;
+  return accurate;
 }
 
 ovl_status sign_op(ovl_ctx* c, int mode, const Field& v, int voff, Field& out, int ooff, int n, const double* eta,
                    double c1, double c2, const double* coef, int herm, const Field* dot_w, int woff, double* dots,
                    SignStats* stats) {
   if (n <= 0) return OVL_OK;
-  const int PL = mode == SIGN64 ? P64 : mode == SIGN32 ? P32 : P16;
-  const int PR = mode == SIGN64 ? P64 : P32;
+  const int PL = mode == SIGN64 ? P64 : mode == SIGN32 ? P32 : mode == SIGN16 ? P16 : P64E;
+  const int PR = mode == SIGN64 ? P64 : mode == SIGN64E ? P64E : P32;
   const int PP = PL;
   const int V = c->V;
   const int np = c->npoles;
@@ -304,8 +305,8 @@ ovl_status sign_op(ovl_ctx* c, int mode, const Field& v, int voff, Field& out, i
   }
   OVL_CUDA(c, cudaMemcpyAsync(c->dscal, c->hpin, sizeof(double) * ncopy, cudaMemcpyHostToDevice, c->st));
   const LinkRef L = links_of(c, PL);
-  const int wcls = PL;  // profiler class of the Wilson launches
-  const double lbytes = (PL == P64 ? 384.0 : PL == P32 ? 192.0 : 96.0) * V;
+  const int wcls = PL == P64E ? 8 : PL;  // profiler class of the Wilson launches
+  const double lbytes = (PL == P64 || PL == P64E ? 384.0 : PL == P32 ? 192.0 : 96.0) * V;
   const double sbytes = (double)spinor_bytes(PP) * V, rbytes = (double)spinor_bytes(PR) * V;
   ProfPair pp;
 

@@ -25,10 +25,10 @@ struct Field {
   int V = 0;
   void* data = nullptr;
   float* norm = nullptr;
-  size_t chunk_bytes() const { return (size_t)n * V * (prec == P64 ? 192 : prec == P32 ? 96 : 48); }
+  size_t chunk_bytes() const { return (size_t)n * V * spinor_site_bytes(prec); }
   SpinorRef ref(int off = 0) const {
     SpinorRef r;
-    const size_t per = (size_t)V * (prec == P64 ? 192 : prec == P32 ? 96 : 48);
+    const size_t per = (size_t)V * spinor_site_bytes(prec);
     r.data = data ? (void*)((char*)data + per * off) : nullptr;
     r.norm = norm ? norm + (size_t)V * off : nullptr;
     r.V = V;

@@ -78,7 +78,7 @@ ovl_status axpby_batch(ovl_ctx* c, const std::vector<cd>& a, const Field& x, int
 
 ovl_status copy_convert(ovl_ctx* c, const Field& in, int ioff, Field& out, int ooff, int n) {
   if (in.prec == out.prec) {
-    const size_t per = (size_t)c->V * (in.prec == P64 ? 192 : in.prec == P32 ? 96 : 48);
+    const size_t per = (size_t)c->V * spinor_site_bytes(in.prec);
     OVL_CUDA(c, cudaMemcpyAsync((char*)out.data + per * ooff, (char*)in.data + per * ioff, per * n,
                                 cudaMemcpyDeviceToDevice, c->st));
     if (in.prec == P16)
@@ -103,7 +103,7 @@ ovl_status gram_host(ovl_ctx* c, const Field& A, int aoff, int na, const Field& 
   ProfPair pp;
   prof_begin(c, 6, &pp);
   launch_gram(A.prec, A.ref(aoff), na, B.prec, B.ref(boff), nb, c->V, dG, c->dwork, c->dwork_n - gsz, g5, c->st);
-  prof_end(c, &pp, (double)c->V * ((double)na * (A.prec == P64 ? 192 : 96) + (double)nb * (B.prec == P64 ? 192 : 96)));
+  prof_end(c, &pp, (double)c->V * ((double)na * spinor_site_bytes(A.prec) + (double)nb * spinor_site_bytes(B.prec)));
   OVL_TRY(check_launch(c, __func__));
   std::vector<double> h(gsz);
   OVL_CUDA(c, cudaMemcpyAsync(h.data(), dG, gsz * sizeof(double), cudaMemcpyDeviceToHost, c->st));
@@ -126,7 +126,7 @@ ovl_status combine_host(ovl_ctx* c, const Field& A, int aoff, int na, const std:
   ProfPair pp;
   prof_begin(c, 6, &pp);
   launch_combine(A.prec, A.ref(aoff), na, d, Y.prec, Y.ref(yoff), ny, c->V, add, c->st);
-  prof_end(c, &pp, (double)c->V * ((double)na * (A.prec == P64 ? 192 : 96) + (double)ny * (add + 1) * (Y.prec == P64 ? 192 : 96)));
+  prof_end(c, &pp, (double)c->V * ((double)na * spinor_site_bytes(A.prec) + (double)ny * (add + 1) * spinor_site_bytes(Y.prec)));
   OVL_TRY(check_launch(c, __func__));
   return OVL_OK;
 }
@@ -147,7 +147,7 @@ ovl_status overlap_apply_batch(ovl_ctx* c, const Field& v, int voff, Field& out,
   SignStats ss;
   OVL_TRY(sign_op(c, mode, v, voff, out, ooff, n, eta.data(), 0, 0, coef.data(), herm, nullptr, 0, nullptr, &ss));
   if (wcalls_out) {
-    for (int j = 0; j < n; ++j) wcalls_out[j] += (long long)(2 * ss.iters[j] + 1) * (mode == SIGN64 ? 2 : 1);
+    for (int j = 0; j < n; ++j) wcalls_out[j] += (long long)(2 * ss.iters[j] + 1) * (mode == SIGN64 || mode == SIGN64E ? 2 : 1);
   }
   return OVL_OK;
 }
@@ -262,6 +262,10 @@ ovl_status sumr_batch(ovl_ctx* c, const SumrCfg& cfg, int n, const std::vector<d
     std::vector<cd> co;
     OVL_TRY(defl_start(c, cfg.defl, *fq, 0, n, mus, co));
     const int ne = cfg.defl->n;
+    // co minimises ||b - D psi co||; this solve is for A = 2 D / (1 - mu), whose
+    // minimiser is (1 - mu)/2 co
+    for (int i = 0; i < ne; ++i)
+      for (int j = 0; j < n; ++j) co[(size_t)i * n + j] *= 0.5 * (1.0 - mus[j]);
     // x = psi co
     OVL_TRY(combine_host(c, cfg.defl->v, 0, ne, co, x, xoff, n, 0));
     // q -= A x0 = 2/(1-mu) ((1+mu)/2 psi co + (1-mu)/2 w co)
@@ -337,7 +341,7 @@ ovl_status sumr_batch(ovl_ctx* c, const SumrCfg& cfg, int n, const std::vector<d
     OVL_TRY(sign_op(c, mode, *fq, 0, *fu, 0, n, eta.data(), 0.0, 1.0, nullptr, 0, fqt, 0, dots.data(), &ss));
     for (int j = 0; j < n; ++j)
       if (S[j].active) {
-        res.wcalls[j] += (long long)(2 * ss.iters[j] + 1) * (mode == SIGN64 ? 2 : 1);
+        res.wcalls[j] += (long long)(2 * ss.iters[j] + 1) * (mode == SIGN64 || mode == SIGN64E ? 2 : 1);
         res.sign_calls[j] += 1;
       }
     if (cfg.hook) OVL_TRY(cfg.hook(c, cfg.hook_data, *fq, *fu, iter));
@@ -407,7 +411,7 @@ ovl_status sumr_batch(ovl_ctx* c, const SumrCfg& cfg, int n, const std::vector<d
     prof_begin(c, 4, &pp);
     launch_sumr_update(PS, dsc, d_act, x.ref(xoff), fq->ref(), fqt->ref(), fp->ref(), fS->ref(), fu->ref(), n, V,
                        c->partials, c->st);
-    prof_end(c, &pp, (double)nact * V * (PS == P64 ? 192.0 : 96.0) * 11.0);
+    prof_end(c, &pp, (double)nact * V * (double)spinor_site_bytes(PS) * 11.0);
     OVL_TRY(check_launch(c, __func__));
     std::vector<double> qn(2 * n);
     OVL_TRY(reduce_to_host(c, make_shape(V, n).nsb, n, qn.data()));   // also orders the hact upload

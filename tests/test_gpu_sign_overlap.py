@@ -16,14 +16,15 @@ def _ab(w):
     return 0.95 * np.min(np.abs(w)), 1.05 * np.max(np.abs(w))
 
 
-def test_sign_fp64_matches_per_pole_oracle():
+@pytest.mark.parametrize("prec", [0, 3])
+def test_sign_fp64_matches_per_pole_oracle(prec):
     U, Kd, S, w = dense_4444()
     a, b = _ab(w)
     c = ctx((4, 4, 4, 4), U, a=a, b=b, n_poles=16)
     om, sg, de = zo.zolotarev(16, a, b)
     v = synth.gaussian_source((4, 4, 4, 4), 2001, nvec=2)
     out = np.zeros_like(v)
-    c.sign_apply(v, out, eta=1e-11, prec=0)
+    c.sign_apply(v, out, eta=1e-11, prec=prec)
     for j in range(2):
         ref = overlap.zolotarev_sign_apply(U, v[j], M0, om, sg, tol=1e-14)
         assert rel(out[j], ref) <= 1e-9
@@ -46,16 +47,16 @@ def test_sign_relaxed_accuracy(prec, eta, bound):
     assert err <= bound
 
 
-@pytest.mark.parametrize("mu", [0.05, 0.3])
-def test_overlap_apply_matches_dense(mu):
+@pytest.mark.parametrize("mu,prec", [(0.05, 0), (0.3, 0), (0.05, 3)])
+def test_overlap_apply_matches_dense(mu, prec):
     U, Kd, S, w = dense_4444()
     c = ctx((4, 4, 4, 4), U, mu=mu, n_poles=16)   # bounds from the library's Lanczos estimate
     D = overlap.dense_overlap(S, mu, 256)
     v = synth.gaussian_source((4, 4, 4, 4), 11, nvec=3)
     out = np.zeros_like(v)
-    c.apply(v, out, mu=mu, eta=1e-11, prec=0)
+    c.apply(v, out, mu=mu, eta=1e-11, prec=prec)
     hout = np.zeros_like(v)
-    c.apply(v, hout, mu=mu, eta=1e-11, prec=0, hermitian=True)
+    c.apply(v, hout, mu=mu, eta=1e-11, prec=prec, hermitian=True)
     for j in range(3):
         ref = (D @ v[j].ravel()).reshape(v[j].shape)
         assert rel(out[j], ref) <= 1e-9
@@ -84,6 +85,10 @@ def test_overlap_apply_full_size_properties():
     Ks = wilson.apply_K_sites(U, s1, M0, sites)
     got = np.array([sKv[t, z, y, x] for (x, y, z, t) in sites])
     assert rel(got, Ks) <= 5e-9
+    e1 = np.zeros_like(v)
+    c.sign_apply(v, e1, eta=1e-10, prec=3)
+    print("16^3x32 double-float sign at eta=1e-10: difference to FP64 %.3e" % rel(e1, s1))
+    assert rel(e1, s1) <= 5e-10
     f1 = np.zeros_like(v)
     c.sign_apply(v, f1, eta=1e-5, prec=1)
     print("16^3x32 FP32 sign at eta=1e-5: error vs FP64 %.3e" % rel(f1, s1))

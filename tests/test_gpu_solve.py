@@ -22,10 +22,10 @@ def _check(U, S, x, b, mu, tol):
     return tr, err
 
 
-@pytest.mark.parametrize("mixed,solver", [(1, 0), (0, 0), (1, 1)])
-def test_config1_solve(mixed, solver):
+@pytest.mark.parametrize("mixed,solver,emul", [(1, 0, 0), (0, 0, 0), (1, 1, 0), (1, 0, 1), (0, 0, 1)])
+def test_config1_solve(mixed, solver, emul):
     U, Kd, S, w = dense_4444()
-    c = ctx(DIMS, U, mu=0.05, n_poles=16, mixed=mixed, solver=solver)
+    c = ctx(DIMS, U, mu=0.05, n_poles=16, mixed=mixed, solver=solver, emulate_fp64=emul)
     b = synth.gaussian_source(DIMS, 2001)
     x = np.zeros_like(b)
     info = c.solve(b, x, 1e-10)

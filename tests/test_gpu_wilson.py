@@ -11,11 +11,11 @@ from tests.gpu_util import lib, ctx, rel, M0
 
 pytestmark = pytest.mark.gpu
 
-TOL = {0: 1e-13, 1: 2e-6, 2: 4e-3}
+TOL = {0: 1e-13, 1: 2e-6, 2: 4e-3, 3: 2e-13}
 
 
 @pytest.mark.parametrize("dims", [(4, 4, 4, 4), (6, 2, 4, 6), (2, 2, 2, 2), (8, 8, 8, 4)])
-@pytest.mark.parametrize("prec", [0, 1, 2])
+@pytest.mark.parametrize("prec", [0, 1, 2, 3])
 @pytest.mark.parametrize("apt", [0, 1])
 def test_wilson_matches_oracle(dims, prec, apt):
     U = synth.gauge_links(dims, 0.3, 1001)
@@ -54,7 +54,7 @@ def test_wilson_full_size_sampled(dims):
     sites[0] = (dims[0] - 1, dims[1] - 1, dims[2] - 1, dims[3] - 1)
     sites[1] = (0, 0, 0, 0)
     ref = wilson.apply_K_sites(U, psi, M0, sites)
-    for prec in (0, 1):
+    for prec in (0, 1, 3):
         out = np.zeros_like(psi)
         c.wilson_apply(psi, out, prec)
         got = np.array([out[t, z, y, x] for (x, y, z, t) in sites])
