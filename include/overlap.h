@@ -82,6 +82,8 @@ typedef struct {
   double a_override;    /* >0: use this lower bound a of |lambda(K)|, else estimate by Lanczos  */
   double b_override;    /* >0: use this upper bound b of |lambda(K)|, else estimate by Lanczos  */
   int    batch_max;     /* systems advanced together in one lock-step batch, default 36         */
+  int    wilson_variant;/* Wilson-kernel launch shape: -1 autotune at create (default), 0 one
+                           thread per site, 1 four threads per site (one per direction)        */
   int    verify;        /* 1: after a solve, recompute ||b - D x|| / ||b|| with an FP64 sign at
                            eps_sign (one more sign application per system); 0: report the
                            GMRESR recursive residual. Default 1                                 */
@@ -213,6 +215,12 @@ ovl_status ovl_profile_units(ovl_ctx* ctx, int cls, double* units);
  * (CUDA events on the context stream) and algorithmic bytes per launch. */
 ovl_status ovl_bench_wilson(ovl_ctx* ctx, int prec, int n, int iters, double* ms_per_launch,
                             double* bytes_per_launch);
+
+/* Wilson-kernel autotuner result for one storage precision (OVL_PREC_*): the variant
+ * in use (0 one thread per site, 1 one thread per site and direction) and the measured
+ * milliseconds per launch of both on this lattice (zero when the variant was forced). */
+ovl_status ovl_wilson_tuning(const ovl_ctx* ctx, int prec, int* variant, double* ms_thread_per_site,
+                             double* ms_split);
 
 /* Library version string. */
 const char* ovl_version(void);

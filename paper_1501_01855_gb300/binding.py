@@ -12,7 +12,7 @@ import os
 import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(_HERE, "liboverlap.so")
+LIB_PATH = os.environ.get("OVL_LIB_PATH", os.path.join(_HERE, "liboverlap.so"))
 
 OVL_OK, OVL_EINVAL, OVL_ENOMEM, OVL_ECUDA, OVL_ENOCONV, OVL_EBREAKDOWN, OVL_EAPPROX, OVL_ETIMEOUT = \
     0, -1, -2, -3, -4, -5, -6, -7
@@ -40,7 +40,7 @@ class ovl_params(ctypes.Structure):
                 ("eta_precond", ctypes.c_double), ("relax_factor", ctypes.c_double),
                 ("gmresr_max", ctypes.c_int), ("inner_max", ctypes.c_int), ("mscg_max", ctypes.c_int),
                 ("delta_split", ctypes.c_double), ("c_spec", ctypes.c_double), ("bc_t", ctypes.c_int),
-                ("a_override", ctypes.c_double), ("b_override", ctypes.c_double), ("batch_max", ctypes.c_int),
+                ("a_override", ctypes.c_double), ("b_override", ctypes.c_double), ("batch_max", ctypes.c_int), ("wilson_variant", ctypes.c_int),
                 ("verify", ctypes.c_int), ("stream", ctypes.c_void_p)]
 
 
@@ -86,6 +86,7 @@ _SIGS = {
     "ovl_profile_get": (I, [P, I, LLP, DP, DP]),
     "ovl_profile_units": (I, [P, I, DP]),
     "ovl_bench_wilson": (I, [P, I, I, I, DP, DP]),
+    "ovl_wilson_tuning": (I, [P, I, ctypes.POINTER(I), DP, DP]),
 }
 
 
@@ -300,6 +301,12 @@ class Overlap:
             _check(load().ovl_profile_units(self.h, c, ctypes.byref(u)), self.h)
             out[PROF_NAMES[c]] = {"launches": n.value, "ms": ms.value, "bytes": by.value, "units": u.value}
         return out
+
+    def wilson_tuning(self, prec):
+        v = ctypes.c_int()
+        a, b = ctypes.c_double(), ctypes.c_double()
+        _check(load().ovl_wilson_tuning(self.h, int(prec), ctypes.byref(v), ctypes.byref(a), ctypes.byref(b)), self.h)
+        return v.value, a.value, b.value
 
     def bench_wilson(self, prec, n, iters):
         ms, by = ctypes.c_double(), ctypes.c_double()

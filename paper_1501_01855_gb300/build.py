@@ -14,8 +14,8 @@ import sys
 HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 ROOT = os.path.dirname(HERE)
-BUILD = os.path.join(ROOT, "_build")
-LIB = os.path.join(HERE, "liboverlap.so")
+BUILD = os.environ.get("OVL_BUILD_DIR", os.path.join(ROOT, "_build"))
+LIB = os.environ.get("OVL_LIB_PATH", os.path.join(HERE, "liboverlap.so"))
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-std=c++17", "-lineinfo", "--expt-relaxed-constexpr", "-Xcompiler", "-fPIC",
@@ -73,4 +73,5 @@ def build(verbose=False, extra=()):
 if __name__ == "__main__":
     v = "-v" in sys.argv
     extra = ["-Xptxas", "-v"] if "--ptxas" in sys.argv else []
+    extra += [a for a in sys.argv[1:] if a.startswith("-D")]
     print(build(verbose=v or bool(extra), extra=extra))

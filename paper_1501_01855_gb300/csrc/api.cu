@@ -43,6 +43,7 @@ extern "C" ovl_status ovl_params_default(ovl_params* p) {
   p->a_override = 0.0;
   p->b_override = 0.0;
   p->batch_max = 36;
+  p->wilson_variant = -1;
   p->verify = 1;
   p->stream = nullptr;
   return OVL_OK;
@@ -54,22 +55,24 @@ extern "C" const char* overlap_last_error(const ovl_ctx* c) { return c ? c->err.
 static void convert_links(const double* links, int V, std::vector<double>& l64, std::vector<float>& l32,
                           std::vector<__half>& l16, std::vector<float>& l64e) {
   // canonical [site][mu][row][col] complex -> [mu][chunk][V] keeping rows 0, 1
+  // (all three rows for the double-float copy)
   l64.assign((size_t)4 * 6 * V * 2, 0.0);
   l32.assign((size_t)4 * 3 * V * 4, 0.f);
   l16.assign((size_t)4 * 3 * V * 4, __float2half(0.f));
-  l64e.assign((size_t)4 * 6 * V * 4, 0.f);
+  l64e.assign((size_t)4 * 9 * V * 4, 0.f);
   for (int s = 0; s < V; ++s)
     for (int mu = 0; mu < 4; ++mu) {
       const double* u = links + ((size_t)s * 4 + mu) * 18;   // 9 complex
-      for (int e = 0; e < 6; ++e) {
+      for (int e = 0; e < 9; ++e) {
         const double re = u[2 * e], im = u[2 * e + 1];
+        const float rh = (float)re, ih = (float)im;
+        l64e[(((size_t)mu * 9 + e) * V + s) * 4 + 0] = rh;
+        l64e[(((size_t)mu * 9 + e) * V + s) * 4 + 1] = (float)(re - (double)rh);
+        l64e[(((size_t)mu * 9 + e) * V + s) * 4 + 2] = ih;
+        l64e[(((size_t)mu * 9 + e) * V + s) * 4 + 3] = (float)(im - (double)ih);
+        if (e >= 6) continue;
         l64[(((size_t)mu * 6 + e) * V + s) * 2 + 0] = re;
         l64[(((size_t)mu * 6 + e) * V + s) * 2 + 1] = im;
-        const float rh = (float)re, ih = (float)im;
-        l64e[(((size_t)mu * 6 + e) * V + s) * 4 + 0] = rh;
-        l64e[(((size_t)mu * 6 + e) * V + s) * 4 + 1] = (float)(re - (double)rh);
-        l64e[(((size_t)mu * 6 + e) * V + s) * 4 + 2] = ih;
-        l64e[(((size_t)mu * 6 + e) * V + s) * 4 + 3] = (float)(im - (double)ih);
         const int ch = e / 2, w = e % 2;
         l32[(((size_t)mu * 3 + ch) * V + s) * 4 + 2 * w + 0] = (float)re;
         l32[(((size_t)mu * 3 + ch) * V + s) * 4 + 2 * w + 1] = (float)im;
@@ -77,6 +80,53 @@ static void convert_links(const double* links, int V, std::vector<double>& l64, 
         l16[(((size_t)mu * 3 + ch) * V + s) * 4 + 2 * w + 1] = __float2half_rn((float)im);
       }
     }
+}
+
+// Autotuner: time both Wilson-kernel variants for every storage precision on this
+// lattice (one system, random input) and keep the faster one.
+static ovl_status autotune_wilson(ovl_ctx* c) {
+  const int forced = c->P.wilson_variant;
+  std::vector<double> h((size_t)24 * c->V);
+  unsigned long long st = 777;
+  for (auto& x : h) {
+    st = st * 6364136223846793005ull + 1442695040888963407ull;
+    x = ((double)(st >> 11) / 9007199254740992.0) - 0.5;
+  }
+  cudaEvent_t e0, e1;
+  OVL_CUDA(c, cudaEventCreate(&e0));
+  OVL_CUDA(c, cudaEventCreate(&e1));
+  for (int p = 0; p < 4; ++p) {
+    if (forced == 0 || forced == 1) {
+      c->wvar[p] = forced;
+      continue;
+    }
+    Field *fi, *fo;
+    OVL_TRY(get_field(c, "at_in", p, 1, &fi));
+    OVL_TRY(get_field(c, "at_out", p, 1, &fo));
+    OVL_TRY(import_spinors(c, h.data(), OVL_C128, 0, 1, *fi, 0));
+    for (int v = 0; v < 2; ++v) {
+      LinkRef L = links_of(c, p);
+      L.variant = v;
+      const int reps = p == P64 ? 3 : 8;
+      for (int w = 0; w < 2; ++w)
+        launch_wilson_K(p, p, p, c->g, c->kappa, L, fi->ref(), fo->ref(), 1, nullptr, nullptr, c->st);
+      OVL_CUDA(c, cudaEventRecord(e0, c->st));
+      for (int w = 0; w < reps; ++w)
+        launch_wilson_K(p, p, p, c->g, c->kappa, L, fi->ref(), fo->ref(), 1, nullptr, nullptr, c->st);
+      OVL_CUDA(c, cudaEventRecord(e1, c->st));
+      OVL_CUDA(c, cudaEventSynchronize(e1));
+      OVL_TRY(check_launch(c, __func__));
+      float ms = 0.f;
+      cudaEventElapsedTime(&ms, e0, e1);
+      c->wtime[p][v] = ms / reps;
+    }
+    c->wvar[p] = c->wtime[p][1] < c->wtime[p][0] ? 1 : 0;
+    free_field(c->ws["at_in"]);
+    free_field(c->ws["at_out"]);
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  return OVL_OK;
 }
 
 // Extreme eigenvalues of K^2 by FP64 Lanczos (no reorthogonalisation; only the
@@ -143,6 +193,7 @@ extern "C" void overlap_destroy(ovl_ctx* c) {
   if (c->dwork) cudaFree(c->dwork);
   if (c->hpin) cudaFreeHost(c->hpin);
   if (c->hstage) cudaFreeHost(c->hstage);
+  if (c->stage_ev) cudaEventDestroy(c->stage_ev);
   for (auto& q : c->prof.pending) {
     cudaEventDestroy(q.a);
     cudaEventDestroy(q.b);
@@ -189,6 +240,7 @@ static ovl_status create_impl(ovl_ctx* c, const int dims[4], const double* links
   OVL_CUDA(c, cudaMalloc((void**)&c->dred, sizeof(double) * NVRED * 4096));
   OVL_CUDA(c, cudaMalloc((void**)&c->dint, sizeof(int) * 4096));
   OVL_CUDA(c, cudaMalloc((void**)&c->dpoles, sizeof(Poles)));
+  OVL_CUDA(c, cudaEventCreateWithFlags(&c->stage_ev, cudaEventDisableTiming));
   // gauge field in the three storage formats
   {
     std::vector<double> l64;
@@ -205,6 +257,7 @@ static ovl_status create_impl(ovl_ctx* c, const int dims[4], const double* links
     OVL_CUDA(c, cudaMemcpy(c->link[P32], l32.data(), l32.size() * sizeof(float), cudaMemcpyHostToDevice));
     OVL_CUDA(c, cudaMemcpy(c->link[P16], l16.data(), l16.size() * sizeof(__half), cudaMemcpyHostToDevice));
   }
+  OVL_TRY(autotune_wilson(c));
   // spectral bounds of |K|
   double a = c->P.a_override, b = c->P.b_override;
   if (!(a > 0) || !(b > 0)) {
@@ -707,6 +760,14 @@ extern "C" ovl_status ovl_profile_get(ovl_ctx* c, int cls, long long* launches, 
   return OVL_OK;
 }
 
+extern "C" ovl_status ovl_wilson_tuning(const ovl_ctx* c, int prec, int* variant, double* ms0, double* ms1) {
+  if (!c || prec < P64 || prec > P64E) return OVL_EINVAL;
+  if (variant) *variant = c->wvar[prec];
+  if (ms0) *ms0 = c->wtime[prec][0];
+  if (ms1) *ms1 = c->wtime[prec][1];
+  return OVL_OK;
+}
+
 extern "C" ovl_status ovl_profile_units(ovl_ctx* c, int cls, double* units) {
   if (!c || cls < 0 || cls >= OVL_PROF_CLASSES || !units) return OVL_EINVAL;
   prof_flush(c);
@@ -743,7 +804,7 @@ extern "C" ovl_status ovl_bench_wilson(ovl_ctx* c, int prec, int n, int iters, d
   cudaEventDestroy(e1);
   OVL_TRY(check_launch(c, __func__));
   const double sb = prec == P16 ? 52 : spinor_site_bytes(prec);
-  const double lb = (prec == P64 || prec == P64E) ? 384 : prec == P32 ? 192 : 96;
+  const double lb = prec == P64E ? 576 : prec == P64 ? 384 : prec == P32 ? 192 : 96;
   if (ms_per_launch) *ms_per_launch = ms / iters;
   if (bytes_per_launch) *bytes_per_launch = (double)c->V * (2.0 * sb * n + lb);
   return OVL_OK;

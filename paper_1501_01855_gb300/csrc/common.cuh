@@ -278,6 +278,7 @@ __device__ __forceinline__ void store_spinor_any(const SpinorRef& f, int rhs, in
 struct LinkRef {
   const void* data;  // [mu][chunk][V]
   int V;
+  int variant;       // Wilson-kernel variant chosen for this field (0 thread per site, 1 split)
 };
 
 template <typename T>
@@ -291,6 +292,7 @@ __device__ __forceinline__ void reconstruct_row3(cpx<T> u[9]) {
 template <int P> struct LinkIO;
 template <>
 struct LinkIO<P64> {
+  static constexpr bool full = false;
   static __device__ __forceinline__ void load(const LinkRef& L, int mu, int s, cpx<double> u[9]) {
     const double2* p = reinterpret_cast<const double2*>(L.data) + (size_t)mu * 6 * L.V + s;
 #pragma unroll
@@ -300,12 +302,16 @@ struct LinkIO<P64> {
     }
   }
 };
+// Double-float links keep all three rows (18 reals, [mu][9 chunks][V] float4 chunks):
+// the double-float kernel is bound by FP32 instruction issue, not bytes, and
+// rebuilding row 3 in double-float would cost ~20% of its instructions.
 template <>
 struct LinkIO<P64E> {
+  static constexpr bool full = true;
   static __device__ __forceinline__ void load(const LinkRef& L, int mu, int s, cpx<df> u[9]) {
-    const float4* p = reinterpret_cast<const float4*>(L.data) + (size_t)mu * 6 * L.V + s;
+    const float4* p = reinterpret_cast<const float4*>(L.data) + (size_t)mu * 9 * L.V + s;
 #pragma unroll
-    for (int c = 0; c < 6; ++c) {
+    for (int c = 0; c < 9; ++c) {
       float4 w = __ldg(p + (size_t)c * L.V);
       u[c] = cmk(df(w.x, w.y), df(w.z, w.w));
     }
@@ -313,6 +319,7 @@ struct LinkIO<P64E> {
 };
 template <>
 struct LinkIO<P32> {
+  static constexpr bool full = false;
   static __device__ __forceinline__ void load(const LinkRef& L, int mu, int s, cpx<float> u[9]) {
     const float4* p = reinterpret_cast<const float4*>(L.data) + (size_t)mu * 3 * L.V + s;
 #pragma unroll
@@ -325,6 +332,7 @@ struct LinkIO<P32> {
 };
 template <>
 struct LinkIO<P16> {
+  static constexpr bool full = false;
   static __device__ __forceinline__ void load(const LinkRef& L, int mu, int s, cpx<float> u[9]) {
     const uint2* p = reinterpret_cast<const uint2*>(L.data) + (size_t)mu * 3 * L.V + s;
 #pragma unroll
@@ -343,7 +351,7 @@ template <int P, typename T>
 __device__ __forceinline__ void load_link(const LinkRef& L, int mu, int s, cpx<T> u[9]) {
   static_assert(std::is_same<T, typename Real<P>::T>::value, "links load in their own compute type");
   LinkIO<P>::load(L, mu, s, u);
-  reconstruct_row3(u);
+  if constexpr (!LinkIO<P>::full) reconstruct_row3(u);
 }
 
 // ------------------------------------------------------------------ geometry

@@ -55,6 +55,8 @@ struct ovl_ctx {
   cudaStream_t st = nullptr;
   int device = 0;
   void* link[4] = {nullptr, nullptr, nullptr, nullptr};  // P64, P32, P16, P64E 12-real layouts
+  int wvar[4] = {0, 0, 0, 0};                            // Wilson-kernel variant per precision
+  float wtime[4][2] = {{0}};                             // autotuner timings (ms per launch)
   ovl::Poles hpoles;
   ovl::Poles* dpoles = nullptr;
   std::map<std::string, ovl::Field> ws;
@@ -71,6 +73,8 @@ struct ovl_ctx {
   double* dwork = nullptr;       // Gram work buffer
   size_t dwork_n = 0;
   size_t ring_pos = 0;           // scalar upload ring in hpin / dscal, [32768, 262144)
+  cudaEvent_t stage_ev = nullptr;  // last copy out of hstage
+  bool exact_rational = false;   // solve shifted systems past Delta (gradient of the rational)
   std::string err;
   ovl::Profiler prof;
   long long wcalls[4] = {0, 0, 0, 0};  // Wilson applications by precision

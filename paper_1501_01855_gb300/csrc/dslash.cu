@@ -24,23 +24,58 @@ namespace ovl {
 
 enum { MODE_K = 0, MODE_R = 1, MODE_OVL = 2 };
 
+// Minimum resident 256-thread blocks per SM requested from the compiler, which caps
+// registers per thread at 65536 / (256 * MINB). Uncapped, the compiler hoists all
+// neighbour loads and takes ~255 registers (8 warps per SM): the FP32/FP16 kernels
+// are then latency-bound, and the double-float kernel has too few warps to hide its
+// dependent FP32 chains. Measured on 24^3x48: FP32 0.108 -> 0.081 ms at 64
+// registers, double-float 1.04 -> 0.92 ms at 128.
+#ifndef OVL_WILSON_MINB_DF
+#define OVL_WILSON_MINB_DF 2
+#endif
+#ifndef OVL_WILSON_MINB_SP
+#define OVL_WILSON_MINB_SP 4
+#endif
+template <int PL> struct MinBlocks {
+  static constexpr int v = PL == P64E ? OVL_WILSON_MINB_DF : PL == P64 ? 1 : OVL_WILSON_MINB_SP;
+};
+
+// Sums inside the hop term. For double-float operands the sum is "lazy": TwoSum on the
+// high words, the low words and the rounding error added in FP32 without the final
+// renormalisation. A value hi + lo with |lo| a few ulp(hi) is as good an operand for the
+// products below as a normalised one, and the short chains here (at most 8 terms per
+// component) keep lo that small; the epilogue's ordinary double-float operations
+// renormalise.
+template <typename T>
+__device__ __forceinline__ cpx<T> padd(cpx<T> a, cpx<T> b) { return a + b; }
+__device__ __forceinline__ df lazy_add(df a, df b) {
+  const float s = __fadd_rn(a.hi, b.hi);
+  const float v = __fsub_rn(s, a.hi);
+  const float e = __fadd_rn(__fsub_rn(a.hi, __fsub_rn(s, v)), __fsub_rn(b.hi, v));
+  return df(s, __fadd_rn(e, __fadd_rn(a.lo, b.lo)));
+}
+template <>
+__device__ __forceinline__ cpx<df> padd(cpx<df> a, cpx<df> b) { return {lazy_add(a.r, b.r), lazy_add(a.i, b.i)}; }
+template <typename T>
+__device__ __forceinline__ cpx<T> psub(cpx<T> a, cpx<T> b) { return padd(a, -b); }
+
 template <int MU, int S, typename T>
 __device__ __forceinline__ void project(const cpx<T> p[12], cpx<T> h[6]) {
 #pragma unroll
   for (int c = 0; c < 3; ++c) {
     const cpx<T> p0 = p[c], p1 = p[3 + c], p2 = p[6 + c], p3 = p[9 + c];
     if constexpr (MU == 0) {          // h0 = p0 + S i p3, h1 = p1 + S i p2
-      h[c] = S > 0 ? p0 + timesI(p3) : p0 - timesI(p3);
-      h[3 + c] = S > 0 ? p1 + timesI(p2) : p1 - timesI(p2);
+      h[c] = S > 0 ? padd(p0, timesI(p3)) : psub(p0, timesI(p3));
+      h[3 + c] = S > 0 ? padd(p1, timesI(p2)) : psub(p1, timesI(p2));
     } else if constexpr (MU == 1) {   // h0 = p0 - S p3, h1 = p1 + S p2
-      h[c] = S > 0 ? p0 - p3 : p0 + p3;
-      h[3 + c] = S > 0 ? p1 + p2 : p1 - p2;
+      h[c] = S > 0 ? psub(p0, p3) : padd(p0, p3);
+      h[3 + c] = S > 0 ? padd(p1, p2) : psub(p1, p2);
     } else if constexpr (MU == 2) {   // h0 = p0 + S i p2, h1 = p1 - S i p3
-      h[c] = S > 0 ? p0 + timesI(p2) : p0 - timesI(p2);
-      h[3 + c] = S > 0 ? p1 - timesI(p3) : p1 + timesI(p3);
+      h[c] = S > 0 ? padd(p0, timesI(p2)) : psub(p0, timesI(p2));
+      h[3 + c] = S > 0 ? psub(p1, timesI(p3)) : padd(p1, timesI(p3));
     } else {                          // h0 = p0 + S p2, h1 = p1 + S p3
-      h[c] = S > 0 ? p0 + p2 : p0 - p2;
-      h[3 + c] = S > 0 ? p1 + p3 : p1 - p3;
+      h[c] = S > 0 ? padd(p0, p2) : psub(p0, p2);
+      h[3 + c] = S > 0 ? padd(p1, p3) : psub(p1, p3);
     }
   }
 }
@@ -51,20 +86,20 @@ __device__ __forceinline__ void accumulate(cpx<T> acc[12], const cpx<T> w[6]) {
 #pragma unroll
   for (int c = 0; c < 3; ++c) {
     const cpx<T> w0 = w[c], w1 = w[3 + c];
-    acc[c] = acc[c] + w0;
-    acc[3 + c] = acc[3 + c] + w1;
+    acc[c] = padd(acc[c], w0);
+    acc[3 + c] = padd(acc[3 + c], w1);
     if constexpr (MU == 0) {          // lower = (-S i w1, -S i w0)
-      acc[6 + c] = acc[6 + c] + (S > 0 ? timesMinusI(w1) : timesI(w1));
-      acc[9 + c] = acc[9 + c] + (S > 0 ? timesMinusI(w0) : timesI(w0));
+      acc[6 + c] = padd(acc[6 + c], S > 0 ? timesMinusI(w1) : timesI(w1));
+      acc[9 + c] = padd(acc[9 + c], S > 0 ? timesMinusI(w0) : timesI(w0));
     } else if constexpr (MU == 1) {   // lower = (S w1, -S w0)
-      acc[6 + c] = S > 0 ? acc[6 + c] + w1 : acc[6 + c] - w1;
-      acc[9 + c] = S > 0 ? acc[9 + c] - w0 : acc[9 + c] + w0;
+      acc[6 + c] = S > 0 ? padd(acc[6 + c], w1) : psub(acc[6 + c], w1);
+      acc[9 + c] = S > 0 ? psub(acc[9 + c], w0) : padd(acc[9 + c], w0);
     } else if constexpr (MU == 2) {   // lower = (-S i w0, S i w1)
-      acc[6 + c] = acc[6 + c] + (S > 0 ? timesMinusI(w0) : timesI(w0));
-      acc[9 + c] = acc[9 + c] + (S > 0 ? timesI(w1) : timesMinusI(w1));
+      acc[6 + c] = padd(acc[6 + c], S > 0 ? timesMinusI(w0) : timesI(w0));
+      acc[9 + c] = padd(acc[9 + c], S > 0 ? timesI(w1) : timesMinusI(w1));
     } else {                          // lower = (S w0, S w1)
-      acc[6 + c] = S > 0 ? acc[6 + c] + w0 : acc[6 + c] - w0;
-      acc[9 + c] = S > 0 ? acc[9 + c] + w1 : acc[9 + c] - w1;
+      acc[6 + c] = S > 0 ? padd(acc[6 + c], w0) : psub(acc[6 + c], w0);
+      acc[9 + c] = S > 0 ? padd(acc[9 + c], w1) : psub(acc[9 + c], w1);
     }
   }
 }
@@ -84,6 +119,76 @@ __device__ __forceinline__ void su3_dag_mul(const cpx<T> u[9], const cpx<T> h[6]
 #pragma unroll
     for (int a = 0; a < 3; ++a)
       w[3 * sp + a] = cmulc(u[a], h[3 * sp]) + cmulc(u[3 + a], h[3 * sp + 1]) + cmulc(u[6 + a], h[3 * sp + 2]);
+}
+
+// Double-float link products: every output component is a sum of six real products,
+// evaluated as a compensated dot product (Dot2 of Ogita, Rump & Oishi, 2005): the
+// high-word products are split exactly by TwoProd (one FMA), summed with TwoSum, and
+// every rounding error plus the cross terms hi*lo go to a separate FP32 sum. The
+// result (sum, errors) is returned unnormalised; the pair carries about twice FP32
+// precision, like the double-float product and sum it replaces, at ~2/3 of the
+// instructions.
+struct Dot2 {
+  float s, c;
+};
+__device__ __forceinline__ Dot2 dot2_first(df x, df y) {
+  const float p = __fmul_rn(x.hi, y.hi);
+  float e = __fmaf_rn(x.hi, y.hi, -p);
+  e = __fmaf_rn(x.hi, y.lo, e);
+  e = __fmaf_rn(x.lo, y.hi, e);
+  return {p, e};
+}
+__device__ __forceinline__ void dot2_add(Dot2& a, df x, df y) {
+  const float p = __fmul_rn(x.hi, y.hi);
+  float e = __fmaf_rn(x.hi, y.hi, -p);
+  e = __fmaf_rn(x.hi, y.lo, e);
+  e = __fmaf_rn(x.lo, y.hi, e);
+  const float s = __fadd_rn(a.s, p);
+  const float v = __fsub_rn(s, a.s);
+  const float t = __fadd_rn(__fsub_rn(a.s, __fsub_rn(s, v)), __fsub_rn(p, v));
+  a.s = s;
+  a.c = __fadd_rn(a.c, __fadd_rn(t, e));
+}
+// w = U h: re = sum_b (Ur hr - Ui hi), im = sum_b (Ur hi + Ui hr)
+__device__ __forceinline__ void su3_mul(const cpx<df> u[9], const cpx<df> h[6], cpx<df> w[6]) {
+#pragma unroll
+  for (int sp = 0; sp < 2; ++sp)
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      const cpx<df>* r = u + 3 * a;
+      const cpx<df>* v = h + 3 * sp;
+      Dot2 re = dot2_first(r[0].r, v[0].r), im = dot2_first(r[0].r, v[0].i);
+      dot2_add(re, -r[0].i, v[0].i);
+      dot2_add(im, r[0].i, v[0].r);
+#pragma unroll
+      for (int b = 1; b < 3; ++b) {
+        dot2_add(re, r[b].r, v[b].r);
+        dot2_add(re, -r[b].i, v[b].i);
+        dot2_add(im, r[b].r, v[b].i);
+        dot2_add(im, r[b].i, v[b].r);
+      }
+      w[3 * sp + a] = cmk(df(re.s, re.c), df(im.s, im.c));
+    }
+}
+// w = U^dag h: re = sum_b (Ur hr + Ui hi), im = sum_b (Ur hi - Ui hr), U = U[b][a]
+__device__ __forceinline__ void su3_dag_mul(const cpx<df> u[9], const cpx<df> h[6], cpx<df> w[6]) {
+#pragma unroll
+  for (int sp = 0; sp < 2; ++sp)
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      const cpx<df>* v = h + 3 * sp;
+      Dot2 re = dot2_first(u[a].r, v[0].r), im = dot2_first(u[a].r, v[0].i);
+      dot2_add(re, u[a].i, v[0].i);
+      dot2_add(im, -u[a].i, v[0].r);
+#pragma unroll
+      for (int b = 1; b < 3; ++b) {
+        dot2_add(re, u[3 * b + a].r, v[b].r);
+        dot2_add(re, u[3 * b + a].i, v[b].i);
+        dot2_add(im, u[3 * b + a].r, v[b].i);
+        dot2_add(im, -u[3 * b + a].i, v[b].r);
+      }
+      w[3 * sp + a] = cmk(df(re.s, re.c), df(im.s, im.c));
+    }
 }
 
 template <int MU, int PIN, int PL, typename T>
@@ -146,10 +251,78 @@ struct DArgs {
   double c1, c2;
   const double* coef;
   int herm;
+  int variant;   // 0: thread per site, 1: direction split
 };
 
+// Epilogue shared by both kernel variants: acc holds the hop sum of site s.
+template <int MODE, int PIN, int POUT, int PA1, int PA2, typename T>
+__device__ __forceinline__ void wilson_epilogue(const DArgs& a, int rhs, int s, cpx<T> acc[12], double v[NVRED]) {
+  cpx<T> c[12];
+  load_spinor_as_ro<PIN, T>(a.in, rhs, s, c);
+  const T kap = (T)a.kappa;
+  if constexpr (MODE == MODE_K) {
+    // K in = gamma5 (in - kappa acc)
+#pragma unroll
+    for (int k = 0; k < 12; ++k) {
+      cpx<T> o = c[k] - kap * acc[k];
+      if (k >= 6) o = -o;
+      v[0] += (double)norm2(o);
+      v[1] += (double)norm2(c[k]);
+      acc[k] = o;
+    }
+    store_spinor_as<POUT, T>(a.out, rhs, s, acc);
+  } else if constexpr (MODE == MODE_R) {
+    cpx<T> p[12], r[12];
+    load_spinor_as<PA1, T>(a.aux1, rhs, s, p);
+    load_spinor_as<PA2, T>(a.aux2, rhs, s, r);
+    const T sg = (T)a.sigma0;
+    const T al = (T)a.ms[rhs].alpha;
+#pragma unroll
+    for (int k = 0; k < 12; ++k) {
+      cpx<T> o = c[k] - kap * acc[k];
+      if (k >= 6) o = -o;
+      o = o + sg * p[k];
+      r[k] = r[k] - al * o;
+      v[0] += (double)norm2(r[k]);
+    }
+    store_spinor_as<PA2, T>(a.aux2, rhs, s, r);
+  } else {
+    cpx<T> w[12];
+    T c1 = (T)a.c1, c2 = (T)a.c2;
+    if (a.coef != nullptr) {
+      c1 = (T)a.coef[2 * rhs];
+      c2 = (T)a.coef[2 * rhs + 1];
+    }
+    if (c1 != T(0)) {
+      load_spinor_as<PA1, T>(a.aux1, rhs, s, w);
+    } else {
+#pragma unroll
+      for (int k = 0; k < 12; ++k) w[k] = cmk(T(0), T(0));
+    }
+#pragma unroll
+    for (int k = 0; k < 12; ++k) {
+      cpx<T> o = c1 * w[k] + c2 * (c[k] - kap * acc[k]);
+      if (a.herm && k >= 6) o = -o;
+      acc[k] = o;
+    }
+    store_spinor_as<POUT, T>(a.out, rhs, s, acc);
+    if (a.partials != nullptr) {
+      load_spinor_as<PA2, T>(a.aux2, rhs, s, w);
+#pragma unroll
+      for (int k = 0; k < 12; ++k) {
+        cpx<T> d = cmulc(w[k], acc[k]);
+        v[0] += (double)d.r;
+        v[1] += (double)d.i;
+        v[2] += (double)norm2(acc[k]);
+        v[3] += (double)norm2(w[k]);
+      }
+    }
+  }
+}
+
+// Variant 0: one thread per (site, system) walks all eight neighbours.
 template <int MODE, int PIN, int PL, int POUT, int PA1, int PA2>
-__global__ void __launch_bounds__(256) wilson_kernel(const DArgs a) {
+__global__ void __launch_bounds__(256, MinBlocks<PL>::v) wilson_kernel(const DArgs a) {
   using T = typename Real<PL>::T;
   __shared__ double red[4 * (BX / 32) * NVRED];
   const int sb = blockIdx.x / a.ngr;
@@ -160,72 +333,63 @@ __global__ void __launch_bounds__(256) wilson_kernel(const DArgs a) {
   if (live && a.ms != nullptr && (MODE == MODE_K || MODE == MODE_R)) live = !a.ms[rhs].done;
   double v[NVRED] = {0.0, 0.0, 0.0, 0.0};
   if (live) {
-    cpx<T> acc[12], c[12];
+    cpx<T> acc[12];
     hop<PIN, PL, T>(a.g, a.links, a.in, rhs, s, acc);
-    load_spinor_as_ro<PIN, T>(a.in, rhs, s, c);
-    const T kap = (T)a.kappa;
-    if constexpr (MODE == MODE_K) {
-      // K in = gamma5 (in - kappa acc)
-#pragma unroll
-      for (int k = 0; k < 12; ++k) {
-        cpx<T> o = c[k] - kap * acc[k];
-        if (k >= 6) o = -o;
-        v[0] += (double)norm2(o);
-        v[1] += (double)norm2(c[k]);
-        acc[k] = o;
-      }
-      store_spinor_as<POUT, T>(a.out, rhs, s, acc);
-    } else if constexpr (MODE == MODE_R) {
-      cpx<T> p[12], r[12];
-      load_spinor_as<PA1, T>(a.aux1, rhs, s, p);
-      load_spinor_as<PA2, T>(a.aux2, rhs, s, r);
-      const T sg = (T)a.sigma0;
-      const T al = (T)a.ms[rhs].alpha;
-#pragma unroll
-      for (int k = 0; k < 12; ++k) {
-        cpx<T> o = c[k] - kap * acc[k];
-        if (k >= 6) o = -o;
-        o = o + sg * p[k];
-        r[k] = r[k] - al * o;
-        v[0] += (double)norm2(r[k]);
-      }
-      store_spinor_as<PA2, T>(a.aux2, rhs, s, r);
-    } else {
-      cpx<T> w[12];
-      T c1 = (T)a.c1, c2 = (T)a.c2;
-      if (a.coef != nullptr) {
-        c1 = (T)a.coef[2 * rhs];
-        c2 = (T)a.coef[2 * rhs + 1];
-      }
-      if (c1 != T(0)) {
-        load_spinor_as<PA1, T>(a.aux1, rhs, s, w);
-      } else {
-#pragma unroll
-        for (int k = 0; k < 12; ++k) w[k] = cmk(T(0), T(0));
-      }
-#pragma unroll
-      for (int k = 0; k < 12; ++k) {
-        cpx<T> o = c1 * w[k] + c2 * (c[k] - kap * acc[k]);
-        if (a.herm && k >= 6) o = -o;
-        acc[k] = o;
-      }
-      store_spinor_as<POUT, T>(a.out, rhs, s, acc);
-      if (a.partials != nullptr) {
-        load_spinor_as<PA2, T>(a.aux2, rhs, s, w);
-#pragma unroll
-        for (int k = 0; k < 12; ++k) {
-          cpx<T> d = cmulc(w[k], acc[k]);
-          v[0] += (double)d.r;
-          v[1] += (double)d.i;
-          v[2] += (double)norm2(acc[k]);
-          v[3] += (double)norm2(w[k]);
-        }
-      }
-    }
+    wilson_epilogue<MODE, PIN, POUT, PA1, PA2, T>(a, rhs, s, acc, v);
   }
   if (a.partials != nullptr) {
     block_reduce_rows<NVRED>(v, red);
     if (threadIdx.x == 0 && rhs < a.nrhs) {
+#pragma unroll
+      for (int j = 0; j < NVRED; ++j) a.partials[((size_t)rhs * a.nsb + sb) * NVRED + j] = v[j];
+    }
+  }
+}
+
+// Variant 1 (direction split): a block of 4 * BX threads covers BX sites of one system;
+// warp w handles direction w % 4 (forward and backward hop) for the 32 sites of group
+// w / 4, so every thread walks two neighbours instead of eight and the direction is
+// uniform within a warp. The four partial sums meet in shared memory and the
+// direction-0 warps finish the site.
+template <int MODE, int PIN, int PL, int POUT, int PA1, int PA2>
+__global__ void __launch_bounds__(4 * BX, MinBlocks<PL>::v) wilson_split_kernel(const DArgs a) {
+  using T = typename Real<PL>::T;
+  __shared__ cpx<T> part[3][BX][12];
+  __shared__ double red[(4 * BX / 32) * NVRED];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int dir = warp & 3, grp = warp >> 2;
+  const int sb = blockIdx.x / a.nrhs;
+  const int rhs = blockIdx.x - sb * a.nrhs;
+  const int sl = grp * 32 + lane;
+  const int s = sb * BX + sl;
+  bool live = s < a.g.V;
+  if (live && a.ms != nullptr && (MODE == MODE_K || MODE == MODE_R)) live = !a.ms[rhs].done;
+  cpx<T> acc[12];
+#pragma unroll
+  for (int k = 0; k < 12; ++k) acc[k] = cmk(T(0), T(0));
+  if (live) {
+    int x[4];
+    site_coords(a.g, s, x);
+    const int sy = a.g.L[0], sz = sy * a.g.L[1], st = sz * a.g.L[2];
+    if (dir == 0) hop_dir<0, PIN, PL, T>(a.g, a.links, a.in, rhs, s, x, 1, acc);
+    else if (dir == 1) hop_dir<1, PIN, PL, T>(a.g, a.links, a.in, rhs, s, x, sy, acc);
+    else if (dir == 2) hop_dir<2, PIN, PL, T>(a.g, a.links, a.in, rhs, s, x, sz, acc);
+    else hop_dir<3, PIN, PL, T>(a.g, a.links, a.in, rhs, s, x, st, acc);
+  }
+  if (dir != 0) {
+#pragma unroll
+    for (int k = 0; k < 12; ++k) part[dir - 1][sl][k] = acc[k];
+  }
+  __syncthreads();
+  double v[NVRED] = {0.0, 0.0, 0.0, 0.0};
+  if (dir == 0 && live) {
+#pragma unroll
+    for (int k = 0; k < 12; ++k) acc[k] = acc[k] + part[0][sl][k] + part[1][sl][k] + part[2][sl][k];
+    wilson_epilogue<MODE, PIN, POUT, PA1, PA2, T>(a, rhs, s, acc, v);
+  }
+  if (a.partials != nullptr) {
+    block_reduce_rows<NVRED>(v, red);
+    if (threadIdx.x == 0) {
 #pragma unroll
       for (int j = 0; j < NVRED; ++j) a.partials[((size_t)rhs * a.nsb + sb) * NVRED + j] = v[j];
     }
@@ -245,7 +409,12 @@ static void run(DArgs a, cudaStream_t st) {
   Shape sh = make_shape(a.g.V, a.nrhs);
   a.nsb = sh.nsb;
   a.ngr = sh.ngr;
-  wilson_kernel<MODE, PIN, PL, POUT, PA1, PA2><<<sh.grid(), sh.block(), 0, st>>>(a);
+  if (a.variant == 1) {
+    // one system per block; partials keep the (system, BX-site block) layout of variant 0
+    wilson_split_kernel<MODE, PIN, PL, POUT, PA1, PA2><<<dim3((unsigned)(sh.nsb * a.nrhs)), dim3(4 * BX), 0, st>>>(a);
+  } else {
+    wilson_kernel<MODE, PIN, PL, POUT, PA1, PA2><<<sh.grid(), sh.block(), 0, st>>>(a);
+  }
 }
 
 static DArgs base_args(const Geom& g, double kappa, LinkRef links, int nrhs) {
@@ -262,6 +431,7 @@ static DArgs base_args(const Geom& g, double kappa, LinkRef links, int nrhs) {
   a.c1 = a.c2 = 0;
   a.coef = nullptr;
   a.herm = 0;
+  a.variant = links.variant;
   return a;
 }
 

@@ -133,6 +133,7 @@ LinkRef links_of(const ovl_ctx* c, int prec) {
   LinkRef r;
   r.data = c->link[prec];
   r.V = c->V;
+  r.variant = c->wvar[prec];
   return r;
 }
 
@@ -226,9 +227,12 @@ ovl_status import_spinors(ovl_ctx* c, const void* src, int dtype, int on_device,
   if (!on_device) {
     OVL_TRY(get_field(c, "io_canon", P64, (int)((bytes + 192 * (size_t)c->V - 1) / (192 * (size_t)c->V)), &tmp));
     OVL_TRY(ensure_stage(c, bytes));
-    // pinned staging keeps the copy asynchronous with respect to pageable memory rules
+    // the previous copy out of the pinned staging buffer must have finished before it
+    // is overwritten
+    OVL_CUDA(c, cudaEventSynchronize(c->stage_ev));
     memcpy(c->hstage, src, bytes);
     OVL_CUDA(c, cudaMemcpyAsync(tmp->data, c->hstage, bytes, cudaMemcpyHostToDevice, c->st));
+    OVL_CUDA(c, cudaEventRecord(c->stage_ev, c->st));
     dsrc = tmp->data;
   }
   ProfPair pp;
@@ -295,7 +299,9 @@ ovl_status sign_op(ovl_ctx* c, int mode, const Field& v, int voff, Field& out, i
   double* d_coef = c->dscal + 4096;
   for (int j = 0; j < n; ++j) {
     double e = eta[j] > 0 ? eta[j] : c->eps_sign;
-    if (e < c->delta) e = c->delta;
+    // the sign is never more accurate than Delta, so no pole is solved past it, except
+    // when the rational itself is being differentiated (gauge-link gradient)
+    if (e < c->delta && !c->exact_rational) e = c->delta;
     c->hpin[j] = e;
   }
   int ncopy = n;
@@ -306,7 +312,7 @@ ovl_status sign_op(ovl_ctx* c, int mode, const Field& v, int voff, Field& out, i
   OVL_CUDA(c, cudaMemcpyAsync(c->dscal, c->hpin, sizeof(double) * ncopy, cudaMemcpyHostToDevice, c->st));
   const LinkRef L = links_of(c, PL);
   const int wcls = PL == P64E ? 8 : PL;  // profiler class of the Wilson launches
-  const double lbytes = (PL == P64 || PL == P64E ? 384.0 : PL == P32 ? 192.0 : 96.0) * V;
+  const double lbytes = (PL == P64E ? 576.0 : PL == P64 ? 384.0 : PL == P32 ? 192.0 : 96.0) * V;
   const double sbytes = (double)spinor_bytes(PP) * V, rbytes = (double)spinor_bytes(PR) * V;
   ProfPair pp;
 

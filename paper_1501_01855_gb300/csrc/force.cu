@@ -197,6 +197,12 @@ ovl_status force_compute(ovl_ctx* c, double mu, const Field& phi, double tol, do
   std::vector<double> mus(1, mu);
   ovl_params keep = c->P;
   c->P.verify = 0;
+  // every sign below evaluates the rational itself to tol, not just to within Delta
+  struct ExactScope {
+    ovl_ctx* c;
+    ~ExactScope() { c->exact_rational = false; }
+  } scope{c};
+  c->exact_rational = true;
   const double stol = tol;
   OVL_TRY(copy_convert(c, phi, 0, *g1, 0, 1));
   launch_gamma5(P64, g1->ref(), 1, V, c->st);
@@ -215,7 +221,7 @@ ovl_status force_compute(ovl_ctx* c, double mu, const Field& phi, double tol, do
     *S = d[0].real();
   }
   // psi = H chi, K psi
-  std::vector<double> eta(1, std::max(tol * 0.1, c->delta));
+  std::vector<double> eta(1, tol * 0.1);
   OVL_TRY(overlap_apply_batch(c, *chi, 0, *psi, 0, 1, mus, eta, 1, SIGN64, nullptr));
   OVL_TRY(wilson_apply_field(c, P64, *psi, 0, *Kpsi, 0, 1));
   // all shifted solutions for chi and K psi, unit pole weights for the stopping rule
