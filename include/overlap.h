@@ -140,6 +140,24 @@ ovl_status overlap_zolotarev(const ovl_ctx* ctx, double* omega, double* sigma, d
 ovl_status ovl_wilson_apply(ovl_ctx* ctx, const void* in, void* out, int n, int dtype, int on_device,
                             int prec);
 
+/* out = K in, like ovl_wilson_apply, for callers that cannot let the library allocate
+ * device memory during the call: code whose device memory belongs to its own pool or
+ * sits under a hard cap, and loops that must not stall in the allocator. (The paper
+ * has no counterpart; this is a property of the library, not of the method.)
+ *   in, out  device pointers (the context's device must be current), n canonical
+ *            spinors each; dtype and prec as for ovl_wilson_apply.
+ * The two layout-conversion buffers live in one static device array of
+ * OVL_NOALLOC_BYTES (48 MiB) that every device loading the library holds until the
+ * process exits; a call needing more (2 n V x 192 bytes in FP64, x 96 in FP32,
+ * x 104 in FP16, so n V <= 131072 in FP64) returns OVL_EINVAL. No cudaMalloc,
+ * cudaFree or other allocating routine is called. The first call on a device looks up
+ * the array's device address (cudaGetSymbolAddress) once; make that first call before
+ * any stream capture. All calls share the array: calls that overlap on the GPU race
+ * on it, and it keeps the last call's intermediate data (nothing in it has to start at
+ * zero). */
+#define OVL_NOALLOC_BYTES ((size_t)48 << 20)
+ovl_status ovl_wilson_apply_noalloc(ovl_ctx* ctx, const void* in, void* out, int n, int dtype, int prec);
+
 /* out = eps(K) in (Sec. 3) for n spinors, multi-shift CG stopped at accuracy eta
  * (the per-pole rule of the Zolotarev sum; eta <= 0 means eps_sign). prec as above,
  * OVL_PREC_AUTO picks by eta. */

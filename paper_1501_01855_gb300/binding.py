@@ -70,6 +70,7 @@ _SIGS = {
     "overlap_last_error": (ctypes.c_char_p, [P]),
     "overlap_zolotarev": (I, [P, DP, DP, DP, DP, DP]),
     "ovl_wilson_apply": (I, [P, P, P, I, I, I, I]),
+    "ovl_wilson_apply_noalloc": (I, [P, P, P, I, I, I]),
     "ovl_sign_apply": (I, [P, P, P, I, I, I, D, I]),
     "overlap_apply": (I, [P, D, P, P, I, I, I, D, I, I]),
     "overlap_sumr": (I, [P, D, P, P, I, I, I, D, D, I, DP, ctypes.POINTER(I)]),
@@ -220,6 +221,17 @@ class Overlap:
         pi, code, dev, cnt = _spinor_arg(x)
         po, code2, dev2, cnt2 = _spinor_arg(out)
         _check(load().ovl_wilson_apply(self.h, pi, po, self._n(cnt), code, dev, int(prec)), self.h)
+        return out
+
+    def wilson_apply_noalloc(self, x, out, prec=OVL_PREC_F64):
+        """K on device tensors without any allocation during the call (static scratch)."""
+        pi, code, dev, cnt = _spinor_arg(x)
+        po, code2, dev2, _ = _spinor_arg(out)
+        if not (dev and dev2):
+            raise ValueError("ovl_wilson_apply_noalloc takes device buffers only")
+        if code2 != code:
+            raise ValueError("in and out must have the same dtype")
+        _check(load().ovl_wilson_apply_noalloc(self.h, pi, po, self._n(cnt), code, int(prec)), self.h)
         return out
 
     def sign_apply(self, x, out, eta=0.0, prec=OVL_PREC_AUTO):
