@@ -46,8 +46,18 @@ NVEC = 16
 LINK_SEED, SRC_SEED = 1002, 2002
 WILSON_FLOPS_PER_SITE = 1320          # conventional count of the hopping term
 FP64_NOMINAL_TFLOPS = 1.25            # GB300 FP64 (nominal; the ALU roofline of the FP64 kernel)
-FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12   # 80.5: FP32 lanes x FMA x max SM clock
-DF64_FP32_OPS_PER_SITE = 20000        # FP32-pipe operations per site of the double-float kernel (ncu count)
+# FP32-pipe instruction rate: 152 SMs x 128 FP32 lanes x 2.07 GHz (maximum SM clock) = 40.3 T/s
+FP32_ISSUE_PEAK_TOPS = 152 * 128 * 2.07e9 / 1e12
+# FP32 operations one double-float site application needs by construction: per neighbour
+# 12 lazy double-float sums for the projection (8 each), 12 link-product components as
+# 6-term Dot2 sums (4 + 5 x 12 each) and 24 lazy sums into the accumulator (8 each) =
+# 1056; x 8 neighbours, plus the diagonal term in - kappa hop (24 x (7 + 11)). Loads,
+# index arithmetic, phase selects and the epilogue reductions are not counted.
+DF64_FP32_OPS_PER_SITE = 8 * (12 * 8 + 12 * (4 + 5 * 12) + 24 * 8) + 24 * (7 + 11)
+# DRAM bytes (read + write) per launch of the double-float Wilson kernel in this step,
+# from an ncu capture of this command (the summary under profiles/ gives it); None
+# until captured for the current kernel.
+TRAFFIC_WILSON_DF64 = None
 
 
 def peaks():
@@ -269,9 +279,10 @@ def run_ours(args, ws, rank, local):
         ops = d["units"] * DF64_FP32_OPS_PER_SITE
         ach = ops / (d["ms"] * 1e-3) / 1e12
         roof = {"kernel": "wilson_kernel (double-float, msCG steps + final sign/overlap epilogue)", "bound": "alu",
-                "achieved": ach, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s (FP32 pipe ops)",
-                "frac": ach / FP32_PEAK_TFLOPS, "traffic": None,
-                "peak_source": "152 SMs x 128 FP32 lanes x 2 x 2.07 GHz (nominal); FP32 ops per site counted by ncu",
+                "achieved": ach, "peak": FP32_ISSUE_PEAK_TOPS, "unit": "T FP32-pipe ops/s",
+                "frac": ach / FP32_ISSUE_PEAK_TOPS, "traffic": TRAFFIC_WILSON_DF64,
+                "ops_per_site": DF64_FP32_OPS_PER_SITE,
+                "peak_source": "152 SMs x 128 FP32 lanes x 2.07 GHz (nominal maximum clock; no FP32 peak is measured)",
                 "launches": d["launches"], "avg_launch_ms": d["ms"] / max(1, d["launches"]),
                 "share_of_step": d["ms"] / ms_total if ws == 1 else None}
     elif dom == "wilson_f64":
@@ -301,7 +312,9 @@ def run_ours(args, ws, rank, local):
                    "l2": "inputs larger than L2 (16 x 25 MB vectors, 8 GB pole vectors per step)",
                    "parallelism": "replicas" if ws > 1 else "single GPU"},
         "e2e": e2e, "roofline": roof, "gpu_launches": launches, "clocks": clocks,
-        "profile": {k: {"launches": v["launches"], "ms": round(v["ms"], 3)} for k, v in prof.items() if v["launches"]},
+        "profile": {k: {"launches": v["launches"], "ms": round(v["ms"], 3),
+                        "GB/s": round(v["bytes"] / (v["ms"] * 1e-3) / 1e9, 1)}
+                    for k, v in prof.items() if v["launches"]},
     }
     ref_out = dout.cpu().numpy()
 
@@ -365,9 +378,14 @@ def extras(args, ctx, dv, dout, ref_out, B, torch, stream, hbm):
         t0 = time.perf_counter()
         info = cs.solve(b, x, 1e-10)[0]
         dt = time.perf_counter() - t0
+        cs.profile_reset()
+        cs.profile_enable(True)
+        cs.solve(b, x, 1e-10)
+        cs.profile_enable(False)
+        prof = {k: round(v["ms"], 2) for k, v in cs.profile_get().items() if v["launches"]}
         sol[nm] = {"seconds": dt, "solves_per_s": 1.0 / dt, "true_residual": info["true_residual"],
                    "outer": info["outer_iters"], "inner": info["inner_iters"],
-                   "wilson_calls_dp2": info["wilson_calls"]}
+                   "wilson_calls_dp2": info["wilson_calls"], "profile_ms": prof}
         cs.close()
     out["solve_16x16x16x32_mu0.05"] = sol
     return out

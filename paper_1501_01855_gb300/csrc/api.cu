@@ -52,25 +52,46 @@ extern "C" ovl_status ovl_params_default(ovl_params* p) {
 extern "C" const char* overlap_last_error(const ovl_ctx* c) { return c ? c->err.c_str() : "null context"; }
 
 // ---------------------------------------------------------------- create
-static void convert_links(const double* links, int V, std::vector<double>& l64, std::vector<float>& l32,
-                          std::vector<__half>& l16, std::vector<float>& l64e) {
-  // canonical [site][mu][row][col] complex -> [mu][chunk][V] keeping rows 0, 1
-  // (all three rows for the double-float copy)
+static void convert_links(const double* links, const int L[4], int bc_t, std::vector<double>& l64,
+                          std::vector<float>& l32, std::vector<__half>& l16, std::vector<float>& l64e) {
+  const int V = L[0] * L[1] * L[2] * L[3];
+  // canonical [site][mu][row][col] complex -> [mu][chunk][V] keeping rows 0, 1.
+  // The double-float copy holds, for each site x, the matrix of each of the eight hops
+  // in slot n = 2 mu + b: b = 0 U_mu(x), b = 1 U_mu(x - mu)^dag, all 9 entries
+  // ([n][chunk][V]), with the antiperiodic-t sign of the hops that cross the boundary
+  // folded in.
   l64.assign((size_t)4 * 6 * V * 2, 0.0);
   l32.assign((size_t)4 * 3 * V * 4, 0.f);
   l16.assign((size_t)4 * 3 * V * 4, __float2half(0.f));
-  l64e.assign((size_t)4 * 9 * V * 4, 0.f);
-  for (int s = 0; s < V; ++s)
+  l64e.assign((size_t)8 * 9 * V * 4, 0.f);
+  auto put_df = [&](int n, int e, int s, double re, double im) {
+    const float rh = (float)re, ih = (float)im;
+    float* d = &l64e[(((size_t)n * 9 + e) * V + s) * 4];
+    d[0] = rh;
+    d[1] = (float)(re - (double)rh);
+    d[2] = ih;
+    d[3] = (float)(im - (double)ih);
+  };
+  const int str[4] = {1, L[0], L[0] * L[1], L[0] * L[1] * L[2]};
+  for (int s = 0; s < V; ++s) {
+    int x[4], r = s;
+    for (int d = 0; d < 4; ++d) {
+      x[d] = r % L[d];
+      r /= L[d];
+    }
     for (int mu = 0; mu < 4; ++mu) {
       const double* u = links + ((size_t)s * 4 + mu) * 18;   // 9 complex
+      const int sb = x[mu] == 0 ? s + (L[mu] - 1) * str[mu] : s - str[mu];
+      const double* ub = links + ((size_t)sb * 4 + mu) * 18;
+      const double sf = (mu == 3 && bc_t && x[3] == L[3] - 1) ? -1.0 : 1.0;
+      const double sbk = (mu == 3 && bc_t && x[3] == 0) ? -1.0 : 1.0;
       for (int e = 0; e < 9; ++e) {
+        put_df(2 * mu, e, s, sf * u[2 * e], sf * u[2 * e + 1]);
+        const int t = 3 * (e % 3) + e / 3;   // (U^dag)_{ab} = conj(U_{ba})
+        put_df(2 * mu + 1, e, s, sbk * ub[2 * t], -sbk * ub[2 * t + 1]);
+      }
+      for (int e = 0; e < 6; ++e) {
         const double re = u[2 * e], im = u[2 * e + 1];
-        const float rh = (float)re, ih = (float)im;
-        l64e[(((size_t)mu * 9 + e) * V + s) * 4 + 0] = rh;
-        l64e[(((size_t)mu * 9 + e) * V + s) * 4 + 1] = (float)(re - (double)rh);
-        l64e[(((size_t)mu * 9 + e) * V + s) * 4 + 2] = ih;
-        l64e[(((size_t)mu * 9 + e) * V + s) * 4 + 3] = (float)(im - (double)ih);
-        if (e >= 6) continue;
         l64[(((size_t)mu * 6 + e) * V + s) * 2 + 0] = re;
         l64[(((size_t)mu * 6 + e) * V + s) * 2 + 1] = im;
         const int ch = e / 2, w = e % 2;
@@ -80,6 +101,7 @@ static void convert_links(const double* links, int V, std::vector<double>& l64, 
         l16[(((size_t)mu * 3 + ch) * V + s) * 4 + 2 * w + 1] = __float2half_rn((float)im);
       }
     }
+  }
 }
 
 // Autotuner: time both Wilson-kernel variants for every storage precision on this
@@ -247,7 +269,7 @@ static ovl_status create_impl(ovl_ctx* c, const int dims[4], const double* links
     std::vector<float> l32;
     std::vector<__half> l16;
     std::vector<float> l64e;
-    convert_links(links, c->V, l64, l32, l16, l64e);
+    convert_links(links, c->g.L, c->g.bc_t, l64, l32, l16, l64e);
     OVL_CUDA(c, cudaMalloc(&c->link[P64E], l64e.size() * sizeof(float)));
     OVL_CUDA(c, cudaMemcpy(c->link[P64E], l64e.data(), l64e.size() * sizeof(float), cudaMemcpyHostToDevice));
     OVL_CUDA(c, cudaMalloc(&c->link[P64], l64.size() * sizeof(double)));
@@ -804,7 +826,7 @@ extern "C" ovl_status ovl_bench_wilson(ovl_ctx* c, int prec, int n, int iters, d
   cudaEventDestroy(e1);
   OVL_TRY(check_launch(c, __func__));
   const double sb = prec == P16 ? 52 : spinor_site_bytes(prec);
-  const double lb = prec == P64E ? 576 : prec == P64 ? 384 : prec == P32 ? 192 : 96;
+  const double lb = prec == P64E ? 1152 : prec == P64 ? 384 : prec == P32 ? 192 : 96;
   if (ms_per_launch) *ms_per_launch = ms / iters;
   if (bytes_per_launch) *bytes_per_launch = (double)c->V * (2.0 * sb * n + lb);
   return OVL_OK;

@@ -302,14 +302,16 @@ struct LinkIO<P64> {
     }
   }
 };
-// Double-float links keep all three rows (18 reals, [mu][9 chunks][V] float4 chunks):
-// the double-float kernel is bound by FP32 instruction issue, not bytes, and
-// rebuilding row 3 in double-float would cost ~20% of its instructions.
+// Double-float links: eight slots per site, one per hop (slot n = 2 mu + b holds U_mu(x)
+// for b = 0 and U_mu(x - mu)^dag for b = 1), all 9 entries ([n][9 chunks][V] float4
+// chunks). The double-float kernel is bound by FP32 instruction issue, not bytes:
+// rebuilding row 3 would cost ~20% of its instructions, and pre-transposed backward
+// links let one loop body serve all eight neighbours.
 template <>
 struct LinkIO<P64E> {
   static constexpr bool full = true;
-  static __device__ __forceinline__ void load(const LinkRef& L, int mu, int s, cpx<df> u[9]) {
-    const float4* p = reinterpret_cast<const float4*>(L.data) + (size_t)mu * 9 * L.V + s;
+  static __device__ __forceinline__ void load(const LinkRef& L, int slot, int s, cpx<df> u[9]) {
+    const float4* p = reinterpret_cast<const float4*>(L.data) + (size_t)slot * 9 * L.V + s;
 #pragma unroll
     for (int c = 0; c < 9; ++c) {
       float4 w = __ldg(p + (size_t)c * L.V);

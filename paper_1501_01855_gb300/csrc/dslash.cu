@@ -191,9 +191,97 @@ __device__ __forceinline__ void su3_dag_mul(const cpx<df> u[9], const cpx<df> h[
     }
 }
 
+// Per-thread sums for the epilogue reductions, kept in the compute type: GB300 runs
+// FP64 (and FP32 <-> FP64 conversions) at a small fraction of its FP32 rate, so the FP32
+// and FP16-storage kernels sum in FP32 (their own precision) and convert once; the
+// double-float kernel sums with Dot2, which keeps its FP64-level accuracy on FP32 pipes.
+template <typename T> struct RedT { using type = double; };
+template <> struct RedT<float> { using type = float; };
+template <typename T> struct Acc {
+  T s = T(0);
+  __device__ __forceinline__ void add(T x, T y) { s = fma(x, y, s); }
+  __device__ __forceinline__ typename RedT<T>::type get() const { return s; }
+};
+template <> struct Acc<df> {
+  Dot2 d = {0.f, 0.f};
+  __device__ __forceinline__ void add(df x, df y) { dot2_add(d, x, y); }
+  __device__ __forceinline__ double get() const { return (double)d.s + (double)d.c; }
+};
+template <typename T>
+__device__ __forceinline__ void acc_norm(Acc<T>& a, const cpx<T>& z) {
+  a.add(z.r, z.r);
+  a.add(z.i, z.i);
+}
+
+// ---- double-float hop: one rolled loop over the eight neighbours -------------------
+// The double-float kernel issues ~1k FP32 instructions per neighbour; unrolled over all
+// eight it is too large for the instruction cache (ncu: "no instruction" was the top
+// stall). Here one loop body serves every neighbour n = 2 mu + b (b = 0 forward, 1
+// backward): the spin structure of (1 -+ gamma_mu) is the same for all eight up to
+// which lower spin pairs with which upper one and a power of i, and the link of hop n
+// is read from slot n of the eight-slot link field (U_mu(x), or U_mu(x - mu)^dag with
+// the boundary sign folded in), so the product is always U h.
+
+// i^k z, exact (a swap and sign changes), for a runtime k
+__device__ __forceinline__ cpx<df> ipow(const cpx<df>& z, int k) {
+  const bool odd = (k & 1) != 0;
+  const df re = odd ? z.i : z.r;
+  const df im = odd ? z.r : z.i;
+  const float sr = (k == 1 || k == 2) ? -1.f : 1.f;
+  const float si = k >= 2 ? -1.f : 1.f;
+  return {df(__fmul_rn(re.hi, sr), __fmul_rn(re.lo, sr)), df(__fmul_rn(im.hi, si), __fmul_rn(im.lo, si))};
+}
+
+template <int PIN>
+__device__ __forceinline__ void hop_nb_df(const Geom& g, const LinkRef& L, const SpinorRef& in, int rhs, int s,
+                                          const int x[4], int n, cpx<df> acc[12]) {
+  const int mu = n >> 1;
+  const bool fwd = (n & 1) == 0;
+  const int xm = mu == 0 ? x[0] : mu == 1 ? x[1] : mu == 2 ? x[2] : x[3];
+  const int lm = mu == 0 ? g.L[0] : mu == 1 ? g.L[1] : mu == 2 ? g.L[2] : g.L[3];
+  const int st = mu == 0 ? 1 : mu == 1 ? g.L[0] : mu == 2 ? g.L[0] * g.L[1] : g.L[0] * g.L[1] * g.L[2];
+  const int sn = fwd ? (xm == lm - 1 ? s - (lm - 1) * st : s + st) : (xm == 0 ? s + (lm - 1) * st : s - st);
+  // In powers of i, with S = -1 (forward) or +1 (backward) = i^sS:
+  //   h0 = psi0 + i^a0 psi_j0,  h1 = psi1 + i^a1 psi_(5-j0)
+  //   lower spins of (1 + S gamma_mu) w: acc2 += i^b0 w_k0, acc3 += i^b1 w_(1-k0)
+  // mu = 0: j0 3, a0 a1 sS+1, k0 1, b0 b1 sS+3;  mu = 1: j0 3, a0 sS+2, a1 sS, k0 1, b0 sS, b1 sS+2
+  // mu = 2: j0 2, a0 sS+1, a1 sS+3, k0 0, b0 sS+3, b1 sS+1;  mu = 3: j0 2, a0 a1 b0 b1 sS, k0 0
+  const int sS = fwd ? 2 : 0;
+  const bool lo3 = mu <= 1;   // j0 = 3 and k0 = 1
+  const int a0 = (sS + (mu == 0 || mu == 2 ? 1 : mu == 1 ? 2 : 0)) & 3;
+  const int a1 = (sS + (mu == 0 ? 1 : mu == 2 ? 3 : 0)) & 3;
+  const int b0 = (sS + (mu == 0 || mu == 2 ? 3 : 0)) & 3;
+  const int b1 = (sS + (mu == 0 ? 3 : mu == 1 ? 2 : mu == 2 ? 1 : 0)) & 3;
+  cpx<df> psi[12], h[6], w[6], u[9];
+  load_spinor_as_ro<PIN, df>(in, rhs, sn, psi);
+#pragma unroll
+  for (int c = 0; c < 3; ++c) {
+    const cpx<df> pa = lo3 ? psi[9 + c] : psi[6 + c];
+    const cpx<df> pb = lo3 ? psi[6 + c] : psi[9 + c];
+    h[c] = padd(psi[c], ipow(pa, a0));
+    h[3 + c] = padd(psi[3 + c], ipow(pb, a1));
+  }
+  LinkIO<P64E>::load(L, n, s, u);
+  su3_mul(u, h, w);
+#pragma unroll
+  for (int c = 0; c < 3; ++c) {
+    acc[c] = padd(acc[c], w[c]);
+    acc[3 + c] = padd(acc[3 + c], w[3 + c]);
+    const cpx<df> wa = lo3 ? w[3 + c] : w[c];
+    const cpx<df> wb = lo3 ? w[c] : w[3 + c];
+    acc[6 + c] = padd(acc[6 + c], ipow(wa, b0));
+    acc[9 + c] = padd(acc[9 + c], ipow(wb, b1));
+  }
+}
+
 template <int MU, int PIN, int PL, typename T>
 __device__ __forceinline__ void hop_dir(const Geom& g, const LinkRef& L, const SpinorRef& in, int rhs, int s,
                                         const int x[4], int stride, cpx<T> acc[12]) {
+  if constexpr (PL == P64E) {
+    hop_nb_df<PIN>(g, L, in, rhs, s, x, 2 * MU, acc);
+    hop_nb_df<PIN>(g, L, in, rhs, s, x, 2 * MU + 1, acc);
+    return;
+  } else {
   cpx<T> psi[12], h[6], w[6], u[9];
   // forward neighbour: (1 - gamma_mu) U_mu(x) psi(x + mu)
   {
@@ -223,6 +311,7 @@ __device__ __forceinline__ void hop_dir(const Geom& g, const LinkRef& L, const S
     su3_dag_mul(u, h, w);
     accumulate<MU, +1>(acc, w);
   }
+  }
 }
 
 template <int PIN, int PL, typename T>
@@ -232,6 +321,11 @@ __device__ __forceinline__ void hop(const Geom& g, const LinkRef& L, const Spino
   site_coords(g, s, x);
 #pragma unroll
   for (int k = 0; k < 12; ++k) acc[k] = cmk(T(0), T(0));
+  if constexpr (PL == P64E) {
+#pragma unroll 1
+    for (int n = 0; n < 8; ++n) hop_nb_df<PIN>(g, L, in, rhs, s, x, n, acc);
+    return;
+  }
   const int sy = g.L[0], sz = g.L[0] * g.L[1], st = sz * g.L[2];
   hop_dir<0, PIN, PL, T>(g, L, in, rhs, s, x, 1, acc);
   hop_dir<1, PIN, PL, T>(g, L, in, rhs, s, x, sy, acc);
@@ -254,23 +348,34 @@ struct DArgs {
   int variant;   // 0: thread per site, 1: direction split
 };
 
-// Epilogue shared by both kernel variants: acc holds the hop sum of site s.
+// Epilogue shared by both kernel variants: acc holds the hop sum of site s; v gets this
+// thread's contributions to the NVRED partial sums (see the mode list at the top).
 template <int MODE, int PIN, int POUT, int PA1, int PA2, typename T>
-__device__ __forceinline__ void wilson_epilogue(const DArgs& a, int rhs, int s, cpx<T> acc[12], double v[NVRED]) {
+__device__ __forceinline__ void wilson_epilogue(const DArgs& a, int rhs, int s, cpx<T> acc[12],
+                                                typename RedT<T>::type v[NVRED]) {
   cpx<T> c[12];
   load_spinor_as_ro<PIN, T>(a.in, rhs, s, c);
   const T kap = (T)a.kappa;
+  const bool red = a.partials != nullptr;
   if constexpr (MODE == MODE_K) {
     // K in = gamma5 (in - kappa acc)
 #pragma unroll
     for (int k = 0; k < 12; ++k) {
       cpx<T> o = c[k] - kap * acc[k];
       if (k >= 6) o = -o;
-      v[0] += (double)norm2(o);
-      v[1] += (double)norm2(c[k]);
       acc[k] = o;
     }
     store_spinor_as<POUT, T>(a.out, rhs, s, acc);
+    if (red) {
+      Acc<T> n0, n1;
+#pragma unroll
+      for (int k = 0; k < 12; ++k) {
+        acc_norm(n0, acc[k]);
+        acc_norm(n1, c[k]);
+      }
+      v[0] = n0.get();
+      v[1] = n1.get();
+    }
   } else if constexpr (MODE == MODE_R) {
     cpx<T> p[12], r[12];
     load_spinor_as<PA1, T>(a.aux1, rhs, s, p);
@@ -283,9 +388,14 @@ __device__ __forceinline__ void wilson_epilogue(const DArgs& a, int rhs, int s, 
       if (k >= 6) o = -o;
       o = o + sg * p[k];
       r[k] = r[k] - al * o;
-      v[0] += (double)norm2(r[k]);
     }
     store_spinor_as<PA2, T>(a.aux2, rhs, s, r);
+    if (red) {
+      Acc<T> n0;
+#pragma unroll
+      for (int k = 0; k < 12; ++k) acc_norm(n0, r[k]);
+      v[0] = n0.get();
+    }
   } else {
     cpx<T> w[12];
     T c1 = (T)a.c1, c2 = (T)a.c2;
@@ -306,16 +416,49 @@ __device__ __forceinline__ void wilson_epilogue(const DArgs& a, int rhs, int s, 
       acc[k] = o;
     }
     store_spinor_as<POUT, T>(a.out, rhs, s, acc);
-    if (a.partials != nullptr) {
+    if (red) {
       load_spinor_as<PA2, T>(a.aux2, rhs, s, w);
+      Acc<T> dr, di, n0, n1;   // (w, out) = sum conj(w) out
 #pragma unroll
       for (int k = 0; k < 12; ++k) {
-        cpx<T> d = cmulc(w[k], acc[k]);
-        v[0] += (double)d.r;
-        v[1] += (double)d.i;
-        v[2] += (double)norm2(acc[k]);
-        v[3] += (double)norm2(w[k]);
+        dr.add(w[k].r, acc[k].r);
+        dr.add(w[k].i, acc[k].i);
+        di.add(w[k].r, acc[k].i);
+        di.add(-w[k].i, acc[k].r);
+        acc_norm(n0, acc[k]);
+        acc_norm(n1, w[k]);
       }
+      v[0] = dr.get();
+      v[1] = di.get();
+      v[2] = n0.get();
+      v[3] = n1.get();
+    }
+  }
+}
+
+// Block sum of the per-thread partials: warp stage in R (FP32 for the FP32 kernels),
+// then FP64 across warps in a fixed order; the result is valid on thread (0, y).
+template <typename R>
+__device__ __forceinline__ void block_reduce_partials(R v[NVRED], double* smem, double out[NVRED]) {
+  const int lane = threadIdx.x & 31;
+  const int warp = threadIdx.x >> 5;
+  const int nwarp = blockDim.x >> 5;
+#pragma unroll
+  for (int j = 0; j < NVRED; ++j) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v[j] += __shfl_down_sync(0xffffffffu, v[j], o);
+  }
+  if (lane == 0) {
+#pragma unroll
+    for (int j = 0; j < NVRED; ++j) smem[(threadIdx.y * nwarp + warp) * NVRED + j] = (double)v[j];
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+#pragma unroll
+    for (int j = 0; j < NVRED; ++j) {
+      double t = 0.0;
+      for (int w = 0; w < nwarp; ++w) t += smem[(threadIdx.y * nwarp + w) * NVRED + j];
+      out[j] = t;
     }
   }
 }
@@ -331,17 +474,19 @@ __global__ void __launch_bounds__(256, MinBlocks<PL>::v) wilson_kernel(const DAr
   const int s = sb * BX + threadIdx.x;
   bool live = (s < a.g.V) && (rhs < a.nrhs);
   if (live && a.ms != nullptr && (MODE == MODE_K || MODE == MODE_R)) live = !a.ms[rhs].done;
-  double v[NVRED] = {0.0, 0.0, 0.0, 0.0};
+  using R = typename RedT<T>::type;
+  R v[NVRED] = {R(0), R(0), R(0), R(0)};
   if (live) {
     cpx<T> acc[12];
     hop<PIN, PL, T>(a.g, a.links, a.in, rhs, s, acc);
     wilson_epilogue<MODE, PIN, POUT, PA1, PA2, T>(a, rhs, s, acc, v);
   }
   if (a.partials != nullptr) {
-    block_reduce_rows<NVRED>(v, red);
+    double tot[NVRED];
+    block_reduce_partials<R>(v, red, tot);
     if (threadIdx.x == 0 && rhs < a.nrhs) {
 #pragma unroll
-      for (int j = 0; j < NVRED; ++j) a.partials[((size_t)rhs * a.nsb + sb) * NVRED + j] = v[j];
+      for (int j = 0; j < NVRED; ++j) a.partials[((size_t)rhs * a.nsb + sb) * NVRED + j] = tot[j];
     }
   }
 }
@@ -381,17 +526,19 @@ __global__ void __launch_bounds__(4 * BX, MinBlocks<PL>::v) wilson_split_kernel(
     for (int k = 0; k < 12; ++k) part[dir - 1][sl][k] = acc[k];
   }
   __syncthreads();
-  double v[NVRED] = {0.0, 0.0, 0.0, 0.0};
+  using R = typename RedT<T>::type;
+  R v[NVRED] = {R(0), R(0), R(0), R(0)};
   if (dir == 0 && live) {
 #pragma unroll
     for (int k = 0; k < 12; ++k) acc[k] = acc[k] + part[0][sl][k] + part[1][sl][k] + part[2][sl][k];
     wilson_epilogue<MODE, PIN, POUT, PA1, PA2, T>(a, rhs, s, acc, v);
   }
   if (a.partials != nullptr) {
-    block_reduce_rows<NVRED>(v, red);
+    double tot[NVRED];
+    block_reduce_partials<R>(v, red, tot);
     if (threadIdx.x == 0) {
 #pragma unroll
-      for (int j = 0; j < NVRED; ++j) a.partials[((size_t)rhs * a.nsb + sb) * NVRED + j] = v[j];
+      for (int j = 0; j < NVRED; ++j) a.partials[((size_t)rhs * a.nsb + sb) * NVRED + j] = tot[j];
     }
   }
 }

@@ -312,7 +312,7 @@ ovl_status sign_op(ovl_ctx* c, int mode, const Field& v, int voff, Field& out, i
   OVL_CUDA(c, cudaMemcpyAsync(c->dscal, c->hpin, sizeof(double) * ncopy, cudaMemcpyHostToDevice, c->st));
   const LinkRef L = links_of(c, PL);
   const int wcls = PL == P64E ? 8 : PL;  // profiler class of the Wilson launches
-  const double lbytes = (PL == P64E ? 576.0 : PL == P64 ? 384.0 : PL == P32 ? 192.0 : 96.0) * V;
+  const double lbytes = (PL == P64E ? 1152.0 : PL == P64 ? 384.0 : PL == P32 ? 192.0 : 96.0) * V;
   const double sbytes = (double)spinor_bytes(PP) * V, rbytes = (double)spinor_bytes(PR) * V;
   ProfPair pp;
 

@@ -1,0 +1,50 @@
+"""Time the Wilson kernel K alone through the C ABI (ovl_bench_wilson).
+
+    python -m paper_1501_01855_gb300.wilson_bench --dims 24 24 24 48 --prec f32 --nrhs 1
+
+Unit links, a random input spinor, the kernel launched `--iters` times back to back on
+the context stream and timed with CUDA events. Prints milliseconds per launch, the
+algorithmic bytes of one launch (each input spinor read once, each output written once,
+the links read once) and the rate they imply. `--variant` forces a kernel shape (0 one
+thread per site, 1 direction split); the default lets the create-time autotuner choose.
+"""
+import argparse
+
+import numpy as np
+
+from . import binding as B
+
+PRECS = {"f64": B.OVL_PREC_F64, "f32": B.OVL_PREC_F32, "f16": B.OVL_PREC_F16, "df64": B.OVL_PREC_F64E}
+
+
+def unit_links(dims):
+    lx, ly, lz, lt = dims
+    u = np.zeros((lt, lz, ly, lx, 4, 3, 3), dtype=np.complex128)
+    u[..., 0, 0] = u[..., 1, 1] = u[..., 2, 2] = 1.0
+    return u
+
+
+def main(argv=None):
+    ap = argparse.ArgumentParser(description=__doc__.splitlines()[0])
+    ap.add_argument("--dims", type=int, nargs=4, default=[24, 24, 24, 48], metavar=("LX", "LY", "LZ", "LT"))
+    ap.add_argument("--prec", choices=sorted(PRECS), default="f32")
+    ap.add_argument("--nrhs", type=int, default=1)
+    ap.add_argument("--iters", type=int, default=3)
+    ap.add_argument("--variant", type=int, default=-1, choices=[-1, 0, 1])
+    args = ap.parse_args(argv)
+    p = B.ovl_params_default()
+    p.a_override, p.b_override = 0.2, 2.6     # skip the Lanczos bound estimate
+    p.wilson_variant = args.variant
+    ctx = B.Overlap(tuple(args.dims), unit_links(args.dims), 1.4, 0.05, 8, 1e-3, params=p)
+    prec = PRECS[args.prec]
+    ms, nbytes = ctx.bench_wilson(prec, args.nrhs, args.iters)
+    v = int(np.prod(args.dims))
+    variant = ctx.wilson_tuning(prec)[0]
+    print("Wilson K %s, %s, nrhs %d, variant %d: %.4f ms per launch, %.1f MB algorithmic, %.0f GB/s, "
+          "%.2f G site-applications/s" % (args.prec, "x".join(map(str, args.dims)), args.nrhs, variant, ms,
+                                          nbytes / 1e6, nbytes / ms / 1e6, v * args.nrhs / ms / 1e6))
+    ctx.close()
+
+
+if __name__ == "__main__":
+    main()
