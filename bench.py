@@ -57,7 +57,7 @@ DF64_FP32_OPS_PER_SITE = 8 * (12 * 8 + 12 * (4 + 5 * 12) + 24 * 8) + 24 * (7 + 1
 # DRAM bytes (read + write) per launch of the double-float Wilson kernel in this step,
 # from an ncu capture of this command (the summary under profiles/ gives it); None
 # until captured for the current kernel.
-TRAFFIC_WILSON_DF64 = None
+TRAFFIC_WILSON_DF64 = 1.502e9
 
 
 def peaks():
@@ -388,7 +388,60 @@ def extras(args, ctx, dv, dout, ref_out, B, torch, stream, hbm):
                    "wilson_calls_dp2": info["wilson_calls"], "profile_ms": prof}
         cs.close()
     out["solve_16x16x16x32_mu0.05"] = sol
+    out["deflated_batched_16x16x16x32_mu0.02"] = deflated_batched(B, stream)
     return out
+
+
+def deflated_batched(B, stream):
+    """Deflated, batched right-hand sides (the shape of the paper's use case): an eigSUMR
+    solve of one Gaussian source accumulates 32 low modes (basis 64), then the 12
+    spin-colour point sources at one site are solved in one lock-step batch with the
+    deflated start; compared with the same batch undeflated and with one plain-FP64
+    (no mixed precision, no deflation) solve per source. mu = 0.02, 1e-10."""
+    import synth
+    mu, tol = 0.02, 1e-10
+    U = synth.gauge_links(DIMS, 0.3, 1003)
+    srcs = np.stack([synth.point_source(DIMS, s, c) for s in range(4) for c in range(3)])
+    res = {}
+    p = B.ovl_params_default()
+    p.stream = stream.cuda_stream
+    ctx = B.Overlap(DIMS, U, M0, mu, NPOLES, EPS, params=p)
+    b0 = synth.gaussian_source(DIMS, 2003)
+    x0 = np.zeros_like(b0)
+    t0 = time.perf_counter()
+    defl, info0 = ctx.eigsumr_accumulate(b0, x0, tol, 32, 64)
+    res["eigsumr_accumulation_solve_s"] = time.perf_counter() - t0
+    ritz, rres = defl.info()
+    res["eigsumr_outer_inner"] = [info0["outer_iters"], info0["inner_iters"]]
+    res["ritz_values_lowest4"] = [float(v) for v in ritz[:4]]
+    res["ritz_residual_max"] = float(np.max(rres)) if len(rres) else None
+    xs = np.zeros_like(srcs)
+    for name, d in (("mixed_batched_undeflated", None), ("mixed_batched_deflated", defl)):
+        t0 = time.perf_counter()
+        infos = ctx.solve(srcs, xs, tol, defl=d)
+        dt = time.perf_counter() - t0
+        res[name] = {"seconds": dt, "rhs_solves_per_s": len(srcs) / dt,
+                     "max_true_residual": max(i["true_residual"] for i in infos),
+                     "inner_iters_mean": float(np.mean([i["inner_iters"] for i in infos])),
+                     "wilson_calls_dp2_total": int(sum(i["wilson_calls"] for i in infos))}
+    defl.close()
+    ctx.close()
+    p = B.ovl_params_default()
+    p.mixed = 0
+    p.emulate_fp64 = 0
+    p.stream = stream.cuda_stream
+    cp = B.Overlap(DIMS, U, M0, mu, NPOLES, EPS, params=p)
+    x1 = np.zeros_like(srcs[:1])
+    t0 = time.perf_counter()
+    info = cp.solve(srcs[:1], x1, tol)[0]
+    dt = time.perf_counter() - t0
+    res["plain_fp64_single_rhs"] = {"seconds": dt, "rhs_solves_per_s": 1.0 / dt,
+                                    "true_residual": info["true_residual"], "inner_iters": info["inner_iters"],
+                                    "wilson_calls_dp2": info["wilson_calls"]}
+    cp.close()
+    res["deflated_batched_over_plain_fp64"] = (res["mixed_batched_deflated"]["rhs_solves_per_s"]
+                                               / res["plain_fp64_single_rhs"]["rhs_solves_per_s"])
+    return res
 
 
 def run_reference(args, ws, rank):

@@ -84,6 +84,8 @@ typedef struct {
   int    batch_max;     /* systems advanced together in one lock-step batch, default 36         */
   int    wilson_variant;/* Wilson-kernel launch shape: -1 autotune at create (default), 0 one
                            thread per site, 1 four threads per site (one per direction)        */
+  int    use_graphs;    /* 1 (default): run the multi-shift CG iterations as cached CUDA graphs
+                           (not while profiling); 0: launch every kernel on the stream        */
   int    verify;        /* 1: after a solve, recompute ||b - D x|| / ||b|| with an FP64 sign at
                            eps_sign (one more sign application per system); 0: report the
                            GMRESR recursive residual. Default 1                                 */

@@ -41,6 +41,7 @@ class ovl_params(ctypes.Structure):
                 ("gmresr_max", ctypes.c_int), ("inner_max", ctypes.c_int), ("mscg_max", ctypes.c_int),
                 ("delta_split", ctypes.c_double), ("c_spec", ctypes.c_double), ("bc_t", ctypes.c_int),
                 ("a_override", ctypes.c_double), ("b_override", ctypes.c_double), ("batch_max", ctypes.c_int), ("wilson_variant", ctypes.c_int),
+                ("use_graphs", ctypes.c_int),
                 ("verify", ctypes.c_int), ("stream", ctypes.c_void_p)]
 
 

@@ -44,6 +44,7 @@ extern "C" ovl_status ovl_params_default(ovl_params* p) {
   p->b_override = 0.0;
   p->batch_max = 36;
   p->wilson_variant = -1;
+  p->use_graphs = 1;
   p->verify = 1;
   p->stream = nullptr;
   return OVL_OK;
@@ -216,6 +217,9 @@ extern "C" void overlap_destroy(ovl_ctx* c) {
   if (c->hpin) cudaFreeHost(c->hpin);
   if (c->hstage) cudaFreeHost(c->hstage);
   if (c->stage_ev) cudaEventDestroy(c->stage_ev);
+  for (auto& g : c->graphs)
+    if (g.exec) cudaGraphExecDestroy(g.exec);
+  if (c->cap_st) cudaStreamDestroy(c->cap_st);
   for (auto& q : c->prof.pending) {
     cudaEventDestroy(q.a);
     cudaEventDestroy(q.b);
@@ -263,6 +267,7 @@ static ovl_status create_impl(ovl_ctx* c, const int dims[4], const double* links
   OVL_CUDA(c, cudaMalloc((void**)&c->dint, sizeof(int) * 4096));
   OVL_CUDA(c, cudaMalloc((void**)&c->dpoles, sizeof(Poles)));
   OVL_CUDA(c, cudaEventCreateWithFlags(&c->stage_ev, cudaEventDisableTiming));
+  OVL_CUDA(c, cudaStreamCreateWithFlags(&c->cap_st, cudaStreamNonBlocking));
   // gauge field in the three storage formats
   {
     std::vector<double> l64;

@@ -36,6 +36,14 @@ struct Profiler {
 // SIGN64E: FP64-accurate sign computed in double-float on the FP32 pipes.
 enum SignMode { SIGN64 = 0, SIGN32 = 1, SIGN16 = 2, SIGN64E = 3 };
 
+// An instantiated CUDA graph of G multi-shift CG iterations (5 launches each), keyed by
+// everything its launches capture (field pointers, precisions, counts, constants).
+struct MsGraph {
+  std::vector<unsigned long long> key;
+  cudaGraphExec_t exec = nullptr;
+  long long last_use = 0;
+};
+
 struct SignStats {
   std::vector<int> iters;     // multi-shift CG iterations per system
   std::vector<int> status;    // 0 converged, 1 iteration limit, 2 breakdown
@@ -74,6 +82,9 @@ struct ovl_ctx {
   size_t dwork_n = 0;
   size_t ring_pos = 0;           // scalar upload ring in hpin / dscal, [32768, 262144)
   cudaEvent_t stage_ev = nullptr;  // last copy out of hstage
+  cudaStream_t cap_st = nullptr;   // private stream for graph capture (the context stream may be the legacy one)
+  std::vector<ovl::MsGraph> graphs;  // cached multi-shift CG iteration graphs
+  long long graph_clock = 0;
   bool exact_rational = false;   // solve shifted systems past Delta (gradient of the rational)
   std::string err;
   ovl::Profiler prof;

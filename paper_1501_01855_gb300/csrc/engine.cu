@@ -276,6 +276,49 @@ int choose_mode(const ovl_ctx* c, double eta) {
   return accurate;
 }
 
+// Find or capture the cached graph for key. capture(stream) issues the launches; they
+// are recorded on the context's private capture stream and instantiated once. At most
+// kMaxGraphs graphs are kept (least recently used dropped).
+static constexpr int kGraphIters = 8;
+static constexpr size_t kMaxGraphs = 16;
+template <typename F>
+static ovl_status ms_graph(ovl_ctx* c, const std::vector<unsigned long long>& key, cudaGraphExec_t* out, F capture) {
+  ++c->graph_clock;
+  for (auto& g : c->graphs)
+    if (g.key == key) {
+      g.last_use = c->graph_clock;
+      *out = g.exec;
+      return OVL_OK;
+    }
+  // the capture stream must not start before the work already queued on the context
+  // stream that the graph will follow: graphs are launched on the context stream, so
+  // capturing itself needs no ordering, only launches do.
+  OVL_CUDA(c, cudaStreamBeginCapture(c->cap_st, cudaStreamCaptureModeThreadLocal));
+  capture(c->cap_st);
+  cudaGraph_t graph = nullptr;
+  const cudaError_t e1 = cudaStreamEndCapture(c->cap_st, &graph);
+  OVL_TRY(check_launch(c, "multi-shift CG graph capture"));
+  if (e1 != cudaSuccess) return cuda_check(c, e1, "cudaStreamEndCapture");
+  cudaGraphExec_t exec = nullptr;
+  const cudaError_t e2 = cudaGraphInstantiate(&exec, graph, 0);
+  cudaGraphDestroy(graph);
+  if (e2 != cudaSuccess) return cuda_check(c, e2, "cudaGraphInstantiate");
+  if (c->graphs.size() >= kMaxGraphs) {
+    size_t old = 0;
+    for (size_t i = 1; i < c->graphs.size(); ++i)
+      if (c->graphs[i].last_use < c->graphs[old].last_use) old = i;
+    cudaGraphExecDestroy(c->graphs[old].exec);
+    c->graphs.erase(c->graphs.begin() + old);
+  }
+  MsGraph g;
+  g.key = key;
+  g.exec = exec;
+  g.last_use = c->graph_clock;
+  c->graphs.push_back(g);
+  *out = exec;
+  return OVL_OK;
+}
+
 ovl_status sign_op(ovl_ctx* c, int mode, const Field& v, int voff, Field& out, int ooff, int n, const double* eta,
                    double c1, double c2, const double* coef, int herm, const Field* dot_w, int woff, double* dots,
                    SignStats* stats) {
@@ -328,8 +371,33 @@ ovl_status sign_op(ovl_ctx* c, int mode, const Field& v, int voff, Field& out, i
   int* hdone = reinterpret_cast<int*>(c->hpin + 8192);
   int total = 0;
   int chunk = 8;
+  // Without profiling, the iterations run as a CUDA graph of kGraphIters iterations,
+  // captured once per field configuration and replayed: one graph launch instead of
+  // 5 kGraphIters kernel launches (a single-system step on 16^3 x 32 is ~50 us of
+  // kernels, comparable to the launch overhead of its 5 launches).
+  cudaGraphExec_t gexec = nullptr;
+  if (!c->prof.on && c->P.use_graphs) {
+    const std::vector<unsigned long long> key = {
+        (unsigned long long)PP, (unsigned long long)PL, (unsigned long long)PR, (unsigned long long)n,
+        (unsigned long long)np, (unsigned long long)(uintptr_t)pb->data, (unsigned long long)(uintptr_t)t->data,
+        (unsigned long long)(uintptr_t)r->data, (unsigned long long)(uintptr_t)y->data,
+        (unsigned long long)(uintptr_t)c->partials, (unsigned long long)(uintptr_t)c->ms,
+        (unsigned long long)(uintptr_t)L.data, (unsigned long long)L.variant};
+    OVL_TRY(ms_graph(c, key, &gexec, [&](cudaStream_t cs) {
+      for (int k = 0; k < kGraphIters; ++k) {
+        launch_wilson_K(PP, PL, PP, c->g, c->kappa, L, pb->ref(), t->ref(), n, c->partials, c->ms, cs);
+        launch_ms_scalar1(c->ms, c->partials, sh.nsb, n, c->dpoles, cs);
+        launch_wilson_mscg_r(PP, PL, PR, PP, c->g, c->kappa, L, t->ref(), pb->ref(), r->ref(), n,
+                             c->hpoles.sigma0, c->partials, c->ms, cs);
+        launch_ms_scalar2(c->ms, c->partials, sh.nsb, n, c->dpoles, cs);
+        launch_ms_update(PR, PP, r->ref(), pb->ref(), y->ref(), np, n, V, c->ms, cs);
+      }
+    }));
+  }
   while (true) {
-    for (int k = 0; k < chunk; ++k) {
+    if (gexec) {
+      for (int k = 0; k < chunk; k += kGraphIters) OVL_CUDA(c, cudaGraphLaunch(gexec, c->st));
+    } else for (int k = 0; k < chunk; ++k) {
       prof_begin(c, wcls, &pp);
       launch_wilson_K(PP, PL, PP, c->g, c->kappa, L, pb->ref(), t->ref(), n, c->partials, c->ms, c->st);
       prof_end(c, &pp, 0.0);
