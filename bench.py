@@ -393,11 +393,13 @@ def extras(args, ctx, dv, dout, ref_out, B, torch, stream, hbm):
 
 
 def deflated_batched(B, stream):
-    """Deflated, batched right-hand sides (the shape of the paper's use case): an eigSUMR
-    solve of one Gaussian source accumulates 32 low modes (basis 64), then the 12
-    spin-colour point sources at one site are solved in one lock-step batch with the
-    deflated start; compared with the same batch undeflated and with one plain-FP64
-    (no mixed precision, no deflation) solve per source. mu = 0.02, 1e-10."""
+    """Deflated, batched right-hand sides (the shape of the paper's use case): eigSUMR
+    solves of three Gaussian sources accumulate and refine 32 low modes of D^dag D
+    (basis 96), then the 12 spin-colour point sources at one site are solved in one
+    lock-step batch, undeflated and deflated, with relSUMR (deflated start) and relCG
+    (spectral preconditioner; the space is handed over through ovl_defl_save/load),
+    against one plain-FP64 (no mixed precision, no deflation) solve. mu = 0.02, 1e-10."""
+    import tempfile
     import synth
     mu, tol = 0.02, 1e-10
     U = synth.gauge_links(DIMS, 0.3, 1003)
@@ -406,26 +408,44 @@ def deflated_batched(B, stream):
     p = B.ovl_params_default()
     p.stream = stream.cuda_stream
     ctx = B.Overlap(DIMS, U, M0, mu, NPOLES, EPS, params=p)
-    b0 = synth.gaussian_source(DIMS, 2003)
-    x0 = np.zeros_like(b0)
+    defl = None
     t0 = time.perf_counter()
-    defl, info0 = ctx.eigsumr_accumulate(b0, x0, tol, 32, 64)
-    res["eigsumr_accumulation_solve_s"] = time.perf_counter() - t0
+    for k in range(3):
+        b0 = synth.gaussian_source(DIMS, 2003 + k)
+        x0 = np.zeros_like(b0)
+        defl, info0 = ctx.eigsumr_accumulate(b0, x0, tol, 32, 96, defl=defl)
+    res["eigsumr_3_accumulation_solves_s"] = time.perf_counter() - t0
     ritz, rres = defl.info()
-    res["eigsumr_outer_inner"] = [info0["outer_iters"], info0["inner_iters"]]
     res["ritz_values_lowest4"] = [float(v) for v in ritz[:4]]
-    res["ritz_residual_max"] = float(np.max(rres)) if len(rres) else None
-    xs = np.zeros_like(srcs)
-    for name, d in (("mixed_batched_undeflated", None), ("mixed_batched_deflated", defl)):
+    res["ritz_residual_lowest8_max"] = float(np.max(rres[:8]))
+    res["ritz_residual_median"] = float(np.median(rres))
+
+    def batch(c, d):
+        xs = np.zeros_like(srcs)
         t0 = time.perf_counter()
-        infos = ctx.solve(srcs, xs, tol, defl=d)
+        infos = c.solve(srcs, xs, tol, defl=d)
         dt = time.perf_counter() - t0
-        res[name] = {"seconds": dt, "rhs_solves_per_s": len(srcs) / dt,
-                     "max_true_residual": max(i["true_residual"] for i in infos),
-                     "inner_iters_mean": float(np.mean([i["inner_iters"] for i in infos])),
-                     "wilson_calls_dp2_total": int(sum(i["wilson_calls"] for i in infos))}
-    defl.close()
-    ctx.close()
+        return {"seconds": dt, "rhs_solves_per_s": len(srcs) / dt,
+                "max_true_residual": max(i["true_residual"] for i in infos),
+                "inner_iters_mean": float(np.mean([i["inner_iters"] for i in infos])),
+                "wilson_calls_dp2_total": int(sum(i["wilson_calls"] for i in infos))}
+
+    res["relSUMR_undeflated"] = batch(ctx, None)
+    res["relSUMR_deflated"] = batch(ctx, defl)
+    with tempfile.TemporaryDirectory() as d:
+        path = os.path.join(d, "defl.bin")
+        defl.save(path)
+        defl.close()
+        ctx.close()
+        p = B.ovl_params_default()
+        p.solver = B.OVL_SOLVER_CG
+        p.stream = stream.cuda_stream
+        cc = B.Overlap(DIMS, U, M0, mu, NPOLES, EPS, params=p)
+        dc = B.Deflation.load_file(cc, path)
+        res["relCG_undeflated"] = batch(cc, None)
+        res["relCG_deflated"] = batch(cc, dc)
+        dc.close()
+        cc.close()
     p = B.ovl_params_default()
     p.mixed = 0
     p.emulate_fp64 = 0
@@ -439,8 +459,8 @@ def deflated_batched(B, stream):
                                     "true_residual": info["true_residual"], "inner_iters": info["inner_iters"],
                                     "wilson_calls_dp2": info["wilson_calls"]}
     cp.close()
-    res["deflated_batched_over_plain_fp64"] = (res["mixed_batched_deflated"]["rhs_solves_per_s"]
-                                               / res["plain_fp64_single_rhs"]["rhs_solves_per_s"])
+    best = max(res[k]["rhs_solves_per_s"] for k in ("relSUMR_deflated", "relCG_deflated"))
+    res["best_deflated_batched_over_plain_fp64"] = best / res["plain_fp64_single_rhs"]["rhs_solves_per_s"]
     return res
 
 

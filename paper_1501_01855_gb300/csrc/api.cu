@@ -105,8 +105,9 @@ static void convert_links(const double* links, const int L[4], int bc_t, std::ve
   }
 }
 
-// Autotuner: time both Wilson-kernel variants for every storage precision on this
-// lattice (one system, random input) and keep the faster one.
+// Autotuner: time the Wilson-kernel variants (thread per site, direction split, and 4D
+// tiles when the lattice divides into them) for every storage precision on this
+// lattice (one system, random input) and keep the fastest.
 static ovl_status autotune_wilson(ovl_ctx* c) {
   const int forced = c->P.wilson_variant;
   std::vector<double> h((size_t)24 * c->V);
@@ -119,15 +120,16 @@ static ovl_status autotune_wilson(ovl_ctx* c) {
   OVL_CUDA(c, cudaEventCreate(&e0));
   OVL_CUDA(c, cudaEventCreate(&e1));
   for (int p = 0; p < 4; ++p) {
-    if (forced == 0 || forced == 1) {
-      c->wvar[p] = forced;
+    if (forced >= 0 && forced <= 2) {
+      c->wvar[p] = (forced == 2 && !wilson_tiles_fit(c->g)) ? 0 : forced;
       continue;
     }
     Field *fi, *fo;
     OVL_TRY(get_field(c, "at_in", p, 1, &fi));
     OVL_TRY(get_field(c, "at_out", p, 1, &fo));
     OVL_TRY(import_spinors(c, h.data(), OVL_C128, 0, 1, *fi, 0));
-    for (int v = 0; v < 2; ++v) {
+    const int nv = wilson_tiles_fit(c->g) ? 3 : 2;
+    for (int v = 0; v < nv; ++v) {
       LinkRef L = links_of(c, p);
       L.variant = v;
       const int reps = p == P64 ? 3 : 8;
@@ -143,7 +145,10 @@ static ovl_status autotune_wilson(ovl_ctx* c) {
       cudaEventElapsedTime(&ms, e0, e1);
       c->wtime[p][v] = ms / reps;
     }
-    c->wvar[p] = c->wtime[p][1] < c->wtime[p][0] ? 1 : 0;
+    int best = 0;
+    for (int v = 1; v < nv; ++v)
+      if (c->wtime[p][v] < c->wtime[p][best]) best = v;
+    c->wvar[p] = best;
     free_field(c->ws["at_in"]);
     free_field(c->ws["at_out"]);
   }
@@ -621,7 +626,7 @@ extern "C" ovl_status eigsumr_accumulate(ovl_ctx* c, ovl_defl** defl, int n_eig,
     return st;
   }
   // final Ritz step over whatever the basis holds
-  if (e.k > e.n_seeded || e.ndiag == 0) OVL_TRY(ritz_step(c, &e, n_eig));
+  if (e.k > e.n_seeded || e.ndiag == 0 || e.k > n_eig) OVL_TRY(ritz_step(c, &e, n_eig));
   const int nk = e.k;
   if (nk < 1) {
     if (fresh) ovl_defl_destroy(d);
@@ -787,11 +792,13 @@ extern "C" ovl_status ovl_profile_get(ovl_ctx* c, int cls, long long* launches, 
   return OVL_OK;
 }
 
-extern "C" ovl_status ovl_wilson_tuning(const ovl_ctx* c, int prec, int* variant, double* ms0, double* ms1) {
+extern "C" ovl_status ovl_wilson_tuning(const ovl_ctx* c, int prec, int* variant, double* ms0, double* ms1,
+                                        double* ms2) {
   if (!c || prec < P64 || prec > P64E) return OVL_EINVAL;
   if (variant) *variant = c->wvar[prec];
   if (ms0) *ms0 = c->wtime[prec][0];
   if (ms1) *ms1 = c->wtime[prec][1];
+  if (ms2) *ms2 = c->wtime[prec][2];
   return OVL_OK;
 }
 

@@ -316,9 +316,7 @@ __device__ __forceinline__ void hop_dir(const Geom& g, const LinkRef& L, const S
 
 template <int PIN, int PL, typename T>
 __device__ __forceinline__ void hop(const Geom& g, const LinkRef& L, const SpinorRef& in, int rhs, int s,
-                                    cpx<T> acc[12]) {
-  int x[4];
-  site_coords(g, s, x);
+                                    const int x[4], cpx<T> acc[12]) {
 #pragma unroll
   for (int k = 0; k < 12; ++k) acc[k] = cmk(T(0), T(0));
   if constexpr (PL == P64E) {
@@ -345,7 +343,7 @@ struct DArgs {
   double c1, c2;
   const double* coef;
   int herm;
-  int variant;   // 0: thread per site, 1: direction split
+  int variant;   // 0: thread per site, 1: direction split, 2: 4D tiles
 };
 
 // Epilogue shared by both kernel variants: acc holds the hop sum of site s; v gets this
@@ -463,22 +461,53 @@ __device__ __forceinline__ void block_reduce_partials(R v[NVRED], double* smem, 
   }
 }
 
-// Variant 0: one thread per (site, system) walks all eight neighbours.
-template <int MODE, int PIN, int PL, int POUT, int PA1, int PA2>
+// Variant 0: one thread per (site, system) walks all eight neighbours; a block is BX
+// consecutive sites (x fastest) times up to 4 systems.
+// Variant 2 (TILED): a block is one system on a 4D tile of TX x TY x TZ x TT = 256 sites,
+// so that the neighbours in all four directions mostly lie in the block's own tile
+// (L1 hits) instead of BX/Lx rows away in z and t. Needs every extent divisible by the
+// tile. Its block sum goes to the first of the tile's 256/BX partial slots (the others
+// get zero), so the partial layout (system, BX-site block) is the same for all variants.
+constexpr int TX = 8, TY = 4, TZ = 4, TT = 2;
+template <int MODE, int PIN, int PL, int POUT, int PA1, int PA2, bool TILED>
 __global__ void __launch_bounds__(256, MinBlocks<PL>::v) wilson_kernel(const DArgs a) {
   using T = typename Real<PL>::T;
   __shared__ double red[4 * (BX / 32) * NVRED];
-  const int sb = blockIdx.x / a.ngr;
-  const int rg = blockIdx.x - sb * a.ngr;
-  const int rhs = rg * blockDim.y + threadIdx.y;
-  const int s = sb * BX + threadIdx.x;
-  bool live = (s < a.g.V) && (rhs < a.nrhs);
+  int sb, rhs, s;
+  int x[4];
+  bool live;
+  if constexpr (TILED) {
+    const int ntx = a.g.L[0] / TX, nty = a.g.L[1] / TY, ntz = a.g.L[2] / TZ;
+    int b = blockIdx.x;
+    const int bx = b % ntx;
+    b /= ntx;
+    const int by = b % nty;
+    b /= nty;
+    const int bz = b % ntz;
+    const int bt = b / ntz;
+    const int t = threadIdx.x;
+    x[0] = bx * TX + (t & 7);
+    x[1] = by * TY + ((t >> 3) & 3);
+    x[2] = bz * TZ + ((t >> 5) & 3);
+    x[3] = bt * TT + (t >> 7);
+    s = ((x[3] * a.g.L[2] + x[2]) * a.g.L[1] + x[1]) * a.g.L[0] + x[0];
+    rhs = blockIdx.y;
+    sb = blockIdx.x * (TX * TY * TZ * TT / BX);
+    live = rhs < a.nrhs;
+  } else {
+    sb = blockIdx.x / a.ngr;
+    const int rg = blockIdx.x - sb * a.ngr;
+    rhs = rg * blockDim.y + threadIdx.y;
+    s = sb * BX + threadIdx.x;
+    live = (s < a.g.V) && (rhs < a.nrhs);
+    if (live) site_coords(a.g, s, x);
+  }
   if (live && a.ms != nullptr && (MODE == MODE_K || MODE == MODE_R)) live = !a.ms[rhs].done;
   using R = typename RedT<T>::type;
   R v[NVRED] = {R(0), R(0), R(0), R(0)};
   if (live) {
     cpx<T> acc[12];
-    hop<PIN, PL, T>(a.g, a.links, a.in, rhs, s, acc);
+    hop<PIN, PL, T>(a.g, a.links, a.in, rhs, s, x, acc);
     wilson_epilogue<MODE, PIN, POUT, PA1, PA2, T>(a, rhs, s, acc, v);
   }
   if (a.partials != nullptr) {
@@ -487,8 +516,18 @@ __global__ void __launch_bounds__(256, MinBlocks<PL>::v) wilson_kernel(const DAr
     if (threadIdx.x == 0 && rhs < a.nrhs) {
 #pragma unroll
       for (int j = 0; j < NVRED; ++j) a.partials[((size_t)rhs * a.nsb + sb) * NVRED + j] = tot[j];
+      if constexpr (TILED) {
+        for (int q = 1; q < TX * TY * TZ * TT / BX; ++q)
+#pragma unroll
+          for (int j = 0; j < NVRED; ++j) a.partials[((size_t)rhs * a.nsb + sb + q) * NVRED + j] = 0.0;
+      }
     }
   }
+}
+
+// true when the lattice can be covered by whole variant-2 tiles
+bool wilson_tiles_fit(const Geom& g) {
+  return g.L[0] % TX == 0 && g.L[1] % TY == 0 && g.L[2] % TZ == 0 && g.L[3] % TT == 0;
 }
 
 // Variant 1 (direction split): a block of 4 * BX threads covers BX sites of one system;
@@ -559,8 +598,11 @@ static void run(DArgs a, cudaStream_t st) {
   if (a.variant == 1) {
     // one system per block; partials keep the (system, BX-site block) layout of variant 0
     wilson_split_kernel<MODE, PIN, PL, POUT, PA1, PA2><<<dim3((unsigned)(sh.nsb * a.nrhs)), dim3(4 * BX), 0, st>>>(a);
+  } else if (a.variant == 2 && wilson_tiles_fit(a.g)) {
+    const unsigned ntiles = (unsigned)(a.g.V / (TX * TY * TZ * TT));
+    wilson_kernel<MODE, PIN, PL, POUT, PA1, PA2, true><<<dim3(ntiles, (unsigned)a.nrhs), dim3(TX * TY * TZ * TT), 0, st>>>(a);
   } else {
-    wilson_kernel<MODE, PIN, PL, POUT, PA1, PA2><<<sh.grid(), sh.block(), 0, st>>>(a);
+    wilson_kernel<MODE, PIN, PL, POUT, PA1, PA2, false><<<sh.grid(), sh.block(), 0, st>>>(a);
   }
 }
 

@@ -31,7 +31,7 @@
 
 namespace ovl {
 
-ovl_status ritz_step(ovl_ctx* c, EigState* e, int keep) {
+ovl_status ritz_step(ovl_ctx* c, EigState* e, int keep, bool restart) {
   const int k = e->k;
   if (k == 0) return OVL_OK;
   keep = std::min(keep, k);
@@ -100,14 +100,85 @@ ovl_status ritz_step(ovl_ctx* c, EigState* e, int keep) {
       T[(size_t)i * r + j] = s;
     }
   std::vector<double> lam(r);
+  std::vector<cd> T0 = T;
   eigh_jacobi(r, T.data(), lam.data(), Y.data());
   keep = std::min(keep, r);
-  // C = B Y[:, :keep]  (k x keep)
+  // Locally optimal restart (the eigCG restart that the accumulation of Sec. 5 adapts):
+  // at a basis restart keep the lowest Ritz vectors of the whole basis and those of the
+  // basis without its newest vector, Rayleigh-Ritz on their span. With the Cholesky
+  // coordinates (B upper triangular) the first k-1 columns of B span the first k-1
+  // basis vectors, so the second set comes from the leading block of T.
+  const bool lo = restart && r == k && 2 * keep + 1 <= k;
+  int nout = keep;
+  std::vector<cd> Yc((size_t)r * keep);   // r x nout coefficients in B coordinates
+  for (int i = 0; i < r; ++i)
+    for (int j = 0; j < keep; ++j) Yc[(size_t)i * keep + j] = Y[(size_t)i * r + j];
+  if (lo) {
+    const int k1 = k - 1;
+    std::vector<cd> T1((size_t)k1 * k1), Y1((size_t)k1 * k1);
+    for (int i = 0; i < k1; ++i)
+      for (int j = 0; j < k1; ++j) T1[(size_t)i * k1 + j] = T0[(size_t)i * k + j];
+    std::vector<double> lam1(k1);
+    eigh_jacobi(k1, T1.data(), lam1.data(), Y1.data());
+    // Z = [Y[:, :keep], (Y1[:, :keep]; 0)], orthonormalised (modified Gram-Schmidt)
+    std::vector<std::vector<cd>> Z;
+    for (int j = 0; j < 2 * keep; ++j) {
+      std::vector<cd> z(k, 0.0);
+      if (j < keep)
+        for (int i = 0; i < k; ++i) z[i] = Y[(size_t)i * k + j];
+      else
+        for (int i = 0; i < k1; ++i) z[i] = Y1[(size_t)i * k1 + (j - keep)];
+      for (int pass = 0; pass < 2; ++pass)
+        for (const auto& q : Z) {
+          cd d = 0;
+          for (int i = 0; i < k; ++i) d += std::conj(q[i]) * z[i];
+          for (int i = 0; i < k; ++i) z[i] -= d * q[i];
+        }
+      double nz = 0;
+      for (int i = 0; i < k; ++i) nz += std::norm(z[i]);
+      nz = std::sqrt(nz);
+      if (nz < 1e-8) continue;
+      for (int i = 0; i < k; ++i) z[i] /= nz;
+      Z.push_back(z);
+    }
+    const int q = (int)Z.size();
+    // Rayleigh-Ritz on span Z: T2 = Z^dag T Z
+    std::vector<cd> T2((size_t)q * q), Y2((size_t)q * q);
+    for (int a2 = 0; a2 < q; ++a2)
+      for (int b2 = 0; b2 < q; ++b2) {
+        cd sacc = 0;
+        for (int i = 0; i < k; ++i) {
+          cd ti = 0;
+          for (int l = 0; l < k; ++l) ti += T0[(size_t)i * k + l] * Z[b2][l];
+          sacc += std::conj(Z[a2][i]) * ti;
+        }
+        T2[(size_t)a2 * q + b2] = sacc;
+      }
+    for (int a2 = 0; a2 < q; ++a2)
+      for (int b2 = a2 + 1; b2 < q; ++b2) {
+        const cd h = 0.5 * (T2[(size_t)a2 * q + b2] + std::conj(T2[(size_t)b2 * q + a2]));
+        T2[(size_t)a2 * q + b2] = h;
+        T2[(size_t)b2 * q + a2] = std::conj(h);
+      }
+    std::vector<double> lam2(q);
+    eigh_jacobi(q, T2.data(), lam2.data(), Y2.data());
+    nout = q;
+    Yc.assign((size_t)r * nout, 0.0);
+    for (int i = 0; i < k; ++i)
+      for (int j = 0; j < nout; ++j) {
+        cd sacc = 0;
+        for (int l = 0; l < q; ++l) sacc += Z[l][i] * Y2[(size_t)l * q + j];
+        Yc[(size_t)i * nout + j] = sacc;
+      }
+    lam.assign(lam2.begin(), lam2.end());
+  }
+  keep = nout;
+  // C = B Yc  (k x keep)
   std::vector<cd> C((size_t)k * keep);
   for (int i = 0; i < k; ++i)
     for (int j = 0; j < keep; ++j) {
       cd s = 0;
-      for (int l = 0; l < r; ++l) s += B[(size_t)i * r + l] * Y[(size_t)l * r + j];
+      for (int l = 0; l < r; ++l) s += B[(size_t)i * r + l] * Yc[(size_t)l * keep + j];
       C[(size_t)i * keep + j] = s;
     }
   // rotate v and w
@@ -149,6 +220,12 @@ ovl_status ritz_step(ovl_ctx* c, EigState* e, int keep) {
   const double den = std::sqrt((double)std::max(1, e->m - e->n_eig) * e->kk) * std::max(avg, 1e-12);
   double cap = num / den;
   if (!(cap > 0)) cap = e->eps_v;
+  // The bound is absolute, but an error in v^D = D v only leaves the low Ritz pairs
+  // usable while it is small against their singular values (Sec. 5.1 warns that too
+  // low an accuracy for v^D makes the eigenvalue estimates diverge): cap it at 5% of
+  // the smallest Ritz singular value (never below mu, the bound of D's spectrum).
+  const double lmin = std::max(e->ritz.empty() ? mu * mu : e->ritz[0], mu * mu);
+  cap = std::min(cap, 0.05 * std::sqrt(lmin));
   e->eta_cap = std::min(std::max(cap, 1e-10), c->P.eta_floor);
   if (e->eig) e->eig->eta_cap = e->eta_cap;
   return OVL_OK;
@@ -161,7 +238,7 @@ ovl_status eig_hook(ovl_ctx* c, void* data, const Field& q, const Field& u, int 
   OVL_TRY(copy_convert(c, q, 0, *e->V, e->k, 1));
   OVL_TRY(copy_convert(c, u, 0, *e->W, e->k, 1));
   e->k += 1;
-  if (e->k == e->m) OVL_TRY(ritz_step(c, e, e->n_eig));
+  if (e->k == e->m) OVL_TRY(ritz_step(c, e, e->n_eig, true));
   return OVL_OK;
 }
 

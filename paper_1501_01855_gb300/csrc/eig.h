@@ -22,7 +22,9 @@ struct EigState {
   EigHook* eig = nullptr;
 };
 
-ovl_status ritz_step(ovl_ctx* c, EigState* e, int keep);
+// keep the lowest `keep` Ritz vectors; restart = a basis restart inside the solve (also
+// keeps the lowest Ritz vectors of the basis without its newest vector)
+ovl_status ritz_step(ovl_ctx* c, EigState* e, int keep, bool restart = false);
 ovl_status eig_hook(ovl_ctx* c, void* data, const Field& q, const Field& u, int iter);
 
 }  // namespace ovl

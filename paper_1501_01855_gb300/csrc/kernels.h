@@ -64,6 +64,8 @@ struct Shape {
   dim3 block() const { return dim3(BX, by); }
 };
 Shape make_shape(int V, int nrhs);
+// the lattice is covered by whole tiles of Wilson-kernel variant 2
+bool wilson_tiles_fit(const Geom& g);
 
 // ---------------------------------------------------------------- Wilson kernel
 // K in (Sec. 1) with optional per-(rhs, block) partials {||out||^2, ||in||^2}.

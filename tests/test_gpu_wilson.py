@@ -67,3 +67,38 @@ def test_wilson_full_size_sampled(dims):
     c.wilson_apply(psi, Kpsi, 0)
     l, r = np.vdot(psi, Kb), np.vdot(Kpsi, b)
     assert abs(l - r) <= 1e-12 * abs(l)
+
+
+@pytest.mark.parametrize("variant", [0, 1, 2])
+@pytest.mark.parametrize("prec", [0, 1, 2, 3])
+def test_wilson_launch_variants(variant, prec):
+    """Every launch shape the autotuner can pick (thread per site, direction split, 4D
+    tiles) gives K to the precision's tolerance, on a lattice that divides into tiles
+    (two tiles in t) with antiperiodic t, for several systems at once."""
+    dims = (8, 4, 8, 4)
+    U = synth.gauge_links(dims, 0.3, 1021)
+    c = ctx(dims, U, a=0.1, b=2.6, bc_t=1, wilson_variant=variant)
+    assert c.wilson_tuning(prec)[0] == variant
+    psi = synth.gaussian_source(dims, 2021, nvec=5)
+    out = np.zeros_like(psi)
+    c.wilson_apply(psi, out, prec)
+    for j in range(5):
+        assert rel(out[j], wilson.apply_K(U, psi[j], M0, True)) <= TOL[prec]
+
+
+@pytest.mark.parametrize("variant", [0, 1, 2])
+def test_sign_with_launch_variants(variant):
+    """The multi-shift CG reads its scalars from the Wilson kernel's partial sums; every
+    launch shape must give the same sign function (to the FP64 rounding of different
+    summation orders)."""
+    dims = (8, 4, 8, 4)
+    U = synth.gauge_links(dims, 0.3, 1022)
+    v = synth.gaussian_source(dims, 2022, nvec=2)
+    ref = np.zeros_like(v)
+    ctx(dims, U, n_poles=16, a=0.2, b=2.6, wilson_variant=0).sign_apply(v, ref, eta=1e-11, prec=0)
+    c = ctx(dims, U, n_poles=16, a=0.2, b=2.6, wilson_variant=variant)
+    for prec in (0, 3):
+        out = np.zeros_like(v)
+        c.sign_apply(v, out, eta=1e-11, prec=prec)
+        for j in range(2):
+            assert rel(out[j], ref[j]) <= 1e-10
