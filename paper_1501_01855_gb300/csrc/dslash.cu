@@ -24,20 +24,22 @@ namespace ovl {
 
 enum { MODE_K = 0, MODE_R = 1, MODE_OVL = 2 };
 
-// Minimum resident 256-thread blocks per SM requested from the compiler, which caps
-// registers per thread at 65536 / (256 * MINB). Uncapped, the compiler hoists all
+// Register cap per thread, by link precision. Uncapped, the compiler hoists all
 // neighbour loads and takes ~255 registers (8 warps per SM): the FP32/FP16 kernels
 // are then latency-bound, and the double-float kernel has too few warps to hide its
-// dependent FP32 chains. Measured on 24^3x48: FP32 0.108 -> 0.081 ms at 64
-// registers, double-float 1.04 -> 0.92 ms at 128.
-#ifndef OVL_WILSON_MINB_DF
-#define OVL_WILSON_MINB_DF 2
+// dependent FP32 chains. Swept on 24^3x48 (one system, ms per launch):
+//   FP32 K   64: 0.0619 (spills 148 B; the multi-shift r-update form 440 B)
+//            72: 0.0555   80: 0.0557 (best for 12 systems and for a whole FP32 sign)
+//            96: 0.0594
+//   double-float K  104: 0.375  112: 0.365  120: 0.438  128: 0.329
+#ifndef OVL_WILSON_REG_DF
+#define OVL_WILSON_REG_DF 128
 #endif
-#ifndef OVL_WILSON_MINB_SP
-#define OVL_WILSON_MINB_SP 4
+#ifndef OVL_WILSON_REG_SP
+#define OVL_WILSON_REG_SP 80
 #endif
-template <int PL> struct MinBlocks {
-  static constexpr int v = PL == P64E ? OVL_WILSON_MINB_DF : PL == P64 ? 1 : OVL_WILSON_MINB_SP;
+template <int PL> struct MaxReg {
+  static constexpr int v = PL == P64E ? OVL_WILSON_REG_DF : PL == P64 ? 255 : OVL_WILSON_REG_SP;
 };
 
 // Sums inside the hop term. For double-float operands the sum is "lazy": TwoSum on the
@@ -232,15 +234,21 @@ __device__ __forceinline__ cpx<df> ipow(const cpx<df>& z, int k) {
   return {df(__fmul_rn(re.hi, sr), __fmul_rn(re.lo, sr)), df(__fmul_rn(im.hi, si), __fmul_rn(im.lo, si))};
 }
 
-template <int PIN>
-__device__ __forceinline__ void hop_nb_df(const Geom& g, const LinkRef& L, const SpinorRef& in, int rhs, int s,
-                                          const int x[4], int n, cpx<df> acc[12]) {
+// site of neighbour n = 2 mu + b of site s (coordinates x), periodic wrap
+__device__ __forceinline__ int nb_site(const Geom& g, const int x[4], int s, int n) {
   const int mu = n >> 1;
   const bool fwd = (n & 1) == 0;
   const int xm = mu == 0 ? x[0] : mu == 1 ? x[1] : mu == 2 ? x[2] : x[3];
   const int lm = mu == 0 ? g.L[0] : mu == 1 ? g.L[1] : mu == 2 ? g.L[2] : g.L[3];
   const int st = mu == 0 ? 1 : mu == 1 ? g.L[0] : mu == 2 ? g.L[0] * g.L[1] : g.L[0] * g.L[1] * g.L[2];
-  const int sn = fwd ? (xm == lm - 1 ? s - (lm - 1) * st : s + st) : (xm == 0 ? s + (lm - 1) * st : s - st);
+  return fwd ? (xm == lm - 1 ? s - (lm - 1) * st : s + st) : (xm == 0 ? s + (lm - 1) * st : s - st);
+}
+
+// hop n given the neighbour spinor psi: acc += (1 -+ gamma_mu) W_n(s) psi
+__device__ __forceinline__ void hop_nb_df_core(const LinkRef& L, int s, int n, const cpx<df> psi[12],
+                                               cpx<df> acc[12]) {
+  const int mu = n >> 1;
+  const bool fwd = (n & 1) == 0;
   // In powers of i, with S = -1 (forward) or +1 (backward) = i^sS:
   //   h0 = psi0 + i^a0 psi_j0,  h1 = psi1 + i^a1 psi_(5-j0)
   //   lower spins of (1 + S gamma_mu) w: acc2 += i^b0 w_k0, acc3 += i^b1 w_(1-k0)
@@ -252,8 +260,7 @@ __device__ __forceinline__ void hop_nb_df(const Geom& g, const LinkRef& L, const
   const int a1 = (sS + (mu == 0 ? 1 : mu == 2 ? 3 : 0)) & 3;
   const int b0 = (sS + (mu == 0 || mu == 2 ? 3 : 0)) & 3;
   const int b1 = (sS + (mu == 0 ? 3 : mu == 1 ? 2 : mu == 2 ? 1 : 0)) & 3;
-  cpx<df> psi[12], h[6], w[6], u[9];
-  load_spinor_as_ro<PIN, df>(in, rhs, sn, psi);
+  cpx<df> h[6], w[6], u[9];
 #pragma unroll
   for (int c = 0; c < 3; ++c) {
     const cpx<df> pa = lo3 ? psi[9 + c] : psi[6 + c];
@@ -272,6 +279,14 @@ __device__ __forceinline__ void hop_nb_df(const Geom& g, const LinkRef& L, const
     acc[6 + c] = padd(acc[6 + c], ipow(wa, b0));
     acc[9 + c] = padd(acc[9 + c], ipow(wb, b1));
   }
+}
+
+template <int PIN>
+__device__ __forceinline__ void hop_nb_df(const Geom& g, const LinkRef& L, const SpinorRef& in, int rhs, int s,
+                                          const int x[4], int n, cpx<df> acc[12]) {
+  cpx<df> psi[12];
+  load_spinor_as_ro<PIN, df>(in, rhs, nb_site(g, x, s, n), psi);
+  hop_nb_df_core(L, s, n, psi, acc);
 }
 
 template <int MU, int PIN, int PL, typename T>
@@ -470,7 +485,7 @@ __device__ __forceinline__ void block_reduce_partials(R v[NVRED], double* smem, 
 // get zero), so the partial layout (system, BX-site block) is the same for all variants.
 constexpr int TX = 8, TY = 4, TZ = 4, TT = 2;
 template <int MODE, int PIN, int PL, int POUT, int PA1, int PA2, bool TILED>
-__global__ void __launch_bounds__(256, MinBlocks<PL>::v) wilson_kernel(const DArgs a) {
+__global__ void __launch_bounds__(256) __maxnreg__(MaxReg<PL>::v) wilson_kernel(const DArgs a) {
   using T = typename Real<PL>::T;
   __shared__ double red[4 * (BX / 32) * NVRED];
   int sb, rhs, s;
@@ -536,7 +551,7 @@ bool wilson_tiles_fit(const Geom& g) {
 // uniform within a warp. The four partial sums meet in shared memory and the
 // direction-0 warps finish the site.
 template <int MODE, int PIN, int PL, int POUT, int PA1, int PA2>
-__global__ void __launch_bounds__(4 * BX, MinBlocks<PL>::v) wilson_split_kernel(const DArgs a) {
+__global__ void __launch_bounds__(4 * BX) __maxnreg__(MaxReg<PL>::v) wilson_split_kernel(const DArgs a) {
   using T = typename Real<PL>::T;
   __shared__ cpx<T> part[3][BX][12];
   __shared__ double red[(4 * BX / 32) * NVRED];

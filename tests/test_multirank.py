@@ -1,0 +1,60 @@
+"""Multi-process paths of bench.py on CPU (gloo, world size 2): the path only has
+independent replicas (each rank solves its own right-hand sides), so what is checked is
+the host logic around them: rendezvous, the barrier, the max-over-ranks timing and the
+reference arm, which rank 0 alone runs and prints while the other ranks exit 0."""
+import json
+import os
+import socket
+import subprocess
+import sys
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _free_port():
+    with socket.socket() as s:
+        s.bind(("127.0.0.1", 0))
+        return s.getsockname()[1]
+
+
+def _rank_main(rank, ws, port, out_dir):
+    os.environ.update({"RANK": str(rank), "WORLD_SIZE": str(ws), "LOCAL_RANK": str(rank),
+                       "MASTER_ADDR": "127.0.0.1", "MASTER_PORT": str(port)})
+    sys.path.insert(0, ROOT)
+    import bench
+    import torch.distributed as dist
+    got_ws, got_rank, _ = bench.dist_setup()
+    bench.barrier(got_ws)
+    m = bench.max_over_ranks(1.5 + got_rank, got_ws)
+    with open(os.path.join(out_dir, "rank%d.json" % rank), "w") as f:
+        json.dump({"ws": got_ws, "rank": got_rank, "max": m, "backend": dist.get_backend()}, f)
+    bench.barrier(got_ws)
+    dist.destroy_process_group()
+
+
+def test_gloo_barrier_and_max_over_ranks(tmp_path):
+    import torch.multiprocessing as mp
+    port = _free_port()
+    mp.spawn(_rank_main, args=(2, port, str(tmp_path)), nprocs=2, join=True)
+    for r in range(2):
+        d = json.load(open(tmp_path / ("rank%d.json" % r)))
+        assert d == {"ws": 2, "rank": r, "max": 2.5, "backend": "gloo"}
+
+
+@pytest.mark.timeout(600)
+def test_reference_arm_under_torchrun_prints_one_line():
+    port = _free_port()
+    env = dict(os.environ, CUDA_VISIBLE_DEVICES="")
+    cmd = [sys.executable, "-m", "torch.distributed.run", "--nnodes=1", "--nproc-per-node", "2",
+           "--master-addr", "127.0.0.1", "--master-port", str(port), os.path.join(ROOT, "bench.py"),
+           "--impl", "reference", "--gpus", "2", "--steps", "1", "--warmup", "3", "--cpu-budget", "1"]
+    r = subprocess.run(cmd, cwd=ROOT, env=env, capture_output=True, text=True, timeout=600)
+    assert r.returncode == 0, r.stderr[-2000:]
+    lines = [l for l in r.stdout.splitlines() if l.startswith("{")]
+    assert len(lines) == 1
+    d = json.loads(lines[0])
+    assert d["impl"] == "reference" and d["n_gpus"] == 2 and d["unit"] == "applies/s"
+    assert d["value"] > 0 and d["cpu_baseline"]["kind"] == "oracle"
+    assert d["e2e"]["h2d_bytes_per_step"] == 0
