@@ -24,7 +24,9 @@
  *   - The gamma matrices are the Hermitian chiral (DeGrand-Rossi) set, gamma5 =
  *     diag(1,1,-1,-1).
  *   - "on_device" = 1: the pointers are CUDA device pointers on the context's
- *     device; 0: host pointers (the library copies through pinned staging).
+ *     device; 0: host pointers. Page-locked host buffers (cudaHostAlloc,
+ *     cudaHostRegister) are copied by DMA directly; pageable ones go through the
+ *     context's pinned staging buffer.
  *   - The library never frees or keeps caller memory. All internal memory is
  *     owned by the context (or the deflation object) and released by the
  *     matching destroy call.

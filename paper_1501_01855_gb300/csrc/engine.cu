@@ -219,6 +219,18 @@ ovl_status reduce_to_host(ovl_ctx* c, int nsb, int nrhs, double* host_pairs) {
 }
 
 // ---------------------------------------------------------------- caller I/O
+// Host buffers that are page-locked (cudaHostAlloc, cudaHostRegister, a pinned torch
+// tensor) are copied by DMA directly; pageable ones go through the context's pinned
+// staging buffer (one host memcpy each way).
+static bool host_pinned(const void* p) {
+  cudaPointerAttributes a;
+  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return a.type == cudaMemoryTypeHost;
+}
+
 ovl_status import_spinors(ovl_ctx* c, const void* src, int dtype, int on_device, int n, Field& dst, int off) {
   const size_t esz = dtype == OVL_C128 ? 16 : 8;
   const size_t bytes = esz * 12 * (size_t)c->V * n;
@@ -226,13 +238,17 @@ ovl_status import_spinors(ovl_ctx* c, const void* src, int dtype, int on_device,
   Field* tmp = nullptr;
   if (!on_device) {
     OVL_TRY(get_field(c, "io_canon", P64, (int)((bytes + 192 * (size_t)c->V - 1) / (192 * (size_t)c->V)), &tmp));
-    OVL_TRY(ensure_stage(c, bytes));
-    // the previous copy out of the pinned staging buffer must have finished before it
-    // is overwritten
-    OVL_CUDA(c, cudaEventSynchronize(c->stage_ev));
-    memcpy(c->hstage, src, bytes);
-    OVL_CUDA(c, cudaMemcpyAsync(tmp->data, c->hstage, bytes, cudaMemcpyHostToDevice, c->st));
-    OVL_CUDA(c, cudaEventRecord(c->stage_ev, c->st));
+    if (host_pinned(src)) {
+      OVL_CUDA(c, cudaMemcpyAsync(tmp->data, src, bytes, cudaMemcpyHostToDevice, c->st));
+    } else {
+      OVL_TRY(ensure_stage(c, bytes));
+      // the previous copy out of the pinned staging buffer must have finished before it
+      // is overwritten
+      OVL_CUDA(c, cudaEventSynchronize(c->stage_ev));
+      memcpy(c->hstage, src, bytes);
+      OVL_CUDA(c, cudaMemcpyAsync(tmp->data, c->hstage, bytes, cudaMemcpyHostToDevice, c->st));
+      OVL_CUDA(c, cudaEventRecord(c->stage_ev, c->st));
+    }
     dsrc = tmp->data;
   }
   ProfPair pp;
@@ -256,14 +272,15 @@ ovl_status export_spinors(ovl_ctx* c, void* dst, int dtype, int on_device, int n
   }
   Field* tmp = nullptr;
   OVL_TRY(get_field(c, "io_canon", P64, (int)((bytes + 192 * (size_t)c->V - 1) / (192 * (size_t)c->V)), &tmp));
-  OVL_TRY(ensure_stage(c, bytes));
+  const bool pinned = host_pinned(dst);
+  if (!pinned) OVL_TRY(ensure_stage(c, bytes));
   ProfPair pp;
   prof_begin(c, 4, &pp);
   launch_unpack(dtype, tmp->data, src.prec, src.ref(off), n, c->V, c->st);
   prof_end(c, &pp, (double)bytes + (double)n * c->V * spinor_bytes(src.prec));
-  OVL_CUDA(c, cudaMemcpyAsync(c->hstage, tmp->data, bytes, cudaMemcpyDeviceToHost, c->st));
+  OVL_CUDA(c, cudaMemcpyAsync(pinned ? dst : c->hstage, tmp->data, bytes, cudaMemcpyDeviceToHost, c->st));
   OVL_CUDA(c, cudaStreamSynchronize(c->st));
-  memcpy(dst, c->hstage, bytes);
+  if (!pinned) memcpy(dst, c->hstage, bytes);
   return OVL_OK;
 }
 
