@@ -413,8 +413,17 @@ def deflated_batched(B, stream):
     for k in range(3):
         b0 = synth.gaussian_source(DIMS, 2003 + k)
         x0 = np.zeros_like(b0)
+        if k == 2:
+            ctx.profile_reset()
+            ctx.profile_enable(True)
         defl, info0 = ctx.eigsumr_accumulate(b0, x0, tol, 32, 96, defl=defl)
+    ctx.profile_enable(False)
     res["eigsumr_3_accumulation_solves_s"] = time.perf_counter() - t0
+    prof = ctx.profile_get()
+    tot = sum(v["ms"] for v in prof.values())
+    # the dense contractions (Gram blocks of the Ritz steps, basis rotations) against the
+    # whole third accumulation solve, as timed by the profiler
+    res["gram_combine_share_of_accumulation_solve"] = prof["gram"]["ms"] / tot if tot > 0 else None
     ritz, rres = defl.info()
     res["ritz_values_lowest4"] = [float(v) for v in ritz[:4]]
     res["ritz_residual_lowest8_max"] = float(np.max(rres[:8]))

@@ -1,0 +1,41 @@
+"""The fermion action and its gauge-link gradient as a torch.autograd.Function.
+
+    S(U) = phi^dag (D(mu)^dag D(mu))^-1 phi
+
+The gradient comes from the library's own adjoint computation (overlap_force: every
+Zolotarev pole's shifted solutions and the link outer products of the Wilson hop, on the
+GPU); this module only moves tensors. PyTorch's convention for a real loss L of a
+complex tensor z is dL = Re(sum conj(z.grad) dz); the library returns G with
+dS = 2 Re(sum conj(G) dU), so z.grad = 2 G.
+
+The context must have been created from the same gauge field U that is passed in (the
+library copies the links at create); phi is treated as a constant (no gradient).
+"""
+import numpy as np
+import torch
+
+
+class OverlapAction(torch.autograd.Function):
+    @staticmethod
+    def forward(fctx, U, phi, ovl, mu, tol):
+        ph = phi.detach()
+        if ph.is_cuda:
+            ph = ph.contiguous()
+        else:
+            ph = np.ascontiguousarray(ph.numpy())
+        G, S = ovl.force(ph, mu=mu, tol=tol)
+        fctx.save_for_backward(torch.from_numpy(np.ascontiguousarray(G)).to(U.device))
+        return torch.tensor(S, dtype=torch.float64, device=U.device)
+
+    @staticmethod
+    def backward(fctx, gS):
+        (G,) = fctx.saved_tensors
+        return 2.0 * gS * G, None, None, None, None
+
+
+def overlap_action(U, phi, ovl, mu=None, tol=1e-10):
+    """S = phi^dag (D^dag D)^-1 phi at mass mu (default: the context's), differentiable
+    in the gauge links U (complex128, canonical [t][z][y][x][mu][row][col] layout)."""
+    if U.dtype != torch.complex128:
+        raise TypeError("U must be complex128")
+    return OverlapAction.apply(U, phi, ovl, ovl.mu if mu is None else mu, tol)

@@ -48,3 +48,23 @@ def test_force_finite_differences_8888():
         an = 2 * np.real(np.sum(np.conj(G) * (1j * X @ U)))
         # truncation O(h^2) plus the solve accuracy of S (1e-11 relative) over 2h
         assert abs(fd - an) <= 1e-5 * abs(an) + 10 * 1e-11 * abs(S0) / h, (fd, an)
+
+
+def test_autograd_action_gradient_matches_oracle():
+    """overlap_action (torch.autograd.Function over overlap_force): the action and U.grad
+    against the oracle action and gradient (grad = 2 G in PyTorch's convention)."""
+    import torch
+    from paper_1501_01855_gb300.autograd import overlap_action
+    dims = (2, 2, 2, 2)
+    U = synth.gauge_links(dims, 0.3, 41)
+    phi = synth.gaussian_source(dims, 42)
+    a, b = 0.15, 2.6
+    c = ctx(dims, U, mu=MU, n_poles=8, eps=1e-6, a=a, b=b, mixed=0)
+    Ut = torch.from_numpy(U.copy()).requires_grad_(True)
+    S = overlap_action(Ut, torch.from_numpy(phi), c, tol=1e-12)
+    S.backward()
+    om, sg, _ = zo.zolotarev(8, a, b)
+    Sref, _ = force.action(U, phi, M0, MU, om, sg, tol=1e-13)
+    Gref = force.gradient(U, phi, M0, MU, om, sg, tol=1e-13)
+    assert abs(S.item() - Sref) <= 1e-9 * abs(Sref)
+    assert rel(Ut.grad.numpy(), 2.0 * Gref) <= 1e-8
