@@ -69,7 +69,8 @@ typedef struct {
                            0: plain FP64 everywhere                                              */
   int    half_storage;  /* 1: FP16 links/vectors in the sign when eta >= half_switch            */
   int    emulate_fp64;  /* 1: accurate signs (eta < sp_switch, or mixed = 0) in double-float on
-                           the FP32 pipes (OVL_PREC_F64E); 0: native FP64. Default 0          */
+                           the FP32 pipes (OVL_PREC_F64E; GB300 runs FP64 at 1/60 of its FP32
+                           rate); 0: native FP64. Default 1                                  */
   double eta_floor;     /* sign accuracy never worse than this (Sec. 3): default 1e-2           */
   double sp_switch;     /* eta above which the FP32 sign is used: default 1e-6                  */
   double half_switch;   /* eta above which FP16 storage is used: default 2e-3                    */

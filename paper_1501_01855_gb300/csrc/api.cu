@@ -28,7 +28,7 @@ extern "C" ovl_status ovl_params_default(ovl_params* p) {
   p->solver = OVL_SOLVER_SUMR;
   p->mixed = 1;
   p->half_storage = 0;
-  p->emulate_fp64 = 0;
+  p->emulate_fp64 = 1;
   p->eta_floor = 1e-2;
   p->sp_switch = 1e-6;
   p->half_switch = 2e-3;
@@ -457,12 +457,15 @@ extern "C" ovl_status overlap_sumr(ovl_ctx* c, double mu, const void* b, void* x
 }
 
 // true residual ||b - D x|| / ||b|| with an FP64 sign at eps_sign
+// ||b - D x|| / ||b|| with a sign accurate enough to resolve tol: its error enters as
+// (1 - mu)/2 eta ||x||, and ||x|| can reach ||b|| / mu.
 static ovl_status true_residuals(ovl_ctx* c, const Field& b, int boff, const Field& x, int xoff, int n,
-                                 const std::vector<double>& mus, std::vector<double>& out) {
+                                 const std::vector<double>& mus, double tol, std::vector<double>& out) {
   Field* t;
   OVL_TRY(get_field(c, "tr_t", P64, n, &t));
-  std::vector<double> etas(n, c->eps_sign);
-  OVL_TRY(overlap_apply_batch(c, x, xoff, *t, 0, n, mus, etas, 0, SIGN64, nullptr));
+  std::vector<double> etas(n);
+  for (int j = 0; j < n; ++j) etas[j] = std::min(c->eps_sign, 0.1 * tol * mus[j]);
+  OVL_TRY(overlap_apply_batch(c, x, xoff, *t, 0, n, mus, etas, 0, c->P.emulate_fp64 ? SIGN64E : SIGN64, nullptr));
   std::vector<cd> one(n, 1.0), mone(n, -1.0);
   OVL_TRY(axpby_batch(c, one, b, boff, mone, *t, 0, *t, 0, n));
   std::vector<double> rn, bn;
@@ -508,7 +511,7 @@ extern "C" ovl_status overlap_solve(ovl_ctx* c, int nrhs, const double* mus, int
     if (st == OVL_ENOCONV) worst = st;
     if (c->P.verify) {
       std::vector<double> tr;
-      OVL_TRY(true_residuals(c, *bb, 0, *bx, 0, n, bmus, tr));
+      OVL_TRY(true_residuals(c, *bb, 0, *bx, 0, n, bmus, tol, tr));
       if (info)
         for (int q = 0; q < n; ++q) {
           info[s0 + q].true_residual = tr[q];
@@ -661,11 +664,16 @@ extern "C" ovl_status eigsumr_accumulate(ovl_ctx* c, ovl_defl** defl, int n_eig,
   OVL_TRY(export_spinors(c, x, dtype, on_device, 1, *fx, 0));
   if (info && c->P.verify) {
     std::vector<double> tr;
-    OVL_TRY(true_residuals(c, *fb, 0, *fx, 0, 1, mus, tr));
+    OVL_TRY(true_residuals(c, *fb, 0, *fx, 0, 1, mus, tol, tr));
     info[0].true_residual = tr[0];
     info[0].converged = tr[0] <= tol * 1.0000001 ? 1 : 0;
   }
   OVL_CUDA(c, cudaStreamSynchronize(c->st));
+  // the accumulation basis (4 x m_basis spinors) is not needed between solves
+  for (const char* nm : {"e_V", "e_W", "e_VD", "e_T"}) {
+    auto it = c->ws.find(nm);
+    if (it != c->ws.end()) free_field(it->second);
+  }
   *defl = d;
   return st;
 }

@@ -336,10 +336,42 @@ static ovl_status ms_graph(ovl_ctx* c, const std::vector<unsigned long long>& ke
   return OVL_OK;
 }
 
+static ovl_status sign_op_batch(ovl_ctx* c, int mode, const Field& v, int voff, Field& out, int ooff, int n,
+                                const double* eta, double c1, double c2, const double* coef, int herm,
+                                const Field* dot_w, int woff, double* dots, SignStats* stats);
+
+// Systems per multi-shift solve are capped so that the pole vectors of one batch stay
+// within kPoleBytes (24 poles x 36 systems of 24^3 x 48 in double-float would be 110 GB);
+// larger requests run as consecutive sub-batches.
+static constexpr double kPoleBytes = 64e9;
 ovl_status sign_op(ovl_ctx* c, int mode, const Field& v, int voff, Field& out, int ooff, int n, const double* eta,
                    double c1, double c2, const double* coef, int herm, const Field* dot_w, int woff, double* dots,
                    SignStats* stats) {
   if (n <= 0) return OVL_OK;
+  const int PP = mode == SIGN64 ? P64 : mode == SIGN32 ? P32 : mode == SIGN16 ? P16 : P64E;
+  const double per = (double)c->npoles * c->V * spinor_bytes(PP);
+  int nb = std::max(1, std::min(c->P.batch_max, (int)(kPoleBytes / per)));
+  if (n <= nb) return sign_op_batch(c, mode, v, voff, out, ooff, n, eta, c1, c2, coef, herm, dot_w, woff, dots, stats);
+  if (stats) {
+    stats->iters.clear();
+    stats->status.clear();
+  }
+  for (int j0 = 0; j0 < n; j0 += nb) {
+    const int m = std::min(nb, n - j0);
+    SignStats sub;
+    OVL_TRY(sign_op_batch(c, mode, v, voff + j0, out, ooff + j0, m, eta + j0, c1, c2, coef ? coef + 2 * j0 : nullptr,
+                          herm, dot_w, woff + j0, dots ? dots + 4 * j0 : nullptr, stats ? &sub : nullptr));
+    if (stats) {
+      stats->iters.insert(stats->iters.end(), sub.iters.begin(), sub.iters.end());
+      stats->status.insert(stats->status.end(), sub.status.begin(), sub.status.end());
+    }
+  }
+  return OVL_OK;
+}
+
+static ovl_status sign_op_batch(ovl_ctx* c, int mode, const Field& v, int voff, Field& out, int ooff, int n,
+                                const double* eta, double c1, double c2, const double* coef, int herm,
+                                const Field* dot_w, int woff, double* dots, SignStats* stats) {
   const int PL = mode == SIGN64 ? P64 : mode == SIGN32 ? P32 : mode == SIGN16 ? P16 : P64E;
   const int PR = mode == SIGN64 ? P64 : mode == SIGN64E ? P64E : P32;
   const int PP = PL;

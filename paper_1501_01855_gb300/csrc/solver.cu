@@ -566,10 +566,12 @@ ovl_status gmresr_batch(ovl_ctx* c, int n, const std::vector<double>& mus, const
   const int V = c->V;
   const int kmax = std::max(1, c->P.gmresr_max);
   const int PS = c->P.mixed ? P32 : P64;
-  Field *fr, *fC, *fU, *fmid_b, *fmid_x, *fu, *fc;
+  Field *fr, *fmid_b, *fmid_x, *fu, *fc;
+  // the stored directions C_k, U_k get one workspace per outer step, allocated when the
+  // step is reached (GMRESR needs 3-4 steps here; reserving gmresr_max of them for a
+  // large batch would take tens of GB)
+  std::vector<Field*> fC, fU;
   OVL_TRY(get_field(c, "g_r", P64, n, &fr));
-  OVL_TRY(get_field(c, "g_C", P64, kmax * n, &fC));
-  OVL_TRY(get_field(c, "g_U", P64, kmax * n, &fU));
   OVL_TRY(get_field(c, "g_u", P64, n, &fu));
   OVL_TRY(get_field(c, "g_c", P64, n, &fc));
   OVL_TRY(get_field(c, "m_b", PS, n, &fmid_b));
@@ -627,7 +629,11 @@ ovl_status gmresr_batch(ovl_ctx* c, int n, const std::vector<double>& mus, const
     std::vector<double> eta(n);
     double emin = 1e300;
     for (int j = 0; j < n; ++j) {
-      eta[j] = active[j] ? std::min(c->P.eta_floor, tol * bn[j] / std::max(rn[j], 1e-300)) : c->P.eta_floor;
+      // Alg. 3 bounds ||A u - c|| relative to ||u||; through the update r -= alpha c that
+      // error reaches r amplified by up to ||u|| / ||A u|| <= 1/mu (D^dag D >= mu^2), so
+      // the factor mu/2 keeps the final true residual within tol
+      eta[j] = active[j] ? std::min(c->P.eta_floor, 0.5 * mus[j] * tol * bn[j] / std::max(rn[j], 1e-300))
+                         : c->P.eta_floor;
       emin = std::min(emin, eta[j]);
     }
     std::vector<long long> wc(n, 0);
@@ -640,30 +646,35 @@ ovl_status gmresr_batch(ovl_ctx* c, int n, const std::vector<double>& mus, const
     // orthogonalise against the stored C (same combination on u)
     for (int i = 0; i < k; ++i) {
       std::vector<cd> beta;
-      OVL_TRY(dots_batch(c, *fC, i * n, *fc, 0, n, beta));
+      OVL_TRY(dots_batch(c, *fC[i], 0, *fc, 0, n, beta));
       std::vector<cd> one(n, 1.0), mb(n);
       for (int j = 0; j < n; ++j) mb[j] = -beta[j];
-      OVL_TRY(axpby_batch(c, one, *fc, 0, mb, *fC, i * n, *fc, 0, n));
-      OVL_TRY(axpby_batch(c, one, *fu, 0, mb, *fU, i * n, *fu, 0, n));
+      OVL_TRY(axpby_batch(c, one, *fc, 0, mb, *fC[i], 0, *fc, 0, n));
+      OVL_TRY(axpby_batch(c, one, *fu, 0, mb, *fU[i], 0, *fu, 0, n));
     }
     std::vector<double> nu;
     OVL_TRY(norms_batch(c, *fc, 0, n, nu));
     {
       std::vector<cd> a(n), z(n, 0.0);
       for (int j = 0; j < n; ++j) a[j] = nu[j] > 0 ? 1.0 / nu[j] : 0.0;
-      OVL_TRY(axpby_batch(c, a, *fc, 0, z, *fc, 0, *fC, k * n, n));
-      OVL_TRY(axpby_batch(c, a, *fu, 0, z, *fu, 0, *fU, k * n, n));
+      Field *ck, *uk;
+      OVL_TRY(get_field(c, "g_C" + std::to_string(k), P64, n, &ck));
+      OVL_TRY(get_field(c, "g_U" + std::to_string(k), P64, n, &uk));
+      fC.push_back(ck);
+      fU.push_back(uk);
+      OVL_TRY(axpby_batch(c, a, *fc, 0, z, *fc, 0, *fC[k], 0, n));
+      OVL_TRY(axpby_batch(c, a, *fu, 0, z, *fu, 0, *fU[k], 0, n));
     }
     std::vector<cd> alpha;
-    OVL_TRY(dots_batch(c, *fC, k * n, *fr, 0, n, alpha));
+    OVL_TRY(dots_batch(c, *fC[k], 0, *fr, 0, n, alpha));
     {
       std::vector<cd> one(n, 1.0), al(n), mal(n);
       for (int j = 0; j < n; ++j) {
         al[j] = active[j] ? alpha[j] : 0.0;
         mal[j] = -al[j];
       }
-      OVL_TRY(axpby_batch(c, one, x, xoff, al, *fU, k * n, x, xoff, n));
-      OVL_TRY(axpby_batch(c, one, *fr, 0, mal, *fC, k * n, *fr, 0, n));
+      OVL_TRY(axpby_batch(c, one, x, xoff, al, *fU[k], 0, x, xoff, n));
+      OVL_TRY(axpby_batch(c, one, *fr, 0, mal, *fC[k], 0, *fr, 0, n));
     }
     OVL_TRY(norms_batch(c, *fr, 0, n, rn));
     if (log_level() >= 1)

@@ -126,3 +126,19 @@ def test_pinned_host_buffers_match_pageable():
     op = torch.zeros(v.shape, dtype=torch.complex128).pin_memory()
     c.apply(vp.numpy(), op.numpy(), eta=1e-10)
     assert np.array_equal(op.numpy(), o1)
+
+
+def test_sign_sub_batches_match_one_batch():
+    """Requests larger than the batch size run as consecutive multi-shift sub-batches;
+    every system's arithmetic is independent of its batch, so the result is identical."""
+    dims = (8, 8, 8, 8)
+    U = synth.gauge_links(dims, 0.3, 1041)
+    v = synth.gaussian_source(dims, 2041, nvec=5)
+    outs = []
+    for bm in (36, 2):
+        c = ctx(dims, U, n_poles=16, eps=1e-10, a=0.2, b=2.6, batch_max=bm)
+        o = np.zeros_like(v)
+        c.sign_apply(v, o, eta=1e-10, prec=3)
+        outs.append(o)
+        c.close()
+    assert np.array_equal(outs[0], outs[1])
