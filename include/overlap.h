@@ -103,19 +103,22 @@ typedef struct {
   int    sign_calls;       /* applications of the sign function                                  */
   long long wilson_calls;  /* Wilson-kernel applications, FP64 counted as 2 (Sec. 6)             */
   long long wilson_f64, wilson_f32, wilson_f16;   /* raw counts per precision                   */
-  double true_residual;    /* ||b - D x|| / ||b||: with params.verify, recomputed with an FP64
-                              sign at eps_sign accuracy; else the GMRESR recursive residual      */
+  double true_residual;    /* ||b - D x|| / ||b||: with params.verify, recomputed with an accurate
+                              sign (double-float, or FP64 when emulate_fp64 = 0) at accuracy
+                              min(eps_sign, 0.1 tol mu); else the GMRESR recursive residual      */
   double seconds;          /* wall time of this system's solve (shared by a batch)               */
 } ovl_solve_info;
 
 /* Fill *p with the defaults listed above. */
 ovl_status ovl_params_default(ovl_params* p);
 
-/* Build a context for one gauge field.
+/* Build a context for one gauge field (the device current at the call).
+ *   ctx       receives the new context (caller frees it with overlap_destroy).
  *   dims[4]   {Lx, Ly, Lz, Lt}, each even and >= 2.
- *   links     host, canonical layout, complex128, 4*9*V entries; copied and
- *             converted to the library's 12-real device layouts (row 3 of every
- *             SU(3) link is rebuilt as conj(row1 x row2) in registers).
+ *   links     host, canonical layout, complex128, 4*9*V entries; copied (the caller
+ *             keeps ownership) into the library's device layouts: 12-real FP64 / FP32 /
+ *             FP16 copies (row 3 of every SU(3) link rebuilt as conj(row1 x row2) in
+ *             registers) and an 18-real double-float copy with one slot per hop.
  *   m0        Wilson mass, kappa = 1/(8 - 2 m0) (Sec. 1).
  *   mu        default overlap mass parameter of D(mu) (Sec. 1).
  *   n_poles   Zolotarev order N_Z (Sec. 3), 1..64.
@@ -124,10 +127,17 @@ ovl_status ovl_params_default(ovl_params* p);
  *   params    may be NULL (defaults).
  * The spectral bounds a = min|lambda(K)|, b = max|lambda(K)| come from
  * params->a_override / b_override when positive, else from an FP64 Lanczos run
- * on K^2 with safety margins (a * 0.9, b * 1.05). */
+ * on K^2 with safety margins (a * 0.95, b * 1.05). Create also times the Wilson-kernel
+ * launch shapes (autotuner, see ovl_wilson_tuning). Errors: OVL_EINVAL (bad sizes,
+ * m0 outside (0, 4), mu outside [0, 1)), OVL_EAPPROX, OVL_ENOMEM, OVL_ECUDA; *ctx is
+ * then NULL. */
 ovl_status overlap_create(ovl_ctx** ctx, const int dims[4], const double* links, double m0, double mu,
                           int n_poles, double eps_sign, const ovl_params* params);
+/* Free every device and host resource of the context (NULL is allowed). Deflation
+ * spaces made with it must be destroyed first. */
 void overlap_destroy(ovl_ctx* ctx);
+/* One-line reason of the last failed call on ctx ("" if none); valid until the next
+ * call on the same context. */
 const char* overlap_last_error(const ovl_ctx* ctx);
 
 /* Host-only (no GPU needed): the Zolotarev rational of order n on a < |x| < b
@@ -140,9 +150,10 @@ ovl_status ovl_zolotarev_coeffs(int n, double a, double b, double* omega, double
 ovl_status overlap_zolotarev(const ovl_ctx* ctx, double* omega, double* sigma, double* delta,
                              double* a, double* b);
 
-/* out = K in for n spinors (Sec. 1). prec selects the kernel: OVL_PREC_F64 computes
- * in FP64; OVL_PREC_F32 / F16 round the input to FP32 / FP16 storage and compute in
- * FP32. */
+/* out = K in for n spinors (Sec. 1); in and out may not alias. prec selects the kernel:
+ * OVL_PREC_F64 computes in FP64, OVL_PREC_F64E in double-float, OVL_PREC_F32 / F16
+ * round the input to FP32 / FP16 storage and compute in FP32. OVL_EINVAL for a null
+ * pointer, n < 1 or an unknown dtype / prec. */
 ovl_status ovl_wilson_apply(ovl_ctx* ctx, const void* in, void* out, int n, int dtype, int on_device,
                             int prec);
 
@@ -203,29 +214,41 @@ ovl_status eigsumr_accumulate(ovl_ctx* ctx, ovl_defl** defl, int n_eig, int m_ba
                               ovl_solve_info* info);
 
 /* Ritz values (n) and eigenvector residuals ||gamma5 D v - v (v, gamma5 D v)|| (n)
- * of a deflation space; *n receives the number of vectors held. */
+ * of a deflation space; *n receives the number of vectors held; ritz and residuals
+ * may be NULL (then only *n is set). */
 ovl_status ovl_defl_info(const ovl_defl* defl, int* n, double* ritz, double* residuals);
 
-/* Copy vector i of the space (v_i and v^D_i = D v_i) to host complex128 buffers. */
+/* Copy vector i of the space (v_i and v^D_i = D v_i) to host complex128 buffers of
+ * 12 V complex entries each (canonical layout; v or vD may be NULL). OVL_EINVAL when
+ * i is outside 0..n-1. */
 ovl_status ovl_defl_vector(const ovl_defl* defl, int i, double* v, double* vD);
 
-/* Raw little-endian save / load of a deflation space (a text header line, then
- * v and v^D as complex128 canonical spinors). */
+/* Raw little-endian save / load of a deflation space (checkpoint / resume): a text
+ * header line "OVLDEFL 1 n=<n> V=<V> mu=<mu>", then per vector v_i and
+ * w_i = gamma5 eps(K) v_i as complex128 canonical spinors, then the n Ritz values
+ * and n residuals as float64. Load creates a new space on ctx (OVL_EINVAL if the file
+ * is malformed or V differs from the context's); save and load round-trip bit-exactly. */
 ovl_status ovl_defl_save(const ovl_defl* defl, const char* path);
 ovl_status ovl_defl_load(ovl_ctx* ctx, ovl_defl** defl, const char* path);
+/* Free a deflation space (NULL is allowed). */
 void ovl_defl_destroy(ovl_defl* defl);
 
 /* Gauge-link gradient of S = phi^dag (D^dag D)^-1 phi through the Zolotarev rational
  * with fixed coefficients (not in the paper; dS = 2 Re sum conj(G) dU).
- * dSdU receives 4*9*V complex128 entries in the canonical link layout; S (may be
- * NULL) receives the action. tol is the accuracy of every inner solve. */
+ *   phi   one canonical spinor (dtype, on_device as everywhere).
+ *   dSdU  host, receives 4*9*V complex128 entries (8*9*V doubles) in the canonical
+ *         link layout; S (host, may be NULL) receives the action.
+ *   tol   accuracy of every inner solve and shifted system.
+ * With respect to the links the context was created from. */
 ovl_status overlap_force(ovl_ctx* ctx, double mu, const void* phi, int dtype, int on_device, double tol,
                          double* dSdU, double* S);
 
 /* Kernel-level timing collected with CUDA events on the context stream while
  * enabled: per kernel class, launches, total milliseconds and algorithmic bytes.
  * Classes: 0 Wilson FP64, 1 Wilson FP32, 2 Wilson FP16-storage, 3 multi-shift
- * update, 4 vector ops, 5 reductions/scalars, 6 Gram/rotate, 7 force. */
+ * update, 4 vector ops, 5 reductions/scalars, 6 Gram/rotate, 7 force, 8 Wilson
+ * double-float. While enabled, the multi-shift iterations are launched one by one
+ * (not as CUDA graphs) so that every launch can be timed. */
 enum { OVL_PROF_CLASSES = 9 };
 ovl_status ovl_profile_enable(ovl_ctx* ctx, int on);
 ovl_status ovl_profile_reset(ovl_ctx* ctx);
