@@ -158,8 +158,9 @@ static ovl_status shifted_solutions(ovl_ctx* c, const Field& v, Field& xs, doubl
   Field* y;
   OVL_TRY(get_field(c, "f_y", P64, 1, &y));
   launch_ms_init(P64, P64, P64, v.ref(), r->ref(), pb->ref(), y->ref(), np, 1, V, c->partials, c->st);
-  // eta' = tol * N_Z with unit weights makes the per-pole rule |zeta_i| ||r|| <= tol ||v||
-  c->hpin[0] = tol * np;
+  // with unit weights the stopping rule bounds sum_i |zeta_i| ||r|| (plus the poles
+  // already stopped) by eta ||v||: eta = tol makes every shifted system accurate to tol
+  c->hpin[0] = tol;
   OVL_CUDA(c, cudaMemcpyAsync(c->dscal, c->hpin, sizeof(double), cudaMemcpyHostToDevice, c->st));
   const Shape sh = make_shape(V, 1);
   launch_ms_scalar0(c->ms, c->partials, sh.nsb, 1, dpol, c->dscal, c->P.mscg_max, c->st);

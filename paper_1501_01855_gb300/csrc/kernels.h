@@ -39,7 +39,8 @@ struct Field {
 // Per-system multi-shift CG state, device resident (Sec. 3: the shifted systems
 // (K^2 + sigma_i) x_i = v of the Zolotarev sum solved with one Krylov space).
 struct MsRhs {
-  double rr, alpha, alpha_prev, beta_prev, thr, vnorm2;
+  double rr, alpha, alpha_prev, beta_prev, thr;
+  double consumed;   // error bound frozen by the poles already dropped
   int active, nact_y, done, iter, status, maxit;
   long long p_reads, p_writes;   // pole-vector passes of the fused update (bytes accounting)
   double zeta[NPMAX], zeta_prev[NPMAX], zeta_next[NPMAX];

@@ -108,11 +108,14 @@ __global__ void ms_scalar0_kernel(MsRhs* ms, const double* partials, int nsb, co
   }
   if (threadIdx.x == 0) {
     m.rr = s[0];
-    m.vnorm2 = s[0];
+    m.consumed = 0.0;
     m.alpha = 0.0;
     m.alpha_prev = 1.0;
     m.beta_prev = 0.0;
-    m.thr = eta[rhs] * sqrt(s[0]) / (double)P->n;
+    // per-pole share of the error budget eta ||v||; its sign selects the stopping rule:
+    // positive (accurate signs, eta < 1e-6) shared budget, negative (relaxed signs inside
+    // the middle solves) every pole within its even share
+    m.thr = (eta[rhs] < 1e-6 ? 1.0 : -1.0) * eta[rhs] * sqrt(s[0]) / (double)P->n;
     m.active = P->n;
     m.nact_y = 0;
     m.iter = 0;
@@ -178,8 +181,29 @@ __global__ void ms_scalar2_kernel(MsRhs* ms, const double* partials, int nsb, co
   if (threadIdx.x == 0) {
     m.nact_y = act;
     const double rn = sqrt(rr_new);
+    // Error bound of pole i if stopped now: omega_i g_i |zeta_i| ||r||; the sign is within
+    // eta ||v|| = N |thr| once the bounds of the stopped and the running poles add up to
+    // less. Accurate signs: shifted poles (largest sigma first) stop at a quarter of the
+    // even share, which saves their update passes, and the system stops as soon as the
+    // sum of all bounds is within the whole budget, so the slowest (base) pole uses what
+    // the others left. Relaxed signs (middle solves): every pole within its even share,
+    // which keeps the actual sign error well below the relaxation's eta_j.
+    auto bound = [&](int i) { return P->omega[i] * P->gbound[i] * fabs(m.zeta_next[i]) * rn; };
     int a = act;
-    while (a > 0 && P->omega[a - 1] * P->gbound[a - 1] * fabs(m.zeta_next[a - 1]) * rn <= m.thr) --a;
+    if (m.thr > 0.0) {
+      while (a > 1 && bound(a - 1) <= 0.25 * m.thr) {
+        m.consumed += bound(a - 1);
+        --a;
+      }
+      double tot = m.consumed;
+      for (int i = 0; i < a; ++i) tot += bound(i);
+      if (tot <= m.thr * (double)P->n) {
+        m.consumed = tot;
+        a = 0;
+      }
+    } else {
+      while (a > 0 && bound(a - 1) <= -m.thr) --a;
+    }
     m.active = a;
     m.p_reads += act;
     m.p_writes += a;
