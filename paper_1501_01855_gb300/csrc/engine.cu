@@ -394,7 +394,11 @@ static ovl_status sign_op_batch(ovl_ctx* c, int mode, const Field& v, int voff, 
     // the sign is never more accurate than Delta, so no pole is solved past it, except
     // when the rational itself is being differentiated (gauge-link gradient)
     if (e < c->delta && !c->exact_rational) e = c->delta;
-    c->hpin[j] = e;
+    // stopping rule (see ms_scalar2): one error budget shared by the poles, except for the
+    // relaxed signs of relCG (spectrally preconditioned CGNE lost convergence at mu = 0.01
+    // when its signs came close to eta_j), which keep an even share per pole (negative)
+    const bool shared = e < 1e-6 || c->P.solver != OVL_SOLVER_CG;
+    c->hpin[j] = shared ? e : -e;
   }
   int ncopy = n;
   if (coef) {

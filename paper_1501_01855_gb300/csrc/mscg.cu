@@ -112,10 +112,10 @@ __global__ void ms_scalar0_kernel(MsRhs* ms, const double* partials, int nsb, co
     m.alpha = 0.0;
     m.alpha_prev = 1.0;
     m.beta_prev = 0.0;
-    // per-pole share of the error budget eta ||v||; its sign selects the stopping rule:
-    // positive (accurate signs, eta < 1e-6) shared budget, negative (relaxed signs inside
-    // the middle solves) every pole within its even share
-    m.thr = (eta[rhs] < 1e-6 ? 1.0 : -1.0) * eta[rhs] * sqrt(s[0]) / (double)P->n;
+    // per-pole share of the error budget |eta| ||v||; the sign of eta (set by the host)
+    // selects the stopping rule: positive, one budget shared by all poles; negative,
+    // every pole within its even share
+    m.thr = eta[rhs] * sqrt(s[0]) / (double)P->n;
     m.active = P->n;
     m.nact_y = 0;
     m.iter = 0;
@@ -186,7 +186,7 @@ __global__ void ms_scalar2_kernel(MsRhs* ms, const double* partials, int nsb, co
     // less. Accurate signs: shifted poles (largest sigma first) stop at a quarter of the
     // even share, which saves their update passes, and the system stops as soon as the
     // sum of all bounds is within the whole budget, so the slowest (base) pole uses what
-    // the others left. Relaxed signs (middle solves): every pole within its even share,
+    // the others left. Even shares (relaxed signs of relCG): every pole within thr,
     // which keeps the actual sign error well below the relaxation's eta_j.
     auto bound = [&](int i) { return P->omega[i] * P->gbound[i] * fabs(m.zeta_next[i]) * rn; };
     int a = act;
