@@ -274,9 +274,69 @@ __global__ void __launch_bounds__(256) ms_update_kernel(SpinorRef r, SpinorRef p
   store_spinor_as<PR, T>(y, rhs, s, yv);
 }
 
+// Double-float form of the same pass, chunk-major: for each 16-byte chunk (one complex
+// component) of r and y, every active pole's chunk is read, y accumulated and the pole
+// rewritten. Holding one component instead of whole spinors keeps the thread small
+// (the spinor-at-a-time form needs ~250 registers: 8 warps per SM, 78% of the copy
+// bandwidth), and the pole coefficients are converted to double-float once per block
+// into shared memory instead of per thread and pole.
+__global__ void __launch_bounds__(256) ms_update_df_kernel(SpinorRef r, SpinorRef pb, SpinorRef y, int nrhs, int V,
+                                                           int ngr, const MsRhs* ms) {
+  __shared__ float2 cf[4][NPMAX][3];   // (y, r, p) coefficients of the block's systems
+  const int sb = blockIdx.x / ngr;
+  const int rg = blockIdx.x - sb * ngr;
+  const int rhs = rg * blockDim.y + threadIdx.y;
+  const bool in_rhs = rhs < nrhs;
+  const int ny = in_rhs ? ms[rhs].nact_y : 0;
+  if (in_rhs) {
+    const MsRhs& m = ms[rhs];
+    for (int i = threadIdx.x; i < ny; i += blockDim.x) {
+      const double c3[3] = {m.coef_y[i], m.coef_r[i], m.coef_p[i]};
+#pragma unroll
+      for (int k = 0; k < 3; ++k) {
+        const float h = (float)c3[k];
+        cf[threadIdx.y][i][k] = make_float2(h, (float)(c3[k] - (double)h));
+      }
+    }
+  }
+  __syncthreads();
+  const int s = sb * BX + threadIdx.x;
+  if (s >= V || !in_rhs || ny == 0) return;
+  const int na = ms[rhs].active;
+  const size_t Vs = (size_t)V;
+  const float4* rr = reinterpret_cast<const float4*>(r.data) + (size_t)rhs * 12 * Vs + s;
+  float4* yy = reinterpret_cast<float4*>(y.data) + (size_t)rhs * 12 * Vs + s;
+  float4* pp = reinterpret_cast<float4*>(pb.data) + (size_t)rhs * 12 * Vs + s;
+  const size_t pole_stride = (size_t)nrhs * 12 * Vs;
+  const float2(*c)[3] = cf[threadIdx.y];
+  for (int k = 0; k < 12; ++k) {
+    const float4 rw = rr[(size_t)k * Vs];
+    const cpx<df> rc = cmk(df(rw.x, rw.y), df(rw.z, rw.w));
+    const float4 yw = yy[(size_t)k * Vs];
+    cpx<df> yc = cmk(df(yw.x, yw.y), df(yw.z, yw.w));
+    for (int i = 0; i < ny; ++i) {
+      float4* pi = pp + (size_t)i * pole_stride + (size_t)k * Vs;
+      const float4 pw = *pi;
+      cpx<df> pc = cmk(df(pw.x, pw.y), df(pw.z, pw.w));
+      const df cy(c[i][0].x, c[i][0].y);
+      yc = yc + cy * pc;
+      if (i < na) {
+        const df cr(c[i][1].x, c[i][1].y), cp(c[i][2].x, c[i][2].y);
+        pc = cr * rc + cp * pc;
+        *pi = make_float4(pc.r.hi, pc.r.lo, pc.i.hi, pc.i.lo);
+      }
+    }
+    yy[(size_t)k * Vs] = make_float4(yc.r.hi, yc.r.lo, yc.i.hi, yc.i.lo);
+  }
+}
+
 void launch_ms_update(int pr, int pp, SpinorRef r, SpinorRef pb, SpinorRef y, int npoles, int nrhs, int V,
                       const MsRhs* ms, cudaStream_t st) {
   Shape sh = make_shape(V, nrhs);
+  if (pr == P64E && pp == P64E) {
+    ms_update_df_kernel<<<sh.grid(), sh.block(), 0, st>>>(r, pb, y, nrhs, V, sh.ngr, ms);
+    return;
+  }
   if (pr == P64 && pp == P64) ms_update_kernel<P64, P64><<<sh.grid(), sh.block(), 0, st>>>(r, pb, y, npoles, nrhs, V, sh.ngr, ms);
   else if (pr == P32 && pp == P32) ms_update_kernel<P32, P32><<<sh.grid(), sh.block(), 0, st>>>(r, pb, y, npoles, nrhs, V, sh.ngr, ms);
   else if (pr == P32 && pp == P16) ms_update_kernel<P32, P16><<<sh.grid(), sh.block(), 0, st>>>(r, pb, y, npoles, nrhs, V, sh.ngr, ms);

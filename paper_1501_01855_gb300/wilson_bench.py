@@ -1,4 +1,5 @@
-"""Time the Wilson kernel K alone through the C ABI (ovl_bench_wilson).
+"""Time the Wilson kernel K alone through the C ABI (ovl_bench_wilson), or one
+sign-function application (--sign ETA).
 
     python -m paper_1501_01855_gb300.wilson_bench --dims 24 24 24 48 --prec f32 --nrhs 1
 
@@ -32,7 +33,12 @@ def main(argv=None):
     ap.add_argument("--nrhs", type=int, default=1)
     ap.add_argument("--iters", type=int, default=3)
     ap.add_argument("--variant", type=int, default=-1, choices=[-1, 0, 1, 2])
+    ap.add_argument("--sign", type=float, default=0.0, metavar="ETA",
+                    help="instead: one sign-function application (multi-shift CG) to accuracy ETA "
+                         "on nrhs random vectors, 20 poles")
     args = ap.parse_args(argv)
+    if args.sign > 0:
+        return sign_main(args)
     p = B.ovl_params_default()
     p.a_override, p.b_override = 0.2, 2.6     # skip the Lanczos bound estimate
     p.wilson_variant = args.variant
@@ -44,6 +50,25 @@ def main(argv=None):
     print("Wilson K %s, %s, nrhs %d, variant %d: %.4f ms per launch, %.1f MB algorithmic, %.0f GB/s, "
           "%.2f G site-applications/s" % (args.prec, "x".join(map(str, args.dims)), args.nrhs, variant, ms,
                                           nbytes / 1e6, nbytes / ms / 1e6, v * args.nrhs / ms / 1e6))
+    ctx.close()
+
+
+def sign_main(args):
+    import time
+    p = B.ovl_params_default()
+    p.a_override, p.b_override = 0.2, 2.6
+    p.wilson_variant = args.variant
+    ctx = B.Overlap(tuple(args.dims), unit_links(args.dims), 1.4, 0.05, 20, 1e-10, params=p)
+    rng = np.random.default_rng(7)
+    shp = (args.nrhs,) + tuple(reversed(args.dims)) + (4, 3)
+    v = rng.standard_normal(shp) + 1j * rng.standard_normal(shp)
+    out = np.empty_like(v)
+    t0 = time.perf_counter()
+    for _ in range(args.iters):
+        ctx.sign_apply(v, out, eta=args.sign, prec=PRECS[args.prec])
+    dt = (time.perf_counter() - t0) / args.iters
+    print("sign %s, %s, nrhs %d, eta %g: %.1f ms per application (host buffers)"
+          % (args.prec, "x".join(map(str, args.dims)), args.nrhs, args.sign, dt * 1e3))
     ctx.close()
 
 
