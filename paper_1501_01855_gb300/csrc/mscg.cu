@@ -340,7 +340,6 @@ void launch_ms_update(int pr, int pp, SpinorRef r, SpinorRef pb, SpinorRef y, in
   if (pr == P64 && pp == P64) ms_update_kernel<P64, P64><<<sh.grid(), sh.block(), 0, st>>>(r, pb, y, npoles, nrhs, V, sh.ngr, ms);
   else if (pr == P32 && pp == P32) ms_update_kernel<P32, P32><<<sh.grid(), sh.block(), 0, st>>>(r, pb, y, npoles, nrhs, V, sh.ngr, ms);
   else if (pr == P32 && pp == P16) ms_update_kernel<P32, P16><<<sh.grid(), sh.block(), 0, st>>>(r, pb, y, npoles, nrhs, V, sh.ngr, ms);
-  else if (pr == P64E && pp == P64E) ms_update_kernel<P64E, P64E><<<sh.grid(), sh.block(), 0, st>>>(r, pb, y, npoles, nrhs, V, sh.ngr, ms);
   else note_bad_combo("ms_update");
 }
 
