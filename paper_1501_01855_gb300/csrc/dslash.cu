@@ -4,11 +4,16 @@
 //                                              + (1+gamma_mu) U_mu(x-mu)^dag psi(x-mu) ) ]
 //
 // One thread per (site, system). (1 -+ gamma_mu) has rank 2, so each neighbour is
-// projected to a half spinor (2 spins x 3 colours), multiplied by the 12-real link
-// (row 3 rebuilt in registers) and expanded again; the spin algebra below is the
-// DeGrand-Rossi chiral basis, gamma5 = diag(1, 1, -1, -1). Threads of one block
-// that share a site but belong to different systems read the same links, so the
-// link bytes of a multi-system launch come from L1 once per block.
+// projected to a half spinor (2 spins x 3 colours), multiplied by the link and
+// expanded again; the spin algebra below is the DeGrand-Rossi chiral basis,
+// gamma5 = diag(1, 1, -1, -1). FP64 / FP32 / FP16 links are 12-real (row 3 rebuilt in
+// registers) and the eight neighbours are unrolled; the double-float kernel reads an
+// 18-real eight-slot link field and runs one rolled loop over the neighbours (see
+// hop_nb_df_core). Threads of one block that share a site but belong to different
+// systems read the same links, so the link bytes of a multi-system launch come from L1
+// once per block. Launch shapes (chosen per precision by the autotuner at create):
+// BX consecutive sites x up to 4 systems per block; four threads per site, one per
+// direction; 8x4x4x2 site tiles.
 //
 // Three fused epilogues cover every use in the sign function (Sec. 3):
 //   MODE_K    out = K in, partial sums of ||out||^2 and ||in||^2

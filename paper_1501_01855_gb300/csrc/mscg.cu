@@ -12,10 +12,11 @@
 //
 // Stopping rule (the reading of "eta = Delta or the error in the inversion of
 // x^2 + sigma_i, whichever is larger"): pole i contributes at most
-// omega_i g_i |zeta_i| ||r|| to the error of eps(K) v, with
-// g_i = max_{a<=x<=b} x/(x^2+sigma_i); pole i stops once that is below
-// eta ||v|| / N_Z, poles dropping from the largest shift down (they converge
-// first), and the solve ends when none is left.
+// e_i = omega_i g_i |zeta_i| ||r|| to the error of eps(K) v, with
+// g_i = max_{a<=x<=b} x/(x^2+sigma_i), and the solve may end once the e_i of the
+// running poles and those frozen by the stopped ones sum to eta ||v||; poles drop
+// from the largest shift down (they converge first). See ms_scalar2_kernel for how
+// the budget is shared.
 #include "kernels.h"
 
 namespace ovl {
