@@ -162,7 +162,8 @@ ovl_status ovl_wilson_apply(ovl_ctx* ctx, const void* in, void* out, int n, int 
  * sits under a hard cap, and loops that must not stall in the allocator. (The paper
  * has no counterpart; this is a property of the library, not of the method.)
  *   in, out  device pointers (the context's device must be current), n canonical
- *            spinors each; dtype and prec as for ovl_wilson_apply.
+ *            spinors each; dtype as for ovl_wilson_apply, prec OVL_PREC_F64, F32 or F16
+ *            (anything else returns OVL_EINVAL).
  * The two layout-conversion buffers live in one static device array of
  * OVL_NOALLOC_BYTES (48 MiB) that every device loading the library holds until the
  * process exits; a call needing more (2 n V x 192 bytes in FP64, x 96 in FP32,
