@@ -72,6 +72,82 @@ def cg(apply, b, tol, maxiter=100000):
     return x, it
 
 
+# ---------------------------------------------------------------- larger lattices
+# The per-pole CGs of every (vector, pole) pair are independent, so they run in a pool of
+# worker processes (spawn start method: the workers import only numpy, scipy and this
+# package), each holding K as a sparse matrix (wilson.sparse_K).
+_WORKER_K = None
+
+
+def _worker_init(U, m0, antiperiodic_t):
+    global _WORKER_K
+    _WORKER_K = wilson.sparse_K(U, m0, antiperiodic_t)
+
+
+def _worker_pole_solve(task):
+    v, s, tol = task
+    K = _WORKER_K
+    return cg(lambda p: K @ (K @ p) + s * p, v, tol)
+
+
+def shifted_solves(U, vs, m0, sigma, tol=1e-13, antiperiodic_t=False, workers=1):
+    """x_ij = (K^2 + sigma_i)^-1 v_j by plain CG for every pole i and vector j (flat
+    vectors), returned as xs[j][i] with the iteration counts its[j][i]. workers > 1 runs
+    the solves in a spawn-context process pool; workers = 1 runs them here."""
+    vs = np.asarray(vs)
+    nv = vs.shape[0]
+    tasks = [(vs[j].ravel(), float(s), tol) for j in range(nv) for s in sigma]
+    if workers <= 1:
+        _worker_init(U, m0, antiperiodic_t)
+        res = [_worker_pole_solve(t) for t in tasks]
+    else:
+        import multiprocessing as mp
+        import os
+        # one BLAS thread per worker: the parallelism is the pool's
+        keep = {k: os.environ.get(k) for k in ("OPENBLAS_NUM_THREADS", "OMP_NUM_THREADS", "MKL_NUM_THREADS")}
+        for k in keep:
+            os.environ[k] = "1"
+        try:
+            with mp.get_context("spawn").Pool(workers, initializer=_worker_init,
+                                              initargs=(U, m0, antiperiodic_t)) as pool:
+                res = pool.map(_worker_pole_solve, tasks, chunksize=1)
+        finally:
+            for k, v in keep.items():
+                if v is None:
+                    os.environ.pop(k, None)
+                else:
+                    os.environ[k] = v
+    npol = len(sigma)
+    xs = [[res[j * npol + i][0] for i in range(npol)] for j in range(nv)]
+    its = [[res[j * npol + i][1] for i in range(npol)] for j in range(nv)]
+    return xs, its
+
+
+def zolotarev_sign_apply_many(U, vs, m0, omega, sigma, tol=1e-13, antiperiodic_t=False, workers=1):
+    """epsilon(K) v_j = K sum_i omega_i (K^2 + sigma_i)^-1 v_j for a batch vs (n, ...),
+    every pole of every vector by its own CG (shifted_solves). Returns (out, iterations)."""
+    vs = np.asarray(vs)
+    xs, its = shifted_solves(U, vs, m0, sigma, tol, antiperiodic_t, workers)
+    K = wilson.sparse_K(U, m0, antiperiodic_t)
+    out = np.empty_like(vs)
+    for j in range(vs.shape[0]):
+        y = sum(om * x for om, x in zip(omega, xs[j]))
+        out[j] = (K @ y).reshape(vs.shape[1:])
+    return out, its
+
+
+def overlap_apply_many(U, vs, m0, mu, omega, sigma, tol=1e-13, antiperiodic_t=False, workers=1):
+    """D(mu) v = 1/2 (1+mu) v + 1/2 (1-mu) gamma5 epsilon(K) v for a batch vs (n, ...);
+    mu may be one mass or one per vector."""
+    vs = np.asarray(vs)
+    s, _ = zolotarev_sign_apply_many(U, vs, m0, omega, sigma, tol, antiperiodic_t, workers)
+    mus = np.broadcast_to(np.asarray(mu, dtype=np.float64), (vs.shape[0],))
+    out = np.empty_like(vs)
+    for j in range(vs.shape[0]):
+        out[j] = 0.5 * (1.0 + mus[j]) * vs[j] + 0.5 * (1.0 - mus[j]) * wilson.apply_gamma5(s[j])
+    return out
+
+
 def zolotarev_sign_apply(U, v, m0, omega, sigma, tol=1e-13, antiperiodic_t=False,
                          return_solutions=False):
     """epsilon(K) v = K sum_i omega_i (K^2 + sigma_i)^-1 v, every pole by its own CG."""

@@ -132,6 +132,48 @@ def dense_K(U, m0, antiperiodic_t=False):
     return dense_operator(lambda v: apply_K(U, v, m0, antiperiodic_t), site_shape)
 
 
+def sparse_K(U, m0, antiperiodic_t=False):
+    """K of Sec. 1 (aK_xy) as a scipy CSR matrix on the flattened canonical spinor
+    ordering (site, spin, colour), for the larger lattices where dense_K does not fit.
+
+    Block row x holds gamma5 (1 x 1) at column block x, -kappa gamma5 (1 - gamma_mu) x U_mu(x)
+    at x + mu and -kappa gamma5 (1 + gamma_mu) x U_mu(x - mu)^dag at x - mu, the t hops that
+    cross the boundary negated when antiperiodic_t. The same formula as apply_K, assembled
+    as explicit 12 x 12 (spin x colour) blocks instead of applied."""
+    import scipy.sparse as sps
+    lt, lz, ly, lx = U.shape[:4]
+    V = lt * lz * ly * lx
+    kap = kappa_of_m(m0)
+    site = np.arange(V).reshape(lt, lz, ly, lx)
+    Us = U.reshape(V, 4, 3, 3)
+    tco = np.broadcast_to(np.arange(lt)[:, None, None, None], (lt, lz, ly, lx)).ravel()
+    blocks = [np.broadcast_to(np.kron(GAMMA5, np.eye(3)), (V, 12, 12))]
+    cols = [site.ravel()]
+    for mu in range(4):
+        ax = MU_AXIS[mu]
+        fwd = np.roll(site, -1, axis=ax).ravel()      # x + mu
+        bwd = np.roll(site, +1, axis=ax).ravel()      # x - mu
+        sf = np.ones(V)
+        sb = np.ones(V)
+        if antiperiodic_t and mu == 3:
+            sf[tco == lt - 1] = -1.0
+            sb[tco == 0] = -1.0
+        Pm = GAMMA5 @ (I4 - GAMMA[mu])
+        Pp = GAMMA5 @ (I4 + GAMMA[mu])
+        # (P x W)[(s, a), (t, b)] = P[s, t] W[a, b]
+        Bf = np.einsum("st,xab->xsatb", Pm, Us[:, mu]).reshape(V, 12, 12)
+        Bb = np.einsum("st,xba->xsatb", Pp, np.conj(Us[bwd, mu])).reshape(V, 12, 12)
+        blocks += [-kap * sf[:, None, None] * Bf, -kap * sb[:, None, None] * Bb]
+        cols += [fwd, bwd]
+    data = np.stack(blocks, axis=1).reshape(-1, 12, 12)
+    indices = np.stack(cols, axis=1).ravel()
+    indptr = np.arange(0, 9 * V + 1, 9)
+    M = sps.bsr_matrix((data, indices, indptr), shape=(12 * V, 12 * V)).tocsr()
+    M.sum_duplicates()          # 2-site extents: x + mu and x - mu are one site
+    M.eliminate_zeros()
+    return M
+
+
 def free_field_K_abs_spectrum(dims, m0, antiperiodic_t=False):
     """|lambda(K)| for U = 1, from the plane-wave closed form.
 

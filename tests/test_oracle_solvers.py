@@ -80,3 +80,58 @@ def test_cgne_spectral_identity_precond():
     b = rng.normal(size=N) + 1j * rng.normal(size=N)
     x, it = solvers.cgne_spectral(lambda v: H @ v, b, 1e-12, lambda v: v)
     assert np.linalg.norm(H @ x - b) <= 1e-9 * np.linalg.norm(b)
+
+
+def _dense_H(mu=0.05):
+    """H = gamma5 D(mu) on the 2^4 lattice with the exact sign (Sec. 1), dense."""
+    from oracle import overlap
+    from tests.oracle_util import dense_setup
+    U, Kd, S, w = dense_setup((2, 2, 2, 2))
+    D = overlap.dense_overlap(S, mu, 16)
+    H = overlap.gamma5_matrix(16) @ D
+    return 0.5 * (H + H.conj().T)
+
+
+def test_cgne_spectral_with_exact_eigenvectors():
+    """Alg. 4 with the spectral preconditioner of Sec. 4 built from the 12 lowest exact
+    eigenvectors of H^2 (H = gamma5 D, 2^4): the solution solves H x = b, the CG iterates
+    are those of plain CG on the explicit matrix Hhat^-1 H^2 Hhat^-1 (one-sided use of
+    Hhat^-1, or a wrong final x = H Hhat^-1 x_j, would break one of the two), the
+    preconditioned operator has the deflated eigenvalues at c^2 = 3/4, and the solve takes
+    fewer iterations than without the preconditioner."""
+    from oracle import deflation
+    H = _dense_H()
+    lam, Q = np.linalg.eigh(H @ H)
+    n = 12
+    shape = (16, 4, 3)
+    psi = [Q[:, i].reshape(shape) for i in range(n)]
+    pre = deflation.spectral_precond(psi, lam[:n])
+    rng = np.random.default_rng(5)
+    b = (rng.normal(size=shape) + 1j * rng.normal(size=shape))
+    applyH = lambda v: (H @ v.ravel()).reshape(v.shape)
+    x, it = solvers.cgne_spectral(applyH, b, 1e-12, pre)
+    assert np.linalg.norm(applyH(x) - b) <= 1e-10 * np.linalg.norm(b)
+    assert np.allclose(x.ravel(), np.linalg.solve(H, b.ravel()), rtol=0, atol=1e-9 * np.linalg.norm(x))
+    # the explicit preconditioned operator: deflated eigenvalues at c^2 = 3/4, others kept
+    P = np.stack([pre(np.eye(192)[:, j].reshape(shape)).ravel() for j in range(192)], axis=1)
+    M = P @ H @ H @ P
+    for i in range(n):
+        assert np.allclose(M @ Q[:, i], 0.75 * Q[:, i], atol=1e-10)
+    for i in range(n, n + 5):
+        assert np.allclose(M @ Q[:, i], lam[i] * Q[:, i], atol=1e-10)
+    # plain CG on M with rhs Hhat^-1 b gives the same solution through x = H Hhat^-1 y
+    y = np.linalg.solve(M, P @ b.ravel())
+    assert np.allclose(x.ravel(), H @ (P @ y), atol=1e-9 * np.linalg.norm(x))
+    _, it0 = solvers.cgne_spectral(applyH, b, 1e-12, lambda v: v)
+    assert it < it0, (it, it0)
+
+
+def test_gmres_solve_matches_dense_solve():
+    """The restarted minimal-residual solve reaches ||b - A x|| <= tol ||b|| and the
+    dense solution, with restarts (restart length 15 < the 60 steps needed)."""
+    U, rho, b = _shifted_unitary(N=100, mu=0.02, seed=8)
+    A = rho * np.eye(len(b)) + U
+    x = solvers.gmres_solve(lambda v: A @ v, b, 1e-12, restart=15)
+    assert np.linalg.norm(b - A @ x) <= 1e-12 * np.linalg.norm(b)
+    xs = np.linalg.solve(A, b)
+    assert np.linalg.norm(x - xs) <= 1e-10 * np.linalg.norm(xs)

@@ -128,3 +128,25 @@ def test_site_formula_matches_full_apply(apt):
     got = wilson.apply_K_sites(U, psi, 1.3, sites, apt)
     ref = np.array([full[t, z, y, x] for (x, y, z, t) in sites])
     assert np.allclose(got, ref, atol=1e-14)
+
+
+@pytest.mark.parametrize("dims,apt", [((2, 2, 2, 2), False), ((4, 2, 2, 4), True), ((2, 4, 2, 2), False)])
+def test_sparse_K_equals_dense_K(dims, apt):
+    """The sparse assembly of K (explicit spin x colour blocks) is the dense operator
+    built by applying the formula to unit vectors, including 2-site extents where the
+    forward and backward neighbours coincide and the antiperiodic t boundary."""
+    U = synth.gauge_links(dims, 0.3, 77)
+    Ks = wilson.sparse_K(U, 1.4, apt).toarray()
+    Kd = wilson.dense_K(U, 1.4, apt)
+    assert np.abs(Ks - Kd).max() <= 1e-14
+
+
+def test_sparse_K_equals_apply_K_larger():
+    dims = (8, 4, 4, 6)
+    U = synth.gauge_links(dims, 0.3, 78)
+    v = synth.gaussian_source(dims, 79, nvec=2)
+    for apt in (False, True):
+        K = wilson.sparse_K(U, 1.4, apt)
+        for j in range(2):
+            got = (K @ v[j].ravel()).reshape(v[j].shape)
+            assert np.abs(got - wilson.apply_K(U, v[j], 1.4, apt)).max() <= 1e-13
