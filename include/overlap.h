@@ -166,19 +166,24 @@ ovl_status ovl_wilson_apply(ovl_ctx* ctx, const void* in, void* out, int n, int 
  *            (anything else returns OVL_EINVAL).
  * The two layout-conversion buffers live in one static device array of
  * OVL_NOALLOC_BYTES (48 MiB) that every device loading the library holds until the
- * process exits; a call needing more (2 n V x 192 bytes in FP64, x 96 in FP32,
- * x 104 in FP16, so n V <= 131072 in FP64) returns OVL_EINVAL. No cudaMalloc,
+ * process exits. A call needs 2 n V x 192 bytes in FP64, x 96 in FP32 and x 52 in FP16
+ * (48 bytes of spinor plus a 4-byte scale per site), each buffer rounded up to 256
+ * bytes, so n V <= 131072 in FP64; a larger call returns OVL_EINVAL. No cudaMalloc,
  * cudaFree or other allocating routine is called. The first call on a device looks up
  * the array's device address (cudaGetSymbolAddress) once; make that first call before
- * any stream capture. All calls share the array: calls that overlap on the GPU race
- * on it, and it keeps the last call's intermediate data (nothing in it has to start at
- * zero). */
+ * any stream capture begins. Like every entry point here, the call returns after its
+ * work on the context stream has completed. All calls share the array: calls that
+ * overlap on the GPU race on it, and it keeps the last call's intermediate data
+ * (nothing in it has to start at zero). */
 #define OVL_NOALLOC_BYTES ((size_t)48 << 20)
 ovl_status ovl_wilson_apply_noalloc(ovl_ctx* ctx, const void* in, void* out, int n, int dtype, int prec);
 
 /* out = eps(K) in (Sec. 3) for n spinors, multi-shift CG stopped at accuracy eta
  * (the per-pole rule of the Zolotarev sum; eta <= 0 means eps_sign). prec as above,
- * OVL_PREC_AUTO picks by eta. */
+ * OVL_PREC_AUTO picks by eta. OVL_ENOCONV when a system reached params.mscg_max
+ * iterations before eta was met (the message names the system), OVL_EBREAKDOWN on a
+ * non-positive or non-finite curvature; every solver that applies the sign passes
+ * these on. */
 ovl_status ovl_sign_apply(ovl_ctx* ctx, const void* in, void* out, int n, int dtype, int on_device,
                           double eta, int prec);
 
@@ -209,7 +214,9 @@ ovl_status overlap_solve(ovl_ctx* ctx, int nrhs, const double* mus, int nmass, c
 /* Solve D(mu) x = b once while accumulating Ritz vectors of D^dag D + 2 mu delta H
  * (eigSUMR, Algs. 5-6, Sec. 5) with basis size m_basis, keeping n_eig. If *defl is
  * NULL a new space is created; otherwise its vectors seed the basis and are
- * improved. The space can then be passed to overlap_solve(). */
+ * improved. The space can then be passed to overlap_solve(). OVL_ENOCONV: the solve
+ * stopped short of tol; the space is still built (or refined) and *defl set, and x
+ * holds the last iterate. */
 ovl_status eigsumr_accumulate(ovl_ctx* ctx, ovl_defl** defl, int n_eig, int m_basis, double mu,
                               const void* rhs, void* x, int dtype, int on_device, double tol,
                               ovl_solve_info* info);
@@ -263,6 +270,12 @@ ovl_status ovl_profile_units(ovl_ctx* ctx, int cls, double* units);
  * (CUDA events on the context stream) and algorithmic bytes per launch. */
 ovl_status ovl_bench_wilson(ovl_ctx* ctx, int prec, int n, int iters, double* ms_per_launch,
                             double* bytes_per_launch);
+
+/* FP32 instruction-issue probe: eight independent FMA chains per thread on every SM;
+ * *fma_per_s receives the measured FP32 FMA instructions per second of this device (the
+ * denominator of the ALU view of the double-float kernels, which run on the FP32 pipes).
+ * Allocates and frees a small result buffer. */
+ovl_status ovl_bench_fp32(ovl_ctx* ctx, double* fma_per_s);
 
 /* Wilson-kernel autotuner result for one storage precision (OVL_PREC_*): the variant
  * in use (0 one thread per site, 1 one thread per site and direction, 2 4D tiles) and

@@ -8,16 +8,23 @@ GPU); this module only moves tensors. PyTorch's convention for a real loss L of 
 complex tensor z is dL = Re(sum conj(z.grad) dz); the library returns G with
 dS = 2 Re(sum conj(G) dU), so z.grad = 2 G.
 
-The context must have been created from the same gauge field U that is passed in (the
-library copies the links at create); phi is treated as a constant (no gradient).
+The library copies the links when the context is created, so the action and its
+gradient are those of that gauge field: forward() compares U with it (a digest of the
+canonical complex128 bytes) and raises ValueError when they differ, rather than return
+the action of other links. phi is treated as a constant (no gradient).
 """
 import numpy as np
 import torch
+
+from .binding import links_digest
 
 
 class OverlapAction(torch.autograd.Function):
     @staticmethod
     def forward(fctx, U, phi, ovl, mu, tol):
+        if links_digest(U.detach().contiguous().cpu().numpy()) != ovl.links_digest:
+            raise ValueError("U differs from the gauge field the overlap context was created from; "
+                             "create a context from these links to differentiate at them")
         ph = phi.detach()
         if ph.is_cuda:
             ph = ph.contiguous()

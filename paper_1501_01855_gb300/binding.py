@@ -89,6 +89,7 @@ _SIGS = {
     "ovl_profile_units": (I, [P, I, DP]),
     "ovl_bench_wilson": (I, [P, I, I, I, DP, DP]),
     "ovl_wilson_tuning": (I, [P, I, ctypes.POINTER(I), DP, DP, DP]),
+    "ovl_bench_fp32": (I, [P, DP]),
 }
 
 
@@ -125,7 +126,7 @@ def _dptr(a):
 
 
 def _spinor_arg(x):
-    """(pointer, dtype code, on_device, count of spinors given the site count)."""
+    """(pointer, dtype code, on_device, element count, CUDA device index or None)."""
     try:
         import torch
         if isinstance(x, torch.Tensor):
@@ -137,7 +138,11 @@ def _spinor_arg(x):
                 code = OVL_C64
             else:
                 raise ValueError("spinors must be complex128 or complex64")
-            return ctypes.c_void_p(x.data_ptr()), code, 1 if x.is_cuda else 0, x.numel()
+            if x.is_cuda:
+                return ctypes.c_void_p(x.data_ptr()), code, 1, x.numel(), x.device.index
+            if x.requires_grad:
+                x = x.detach()
+            x = x.numpy()
     except ImportError:
         pass
     x = np.asarray(x)
@@ -149,7 +154,26 @@ def _spinor_arg(x):
         code = OVL_C64
     else:
         raise ValueError("spinors must be complex128 or complex64")
-    return ctypes.c_void_p(x.ctypes.data), code, 0, x.size
+    return ctypes.c_void_p(x.ctypes.data), code, 0, x.size, None
+
+
+def _io(ctx_dev, x, out, same_count=True):
+    """Marshal an (input, output) pair: both on the same side (host or the context's
+    device), the same element type and, unless same_count is False, the same size, so
+    that the library never writes past the end of out."""
+    pi, code, dev, cnt, di = _spinor_arg(x)
+    po, code2, dev2, cnt2, do = _spinor_arg(out)
+    if dev != dev2:
+        raise ValueError("input and output must both be host arrays or both device tensors")
+    if code2 != code:
+        raise ValueError("input and output must have the same dtype")
+    if same_count and cnt2 != cnt:
+        raise ValueError("output holds %d complex entries, input %d" % (cnt2, cnt))
+    if dev and ctx_dev is not None and (di != ctx_dev or do != ctx_dev):
+        raise ValueError("device tensors must be on cuda:%d, the context's device" % ctx_dev)
+    if not dev and isinstance(out, np.ndarray) and not out.flags["WRITEABLE"]:
+        raise ValueError("output array is read-only")
+    return pi, po, code, dev, cnt
 
 
 def ovl_version():
@@ -168,6 +192,21 @@ def ovl_zolotarev_coeffs(n, a, b):
     de = np.zeros(1)
     _check(load().ovl_zolotarev_coeffs(int(n), float(a), float(b), _dptr(om), _dptr(sg), _dptr(de)))
     return om, sg, float(de[0])
+
+
+def _current_device():
+    try:
+        import torch
+        return torch.cuda.current_device() if torch.cuda.is_available() else None
+    except ImportError:
+        return None
+
+
+def links_digest(links):
+    """Digest of a gauge field in the canonical complex128 layout (bytes as given)."""
+    import hashlib
+    a = np.ascontiguousarray(np.asarray(links, dtype=np.complex128))
+    return hashlib.blake2b(a.view(np.uint8), digest_size=16).hexdigest()
 
 
 class Overlap:
@@ -193,6 +232,9 @@ class Overlap:
             raise OvlError(st, "overlap_create failed (see stderr)")
         self.h = h
         self.m0, self.mu, self.n_poles = m0, mu, n_poles
+        self.device = _current_device()
+        # fingerprint of the gauge field the library copied (checked by the autograd wrapper)
+        self.links_digest = links_digest(links)
 
     def close(self):
         if getattr(self, "h", None):
@@ -219,39 +261,32 @@ class Overlap:
         return om, sg, float(de[0]), float(a[0]), float(b[0])
 
     def wilson_apply(self, x, out, prec=OVL_PREC_F64):
-        pi, code, dev, cnt = _spinor_arg(x)
-        po, code2, dev2, cnt2 = _spinor_arg(out)
+        pi, po, code, dev, cnt = _io(self.device, x, out)
         _check(load().ovl_wilson_apply(self.h, pi, po, self._n(cnt), code, dev, int(prec)), self.h)
         return out
 
     def wilson_apply_noalloc(self, x, out, prec=OVL_PREC_F64):
         """K on device tensors without any allocation during the call (static scratch)."""
-        pi, code, dev, cnt = _spinor_arg(x)
-        po, code2, dev2, _ = _spinor_arg(out)
-        if not (dev and dev2):
+        pi, po, code, dev, cnt = _io(self.device, x, out)
+        if not dev:
             raise ValueError("ovl_wilson_apply_noalloc takes device buffers only")
-        if code2 != code:
-            raise ValueError("in and out must have the same dtype")
         _check(load().ovl_wilson_apply_noalloc(self.h, pi, po, self._n(cnt), code, int(prec)), self.h)
         return out
 
     def sign_apply(self, x, out, eta=0.0, prec=OVL_PREC_AUTO):
-        pi, code, dev, cnt = _spinor_arg(x)
-        po, _, _, _ = _spinor_arg(out)
+        pi, po, code, dev, cnt = _io(self.device, x, out)
         _check(load().ovl_sign_apply(self.h, pi, po, self._n(cnt), code, dev, float(eta), int(prec)), self.h)
         return out
 
     def apply(self, x, out, mu=None, eta=0.0, prec=OVL_PREC_AUTO, hermitian=False):
-        pi, code, dev, cnt = _spinor_arg(x)
-        po, _, _, _ = _spinor_arg(out)
+        pi, po, code, dev, cnt = _io(self.device, x, out)
         mu = self.mu if mu is None else mu
         _check(load().overlap_apply(self.h, float(mu), pi, po, self._n(cnt), code, dev, float(eta), int(prec),
                                     1 if hermitian else 0), self.h)
         return out
 
     def sumr(self, b, x, tol, eta_fixed=0.0, maxit=200, mu=None):
-        pb, code, dev, cnt = _spinor_arg(b)
-        px, _, _, _ = _spinor_arg(x)
+        pb, px, code, dev, cnt = _io(self.device, b, x)
         n = self._n(cnt)
         mu = self.mu if mu is None else mu
         hist = np.zeros(n * maxit)
@@ -262,10 +297,11 @@ class Overlap:
         return [hist[j * maxit:j * maxit + its[j]] for j in range(n)], its
 
     def solve(self, b, x, tol, mus=None, defl=None, allow_noconv=False):
-        pb, code, dev, cnt = _spinor_arg(b)
-        px, _, _, _ = _spinor_arg(x)
+        pb, px, code, dev, cnt = _io(self.device, b, x, same_count=False)
         nrhs = self._n(cnt)
         mus = np.ascontiguousarray([self.mu] if mus is None else mus, dtype=np.float64)
+        if _spinor_arg(x)[3] != cnt * len(mus):
+            raise ValueError("x must hold nmass * nrhs spinors")
         info = (ovl_solve_info * (nrhs * len(mus)))()
         st = load().overlap_solve(self.h, nrhs, _dptr(mus), len(mus), pb, px, code, dev, float(tol),
                                   defl.h if defl is not None else None, info)
@@ -273,10 +309,10 @@ class Overlap:
             _check(st, self.h)
         return [i.as_dict() for i in info]
 
-    def eigsumr_accumulate(self, b, x, tol, n_eig, m_basis, mu=None, defl=None):
-        pb, code, dev, cnt = _spinor_arg(b)
-        px, _, _, _ = _spinor_arg(x)
-        self._n(cnt)
+    def eigsumr_accumulate(self, b, x, tol, n_eig, m_basis, mu=None, defl=None, allow_noconv=False):
+        pb, px, code, dev, cnt = _io(self.device, b, x)
+        if self._n(cnt) != 1:
+            raise ValueError("eigsumr_accumulate takes one source")
         mu = self.mu if mu is None else mu
         h = ctypes.c_void_p(defl.h.value if defl is not None else None)
         info = (ovl_solve_info * 1)()
@@ -286,11 +322,17 @@ class Overlap:
             _check(st, self.h)
         if defl is None:
             defl = Deflation(self, h)
+        if st == OVL_ENOCONV and not allow_noconv:
+            # the space is kept (and refined) even when the solve itself fell short
+            raise OvlError(st, load().overlap_last_error(self.h).decode())
         return defl, info[0].as_dict()
 
     def force(self, phi, mu=None, tol=1e-10):
-        pp, code, dev, cnt = _spinor_arg(phi)
-        self._n(cnt)
+        pp, code, dev, cnt, di = _spinor_arg(phi)
+        if self._n(cnt) != 1:
+            raise ValueError("overlap_force takes one source phi")
+        if dev and self.device is not None and di != self.device:
+            raise ValueError("phi must be on cuda:%d, the context's device" % self.device)
         mu = self.mu if mu is None else mu
         G = np.zeros(self.V * 36 * 2)
         S = np.zeros(1)
@@ -321,6 +363,12 @@ class Overlap:
         t = [ctypes.c_double() for _ in range(3)]
         _check(load().ovl_wilson_tuning(self.h, int(prec), ctypes.byref(v), *[ctypes.byref(x) for x in t]), self.h)
         return (v.value,) + tuple(x.value for x in t)
+
+    def bench_fp32(self):
+        """Measured FP32 FMA instructions per second of the context's device."""
+        r = ctypes.c_double()
+        _check(load().ovl_bench_fp32(self.h, ctypes.byref(r)), self.h)
+        return r.value
 
     def bench_wilson(self, prec, n, iters):
         ms, by = ctypes.c_double(), ctypes.c_double()

@@ -848,8 +848,40 @@ extern "C" ovl_status ovl_bench_wilson(ovl_ctx* c, int prec, int n, int iters, d
   cudaEventDestroy(e1);
   OVL_TRY(check_launch(c, __func__));
   const double sb = prec == P16 ? 52 : spinor_site_bytes(prec);
-  const double lb = prec == P64E ? 1152 : prec == P64 ? 384 : prec == P32 ? 192 : 96;
+  const double lb = prec == P64E ? 576 : prec == P64 ? 384 : prec == P32 ? 192 : 96;   // algorithmic
   if (ms_per_launch) *ms_per_launch = ms / iters;
   if (bytes_per_launch) *bytes_per_launch = (double)c->V * (2.0 * sb * n + lb);
+  return OVL_OK;
+}
+
+// ---------------------------------------------------------------- FP32 issue probe
+namespace ovl {
+void launch_fma_probe(int nblocks, int iters, float* out, cudaStream_t st);
+}
+extern "C" ovl_status ovl_bench_fp32(ovl_ctx* c, double* fma_per_s) {
+  if (!c || !fma_per_s) return OVL_EINVAL;
+  int nsm = 0;
+  OVL_CUDA(c, cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, c->device));
+  const int nblocks = nsm * 8, iters = 4096;
+  float* d = nullptr;
+  OVL_CUDA(c, cudaMalloc((void**)&d, sizeof(float) * nblocks * 256));
+  cudaEvent_t e0, e1;
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  launch_fma_probe(nblocks, iters, d, c->st);
+  cudaEventRecord(e0, c->st);
+  const int reps = 20;
+  for (int r = 0; r < reps; ++r) launch_fma_probe(nblocks, iters, d, c->st);
+  cudaEventRecord(e1, c->st);
+  cudaError_t err = cudaEventSynchronize(e1);
+  float ms = 0.f;
+  cudaEventElapsedTime(&ms, e0, e1);
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  cudaFree(d);
+  if (err != cudaSuccess) return cuda_check(c, err, "ovl_bench_fp32");
+  OVL_TRY(check_launch(c, __func__));
+  // 8 independent FMA chains of `iters` steps per thread, 256 threads per block
+  *fma_per_s = (double)reps * nblocks * 256.0 * 8.0 * iters / (ms * 1e-3);
   return OVL_OK;
 }

@@ -411,4 +411,25 @@ void launch_combine(int pa, SpinorRef A, int na, const double* C, int py, Spinor
 #undef COMB
 }
 
+// ---------------------------------------------------------------- FP32 issue probe
+// Eight independent FMA chains per thread (enough to cover the FMA latency at full
+// occupancy), so that the measured rate is the FP32 pipes' instruction issue rate.
+__global__ void __launch_bounds__(256) fma_probe_kernel(int iters, float* out) {
+  float a[8];
+#pragma unroll
+  for (int k = 0; k < 8; ++k) a[k] = (float)(threadIdx.x + k) * 1e-3f;
+  const float b = 0.999f, cc = 1e-4f;
+  for (int i = 0; i < iters; ++i) {
+#pragma unroll
+    for (int k = 0; k < 8; ++k) a[k] = __fmaf_rn(a[k], b, cc);
+  }
+  float s = 0.f;
+#pragma unroll
+  for (int k = 0; k < 8; ++k) s += a[k];
+  out[blockIdx.x * blockDim.x + threadIdx.x] = s;
+}
+void launch_fma_probe(int nblocks, int iters, float* out, cudaStream_t st) {
+  fma_probe_kernel<<<nblocks, 256, 0, st>>>(iters, out);
+}
+
 }  // namespace ovl

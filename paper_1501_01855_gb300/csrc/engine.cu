@@ -408,7 +408,10 @@ static ovl_status sign_op_batch(ovl_ctx* c, int mode, const Field& v, int voff, 
   OVL_CUDA(c, cudaMemcpyAsync(c->dscal, c->hpin, sizeof(double) * ncopy, cudaMemcpyHostToDevice, c->st));
   const LinkRef L = links_of(c, PL);
   const int wcls = PL == P64E ? 8 : PL;  // profiler class of the Wilson launches
-  const double lbytes = (PL == P64E ? 1152.0 : PL == P64 ? 384.0 : PL == P32 ? 192.0 : 96.0) * V;
+  // algorithmic link bytes per site and launch: four 18-real FP64 links for the
+  // double-float kernel (its eight-slot field stores each link twice, forward and
+  // transposed, which is a layout choice, not work), four 12-real links otherwise
+  const double lbytes = (PL == P64E ? 576.0 : PL == P64 ? 384.0 : PL == P32 ? 192.0 : 96.0) * V;
   const double sbytes = (double)spinor_bytes(PP) * V, rbytes = (double)spinor_bytes(PR) * V;
   ProfPair pp;
 
@@ -420,7 +423,6 @@ static ovl_status sign_op_batch(ovl_ctx* c, int mode, const Field& v, int voff, 
   prof_end(c, &pp, 0.0);
   OVL_TRY(check_launch(c, __func__));
 
-  std::vector<int> done(n, 0);
   int* hdone = reinterpret_cast<int*>(c->hpin + 8192);
   int total = 0;
   int chunk = 8;
@@ -528,7 +530,23 @@ static ovl_status sign_op_batch(ovl_ctx* c, int mode, const Field& v, int voff, 
     stats->status = stt;
   }
   for (int j = 0; j < n; ++j) {
-    if (stt[j] == 2) return set_err(c, OVL_EBREAKDOWN, "multi-shift CG breakdown in the sign function");
+    if (stt[j] == 2) {
+      char m[160];
+      snprintf(m, sizeof(m), "multi-shift CG breakdown in the sign function (system %d, iteration %d)", j, it[j]);
+      return set_err(c, OVL_EBREAKDOWN, m);
+    }
+  }
+  // a system that reached the iteration limit has a sign less accurate than asked for
+  // (the pole stopping rule of Sec. 3 was not met): the caller has to know
+  for (int j = 0; j < n; ++j) {
+    if (stt[j] == 1) {
+      char m[200];
+      snprintf(m, sizeof(m),
+               "multi-shift CG stopped at the iteration limit (mscg_max = %d) before the sign accuracy "
+               "%.3e was met (system %d, %d iterations)",
+               c->P.mscg_max, eta[j], j, it[j]);
+      return set_err(c, OVL_ENOCONV, m);
+    }
   }
   return OVL_OK;
 }

@@ -14,6 +14,7 @@
 // individual x_i (they are stored; at the lattice sizes here they fit in HBM).
 // The outer-product kernel runs over all poles in one pass with an FP64
 // accumulator per link (compute in FP64, or FP32 with the mixed setting).
+#include <stdio.h>
 #include <string.h>
 
 #include <cmath>
@@ -183,6 +184,15 @@ static ovl_status shifted_solutions(ovl_ctx* c, const Field& v, Field& xs, doubl
     if (hd[0] || total > c->P.mscg_max + 16) break;
   }
   c->wcalls[P64] += 2 * total;
+  OVL_CUDA(c, cudaMemcpyAsync(hd, &c->ms[0].status, sizeof(int), cudaMemcpyDeviceToHost, c->st));
+  OVL_CUDA(c, cudaMemcpyAsync(hd + 1, &c->ms[0].iter, sizeof(int), cudaMemcpyDeviceToHost, c->st));
+  OVL_CUDA(c, cudaStreamSynchronize(c->st));
+  if (hd[0] != 0) {
+    char m[200];
+    snprintf(m, sizeof(m), "shifted solves of the gradient: multi-shift CG %s after %d iterations (tolerance %.3e)",
+             hd[0] == 2 ? "broke down" : "reached the iteration limit mscg_max", hd[1], tol);
+    return set_err(c, hd[0] == 2 ? OVL_EBREAKDOWN : OVL_ENOCONV, m);
+  }
   return OVL_OK;
 }
 

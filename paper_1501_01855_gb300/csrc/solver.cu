@@ -583,10 +583,15 @@ ovl_status gmresr_batch(ovl_ctx* c, int n, const std::vector<double>& mus, const
   OVL_TRY(norms_batch(c, b, boff, n, bn));
   rn = bn;
   const double eta_t = c->P.eta_precond > 0 ? c->P.eta_precond : std::cbrt(tol);
+  // The outer loop stops at half the requested tolerance: the recursive residual and the
+  // true one differ by the sign errors allowed in c = A u (below), and the reported true
+  // residual is itself measured with a sign of finite accuracy, so stopping at tol itself
+  // would leave the true residual at tol to within those errors, on either side.
+  const double tstop = 0.5 * tol;
   std::vector<char> active(n);
   std::vector<int> outer(n, 0), inner(n, 0), signs(n, 0);
   std::vector<long long> wcalls(n, 0);
-  for (int j = 0; j < n; ++j) active[j] = rn[j] > tol * bn[j];
+  for (int j = 0; j < n; ++j) active[j] = rn[j] > tstop * bn[j];
   for (int k = 0; k < kmax; ++k) {
     int nact = 0;
     for (int j = 0; j < n; ++j) nact += active[j];
@@ -632,7 +637,7 @@ ovl_status gmresr_batch(ovl_ctx* c, int n, const std::vector<double>& mus, const
       // Alg. 3 bounds ||A u - c|| relative to ||u||; through the update r -= alpha c that
       // error reaches r amplified by up to ||u|| / ||A u|| <= 1/mu (D^dag D >= mu^2), so
       // the factor mu/2 keeps the final true residual within tol
-      eta[j] = active[j] ? std::min(c->P.eta_floor, 0.5 * mus[j] * tol * bn[j] / std::max(rn[j], 1e-300))
+      eta[j] = active[j] ? std::min(c->P.eta_floor, 0.5 * mus[j] * tstop * bn[j] / std::max(rn[j], 1e-300))
                          : c->P.eta_floor;
       emin = std::min(emin, eta[j]);
     }
@@ -684,7 +689,7 @@ ovl_status gmresr_batch(ovl_ctx* c, int n, const std::vector<double>& mus, const
     for (int j = 0; j < n; ++j)
       if (active[j]) {
         outer[j] += 1;
-        if (rn[j] <= tol * bn[j]) active[j] = 0;
+        if (rn[j] <= tstop * bn[j]) active[j] = 0;
       }
     if (eig && eig->after_outer) OVL_TRY(eig->after_outer(c, eig->data, k));
   }

@@ -31,10 +31,10 @@ def test_config1_solve(mixed, solver, emul):
     info = c.solve(b, x, 1e-10)
     tr, err = _check(U, S, x, b, 0.05, 1e-10)
     print("mixed=%d solver=%d true residual %.3e, error %.3e, info %s" % (mixed, solver, tr, err, info[0]))
-    assert tr <= 1.5e-10
-    assert err <= 20 * 1.5e-10
+    assert tr <= 1e-10
+    assert err <= 20 * 1e-10
     assert info[0]["converged"] == 1
-    assert info[0]["true_residual"] <= 1.5e-10
+    assert info[0]["true_residual"] <= 1e-10
 
 
 def test_batched_sources_and_masses():
@@ -47,7 +47,7 @@ def test_batched_sources_and_masses():
     for k, mu in enumerate(mus):
         for j in range(2):
             tr, err = _check(U, S, x[k, j], b[j], mu, 1e-10)
-            assert tr <= 1.5e-10, (k, j, tr)
+            assert tr <= 1e-10, (k, j, tr)
     # lock-step batching gives the per-system answer
     x1 = np.zeros_like(b[1])
     c.solve(np.ascontiguousarray(b[1]), x1, 1e-10, mus=[0.1])

@@ -46,3 +46,23 @@ def test_library_rejects_bad_arguments():
         binding.ovl_zolotarev_coeffs(0, 0.1, 1.0)
     with pytest.raises(binding.OvlError):
         binding.ovl_zolotarev_coeffs(4, 1.0, 0.5)
+
+
+def test_binding_checks_output_buffers():
+    """The binding refuses an output that is smaller than the input, of another dtype or
+    on the other side of the bus, before any library call (so the library never writes
+    past the end of a caller buffer)."""
+    binding = _lib()
+    x = np.zeros((2, 2, 2, 2, 4, 3), dtype=np.complex128)
+    binding._io(None, x, np.zeros_like(x))
+    with pytest.raises(ValueError):
+        binding._io(None, x, np.zeros((1, 2, 2, 2, 4, 3), dtype=np.complex128))
+    with pytest.raises(ValueError):
+        binding._io(None, x, np.zeros_like(x, dtype=np.complex64))
+    ro = np.zeros_like(x)
+    ro.setflags(write=False)
+    with pytest.raises(ValueError):
+        binding._io(None, x, ro)
+    import torch
+    with pytest.raises(ValueError):
+        binding._io(None, torch.zeros((2, 3), dtype=torch.complex128), torch.zeros((2, 2), dtype=torch.complex128))
