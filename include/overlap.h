@@ -93,6 +93,17 @@ typedef struct {
   int    verify;        /* 1: after a solve, recompute ||b - D x|| / ||b|| with an FP64 sign at
                            eps_sign (one more sign application per system); 0: report the
                            GMRESR recursive residual. Default 1                                 */
+  int    sign_method;   /* how the Zolotarev sum (Sec. 3) is evaluated: 0 (default) Lanczos on
+                           K^2 with its basis stored in HBM (one vector per step; every pole's
+                           solution from a tridiagonal solve and one pass over the basis), when
+                           the basis of a batch fits in basis_gb (else as 1); 1 multi-shift CG
+                           (one search direction per pole, updated every step); 2 stored-basis
+                           Lanczos always (sub-batched to fit basis_gb)                        */
+  double basis_gb;      /* device memory for stored Lanczos bases, GB, default 96              */
+  int    lanczos_cap;   /* >0: at most this many basis vectors per Lanczos cycle (a full cycle
+                           restarts from its last vector, to which every pole's residual is
+                           parallel); 0 (default): sized from the steps this context has
+                           needed at that accuracy, else from the CG bound of the base shift */
   void*  stream;        /* cudaStream_t for all work; NULL = legacy default stream              */
 } ovl_params;
 

@@ -42,7 +42,9 @@ class ovl_params(ctypes.Structure):
                 ("delta_split", ctypes.c_double), ("c_spec", ctypes.c_double), ("bc_t", ctypes.c_int),
                 ("a_override", ctypes.c_double), ("b_override", ctypes.c_double), ("batch_max", ctypes.c_int), ("wilson_variant", ctypes.c_int),
                 ("use_graphs", ctypes.c_int),
-                ("verify", ctypes.c_int), ("stream", ctypes.c_void_p)]
+                ("verify", ctypes.c_int), ("sign_method", ctypes.c_int), ("basis_gb", ctypes.c_double),
+                ("lanczos_cap", ctypes.c_int),
+                ("stream", ctypes.c_void_p)]
 
 
 class ovl_solve_info(ctypes.Structure):

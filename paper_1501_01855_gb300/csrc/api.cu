@@ -46,6 +46,9 @@ extern "C" ovl_status ovl_params_default(ovl_params* p) {
   p->wilson_variant = -1;
   p->use_graphs = 1;
   p->verify = 1;
+  p->sign_method = 0;
+  p->basis_gb = 96.0;
+  p->lanczos_cap = 0;
   p->stream = nullptr;
   return OVL_OK;
 }
@@ -219,6 +222,10 @@ extern "C" void overlap_destroy(ovl_ctx* c) {
   if (c->dscal) cudaFree(c->dscal);
   if (c->dint) cudaFree(c->dint);
   if (c->ms) cudaFree(c->ms);
+  if (c->lz) cudaFree(c->lz);
+  if (c->lz_hist) cudaFree(c->lz_hist);
+  if (c->lz_Y) cudaFree(c->lz_Y);
+  if (c->lz_coefW) cudaFree(c->lz_coefW);
   if (c->dpoles) cudaFree(c->dpoles);
   if (c->dwork) cudaFree(c->dwork);
   if (c->hpin) cudaFreeHost(c->hpin);
@@ -259,6 +266,10 @@ static ovl_status create_impl(ovl_ctx* c, const int dims[4], const double* links
   if (!(m0 > 0 && m0 < 4)) return set_err(c, OVL_EINVAL, "m0 must lie in (0, 4)");
   if (!(mu >= 0 && mu < 1)) return set_err(c, OVL_EINVAL, "mu must lie in [0, 1)");
   if (n_poles < 1 || n_poles > NPMAX) return set_err(c, OVL_EINVAL, "n_poles must lie in 1..64");
+  if (c->P.sign_method < 0 || c->P.sign_method > 2) return set_err(c, OVL_EINVAL, "sign_method must be 0, 1 or 2");
+  if (!(c->P.basis_gb > 0)) c->P.basis_gb = 96.0;
+  if (c->P.lanczos_cap != 0 && (c->P.lanczos_cap < 4 || c->P.lanczos_cap > 1024))
+    return set_err(c, OVL_EINVAL, "lanczos_cap must be 0 or lie in 4..1024");
   if (c->P.batch_max < 1) c->P.batch_max = 1;
   if (c->P.batch_max > 256) c->P.batch_max = 256;
   c->m0 = m0;

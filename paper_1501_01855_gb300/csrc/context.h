@@ -75,6 +75,13 @@ struct ovl_ctx {
   int* dint = nullptr;           // per-rhs ints (device), 4096
   ovl::MsRhs* ms = nullptr;
   int ms_n = 0;
+  ovl::LzRhs* lz = nullptr;      // stored-basis Lanczos state per system
+  int lz_n = 0;
+  double* lz_hist = nullptr;     // alpha_j and beta_j histories, 2 * lz_n * lz_cap doubles
+  double* lz_Y = nullptr;        // per-pole tridiagonal solves, lz_n * npoles * 2 lz_cap doubles
+  double* lz_coefW = nullptr;    // coefficients of the stored vectors, lz_n * lz_cap doubles
+  int lz_cap = 0;
+  int lz_kmax[4][17] = {{0}};    // most Lanczos steps seen per sign mode and decade of eta
   double* hpin = nullptr;        // pinned host staging for scalars, 64 * 4096 doubles
   void* hstage = nullptr;        // pinned host staging for spinor copies
   size_t hstage_bytes = 0;
@@ -128,6 +135,7 @@ ovl_status get_field(ovl_ctx* c, const std::string& name, int prec, int n, Field
 void free_field(Field& f);
 ovl_status ensure_partials(ovl_ctx* c, int nrhs);
 ovl_status ensure_ms(ovl_ctx* c, int nrhs);
+ovl_status ensure_lz(ovl_ctx* c, int nrhs, int cap);
 ovl_status ensure_stage(ovl_ctx* c, size_t bytes);
 ovl_status ensure_work(ovl_ctx* c, size_t ndoubles);
 

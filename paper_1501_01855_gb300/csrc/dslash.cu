@@ -23,11 +23,14 @@
 //   MODE_OVL  out = c1 v + c2 (y - kappa hop y) = c1 v + c2 gamma5 K y, optionally times
 //             gamma5, with partial sums of (w, out): gamma5 eps(K) v and D(mu) v are
 //             this with y = sum_i omega_i (K^2 + sigma_i)^-1 v.
+// and two for the stored-basis Lanczos form of the same sum (lanczos.cu):
+//   MODE_LZK  t = (1 / n_j) K W_j with W_j the system's current basis slot, ||t||^2;
+//   MODE_LZL  W_{j+1} = K t - a W_j - b W_{j-1} (the three-term recurrence), ||W_{j+1}||^2.
 #include "kernels.h"
 
 namespace ovl {
 
-enum { MODE_K = 0, MODE_R = 1, MODE_OVL = 2 };
+enum { MODE_K = 0, MODE_R = 1, MODE_OVL = 2, MODE_LZK = 3, MODE_LZL = 4 };
 
 // Register cap per thread, by link precision. Uncapped, the compiler hoists all
 // neighbour loads and takes ~255 registers (8 warps per SM): the FP32/FP16 kernels
@@ -364,18 +367,60 @@ struct DArgs {
   const double* coef;
   int herm;
   int variant;   // 0: thread per site, 1: direction split, 2: 4D tiles
+  const LzRhs* lz;
 };
 
 // Epilogue shared by both kernel variants: acc holds the hop sum of site s; v gets this
 // thread's contributions to the NVRED partial sums (see the mode list at the top).
 template <int MODE, int PIN, int POUT, int PA1, int PA2, typename T>
-__device__ __forceinline__ void wilson_epilogue(const DArgs& a, int rhs, int s, cpx<T> acc[12],
+__device__ __forceinline__ void wilson_epilogue(const DArgs& a, int rhs, int fin, int s, cpx<T> acc[12],
                                                 typename RedT<T>::type v[NVRED]) {
   cpx<T> c[12];
-  load_spinor_as_ro<PIN, T>(a.in, rhs, s, c);
+  load_spinor_as_ro<PIN, T>(a.in, fin, s, c);
   const T kap = (T)a.kappa;
   const bool red = a.partials != nullptr;
-  if constexpr (MODE == MODE_K) {
+  if constexpr (MODE == MODE_LZK) {
+    // t = (1 / n_j) gamma5 (W_j - kappa hop W_j)
+    const T sc = (T)a.lz[rhs].inv_n;
+#pragma unroll
+    for (int k = 0; k < 12; ++k) {
+      cpx<T> o = c[k] - kap * acc[k];
+      if (k >= 6) o = -o;
+      acc[k] = sc * o;
+    }
+    store_spinor_as<POUT, T>(a.out, rhs, s, acc);
+    if (red) {
+      Acc<T> n0;
+#pragma unroll
+      for (int k = 0; k < 12; ++k) acc_norm(n0, acc[k]);
+      v[0] = n0.get();
+    }
+  } else if constexpr (MODE == MODE_LZL) {
+    // W_{j+1} = gamma5 (t - kappa hop t) - a W_j - b W_{j-1}
+    const LzRhs& L = a.lz[rhs];
+    const int j = L.j;
+    const T ca = (T)L.a, cb = (T)L.b;
+    cpx<T> w[12];
+    load_spinor_as<PA1, T>(a.aux1, j * a.nrhs + rhs, s, w);
+#pragma unroll
+    for (int k = 0; k < 12; ++k) {
+      cpx<T> o = c[k] - kap * acc[k];
+      if (k >= 6) o = -o;
+      acc[k] = o - ca * w[k];
+    }
+    if (j > 0) {
+      load_spinor_as<PA1, T>(a.aux1, (j - 1) * a.nrhs + rhs, s, w);
+#pragma unroll
+      for (int k = 0; k < 12; ++k) acc[k] = acc[k] - cb * w[k];
+    }
+    store_spinor_as<POUT, T>(a.out, (j + 1) * a.nrhs + rhs, s, acc);
+    if (red) {
+      Acc<T> n0;
+#pragma unroll
+      for (int k = 0; k < 12; ++k) acc_norm(n0, acc[k]);
+      v[0] = n0.get();
+    }
+  } else if constexpr (MODE == MODE_K) {
     // K in = gamma5 (in - kappa acc)
 #pragma unroll
     for (int k = 0; k < 12; ++k) {
@@ -523,12 +568,17 @@ __global__ void __launch_bounds__(256) __maxnreg__(MaxReg<PL>::v) wilson_kernel(
     if (live) site_coords(a.g, s, x);
   }
   if (live && a.ms != nullptr && (MODE == MODE_K || MODE == MODE_R)) live = !a.ms[rhs].done;
+  int fin = rhs;   // field index of the hop input (the basis slot in MODE_LZK)
+  if constexpr (MODE == MODE_LZK || MODE == MODE_LZL) {
+    if (live) live = !a.lz[rhs].done;
+    if (MODE == MODE_LZK && live) fin = a.lz[rhs].j * a.nrhs + rhs;
+  }
   using R = typename RedT<T>::type;
   R v[NVRED] = {R(0), R(0), R(0), R(0)};
   if (live) {
     cpx<T> acc[12];
-    hop<PIN, PL, T>(a.g, a.links, a.in, rhs, s, x, acc);
-    wilson_epilogue<MODE, PIN, POUT, PA1, PA2, T>(a, rhs, s, acc, v);
+    hop<PIN, PL, T>(a.g, a.links, a.in, fin, s, x, acc);
+    wilson_epilogue<MODE, PIN, POUT, PA1, PA2, T>(a, rhs, fin, s, acc, v);
   }
   if (a.partials != nullptr) {
     double tot[NVRED];
@@ -568,6 +618,11 @@ __global__ void __launch_bounds__(4 * BX) __maxnreg__(MaxReg<PL>::v) wilson_spli
   const int s = sb * BX + sl;
   bool live = s < a.g.V;
   if (live && a.ms != nullptr && (MODE == MODE_K || MODE == MODE_R)) live = !a.ms[rhs].done;
+  int fin = rhs;
+  if constexpr (MODE == MODE_LZK || MODE == MODE_LZL) {
+    if (live) live = !a.lz[rhs].done;
+    if (MODE == MODE_LZK && live) fin = a.lz[rhs].j * a.nrhs + rhs;
+  }
   cpx<T> acc[12];
 #pragma unroll
   for (int k = 0; k < 12; ++k) acc[k] = cmk(T(0), T(0));
@@ -575,10 +630,10 @@ __global__ void __launch_bounds__(4 * BX) __maxnreg__(MaxReg<PL>::v) wilson_spli
     int x[4];
     site_coords(a.g, s, x);
     const int sy = a.g.L[0], sz = sy * a.g.L[1], st = sz * a.g.L[2];
-    if (dir == 0) hop_dir<0, PIN, PL, T>(a.g, a.links, a.in, rhs, s, x, 1, acc);
-    else if (dir == 1) hop_dir<1, PIN, PL, T>(a.g, a.links, a.in, rhs, s, x, sy, acc);
-    else if (dir == 2) hop_dir<2, PIN, PL, T>(a.g, a.links, a.in, rhs, s, x, sz, acc);
-    else hop_dir<3, PIN, PL, T>(a.g, a.links, a.in, rhs, s, x, st, acc);
+    if (dir == 0) hop_dir<0, PIN, PL, T>(a.g, a.links, a.in, fin, s, x, 1, acc);
+    else if (dir == 1) hop_dir<1, PIN, PL, T>(a.g, a.links, a.in, fin, s, x, sy, acc);
+    else if (dir == 2) hop_dir<2, PIN, PL, T>(a.g, a.links, a.in, fin, s, x, sz, acc);
+    else hop_dir<3, PIN, PL, T>(a.g, a.links, a.in, fin, s, x, st, acc);
   }
   if (dir != 0) {
 #pragma unroll
@@ -590,7 +645,7 @@ __global__ void __launch_bounds__(4 * BX) __maxnreg__(MaxReg<PL>::v) wilson_spli
   if (dir == 0 && live) {
 #pragma unroll
     for (int k = 0; k < 12; ++k) acc[k] = acc[k] + part[0][sl][k] + part[1][sl][k] + part[2][sl][k];
-    wilson_epilogue<MODE, PIN, POUT, PA1, PA2, T>(a, rhs, s, acc, v);
+    wilson_epilogue<MODE, PIN, POUT, PA1, PA2, T>(a, rhs, fin, s, acc, v);
   }
   if (a.partials != nullptr) {
     double tot[NVRED];
@@ -641,6 +696,7 @@ static DArgs base_args(const Geom& g, double kappa, LinkRef links, int nrhs) {
   a.coef = nullptr;
   a.herm = 0;
   a.variant = links.variant;
+  a.lz = nullptr;
   return a;
 }
 
@@ -676,6 +732,35 @@ void launch_wilson_mscg_r(int pt, int plink, int pr, int pp, const Geom& g, doub
   else if (pt == P32 && plink == P32 && pr == P32 && pp == P32) run<MODE_R, P32, P32, P32, P32, P32>(a, st);
   else if (pt == P16 && plink == P16 && pr == P32 && pp == P16) run<MODE_R, P16, P16, P32, P16, P32>(a, st);
   else if (pt == P64E && plink == P64E && pr == P64E && pp == P64E) run<MODE_R, P64E, P64E, P64E, P64E, P64E>(a, st);
+  else OVL_BAD_COMBO();
+}
+
+void launch_wilson_lzK(int pw, int plink, int pt, const Geom& g, double kappa, LinkRef links, SpinorRef W,
+                       SpinorRef t, int nrhs, double* partials, const LzRhs* lz, cudaStream_t st) {
+  DArgs a = base_args(g, kappa, links, nrhs);
+  a.in = W;
+  a.out = t;
+  a.partials = partials;
+  a.lz = lz;
+  if (pw == P64 && plink == P64 && pt == P64) run<MODE_LZK, P64, P64, P64, P64, P64>(a, st);
+  else if (pw == P32 && plink == P32 && pt == P32) run<MODE_LZK, P32, P32, P32, P32, P32>(a, st);
+  else if (pw == P16 && plink == P16 && pt == P16) run<MODE_LZK, P16, P16, P16, P16, P16>(a, st);
+  else if (pw == P64E && plink == P64E && pt == P64E) run<MODE_LZK, P64E, P64E, P64E, P64E, P64E>(a, st);
+  else OVL_BAD_COMBO();
+}
+
+void launch_wilson_lzL(int pt, int plink, int pw, const Geom& g, double kappa, LinkRef links, SpinorRef t,
+                       SpinorRef W, int nrhs, double* partials, const LzRhs* lz, cudaStream_t st) {
+  DArgs a = base_args(g, kappa, links, nrhs);
+  a.in = t;
+  a.out = W;
+  a.aux1 = W;
+  a.partials = partials;
+  a.lz = lz;
+  if (pt == P64 && plink == P64 && pw == P64) run<MODE_LZL, P64, P64, P64, P64, P64>(a, st);
+  else if (pt == P32 && plink == P32 && pw == P32) run<MODE_LZL, P32, P32, P32, P32, P32>(a, st);
+  else if (pt == P16 && plink == P16 && pw == P16) run<MODE_LZL, P16, P16, P16, P16, P16>(a, st);
+  else if (pt == P64E && plink == P64E && pw == P64E) run<MODE_LZL, P64E, P64E, P64E, P64E, P64E>(a, st);
   else OVL_BAD_COMBO();
 }
 

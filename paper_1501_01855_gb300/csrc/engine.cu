@@ -109,6 +109,26 @@ ovl_status ensure_ms(ovl_ctx* c, int nrhs) {
   return OVL_OK;
 }
 
+ovl_status ensure_lz(ovl_ctx* c, int nrhs, int cap) {
+  if (nrhs <= c->lz_n && cap <= c->lz_cap) return OVL_OK;
+  const int n = std::max(nrhs, c->lz_n), k = std::max(cap, c->lz_cap);
+  cudaStreamSynchronize(c->st);
+  if (c->lz) cudaFree(c->lz);
+  if (c->lz_hist) cudaFree(c->lz_hist);
+  if (c->lz_Y) cudaFree(c->lz_Y);
+  if (c->lz_coefW) cudaFree(c->lz_coefW);
+  c->lz = nullptr;
+  c->lz_hist = c->lz_Y = c->lz_coefW = nullptr;
+  c->lz_n = c->lz_cap = 0;
+  OVL_CUDA(c, cudaMalloc((void**)&c->lz, sizeof(LzRhs) * n));
+  OVL_CUDA(c, cudaMalloc((void**)&c->lz_hist, sizeof(double) * 2 * (size_t)n * k));
+  OVL_CUDA(c, cudaMalloc((void**)&c->lz_Y, sizeof(double) * (size_t)n * c->npoles * 2 * k));
+  OVL_CUDA(c, cudaMalloc((void**)&c->lz_coefW, sizeof(double) * (size_t)n * k));
+  c->lz_n = n;
+  c->lz_cap = k;
+  return OVL_OK;
+}
+
 ovl_status ensure_stage(ovl_ctx* c, size_t bytes) {
   if (bytes <= c->hstage_bytes) return OVL_OK;
   if (c->hstage) cudaFreeHost(c->hstage);
@@ -297,6 +317,7 @@ int choose_mode(const ovl_ctx* c, double eta) {
 // are recorded on the context's private capture stream and instantiated once. At most
 // kMaxGraphs graphs are kept (least recently used dropped).
 static constexpr int kGraphIters = 8;
+static constexpr int kLzCapMax = 1024;   // basis slots per Lanczos cycle (coefficient buffers)
 static constexpr size_t kMaxGraphs = 16;
 template <typename F>
 static ovl_status ms_graph(ovl_ctx* c, const std::vector<unsigned long long>& key, cudaGraphExec_t* out, F capture) {
@@ -339,16 +360,65 @@ static ovl_status ms_graph(ovl_ctx* c, const std::vector<unsigned long long>& ke
 static ovl_status sign_op_batch(ovl_ctx* c, int mode, const Field& v, int voff, Field& out, int ooff, int n,
                                 const double* eta, double c1, double c2, const double* coef, int herm,
                                 const Field* dot_w, int woff, double* dots, SignStats* stats);
+static ovl_status sign_op_batch_lz(ovl_ctx* c, int mode, const Field& v, int voff, Field& out, int ooff, int n,
+                                   const double* eta, double c1, double c2, const double* coef, int herm,
+                                   const Field* dot_w, int woff, double* dots, SignStats* stats, int cap);
+
+// decade of a sign accuracy, the key of the step-count memory
+static int eta_decade(double e) {
+  const int d = (int)std::floor(-std::log10(std::max(e, 1e-16)));
+  return std::min(16, std::max(0, d));
+}
+
+// Basis slots for one stored-basis Lanczos cycle: the most steps this context has needed
+// at this mode and accuracy, else the CG bound 1/2 sqrt(kappa) ln(2 N_Z / eta) for the
+// base shift (kappa = (b^2 + sigma_0) / (a^2 + sigma_0)), with a quarter's margin.
+static int lz_cap_for(const ovl_ctx* c, int mode, double eta) {
+  if (c->P.lanczos_cap > 0) return c->P.lanczos_cap;
+  const double s0 = c->hpoles.sigma0;
+  const double kap = (c->zb * c->zb + s0) / (c->za * c->za + s0);
+  int k = c->lz_kmax[mode][eta_decade(eta)];
+  if (k <= 0) k = (int)std::ceil(0.5 * std::sqrt(kap) * std::log(2.0 * c->npoles / std::max(eta, 1e-16))) + 10;
+  k = (int)std::ceil(1.25 * k) + 8;
+  return std::max(16, std::min(std::min(k, c->P.mscg_max + 2), kLzCapMax));
+}
 
 // Systems per multi-shift solve are capped so that the pole vectors of one batch stay
 // within kPoleBytes (24 poles x 36 systems of 24^3 x 48 in double-float would be 110 GB);
-// larger requests run as consecutive sub-batches.
+// larger requests run as consecutive sub-batches. The stored-basis Lanczos form is
+// sub-batched so that cap basis vectors per system fit in params.basis_gb.
 static constexpr double kPoleBytes = 64e9;
 ovl_status sign_op(ovl_ctx* c, int mode, const Field& v, int voff, Field& out, int ooff, int n, const double* eta,
                    double c1, double c2, const double* coef, int herm, const Field* dot_w, int woff, double* dots,
                    SignStats* stats) {
   if (n <= 0) return OVL_OK;
   const int PP = mode == SIGN64 ? P64 : mode == SIGN32 ? P32 : mode == SIGN16 ? P16 : P64E;
+  double emin = 1e300;
+  for (int j = 0; j < n; ++j) emin = std::min(emin, eta[j] > 0 ? eta[j] : c->eps_sign);
+  if (!c->exact_rational) emin = std::max(emin, c->delta);
+  const int cap = lz_cap_for(c, mode, emin);
+  const double per_lz = (double)cap * c->V * (spinor_bytes(PP) + (PP == P16 ? 4.0 : 0.0));
+  const int n_fit = (int)std::min(1e9, c->P.basis_gb * 1e9 / per_lz);
+  const bool use_lz = c->P.sign_method == 2 || (c->P.sign_method == 0 && n_fit >= std::min(n, c->P.batch_max));
+  if (use_lz) {
+    const int nb = std::max(1, std::min(c->P.batch_max, n_fit));
+    if (stats) {
+      stats->iters.clear();
+      stats->status.clear();
+    }
+    for (int j0 = 0; j0 < n; j0 += nb) {
+      const int m = std::min(nb, n - j0);
+      SignStats sub;
+      OVL_TRY(sign_op_batch_lz(c, mode, v, voff + j0, out, ooff + j0, m, eta + j0, c1, c2,
+                               coef ? coef + 2 * j0 : nullptr, herm, dot_w, woff + j0, dots ? dots + 4 * j0 : nullptr,
+                               stats ? &sub : nullptr, cap));
+      if (stats) {
+        stats->iters.insert(stats->iters.end(), sub.iters.begin(), sub.iters.end());
+        stats->status.insert(stats->status.end(), sub.status.begin(), sub.status.end());
+      }
+    }
+    return OVL_OK;
+  }
   const double per = (double)c->npoles * c->V * spinor_bytes(PP);
   int nb = std::max(1, std::min(c->P.batch_max, (int)(kPoleBytes / per)));
   if (n <= nb) return sign_op_batch(c, mode, v, voff, out, ooff, n, eta, c1, c2, coef, herm, dot_w, woff, dots, stats);
@@ -364,6 +434,216 @@ ovl_status sign_op(ovl_ctx* c, int mode, const Field& v, int voff, Field& out, i
     if (stats) {
       stats->iters.insert(stats->iters.end(), sub.iters.begin(), sub.iters.end());
       stats->status.insert(stats->status.end(), sub.status.begin(), sub.status.end());
+    }
+  }
+  return OVL_OK;
+}
+
+// Per-system sign accuracies to the device (c->dscal), with the stopping-rule convention
+// of the multi-shift CG: never past Delta (unless the rational itself is differentiated);
+// positive, one error budget shared by the poles; negative, an even share per pole (the
+// relaxed signs of relCG: spectrally preconditioned CGNE at mu = 0.01 lost convergence when
+// its signs came close to eta_j). Returns the pointers of eta and of the (c1, c2) pairs.
+static ovl_status upload_eta_coef(ovl_ctx* c, int n, const double* eta, const double* coef, double** d_eta,
+                                  double** d_coef) {
+  *d_eta = c->dscal;
+  *d_coef = c->dscal + 4096;
+  for (int j = 0; j < n; ++j) {
+    double e = eta[j] > 0 ? eta[j] : c->eps_sign;
+    if (e < c->delta && !c->exact_rational) e = c->delta;
+    const bool shared = e < 1e-6 || c->P.solver != OVL_SOLVER_CG;
+    c->hpin[j] = shared ? e : -e;
+  }
+  int ncopy = n;
+  if (coef) {
+    for (int j = 0; j < 2 * n; ++j) c->hpin[4096 + j] = coef[j];
+    ncopy = 4096 + 2 * n;
+  }
+  OVL_CUDA(c, cudaMemcpyAsync(c->dscal, c->hpin, sizeof(double) * ncopy, cudaMemcpyHostToDevice, c->st));
+  return OVL_OK;
+}
+
+// One batch of the sign function by stored-basis Lanczos (lanczos.cu): cycles of at most
+// cap steps, each step the two Wilson launches (MODE_LZK, MODE_LZL) and two one-block
+// scalar kernels, run as cached CUDA graphs of kGraphIters steps without profiling;
+// then the per-pole tridiagonal solves, one pass over the stored basis, and the final
+// Wilson application with the overlap / sign epilogue.
+static ovl_status sign_op_batch_lz(ovl_ctx* c, int mode, const Field& v, int voff, Field& out, int ooff, int n,
+                                   const double* eta, double c1, double c2, const double* coef, int herm,
+                                   const Field* dot_w, int woff, double* dots, SignStats* stats, int cap) {
+  const int PL = mode == SIGN64 ? P64 : mode == SIGN32 ? P32 : mode == SIGN16 ? P16 : P64E;
+  const int PR = mode == SIGN64 ? P64 : mode == SIGN64E ? P64E : P32;   // y
+  const int PB = PL;                                                      // basis and t
+  const int V = c->V;
+  const std::string tag = std::to_string(mode);
+  Field *W, *t, *y;
+  OVL_TRY(get_field(c, "lz_W" + tag, PB, cap * n, &W));
+  OVL_TRY(get_field(c, "lz_t" + tag, PB, n, &t));
+  OVL_TRY(get_field(c, "lz_y" + tag, PR, n, &y));
+  OVL_TRY(ensure_partials(c, n));
+  OVL_TRY(ensure_lz(c, n, cap));
+  const Shape sh = make_shape(V, n);
+  double *d_eta, *d_coef;
+  OVL_TRY(upload_eta_coef(c, n, eta, coef, &d_eta, &d_coef));
+  const LinkRef L = links_of(c, PL);
+  const int wcls = PL == P64E ? 8 : PL;
+  const double lbytes = (PL == P64E ? 576.0 : PL == P64 ? 384.0 : PL == P32 ? 192.0 : 96.0) * V;
+  const double sbytes = (double)spinor_bytes(PB) * V, rbytes = (double)spinor_bytes(PR) * V;
+  double* ahist = c->lz_hist;
+  double* bhist = c->lz_hist + (size_t)c->lz_n * c->lz_cap;
+  const int hcap = c->lz_cap;   // row length of the histories and coefficient buffers
+  ProfPair pp;
+
+  prof_begin(c, 4, &pp);
+  launch_lz_init(v.prec, PB, PR, v.ref(voff), W->ref(), y->ref(), n, V, c->partials, c->st);
+  prof_end(c, &pp, (double)n * V * (spinor_bytes(v.prec) + spinor_bytes(PB) + spinor_bytes(PR)));
+  prof_begin(c, 5, &pp);
+  launch_lz_start(c->lz, c->partials, sh.nsb, n, c->dpoles, d_eta, c->P.mscg_max, cap, 1, c->st);
+  prof_end(c, &pp, 0.0);
+  OVL_TRY(check_launch(c, __func__));
+
+  cudaGraphExec_t gexec = nullptr;
+  if (!c->prof.on && c->P.use_graphs) {
+    const std::vector<unsigned long long> key = {
+        1000ull + (unsigned long long)PB, (unsigned long long)PL, (unsigned long long)n, (unsigned long long)hcap,
+        (unsigned long long)(uintptr_t)W->data, (unsigned long long)(uintptr_t)t->data,
+        (unsigned long long)(uintptr_t)c->partials, (unsigned long long)(uintptr_t)c->lz,
+        (unsigned long long)(uintptr_t)c->lz_hist, (unsigned long long)(uintptr_t)L.data,
+        (unsigned long long)L.variant};
+    OVL_TRY(ms_graph(c, key, &gexec, [&](cudaStream_t cs) {
+      for (int k = 0; k < kGraphIters; ++k) {
+        launch_wilson_lzK(PB, PL, PB, c->g, c->kappa, L, W->ref(), t->ref(), n, c->partials, c->lz, cs);
+        launch_lz_scalar1(c->lz, c->partials, sh.nsb, n, ahist, hcap, cs);
+        launch_wilson_lzL(PB, PL, PB, c->g, c->kappa, L, t->ref(), W->ref(), n, c->partials, c->lz, cs);
+        launch_lz_scalar2(c->lz, c->partials, sh.nsb, n, bhist, hcap, c->dpoles, cs);
+      }
+    }));
+  }
+  int* hflags = reinterpret_cast<int*>(c->hpin + 8192);
+  int total = 0;
+  long long live = 0, wreads = 0;
+  int itmax = 0;
+  double comb_bytes = 0.0;
+  std::vector<int> it(n, 0), stt(n, 0);
+  for (int cycle = 0;; ++cycle) {
+    int chunk = 8;
+    while (true) {
+      if (gexec) {
+        for (int k = 0; k < chunk; k += kGraphIters) OVL_CUDA(c, cudaGraphLaunch(gexec, c->st));
+      } else {
+        for (int k = 0; k < chunk; ++k) {
+          prof_begin(c, wcls, &pp);
+          launch_wilson_lzK(PB, PL, PB, c->g, c->kappa, L, W->ref(), t->ref(), n, c->partials, c->lz, c->st);
+          prof_end(c, &pp, 0.0);
+          prof_begin(c, 5, &pp);
+          launch_lz_scalar1(c->lz, c->partials, sh.nsb, n, ahist, hcap, c->st);
+          prof_end(c, &pp, 0.0);
+          prof_begin(c, wcls, &pp);
+          launch_wilson_lzL(PB, PL, PB, c->g, c->kappa, L, t->ref(), W->ref(), n, c->partials, c->lz, c->st);
+          prof_end(c, &pp, 0.0);
+          prof_begin(c, 5, &pp);
+          launch_lz_scalar2(c->lz, c->partials, sh.nsb, n, bhist, hcap, c->dpoles, c->st);
+          prof_end(c, &pp, 0.0);
+        }
+      }
+      total += chunk;
+      OVL_TRY(check_launch(c, __func__));
+      OVL_CUDA(c, cudaMemcpy2DAsync(hflags, sizeof(int), &c->lz[0].done, sizeof(LzRhs), sizeof(int), n,
+                                    cudaMemcpyDeviceToHost, c->st));
+      OVL_CUDA(c, cudaStreamSynchronize(c->st));
+      bool all = true;
+      for (int j = 0; j < n; ++j) all = all && hflags[j];
+      if (all) break;
+      if (total > c->P.mscg_max + 16 * (cycle + 1)) break;
+      chunk = std::min(32, chunk * 2);
+    }
+    // this cycle's part of y
+    prof_begin(c, 5, &pp);
+    launch_lz_coef(c->lz, ahist, bhist, hcap, c->dpoles, c->lz_Y, c->lz_coefW, n, c->st);
+    prof_end(c, &pp, 0.0);
+    // steps of this cycle per system (the basis vectors the combine reads)
+    OVL_CUDA(c, cudaMemcpy2DAsync(hflags, sizeof(int), &c->lz[0].j, sizeof(LzRhs), sizeof(int), n,
+                                  cudaMemcpyDeviceToHost, c->st));
+    OVL_CUDA(c, cudaStreamSynchronize(c->st));
+    long long kk = 0;
+    for (int j = 0; j < n; ++j) kk += hflags[j];
+    const double cb = (double)kk * sbytes + (double)n * 2.0 * rbytes;
+    comb_bytes += cb;
+    prof_begin(c, 3, &pp);
+    launch_lz_combine(PB, PR, W->ref(), y->ref(), c->lz_coefW, c->lz, hcap, n, V, c->st);
+    prof_end(c, &pp, cb);
+    OVL_TRY(check_launch(c, __func__));
+    // cycles that filled up continue from their last basis vector
+    OVL_CUDA(c, cudaMemcpy2DAsync(hflags, sizeof(int), &c->lz[0].status, sizeof(LzRhs), sizeof(int), n,
+                                  cudaMemcpyDeviceToHost, c->st));
+    OVL_CUDA(c, cudaMemcpy2DAsync(hflags + 4096, sizeof(int), &c->lz[0].finished, sizeof(LzRhs), sizeof(int), n,
+                                  cudaMemcpyDeviceToHost, c->st));
+    OVL_CUDA(c, cudaStreamSynchronize(c->st));
+    bool more = false;
+    for (int j = 0; j < n; ++j) more = more || (hflags[j] == 3 && !hflags[4096 + j]);
+    if (!more) break;
+    prof_begin(c, 4, &pp);
+    launch_lz_restart(PB, W->ref(), c->lz, n, V, c->partials, c->st);
+    prof_end(c, &pp, 2.0 * n * sbytes);
+    launch_lz_start(c->lz, c->partials, sh.nsb, n, c->dpoles, d_eta, c->P.mscg_max, cap, 0, c->st);
+    OVL_TRY(check_launch(c, __func__));
+  }
+  // final Wilson application with the overlap / sign epilogue
+  double* d_part = dot_w ? c->partials : nullptr;
+  prof_begin(c, wcls, &pp);
+  launch_wilson_ovl(PR, PL, out.prec, c->g, c->kappa, L, y->ref(), v.ref(voff), out.ref(ooff),
+                    dot_w ? dot_w->ref(woff) : SpinorRef{nullptr, nullptr, V}, n, c1, c2, coef ? d_coef : nullptr,
+                    herm, d_part, c->st);
+  prof_end(c, &pp, (double)n * V * (spinor_bytes(PR) + 2.0 * spinor_bytes(out.prec)) + lbytes);
+  OVL_TRY(check_launch(c, __func__));
+  if (dot_w) OVL_TRY(reduce_to_host_nv(c, sh.nsb, n, dots, 4));
+  long long* hll = reinterpret_cast<long long*>(c->hpin + 12288);
+  OVL_CUDA(c, cudaMemcpy2DAsync(hflags, sizeof(int), &c->lz[0].total, sizeof(LzRhs), sizeof(int), n,
+                                cudaMemcpyDeviceToHost, c->st));
+  OVL_CUDA(c, cudaMemcpy2DAsync(hflags + 4096, sizeof(int), &c->lz[0].status, sizeof(LzRhs), sizeof(int), n,
+                                cudaMemcpyDeviceToHost, c->st));
+  OVL_CUDA(c, cudaMemcpy2DAsync(hll, sizeof(long long), &c->lz[0].w_reads, sizeof(LzRhs), sizeof(long long), n,
+                                cudaMemcpyDeviceToHost, c->st));
+  OVL_CUDA(c, cudaStreamSynchronize(c->st));
+  for (int j = 0; j < n; ++j) {
+    it[j] = hflags[j];
+    stt[j] = hflags[4096 + j];
+    live += it[j];
+    wreads += hll[j];
+    itmax = std::max(itmax, it[j]);
+  }
+  c->wcalls[PL] += 2 * live + n;
+  double emin = 1e300;
+  for (int j = 0; j < n; ++j) emin = std::min(emin, eta[j] > 0 ? eta[j] : c->eps_sign);
+  if (!c->exact_rational) emin = std::max(emin, c->delta);
+  int& km = c->lz_kmax[mode][eta_decade(emin)];
+  km = std::max(km, itmax);
+  if (c->prof.on) {
+    // algorithmic bytes: the K mode reads W_j and writes t, the L mode reads t and W_j
+    // (and W_{j-1} after the first step) and writes W_{j+1}; links once per launch
+    c->prof.bytes[wcls] += (double)live * 4.0 * sbytes + (double)wreads * sbytes + 2.0 * lbytes * itmax;
+    c->prof.units[wcls] += (2.0 * (double)live + n) * V;
+    c->prof.units[3] += comb_bytes / std::max(1.0, sbytes) * V;
+  }
+  if (stats) {
+    stats->iters = it;
+    stats->status = stt;
+  }
+  for (int j = 0; j < n; ++j) {
+    if (stt[j] == 2) {
+      char m[160];
+      snprintf(m, sizeof(m), "Lanczos breakdown in the sign function (system %d, step %d)", j, it[j]);
+      return set_err(c, OVL_EBREAKDOWN, m);
+    }
+  }
+  for (int j = 0; j < n; ++j) {
+    if (stt[j] == 1) {
+      char m[200];
+      snprintf(m, sizeof(m),
+               "Lanczos sign stopped at the iteration limit (mscg_max = %d) before the sign accuracy %.3e was met "
+               "(system %d, %d steps)",
+               c->P.mscg_max, eta[j], j, it[j]);
+      return set_err(c, OVL_ENOCONV, m);
     }
   }
   return OVL_OK;
@@ -387,25 +667,8 @@ static ovl_status sign_op_batch(ovl_ctx* c, int mode, const Field& v, int voff, 
   OVL_TRY(ensure_ms(c, n));
   const Shape sh = make_shape(V, n);
   // per-system eta and (c1, c2) to the device
-  double* d_eta = c->dscal;
-  double* d_coef = c->dscal + 4096;
-  for (int j = 0; j < n; ++j) {
-    double e = eta[j] > 0 ? eta[j] : c->eps_sign;
-    // the sign is never more accurate than Delta, so no pole is solved past it, except
-    // when the rational itself is being differentiated (gauge-link gradient)
-    if (e < c->delta && !c->exact_rational) e = c->delta;
-    // stopping rule (see ms_scalar2): one error budget shared by the poles, except for the
-    // relaxed signs of relCG (spectrally preconditioned CGNE lost convergence at mu = 0.01
-    // when its signs came close to eta_j), which keep an even share per pole (negative)
-    const bool shared = e < 1e-6 || c->P.solver != OVL_SOLVER_CG;
-    c->hpin[j] = shared ? e : -e;
-  }
-  int ncopy = n;
-  if (coef) {
-    for (int j = 0; j < 2 * n; ++j) c->hpin[4096 + j] = coef[j];
-    ncopy = 4096 + 2 * n;
-  }
-  OVL_CUDA(c, cudaMemcpyAsync(c->dscal, c->hpin, sizeof(double) * ncopy, cudaMemcpyHostToDevice, c->st));
+  double *d_eta, *d_coef;
+  OVL_TRY(upload_eta_coef(c, n, eta, coef, &d_eta, &d_coef));
   const LinkRef L = links_of(c, PL);
   const int wcls = PL == P64E ? 8 : PL;  // profiler class of the Wilson launches
   // algorithmic link bytes per site and launch: four 18-real FP64 links for the

@@ -47,6 +47,35 @@ struct MsRhs {
   double coef_y[NPMAX], coef_r[NPMAX], coef_p[NPMAX], coef_a[NPMAX];
 };
 
+// Per-system state of the stored-basis Lanczos evaluation of the Zolotarev sum (Sec. 3),
+// device resident. The Krylov basis of K^2 is kept in HBM (unnormalised vectors W_l,
+// v_l = W_l / n_l), so that every pole's Galerkin solution comes from its own small
+// tridiagonal solve and one combination of the stored vectors, with no per-pole vector
+// traffic. One cycle holds at most `cap` basis vectors; a cycle that fills up restarts
+// from the last vector, to which every pole's residual is parallel.
+struct LzRhs {
+  double vnorm;        // n_0 = ||W_0|| of this cycle
+  double inv_n;        // 1 / n_j: K-mode scale of the current basis vector
+  double inv_nprev;    // 1 / n_{j-1}
+  double a, b;         // L-mode coefficients alpha_j / n_j and beta_{j-1} / n_{j-1}
+  double alpha;        // alpha_j = (v_j, K^2 v_j)
+  double beta_prev;    // beta_{j-1}
+  double thr;          // error budget eta ||v|| of the caller's vector
+  double err;          // current error bound sum_i |w_i| g_i rho_i
+  int j;               // basis vectors completed in this cycle (next K-mode input W_j)
+  int done;            // 1: this cycle has stopped
+  int status;          // 0 converged, 1 iteration limit, 2 breakdown, 3 cycle full (restart)
+  int total;           // iterations over all cycles
+  int maxit, cap;      // iteration limit, basis slots per cycle
+  int finished;        // 1: no more cycles for this system
+  int cycles;
+  int even;            // 1: stop when every pole is within thr / N_Z (relaxed signs of relCG)
+  long long w_reads;   // basis vector passes of the L mode (bytes accounting)
+  double w[NPMAX];     // pole weights of this cycle (omega_i in the first)
+  double d[NPMAX];     // LDL^T pivots of T_j + sigma_i
+  double rho[NPMAX];   // residual norms of the shifted Galerkin solutions
+};
+
 // Pole data of one context, device resident.
 struct Poles {
   int n;
@@ -84,6 +113,36 @@ void launch_wilson_mscg_r(int pt, int plink, int pr, int pp, const Geom& g, doub
 void launch_wilson_ovl(int py, int plink, int pv, const Geom& g, double kappa, LinkRef links, SpinorRef y,
                        SpinorRef v, SpinorRef out, SpinorRef w, int nrhs, double c1, double c2,
                        const double* coef, int herm, double* partials, cudaStream_t st);
+
+// Stored-basis Lanczos, the two Wilson launches of one iteration. The basis W is a batch
+// of cap * nrhs fields, field l * nrhs + rhs holding W_l of system rhs; lz[rhs].j selects
+// the slot, so that one captured graph serves every iteration.
+//   K mode: t = (1 / n_j) K W_j, partials {||t||^2} (alpha_j = ||K v_j||^2);
+//   L mode: W_{j+1} = K t - a W_j - b W_{j-1}, partials {||W_{j+1}||^2}.
+void launch_wilson_lzK(int pw, int plink, int pt, const Geom& g, double kappa, LinkRef links, SpinorRef W,
+                       SpinorRef t, int nrhs, double* partials, const LzRhs* lz, cudaStream_t st);
+void launch_wilson_lzL(int pt, int plink, int pw, const Geom& g, double kappa, LinkRef links, SpinorRef t,
+                       SpinorRef W, int nrhs, double* partials, const LzRhs* lz, cudaStream_t st);
+// W_0 = v (precision conversion), y = 0, partials {||W_0||^2}
+void launch_lz_init(int pv, int pw, int py, SpinorRef v, SpinorRef W, SpinorRef y, int nrhs, int V,
+                    double* partials, cudaStream_t st);
+// start a cycle from the norm partials of W_0; first = 1: weights omega_i, budget eta ||W_0||
+void launch_lz_start(LzRhs* lz, const double* partials, int nsb, int nrhs, const Poles* poles,
+                     const double* eta, int maxit, int cap, int first, cudaStream_t st);
+void launch_lz_scalar1(LzRhs* lz, const double* partials, int nsb, int nrhs, double* ahist, int cap,
+                       cudaStream_t st);
+void launch_lz_scalar2(LzRhs* lz, const double* partials, int nsb, int nrhs, double* bhist, int cap,
+                       const Poles* poles, cudaStream_t st);
+// coefficients of the stored vectors in y = sum_i w_i x_i (per system, cap doubles) from
+// the tridiagonal solves; Y is scratch of nrhs * npoles * 2 cap doubles. For a system whose
+// cycle filled up, the weights of the next cycle are set too.
+void launch_lz_coef(LzRhs* lz, const double* ahist, const double* bhist, int cap, const Poles* poles, double* Y,
+                    double* coefW, int nrhs, cudaStream_t st);
+// y += sum_l coefW[l] W_l for every system with basis vectors this cycle
+void launch_lz_combine(int pw, int py, SpinorRef W, SpinorRef y, const double* coefW, const LzRhs* lz, int cap,
+                       int nrhs, int V, cudaStream_t st);
+// systems whose cycle filled up: W_0 = W_j, partials {||W_0||^2} (others zero)
+void launch_lz_restart(int pw, SpinorRef W, const LzRhs* lz, int nrhs, int V, double* partials, cudaStream_t st);
 
 // ---------------------------------------------------------------- multi-shift CG
 void launch_ms_init(int pv, int pr, int pp, SpinorRef v, SpinorRef r, SpinorRef pbase, SpinorRef y,

@@ -1,8 +1,9 @@
 """The benchmarked calls against the oracle at sizes the oracle finishes in seconds.
 
 * The overlap apply exactly as bench.py issues it (16 Gaussian vectors in one call,
-  20 Zolotarev poles, eta = 1e-10, double-float sign, cached multi-shift graphs,
-  autotuned Wilson launch shape), on 8^4 and 8^3 x 16, compared element by element with
+  20 Zolotarev poles, eta = 1e-10, double-float stored-basis Lanczos sign, cached step
+  graphs, autotuned Wilson launch shape), on 8^4 and 8^3 x 16 (and the multi-shift CG form
+  on 8^4), compared element by element with
   the oracle's per-pole CG (its own Zolotarev coefficients for the same [a, b]) on
   vectors 0, 7 and 15; every system of the batch is independent arithmetic, which
   test_sign_sub_batches_match_one_batch pins bit for bit.
@@ -32,14 +33,16 @@ def _rel(a, b):
     return float(np.linalg.norm(np.ravel(a - b)) / np.linalg.norm(np.ravel(b)))
 
 
-@pytest.mark.parametrize("dims", [(8, 8, 8, 8), (8, 8, 8, 16)])
-def test_bench_apply_matches_oracle(dims):
+@pytest.mark.parametrize("dims,method", [((8, 8, 8, 8), 0), ((8, 8, 8, 16), 0), ((8, 8, 8, 8), 1)])
+def test_bench_apply_matches_oracle(dims, method):
+    """method 0: the default stored-basis Lanczos sign (the benchmarked path); 1: the
+    multi-shift CG form."""
     import torch
     Bn = lib()
     mu, npoles, eta = 0.05, 20, 1e-10
     U = synth.gauge_links(dims, 0.3, 1002)
     vecs = synth.gaussian_source(dims, 2002, nvec=16)
-    c = ctx(dims, U, mu=mu, n_poles=npoles, eps=1e-10, a=A, b=B)   # graphs on, autotuned shape
+    c = ctx(dims, U, mu=mu, n_poles=npoles, eps=1e-10, a=A, b=B, sign_method=method)   # graphs on, autotuned shape
     dv = torch.from_numpy(vecs).cuda()
     dout = torch.empty_like(dv)
     c.apply(dv, dout, eta=eta, prec=Bn.OVL_PREC_F64E)
@@ -52,7 +55,7 @@ def test_bench_apply_matches_oracle(dims):
     for k, j in enumerate(pick):
         err = _rel(got[j], ref[k])
         pointwise = np.abs(got[j] - ref[k]).max() / np.abs(ref[k]).max()
-        print("%s vector %d: relative error %.3e, max pointwise %.3e" % (dims, j, err, pointwise))
+        print("%s method %d vector %d: relative error %.3e, max pointwise %.3e" % (dims, method, j, err, pointwise))
         assert err <= 1e-9
         assert pointwise <= 1e-9
 

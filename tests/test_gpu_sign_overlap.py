@@ -16,11 +16,13 @@ def _ab(w):
     return 0.95 * np.min(np.abs(w)), 1.05 * np.max(np.abs(w))
 
 
-@pytest.mark.parametrize("prec", [0, 3])
-def test_sign_fp64_matches_per_pole_oracle(prec):
+@pytest.mark.parametrize("prec,method,cap", [(0, 0, 0), (3, 0, 0), (0, 1, 0), (3, 1, 0), (3, 2, 20), (0, 2, 9)])
+def test_sign_fp64_matches_per_pole_oracle(prec, method, cap):
+    """method 0: stored-basis Lanczos (cap 0: one cycle), 1: multi-shift CG, 2: Lanczos
+    restarted every cap steps (several cycles)."""
     U, Kd, S, w = dense_4444()
     a, b = _ab(w)
-    c = ctx((4, 4, 4, 4), U, a=a, b=b, n_poles=16)
+    c = ctx((4, 4, 4, 4), U, a=a, b=b, n_poles=16, sign_method=method, lanczos_cap=cap)
     om, sg, de = zo.zolotarev(16, a, b)
     v = synth.gaussian_source((4, 4, 4, 4), 2001, nvec=2)
     out = np.zeros_like(v)
@@ -33,17 +35,18 @@ def test_sign_fp64_matches_per_pole_oracle(prec):
         assert rel(out[j], exact) <= 2e-10
 
 
+@pytest.mark.parametrize("method", [0, 1])
 @pytest.mark.parametrize("prec,eta,bound", [(1, 1e-5, 2e-5), (2, 1e-2, 2e-2), (0, 1e-6, 2e-6)])
-def test_sign_relaxed_accuracy(prec, eta, bound):
+def test_sign_relaxed_accuracy(prec, eta, bound, method):
     U, Kd, S, w = dense_4444()
     a, b = _ab(w)
-    c = ctx((4, 4, 4, 4), U, a=a, b=b, n_poles=16)
+    c = ctx((4, 4, 4, 4), U, a=a, b=b, n_poles=16, sign_method=method)
     v = synth.gaussian_source((4, 4, 4, 4), 7)
     out = np.zeros_like(v)
     c.sign_apply(v, out, eta=eta, prec=prec)
     exact = (S @ v.ravel()).reshape(v.shape)
     err = rel(out, exact)
-    print("sign prec=%d eta=%g error=%.3e" % (prec, eta, err))
+    print("sign prec=%d eta=%g method=%d error=%.3e" % (prec, eta, method, err))
     assert err <= bound
 
 
