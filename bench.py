@@ -65,7 +65,7 @@ DF64_FP32_OPS_PER_SITE = 8 * (12 * 8 + 12 * (4 + 5 * 12) + 24 * 8) + 24 * (7 + 1
 # DRAM bytes (read + write) per launch of the double-float Wilson kernel in this step,
 # from an ncu capture of this command (the summary under profiles/ gives it); None
 # until captured for the current kernel.
-TRAFFIC_WILSON_DF64 = 1.502e9
+TRAFFIC_WILSON_DF64 = None
 # Algorithmic bytes of one Wilson launch, per site: every system reads its input spinor
 # and writes its output (K mode) or also reads p and r and writes r (r-update mode); the
 # four 18-real FP64 links of the site (576 B) are read once per launch.

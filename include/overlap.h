@@ -87,7 +87,9 @@ typedef struct {
   int    batch_max;     /* systems advanced together in one lock-step batch, default 36         */
   int    wilson_variant;/* Wilson-kernel launch shape: -1 autotune at create (default), 0 one
                            thread per site, 1 four threads per site (one per direction), 2 one
-                           thread per site on 8x4x4x2 tiles (needs extents divisible by those) */
+                           thread per site on 8x4x4x2 tiles (needs extents divisible by those),
+                           3 two threads per site, one per half spinor (double-float only; the
+                           other precisions use 0)                                           */
   int    use_graphs;    /* 1 (default): run the multi-shift CG iterations as cached CUDA graphs
                            (not while profiling); 0: launch every kernel on the stream        */
   int    verify;        /* 1: after a solve, recompute ||b - D x|| / ||b|| with an FP64 sign at
@@ -289,12 +291,13 @@ ovl_status ovl_bench_wilson(ovl_ctx* ctx, int prec, int n, int iters, double* ms
 ovl_status ovl_bench_fp32(ovl_ctx* ctx, double* fma_per_s);
 
 /* Wilson-kernel autotuner result for one storage precision (OVL_PREC_*): the variant
- * in use (0 one thread per site, 1 one thread per site and direction, 2 4D tiles) and
- * the measured milliseconds per launch of each on this lattice (zero when the variant
- * was forced or, for tiles, when the lattice does not divide into them). Any output
- * pointer may be NULL. */
+ * in use (0 one thread per site, 1 one thread per site and direction, 2 4D tiles, 3 two
+ * threads per site, one per half spinor, double-float only) and the measured
+ * milliseconds per launch of each on this lattice (zero when the variant was forced, does
+ * not apply to the precision or, for tiles, when the lattice does not divide into them).
+ * Any output pointer may be NULL. */
 ovl_status ovl_wilson_tuning(const ovl_ctx* ctx, int prec, int* variant, double* ms_thread_per_site,
-                             double* ms_split, double* ms_tiled);
+                             double* ms_split, double* ms_tiled, double* ms_pair);
 
 /* Library version string. */
 const char* ovl_version(void);

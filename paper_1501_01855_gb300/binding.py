@@ -90,7 +90,7 @@ _SIGS = {
     "ovl_profile_get": (I, [P, I, LLP, DP, DP]),
     "ovl_profile_units": (I, [P, I, DP]),
     "ovl_bench_wilson": (I, [P, I, I, I, DP, DP]),
-    "ovl_wilson_tuning": (I, [P, I, ctypes.POINTER(I), DP, DP, DP]),
+    "ovl_wilson_tuning": (I, [P, I, ctypes.POINTER(I), DP, DP, DP, DP]),
     "ovl_bench_fp32": (I, [P, DP]),
 }
 
@@ -360,9 +360,9 @@ class Overlap:
         return out
 
     def wilson_tuning(self, prec):
-        """(variant in use, ms per launch of variants 0, 1, 2) from the create-time autotuner."""
+        """(variant in use, ms per launch of variants 0, 1, 2, 3) from the create-time autotuner."""
         v = ctypes.c_int()
-        t = [ctypes.c_double() for _ in range(3)]
+        t = [ctypes.c_double() for _ in range(4)]
         _check(load().ovl_wilson_tuning(self.h, int(prec), ctypes.byref(v), *[ctypes.byref(x) for x in t]), self.h)
         return (v.value,) + tuple(x.value for x in t)
 

@@ -108,9 +108,10 @@ static void convert_links(const double* links, const int L[4], int bc_t, std::ve
   }
 }
 
-// Autotuner: time the Wilson-kernel variants (thread per site, direction split, and 4D
-// tiles when the lattice divides into them) for every storage precision on this
-// lattice (one system, random input) and keep the fastest.
+// Autotuner: time the Wilson-kernel variants (thread per site, direction split, 4D tiles
+// when the lattice divides into them, and for double-float the lane-pair form) for every
+// storage precision on this lattice (random input; one system, four for double-float,
+// whose sign launches carry several) and keep the fastest.
 static ovl_status autotune_wilson(ovl_ctx* c) {
   const int forced = c->P.wilson_variant;
   std::vector<double> h((size_t)24 * c->V);
@@ -123,24 +124,26 @@ static ovl_status autotune_wilson(ovl_ctx* c) {
   OVL_CUDA(c, cudaEventCreate(&e0));
   OVL_CUDA(c, cudaEventCreate(&e1));
   for (int p = 0; p < 4; ++p) {
-    if (forced >= 0 && forced <= 2) {
-      c->wvar[p] = (forced == 2 && !wilson_tiles_fit(c->g)) ? 0 : forced;
+    if (forced >= 0 && forced <= 3) {
+      c->wvar[p] = (forced == 2 && !wilson_tiles_fit(c->g)) || (forced == 3 && p != P64E) ? 0 : forced;
       continue;
     }
+    const int ns = p == P64E ? std::min(4, c->P.batch_max) : 1;
     Field *fi, *fo;
-    OVL_TRY(get_field(c, "at_in", p, 1, &fi));
-    OVL_TRY(get_field(c, "at_out", p, 1, &fo));
-    OVL_TRY(import_spinors(c, h.data(), OVL_C128, 0, 1, *fi, 0));
-    const int nv = wilson_tiles_fit(c->g) ? 3 : 2;
+    OVL_TRY(get_field(c, "at_in", p, ns, &fi));
+    OVL_TRY(get_field(c, "at_out", p, ns, &fo));
+    for (int j = 0; j < ns; ++j) OVL_TRY(import_spinors(c, h.data(), OVL_C128, 0, 1, *fi, j));
+    const int nv = p == P64E ? 4 : wilson_tiles_fit(c->g) ? 3 : 2;
     for (int v = 0; v < nv; ++v) {
+      if (v == 2 && !wilson_tiles_fit(c->g)) continue;
       LinkRef L = links_of(c, p);
       L.variant = v;
       const int reps = p == P64 ? 3 : 8;
       for (int w = 0; w < 2; ++w)
-        launch_wilson_K(p, p, p, c->g, c->kappa, L, fi->ref(), fo->ref(), 1, nullptr, nullptr, c->st);
+        launch_wilson_K(p, p, p, c->g, c->kappa, L, fi->ref(), fo->ref(), ns, nullptr, nullptr, c->st);
       OVL_CUDA(c, cudaEventRecord(e0, c->st));
       for (int w = 0; w < reps; ++w)
-        launch_wilson_K(p, p, p, c->g, c->kappa, L, fi->ref(), fo->ref(), 1, nullptr, nullptr, c->st);
+        launch_wilson_K(p, p, p, c->g, c->kappa, L, fi->ref(), fo->ref(), ns, nullptr, nullptr, c->st);
       OVL_CUDA(c, cudaEventRecord(e1, c->st));
       OVL_CUDA(c, cudaEventSynchronize(e1));
       OVL_TRY(check_launch(c, __func__));
@@ -152,7 +155,8 @@ static ovl_status autotune_wilson(ovl_ctx* c) {
     // run-to-run noise, and the choice should not flip between runs
     int best = 0;
     for (int v = 1; v < nv; ++v)
-      if (c->wtime[p][v] < 0.95f * c->wtime[p][0] && c->wtime[p][v] < c->wtime[p][best]) best = v;
+      if (c->wtime[p][v] > 0.f && c->wtime[p][v] < 0.95f * c->wtime[p][0] && c->wtime[p][v] < c->wtime[p][best])
+        best = v;
     c->wvar[p] = best;
     free_field(c->ws["at_in"]);
     free_field(c->ws["at_out"]);
@@ -814,12 +818,13 @@ extern "C" ovl_status ovl_profile_get(ovl_ctx* c, int cls, long long* launches, 
 }
 
 extern "C" ovl_status ovl_wilson_tuning(const ovl_ctx* c, int prec, int* variant, double* ms0, double* ms1,
-                                        double* ms2) {
+                                        double* ms2, double* ms3) {
   if (!c || prec < P64 || prec > P64E) return OVL_EINVAL;
   if (variant) *variant = c->wvar[prec];
   if (ms0) *ms0 = c->wtime[prec][0];
   if (ms1) *ms1 = c->wtime[prec][1];
   if (ms2) *ms2 = c->wtime[prec][2];
+  if (ms3) *ms3 = c->wtime[prec][3];
   return OVL_OK;
 }
 

@@ -64,7 +64,7 @@ struct ovl_ctx {
   int device = 0;
   void* link[4] = {nullptr, nullptr, nullptr, nullptr};  // P64, P32, P16, P64E 12-real layouts
   int wvar[4] = {0, 0, 0, 0};                            // Wilson-kernel variant per precision
-  float wtime[4][3] = {{0}};                             // autotuner timings (ms per launch)
+  float wtime[4][4] = {{0}};                             // autotuner timings (ms per launch)
   ovl::Poles hpoles;
   ovl::Poles* dpoles = nullptr;
   std::map<std::string, ovl::Field> ws;

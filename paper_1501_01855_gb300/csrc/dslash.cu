@@ -337,14 +337,41 @@ __device__ __forceinline__ void hop_dir(const Geom& g, const LinkRef& L, const S
   }
 }
 
+// Prefetch into L1 the lines hop n of the double-float loop reads: the neighbour's
+// twelve spinor chunks and the nine link entries of slot n. Issued one hop ahead, so that
+// the loads of the next hop find their lines in L1 instead of waiting on L2; it holds no
+// registers.
+__device__ __forceinline__ void prefetch_l1(const void* p) {
+  asm volatile("prefetch.global.L1 [%0];" ::"l"(p));
+}
+template <int PIN>
+__device__ __forceinline__ void prefetch_hop_df(const Geom& g, const LinkRef& L, const SpinorRef& in, int rhs,
+                                                int s, const int x[4], int n) {
+  if constexpr (PIN == P64E) {
+    const float4* p = reinterpret_cast<const float4*>(in.data) + (size_t)rhs * 12 * in.V + nb_site(g, x, s, n);
+#pragma unroll
+    for (int c = 0; c < 12; ++c) prefetch_l1(p + (size_t)c * in.V);
+  }
+  const float4* q = reinterpret_cast<const float4*>(L.data) + (size_t)n * 9 * L.V + s;
+#pragma unroll
+  for (int c = 0; c < 9; ++c) prefetch_l1(q + (size_t)c * L.V);
+}
+
+#ifndef OVL_DF_PREFETCH
+#define OVL_DF_PREFETCH 1
+#endif
 template <int PIN, int PL, typename T>
 __device__ __forceinline__ void hop(const Geom& g, const LinkRef& L, const SpinorRef& in, int rhs, int s,
                                     const int x[4], cpx<T> acc[12]) {
 #pragma unroll
   for (int k = 0; k < 12; ++k) acc[k] = cmk(T(0), T(0));
   if constexpr (PL == P64E) {
+    if (OVL_DF_PREFETCH) prefetch_hop_df<PIN>(g, L, in, rhs, s, x, 0);
 #pragma unroll 1
-    for (int n = 0; n < 8; ++n) hop_nb_df<PIN>(g, L, in, rhs, s, x, n, acc);
+    for (int n = 0; n < 8; ++n) {
+      if (OVL_DF_PREFETCH && n < 7) prefetch_hop_df<PIN>(g, L, in, rhs, s, x, n + 1);
+      hop_nb_df<PIN>(g, L, in, rhs, s, x, n, acc);
+    }
     return;
   }
   const int sy = g.L[0], sz = g.L[0] * g.L[1], st = sz * g.L[2];
@@ -595,6 +622,193 @@ __global__ void __launch_bounds__(256) __maxnreg__(MaxReg<PL>::v) wilson_kernel(
   }
 }
 
+// ---- variant 3 (double-float only): two threads per (site, system) ----------------------
+// The projection (1 -+ gamma_mu) leaves two half spinors h0, h1 (upper spins 0 and 1 plus a
+// power of i times a lower spin); thread `half` of a lane pair builds h_half, multiplies it
+// by the link (U h_half, row by row) and adds the result to upper spin `half` and to one
+// lower spin, which for mu <= 1 is spin 3 - half and for mu >= 2 spin 2 + half. So each
+// thread holds three accumulators (upper spin, lower spin from mu <= 1, from mu >= 2); at
+// the end one shuffle between the pair completes the lower spins, and thread `half` owns
+// output spins half and 2 + half. No arithmetic is duplicated: the pair does the work of
+// one thread of variant 0 with about two thirds of the registers each, so more warps hide
+// the load latency; the two lanes of a pair read the same link entries (one broadcast).
+__device__ __forceinline__ cpx<df> ld_cdf(const SpinorRef& f, int fld, int s, int k) {
+  const float4 w = *(reinterpret_cast<const float4*>(f.data) + ((size_t)fld * 12 + k) * f.V + s);
+  return cmk(df(w.x, w.y), df(w.z, w.w));
+}
+__device__ __forceinline__ cpx<df> ldg_cdf(const SpinorRef& f, int fld, int s, int k) {
+  const float4 w = __ldg(reinterpret_cast<const float4*>(f.data) + ((size_t)fld * 12 + k) * f.V + s);
+  return cmk(df(w.x, w.y), df(w.z, w.w));
+}
+__device__ __forceinline__ void st_cdf(const SpinorRef& f, int fld, int s, int k, const cpx<df>& v) {
+  *(reinterpret_cast<float4*>(f.data) + ((size_t)fld * 12 + k) * f.V + s) =
+      make_float4(v.r.hi, v.r.lo, v.i.hi, v.i.lo);
+}
+__device__ __forceinline__ cpx<df> shfl_pair(const cpx<df>& v) {
+  return cmk(df(__shfl_xor_sync(0xffffffffu, v.r.hi, 1), __shfl_xor_sync(0xffffffffu, v.r.lo, 1)),
+             df(__shfl_xor_sync(0xffffffffu, v.i.hi, 1), __shfl_xor_sync(0xffffffffu, v.i.lo, 1)));
+}
+
+// acc6 (components 3 half + c and 3 (2 + half) + c of site s) through the epilogue of MODE;
+// v receives this thread's share of the partial sums.
+template <int MODE>
+__device__ __forceinline__ void pair_epilogue(const DArgs& a, int rhs, int fin, int s, int half, cpx<df> acc6[6],
+                                              double v[NVRED]) {
+  const df kap(a.kappa);
+  int kk[6];
+#pragma unroll
+  for (int c = 0; c < 3; ++c) {
+    kk[c] = 3 * half + c;
+    kk[3 + c] = 3 * (2 + half) + c;
+  }
+  // gamma5 (in - kappa hop): the second triple is a lower spin (sign -1)
+  cpx<df> o[6];
+#pragma unroll
+  for (int q = 0; q < 6; ++q) {
+    const cpx<df> c = ldg_cdf(a.in, fin, s, kk[q]);
+    cpx<df> t = c - kap * acc6[q];
+    o[q] = q >= 3 ? -t : t;
+    if (MODE == MODE_K) acc6[q] = c;   // keep the input for ||in||^2
+  }
+  const bool red = a.partials != nullptr;
+  Acc<df> n0, n1;
+  if constexpr (MODE == MODE_K) {
+#pragma unroll
+    for (int q = 0; q < 6; ++q) {
+      st_cdf(a.out, rhs, s, kk[q], o[q]);
+      if (red) {
+        acc_norm(n0, o[q]);
+        acc_norm(n1, acc6[q]);
+      }
+    }
+    v[0] = n0.get();
+    v[1] = n1.get();
+  } else if constexpr (MODE == MODE_R) {
+    const df sg(a.sigma0), al(a.ms[rhs].alpha);
+#pragma unroll
+    for (int q = 0; q < 6; ++q) {
+      const cpx<df> p = ld_cdf(a.aux1, rhs, s, kk[q]);
+      cpx<df> r = ld_cdf(a.aux2, rhs, s, kk[q]);
+      r = r - al * (o[q] + sg * p);
+      st_cdf(a.aux2, rhs, s, kk[q], r);
+      if (red) acc_norm(n0, r);
+    }
+    v[0] = n0.get();
+  } else if constexpr (MODE == MODE_LZK) {
+    const df sc(a.lz[rhs].inv_n);
+#pragma unroll
+    for (int q = 0; q < 6; ++q) {
+      const cpx<df> t = sc * o[q];
+      st_cdf(a.out, rhs, s, kk[q], t);
+      if (red) acc_norm(n0, t);
+    }
+    v[0] = n0.get();
+  } else if constexpr (MODE == MODE_LZL) {
+    const LzRhs& L = a.lz[rhs];
+    const int j = L.j;
+    const df ca(L.a), cb(L.b);
+#pragma unroll
+    for (int q = 0; q < 6; ++q) {
+      cpx<df> w = o[q] - ca * ld_cdf(a.aux1, j * a.nrhs + rhs, s, kk[q]);
+      if (j > 0) w = w - cb * ld_cdf(a.aux1, (j - 1) * a.nrhs + rhs, s, kk[q]);
+      st_cdf(a.out, (j + 1) * a.nrhs + rhs, s, kk[q], w);
+      if (red) acc_norm(n0, w);
+    }
+    v[0] = n0.get();
+  }
+}
+
+// 80 registers: no spills, 24 warps per SM (96: 20; 72 and 64 spill)
+#ifndef OVL_WILSON_REG_PAIR
+#define OVL_WILSON_REG_PAIR 80
+#endif
+template <int MODE>
+__global__ void __maxnreg__(OVL_WILSON_REG_PAIR) wilson_pair_kernel(const DArgs a) {
+  __shared__ double red[(256 / 32) * NVRED];
+  const int half = threadIdx.x & 1;
+  const int sb = blockIdx.x / a.ngr;
+  const int rg = blockIdx.x - sb * a.ngr;
+  const int rhs = rg * blockDim.y + threadIdx.y;
+  const int s = sb * BX + (threadIdx.x >> 1);
+  bool live = s < a.g.V && rhs < a.nrhs;
+  if (live && a.ms != nullptr && (MODE == MODE_K || MODE == MODE_R)) live = !a.ms[rhs].done;
+  int fin = rhs;
+  if constexpr (MODE == MODE_LZK || MODE == MODE_LZL) {
+    if (live) live = !a.lz[rhs].done;
+    if (MODE == MODE_LZK && live) fin = a.lz[rhs].j * a.nrhs + rhs;
+  }
+  double v[NVRED] = {0.0, 0.0, 0.0, 0.0};
+  cpx<df> up[3], la[3], lb[3];
+#pragma unroll
+  for (int c = 0; c < 3; ++c) up[c] = la[c] = lb[c] = cmk(df(0.f), df(0.f));
+  if (live) {
+    int x[4];
+    site_coords(a.g, s, x);
+#pragma unroll 1
+    for (int n = 0; n < 8; ++n) {
+      const int mu = n >> 1;
+      const bool fwd = (n & 1) == 0;
+      const int sS = fwd ? 2 : 0;
+      const bool lo3 = mu <= 1;
+      // powers of i of the projection and of the lower-spin expansion (see hop_nb_df_core)
+      const int a0 = (sS + (mu == 0 || mu == 2 ? 1 : mu == 1 ? 2 : 0)) & 3;
+      const int a1 = (sS + (mu == 0 ? 1 : mu == 2 ? 3 : 0)) & 3;
+      const int b0 = (sS + (mu == 0 || mu == 2 ? 3 : 0)) & 3;
+      const int b1 = (sS + (mu == 0 ? 3 : mu == 1 ? 2 : mu == 2 ? 1 : 0)) & 3;
+      const int other = half == 0 ? (lo3 ? 3 : 2) : (lo3 ? 2 : 3);
+      const int ah = half == 0 ? a0 : a1;
+      const int bh = half == 0 ? (lo3 ? b1 : b0) : (lo3 ? b0 : b1);
+      const int sn = nb_site(a.g, x, s, n);
+      cpx<df> h[3];
+#pragma unroll
+      for (int c = 0; c < 3; ++c)
+        h[c] = padd(ldg_cdf(a.in, fin, sn, 3 * half + c), ipow(ldg_cdf(a.in, fin, sn, 3 * other + c), ah));
+      const float4* lp = reinterpret_cast<const float4*>(a.links.data) + (size_t)n * 9 * a.links.V + s;
+#pragma unroll
+      for (int r = 0; r < 3; ++r) {
+        cpx<df> u[3];
+#pragma unroll
+        for (int b = 0; b < 3; ++b) {
+          const float4 q = __ldg(lp + (size_t)(3 * r + b) * a.links.V);
+          u[b] = cmk(df(q.x, q.y), df(q.z, q.w));
+        }
+        Dot2 re = dot2_first(u[0].r, h[0].r), im = dot2_first(u[0].r, h[0].i);
+        dot2_add(re, -u[0].i, h[0].i);
+        dot2_add(im, u[0].i, h[0].r);
+#pragma unroll
+        for (int b = 1; b < 3; ++b) {
+          dot2_add(re, u[b].r, h[b].r);
+          dot2_add(re, -u[b].i, h[b].i);
+          dot2_add(im, u[b].r, h[b].i);
+          dot2_add(im, u[b].i, h[b].r);
+        }
+        const cpx<df> w = cmk(df(re.s, re.c), df(im.s, im.c));
+        up[r] = padd(up[r], w);
+        const cpx<df> wl = ipow(w, bh);
+        if (lo3) la[r] = padd(la[r], wl);
+        else lb[r] = padd(lb[r], wl);
+      }
+    }
+  }
+  // every lane of the warp takes part in the exchange (a pair shares s and rhs, so both of
+  // its lanes are live or neither is)
+  cpx<df> acc6[6];
+#pragma unroll
+  for (int c = 0; c < 3; ++c) {
+    acc6[c] = up[c];
+    acc6[3 + c] = lb[c] + shfl_pair(la[c]);
+  }
+  if (live) pair_epilogue<MODE>(a, rhs, fin, s, half, acc6, v);
+  if (a.partials != nullptr) {
+    double tot[NVRED];
+    block_reduce_partials<double>(v, red, tot);
+    if (threadIdx.x == 0 && rhs < a.nrhs) {
+#pragma unroll
+      for (int j = 0; j < NVRED; ++j) a.partials[((size_t)rhs * a.nsb + sb) * NVRED + j] = tot[j];
+    }
+  }
+}
+
 // true when the lattice can be covered by whole variant-2 tiles
 bool wilson_tiles_fit(const Geom& g) {
   return g.L[0] % TX == 0 && g.L[1] % TY == 0 && g.L[2] % TZ == 0 && g.L[3] % TT == 0;
@@ -670,6 +884,15 @@ static void run(DArgs a, cudaStream_t st) {
   Shape sh = make_shape(a.g.V, a.nrhs);
   a.nsb = sh.nsb;
   a.ngr = sh.ngr;
+  if constexpr (PIN == P64E && PL == P64E && POUT == P64E && PA1 == P64E && PA2 == P64E && MODE != MODE_OVL) {
+    if (a.variant == 3) {
+      // lane pairs over BX sites x up to 2 systems per block; partials keep the layout
+      const int by = a.nrhs < 2 ? a.nrhs : 2;
+      a.ngr = (a.nrhs + by - 1) / by;
+      wilson_pair_kernel<MODE><<<dim3((unsigned)(sh.nsb * a.ngr)), dim3(2 * BX, by), 0, st>>>(a);
+      return;
+    }
+  }
   if (a.variant == 1) {
     // one system per block; partials keep the (system, BX-site block) layout of variant 0
     wilson_split_kernel<MODE, PIN, PL, POUT, PA1, PA2><<<dim3((unsigned)(sh.nsb * a.nrhs)), dim3(4 * BX), 0, st>>>(a);

@@ -7,8 +7,8 @@ Unit links, a random input spinor, the kernel launched `--iters` times back to b
 the context stream and timed with CUDA events. Prints milliseconds per launch, the
 algorithmic bytes of one launch (each input spinor read once, each output written once,
 the links read once) and the rate they imply. `--variant` forces a kernel shape (0 one
-thread per site, 1 direction split, 2 4D tiles); the default lets the create-time
-autotuner choose.
+thread per site, 1 direction split, 2 4D tiles, 3 lane pairs for double-float); the
+default lets the create-time autotuner choose.
 """
 import argparse
 
@@ -32,7 +32,7 @@ def main(argv=None):
     ap.add_argument("--prec", choices=sorted(PRECS), default="f32")
     ap.add_argument("--nrhs", type=int, default=1)
     ap.add_argument("--iters", type=int, default=3)
-    ap.add_argument("--variant", type=int, default=-1, choices=[-1, 0, 1, 2])
+    ap.add_argument("--variant", type=int, default=-1, choices=[-1, 0, 1, 2, 3])
     ap.add_argument("--sign", type=float, default=0.0, metavar="ETA",
                     help="instead: one sign-function application (multi-shift CG) to accuracy ETA "
                          "on nrhs random vectors, 20 poles")

@@ -6,7 +6,7 @@ import numpy as np
 import pytest
 
 import synth
-from oracle import wilson
+from oracle import wilson, overlap
 from tests.gpu_util import lib, ctx, rel, M0
 
 pytestmark = pytest.mark.gpu
@@ -69,16 +69,17 @@ def test_wilson_full_size_sampled(dims):
     assert abs(l - r) <= 1e-12 * abs(l)
 
 
-@pytest.mark.parametrize("variant", [0, 1, 2])
+@pytest.mark.parametrize("variant", [0, 1, 2, 3])
 @pytest.mark.parametrize("prec", [0, 1, 2, 3])
 def test_wilson_launch_variants(variant, prec):
     """Every launch shape the autotuner can pick (thread per site, direction split, 4D
-    tiles) gives K to the precision's tolerance, on a lattice that divides into tiles
-    (two tiles in t) with antiperiodic t, for several systems at once."""
+    tiles, lane pairs for double-float) gives K to the precision's tolerance, on a lattice
+    that divides into tiles (two tiles in t) with antiperiodic t, for several systems at
+    once."""
     dims = (8, 4, 8, 4)
     U = synth.gauge_links(dims, 0.3, 1021)
     c = ctx(dims, U, a=0.1, b=2.6, bc_t=1, wilson_variant=variant)
-    assert c.wilson_tuning(prec)[0] == variant
+    assert c.wilson_tuning(prec)[0] == (variant if variant != 3 or prec == 3 else 0)
     psi = synth.gaussian_source(dims, 2021, nvec=5)
     out = np.zeros_like(psi)
     c.wilson_apply(psi, out, prec)
@@ -86,17 +87,19 @@ def test_wilson_launch_variants(variant, prec):
         assert rel(out[j], wilson.apply_K(U, psi[j], M0, True)) <= TOL[prec]
 
 
-@pytest.mark.parametrize("variant", [0, 1, 2])
-def test_sign_with_launch_variants(variant):
-    """The multi-shift CG reads its scalars from the Wilson kernel's partial sums; every
-    launch shape must give the same sign function (to the FP64 rounding of different
-    summation orders)."""
+@pytest.mark.parametrize("method", [0, 1])
+@pytest.mark.parametrize("variant", [0, 1, 2, 3])
+def test_sign_with_launch_variants(variant, method):
+    """The sign function reads its scalars from the Wilson kernel's partial sums; with every
+    launch shape, and with the stored-basis Lanczos (method 0) and the multi-shift CG
+    (method 1), it matches the oracle's per-pole CG for the same rational."""
+    from oracle import zolotarev as zo
     dims = (8, 4, 8, 4)
     U = synth.gauge_links(dims, 0.3, 1022)
     v = synth.gaussian_source(dims, 2022, nvec=2)
-    ref = np.zeros_like(v)
-    ctx(dims, U, n_poles=16, a=0.2, b=2.6, wilson_variant=0).sign_apply(v, ref, eta=1e-11, prec=0)
-    c = ctx(dims, U, n_poles=16, a=0.2, b=2.6, wilson_variant=variant)
+    om, sg, _ = zo.zolotarev(16, 0.2, 2.6)
+    ref = [overlap.zolotarev_sign_apply(U, v[j], M0, om, sg, tol=1e-14) for j in range(2)]
+    c = ctx(dims, U, n_poles=16, a=0.2, b=2.6, wilson_variant=variant, sign_method=method)
     for prec in (0, 3):
         out = np.zeros_like(v)
         c.sign_apply(v, out, eta=1e-11, prec=prec)
