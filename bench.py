@@ -400,6 +400,7 @@ def run_ours(args, ws, rank, local):
                                 for k, v in prof.items() if v["launches"]}},
     }
     ref_out = dout.cpu().numpy()
+    ctx.trim()     # the extras create contexts of their own
 
     if rank == 0 and not args.no_extras:
         line["extras"] = extras(args, ctx, dv, dout, ref_out, B, torch, stream, hbm)
@@ -430,6 +431,7 @@ def extras(args, ctx, dv, dout, ref_out, B, torch, stream, hbm):
         got = dout.cpu().numpy()
         err = max(np.linalg.norm(got[j] - ref_out[j]) / np.linalg.norm(ref_out[j]) for j in range(NVEC))
         out[name] = {"applies_per_s": NVEC / (ms * 1e-3), "max_rel_error_vs_df64": err}
+    ctx.trim()
     # Wilson kernel bandwidth on 24^3x48 (working set larger than L2)
     dims = (24, 24, 24, 48)
     p = B.ovl_params_default()
@@ -613,6 +615,90 @@ def config_c4(B, stream):
     return out
 
 
+def deflation_gain(B, stream):
+    """The deflation-gain experiment of Sec. 6 (Figs. 7 and 9) on the synthetic 16^3 x 32
+    ensemble at mu = 0.02: spaces of 15, 30 and 45 vectors, (a) accumulated by eigSUMR
+    during three solves and (b) from the standalone eigensolver, then 4 point sources
+    solved in one batch with relSUMR and relCG, undeflated and deflated. The gain in
+    middle-solver iterations is set against the bound the paper uses,
+    |lambda_{n+1}(gamma5 D)| / |lambda_1(gamma5 D)|, here from the Ritz values of a
+    46-vector space (|lambda(H)|^2 ~ lambda(D^dag D))."""
+    import tempfile
+    import synth
+    mu, tol = 0.02, 1e-10
+    U = synth.gauge_links(DIMS, 0.3, 1003)
+    srcs = np.stack([synth.point_source(DIMS, 0, c) for c in range(3)] + [synth.point_source(DIMS, 1, 0)])
+    out = {"workload": "16^3x32, eps 0.3 links seed 1003, m0 1.4, mu 0.02, 20 poles, 4 point sources, tol 1e-10"}
+
+    def solve(c, d):
+        xs = np.zeros_like(srcs)
+        t0 = time.perf_counter()
+        infos = c.solve(srcs, xs, tol, defl=d)
+        dt = time.perf_counter() - t0
+        return {"inner_iters_mean": float(np.mean([i["inner_iters"] for i in infos])),
+                "wilson_calls_dp2_mean": float(np.mean([i["wilson_calls"] for i in infos])),
+                "seconds": dt, "max_true_residual": max(i["true_residual"] for i in infos)}
+
+    def make(solver):
+        p = B.ovl_params_default()
+        p.stream = stream.cuda_stream
+        p.solver = solver
+        return B.Overlap(DIMS, U, M0, mu, NPOLES, EPS, params=p)
+
+    cs = make(B.OVL_SOLVER_SUMR)
+    ccg = make(B.OVL_SOLVER_CG)
+    out["undeflated"] = {"relSUMR": solve(cs, None), "relCG": solve(ccg, None)}
+
+    def evaluate(defl, key, n, seconds):
+        ritz, res = defl.info()
+        row = {"build_s": seconds, "ritz_residual_median": float(np.median(res)),
+               "ritz_residual_max": float(np.max(res)), "ritz": [float(x) for x in ritz],
+               "relSUMR": solve(cs, defl)}
+        with tempfile.TemporaryDirectory() as dd:
+            path = os.path.join(dd, "defl.bin")
+            defl.save(path)
+            dc = B.Deflation.load_file(ccg, path)
+            row["relCG"] = solve(ccg, dc)
+            dc.close()
+        out.setdefault(key, {})["n%d" % n] = row
+
+    for n in (15, 30, 45):
+        # (a) the accumulation during three solves (eigSUMR), basis 2 n + 64
+        defl = None
+        t0 = time.perf_counter()
+        for k in range(3):
+            b0 = synth.gaussian_source(DIMS, 2003 + k)
+            defl, _ = cs.eigsumr_accumulate(b0, np.zeros_like(b0), tol, n, 2 * n + 64, defl=defl)
+        evaluate(defl, "eigsumr_3_solves", n, time.perf_counter() - t0)
+        defl.close()
+        # (b) the standalone eigensolver, 2500 sign applications at most
+        t0 = time.perf_counter()
+        defl, used = cs.eigensolve(n, 2 * n + 64, 2500, res_tol=1e-3)
+        evaluate(defl, "standalone", n, time.perf_counter() - t0)
+        out["standalone"]["n%d" % n]["sign_applications"] = used
+        if n == 45:
+            ritz_all = defl.info()[0]
+        defl.close()
+    # the bound of Sec. 6: |lambda_{n+1}(H)| / |lambda_1(H)| from the best 45-vector space
+    # (Ritz values of D^dag D + 2 mu delta H ~ lambda(H)^2); lambda_46 from a 46th vector
+    d46, _ = cs.eigensolve(46, 2 * 46 + 64, 2500, res_tol=1e-3)
+    ritz_all = d46.info()[0]
+    d46.close()
+    lam = np.sqrt(np.maximum(np.asarray(ritz_all), 0.0))    # |lambda(H)| estimates, ascending
+    for key in ("eigsumr_3_solves", "standalone"):
+        for n in (15, 30, 45):
+            row = out[key]["n%d" % n]
+            row["bound"] = float(lam[n] / lam[0])
+            for sv in ("relSUMR", "relCG"):
+                row[sv]["gain_inner_iters"] = out["undeflated"][sv]["inner_iters_mean"] / row[sv]["inner_iters_mean"]
+                row[sv]["gain_wilson_calls"] = (out["undeflated"][sv]["wilson_calls_dp2_mean"]
+                                                / row[sv]["wilson_calls_dp2_mean"])
+    out["lambda_H_lowest_from_ritz"] = [float(x) for x in lam[:4]]
+    cs.close()
+    ccg.close()
+    return out
+
+
 def run_reference(args, ws, rank):
     """The oracle on this host's cores as the reference arm: every step is a complete
     oracle apply of as many 8^4 vectors as there are cores (a pool of that many
@@ -663,12 +749,15 @@ def main():
                     help="reference arm: 8^4 vectors per step (default: one per core)")
     ap.add_argument("--config-c4", action="store_true",
                     help="run only the 24^3x48 batched multi-mass deflated solves and print their JSON")
+    ap.add_argument("--deflation-gain", action="store_true",
+                    help="run only the deflation-gain experiment (15/30/45 vectors) and print its JSON")
     args = ap.parse_args()
-    if args.config_c4:
+    if args.config_c4 or args.deflation_gain:
         import torch
         from paper_1501_01855_gb300 import build, binding as B
         build.build()
-        print(json.dumps(config_c4(B, torch.cuda.current_stream())), flush=True)
+        fn = config_c4 if args.config_c4 else deflation_gain
+        print(json.dumps(fn(B, torch.cuda.current_stream())), flush=True)
         return
     if args.warmup < 3:
         args.warmup = 3

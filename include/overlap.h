@@ -102,6 +102,15 @@ typedef struct {
                            (one search direction per pole, updated every step); 2 stored-basis
                            Lanczos always (sub-batched to fit basis_gb)                        */
   double basis_gb;      /* device memory for stored Lanczos bases, GB, default 96              */
+  int    multimass;     /* 1 (default): in undeflated GMRESR(relSUMR) solves of several masses,
+                           batch by source and let the masses of a source share one SUMR basis
+                           (and one sign application per step) in the first middle solve, which
+                           starts from r = b for every mass (Sec. 2: SUMR adapts to many shifts);
+                           0: every system runs its own SUMR                                   */
+  int    force_pole_group;/* overlap_force: >0 solve the shifted systems of this many poles at a
+                           time (their solutions recomputed per group instead of all stored);
+                           0 (default): all poles at once when their fields fit in half the free
+                           device memory, else as many as fit                                */
   int    lanczos_cap;   /* >0: at most this many basis vectors per Lanczos cycle (a full cycle
                            restarts from its last vector, to which every pole's residual is
                            parallel); 0 (default): sized from the steps this context has
@@ -152,6 +161,12 @@ void overlap_destroy(ovl_ctx* ctx);
 /* One-line reason of the last failed call on ctx ("" if none); valid until the next
  * call on the same context. */
 const char* overlap_last_error(const ovl_ctx* ctx);
+
+/* Release the device memory the context caches between calls: every workspace (solver
+ * vectors, multi-shift pole vectors, the stored Lanczos basis) and the captured CUDA
+ * graphs. The gauge field, the Zolotarev data and deflation spaces stay; the next call
+ * allocates what it needs again. Synchronises the context stream. */
+ovl_status ovl_trim(ovl_ctx* ctx);
 
 /* Host-only (no GPU needed): the Zolotarev rational of order n on a < |x| < b
  * (Sec. 3), eps(x) = sum_i omega_i x / (x^2 + sigma_i), sigma ascending, and its
@@ -225,7 +240,10 @@ ovl_status overlap_solve(ovl_ctx* ctx, int nrhs, const double* mus, int nmass, c
                          int dtype, int on_device, double tol, ovl_defl* defl, ovl_solve_info* info);
 
 /* Solve D(mu) x = b once while accumulating Ritz vectors of D^dag D + 2 mu delta H
- * (eigSUMR, Algs. 5-6, Sec. 5) with basis size m_basis, keeping n_eig. If *defl is
+ * (Algs. 5-6, Sec. 5) with basis size m_basis, keeping n_eig, on the Krylov vectors of the
+ * context's middle solver: eigSUMR (params.solver = OVL_SOLVER_SUMR: q_j and V q_j of
+ * Alg. 5) or eigCG (OVL_SOLVER_CG: the residual directions of relCG and D applied to them,
+ * from vectors the CG step computes anyway). If *defl is
  * NULL a new space is created; otherwise its vectors seed the basis and are
  * improved. The space can then be passed to overlap_solve(). OVL_ENOCONV: the solve
  * stopped short of tol; the space is still built (or refined) and *defl set, and x
@@ -233,6 +251,38 @@ ovl_status overlap_solve(ovl_ctx* ctx, int nrhs, const double* mus, int nmass, c
 ovl_status eigsumr_accumulate(ovl_ctx* ctx, ovl_defl** defl, int n_eig, int m_basis, double mu,
                               const void* rhs, void* x, int dtype, int on_device, double tol,
                               ovl_solve_info* info);
+
+/* Standalone eigensolver (Sec. 6): approximate eigenvectors of D^dag D (and of gamma5 D)
+ * at mass mu from the eigSUMR Arnoldi process (Alg. 1 on V = gamma5 eps(K), Algs. 5-6) run
+ * without a linear solve, for callers who want the deflation space first (or a better one
+ * than the accumulation during solves gives). Rounds of round_diags Ritz steps (the paper
+ * used 24): each round ends with a Rayleigh-Ritz step over its vectors and those kept at
+ * the previous two rounds, an accurate recomputation of v^D, and a restart from the last
+ * basis vector orthogonalised against the current ones (also when ||q|| - 1 exceeds 0.1).
+ * The sign accuracy follows the Sec. 5.1 bound.
+ *   defl      in/out: NULL creates a space of n_eig vectors, else it is improved.
+ *   m_basis   Arnoldi basis, >= 2 n_eig + 8 (at a basis restart 2 n_eig vectors are kept).
+ *   start     one canonical spinor (dtype, on_device), or NULL for a Z2 source.
+ *   max_steps budget of sign applications; res_tol: stop once every residual
+ *             ||gamma5 D psi - psi (psi, gamma5 D psi)|| is at most this.
+ *   steps_done (may be NULL) receives the sign applications used. */
+ovl_status ovl_eigensolve(ovl_ctx* ctx, ovl_defl** defl, int n_eig, int m_basis, double mu, const void* start,
+                          int dtype, int on_device, int max_steps, double res_tol, int round_diags, int* steps_done);
+
+/* The Ritz recalculation of Alg. 6 (Sec. 5) on a caller-given basis: m spinors v and
+ * their v^D = D(mu) v (canonical, dtype and on_device as everywhere; m * 12 V entries
+ * each). E = V^dag V is Cholesky-factorised (E = U^dag U; if V has lost linear
+ * independence, orthonormalised through the eigendecomposition of E instead), M =
+ * (V^D)^dag V^D + 2 mu delta V^dag gamma5 V^D, and the eigenvectors Y of L^-1 M U^-1
+ * (ascending) give the new basis V U^-1 Y, of which the lowest n_keep are returned:
+ *   v_out, vD_out  n_keep spinors each (new v and v^D; same side and dtype as v);
+ *   ritz           host, n_keep Ritz values of D^dag D + 2 mu delta H;
+ *   residuals      host, n_keep values ||gamma5 v^D - v (v, gamma5 v^D)|| (may be NULL).
+ * The Gram blocks are summed in FP64 from FP32 products, as in the accumulation.
+ * OVL_EINVAL for null pointers, m < 1, n_keep outside 1..m, mu outside (0, 1). */
+ovl_status ovl_ritz_recalculate(ovl_ctx* ctx, int m, int n_keep, double mu, double delta, const void* v,
+                                const void* vD, void* v_out, void* vD_out, int dtype, int on_device, double* ritz,
+                                double* residuals);
 
 /* Ritz values (n) and eigenvector residuals ||gamma5 D v - v (v, gamma5 D v)|| (n)
  * of a deflation space; *n receives the number of vectors held; ritz and residuals

@@ -68,3 +68,34 @@ def gradient(U, phi, m0, mu, omega, sigma, tol=1e-13, antiperiodic_t=False):
                   - link_outer(b, Ka, m0, antiperiodic_t)
                   - link_outer(Kb, a, m0, antiperiodic_t))
     return G
+
+
+def gradient_dense(U, phi, m0, mu, omega, sigma, antiperiodic_t=False):
+    """The same gradient (same formula, same convention) with K as a dense matrix and the
+    rational and shifted inverses from its eigendecomposition: for lattices up to 4^4,
+    where the matrix-free CGs of gradient() take minutes. Returns (G, S)."""
+    shape = phi.shape
+    Kd = wilson.dense_K(U, m0, antiperiodic_t)
+    lam, Q = np.linalg.eigh(Kd)
+    Qh = np.conj(Q.T)
+    eps = sum(om * lam / (lam * lam + s) for om, s in zip(omega, sigma))
+    n = Kd.shape[0]
+    G5 = overlap.gamma5_matrix(n // 12)
+    H = 0.5 * (1.0 + mu) * G5 + 0.5 * (1.0 - mu) * (Q * eps) @ Qh
+    H = 0.5 * (H + np.conj(H.T))
+    f = phi.ravel()
+    chi = np.linalg.solve(H @ H, f)
+    S = float(np.real(np.vdot(f, chi)))
+    psi = H @ chi
+    Kpsi = Kd @ psi
+    G = np.zeros(U.shape, dtype=np.complex128)
+    for om, s in zip(omega, sigma):
+        Ri = (Q * (1.0 / (lam * lam + s))) @ Qh
+        a = Ri @ chi
+        b = Ri @ Kpsi
+        c = -(1.0 - mu) * om
+        r = lambda v: v.reshape(shape)
+        G += c * (link_outer(r(psi), r(a), m0, antiperiodic_t)
+                  - link_outer(r(b), r(Kd @ a), m0, antiperiodic_t)
+                  - link_outer(r(Kd @ b), r(a), m0, antiperiodic_t))
+    return G, S

@@ -43,7 +43,7 @@ class ovl_params(ctypes.Structure):
                 ("a_override", ctypes.c_double), ("b_override", ctypes.c_double), ("batch_max", ctypes.c_int), ("wilson_variant", ctypes.c_int),
                 ("use_graphs", ctypes.c_int),
                 ("verify", ctypes.c_int), ("sign_method", ctypes.c_int), ("basis_gb", ctypes.c_double),
-                ("lanczos_cap", ctypes.c_int),
+                ("multimass", ctypes.c_int), ("force_pole_group", ctypes.c_int), ("lanczos_cap", ctypes.c_int),
                 ("stream", ctypes.c_void_p)]
 
 
@@ -71,6 +71,7 @@ _SIGS = {
     "overlap_create": (I, [ctypes.POINTER(P), ctypes.POINTER(I), DP, D, D, I, D, ctypes.POINTER(ovl_params)]),
     "overlap_destroy": (None, [P]),
     "overlap_last_error": (ctypes.c_char_p, [P]),
+    "ovl_trim": (I, [P]),
     "overlap_zolotarev": (I, [P, DP, DP, DP, DP, DP]),
     "ovl_wilson_apply": (I, [P, P, P, I, I, I, I]),
     "ovl_wilson_apply_noalloc": (I, [P, P, P, I, I, I]),
@@ -80,6 +81,8 @@ _SIGS = {
     "overlap_solve": (I, [P, I, DP, I, P, P, I, I, D, P, ctypes.POINTER(ovl_solve_info)]),
     "eigsumr_accumulate": (I, [P, ctypes.POINTER(P), I, I, D, P, P, I, I, D, ctypes.POINTER(ovl_solve_info)]),
     "ovl_defl_info": (I, [P, ctypes.POINTER(I), DP, DP]),
+    "ovl_ritz_recalculate": (I, [P, I, I, D, D, P, P, P, P, I, I, DP, DP]),
+    "ovl_eigensolve": (I, [P, ctypes.POINTER(P), I, I, D, P, I, I, I, D, I, ctypes.POINTER(I)]),
     "ovl_defl_vector": (I, [P, I, DP, DP]),
     "ovl_defl_save": (I, [P, ctypes.c_char_p]),
     "ovl_defl_load": (I, [P, ctypes.POINTER(P), ctypes.c_char_p]),
@@ -238,6 +241,10 @@ class Overlap:
         # fingerprint of the gauge field the library copied (checked by the autograd wrapper)
         self.links_digest = links_digest(links)
 
+    def trim(self):
+        """Release the workspaces and graphs the context caches between calls."""
+        _check(load().ovl_trim(self.h), self.h)
+
     def close(self):
         if getattr(self, "h", None):
             load().overlap_destroy(self.h)
@@ -341,6 +348,43 @@ class Overlap:
         _check(load().overlap_force(self.h, float(mu), pp, code, dev, float(tol), _dptr(G), _dptr(S)), self.h)
         Gc = G.view(np.complex128).reshape(tuple(reversed(self.dims)) + (4, 3, 3))
         return Gc, float(S[0])
+
+    def eigensolve(self, n_eig, m_basis, max_steps, res_tol=0.0, mu=None, start=None, defl=None, round_diags=24):
+        """Standalone eigSUMR eigensolver (ovl_eigensolve): returns (space, steps used)."""
+        mu = self.mu if mu is None else mu
+        if start is not None:
+            ps, code, dev, cnt, _ = _spinor_arg(start)
+            if self._n(cnt) != 1:
+                raise ValueError("start must be one spinor")
+        else:
+            ps, code, dev = None, OVL_C128, 0
+        h = ctypes.c_void_p(defl.h.value if defl is not None else None)
+        used = ctypes.c_int()
+        _check(load().ovl_eigensolve(self.h, ctypes.byref(h), int(n_eig), int(m_basis), float(mu), ps, code, dev,
+                                     int(max_steps), float(res_tol), int(round_diags), ctypes.byref(used)), self.h)
+        if defl is None:
+            defl = Deflation(self, h)
+        return defl, used.value
+
+    def ritz_recalculate(self, v, vD, n_keep, mu=None, delta=0.01):
+        """Alg. 6 on the basis v (m spinors) with v^D = D(mu) v: (Ritz values, new v,
+        new v^D, residuals) of the lowest n_keep Ritz pairs."""
+        pv, pd, code, dev, cnt = _io(self.device, v, vD)
+        m = self._n(cnt)
+        mu = self.mu if mu is None else mu
+        if dev:
+            import torch
+            vo = torch.empty((n_keep,) + tuple(v.shape[1:]), dtype=v.dtype, device=v.device)
+            vdo = torch.empty_like(vo)
+        else:
+            vo = np.empty((n_keep,) + tuple(np.shape(v)[1:]), dtype=np.asarray(v).dtype)
+            vdo = np.empty_like(vo)
+        ritz = np.zeros(n_keep)
+        res = np.zeros(n_keep)
+        _check(load().ovl_ritz_recalculate(self.h, m, int(n_keep), float(mu), float(delta), pv, pd,
+                                           _spinor_arg(vo)[0], _spinor_arg(vdo)[0], code, dev, _dptr(ritz),
+                                           _dptr(res)), self.h)
+        return ritz, vo, vdo, res
 
     def profile_enable(self, on=True):
         _check(load().ovl_profile_enable(self.h, 1 if on else 0), self.h)

@@ -48,12 +48,20 @@ extern "C" ovl_status ovl_params_default(ovl_params* p) {
   p->verify = 1;
   p->sign_method = 0;
   p->basis_gb = 96.0;
+  p->multimass = 1;
+  p->force_pole_group = 0;
   p->lanczos_cap = 0;
   p->stream = nullptr;
   return OVL_OK;
 }
 
 extern "C" const char* overlap_last_error(const ovl_ctx* c) { return c ? c->err.c_str() : "null context"; }
+
+extern "C" ovl_status ovl_trim(ovl_ctx* c) {
+  if (!c) return OVL_EINVAL;
+  trim_workspaces(c);
+  return OVL_OK;
+}
 
 // ---------------------------------------------------------------- create
 static void convert_links(const double* links, const int L[4], int bc_t, std::vector<double>& l64,
@@ -219,6 +227,7 @@ extern "C" void overlap_destroy(ovl_ctx* c) {
   if (c->st) cudaStreamSynchronize(c->st);
   else cudaDeviceSynchronize();
   for (auto& kv : c->ws) free_field(kv.second);
+  if (c->lz_pool) cudaFree(c->lz_pool);
   for (int p = 0; p < 4; ++p)
     if (c->link[p]) cudaFree(c->link[p]);
   if (c->partials) cudaFree(c->partials);
@@ -230,6 +239,7 @@ extern "C" void overlap_destroy(ovl_ctx* c) {
   if (c->lz_hist) cudaFree(c->lz_hist);
   if (c->lz_Y) cudaFree(c->lz_Y);
   if (c->lz_coefW) cudaFree(c->lz_coefW);
+  if (c->lz_ctr) cudaFree(c->lz_ctr);
   if (c->dpoles) cudaFree(c->dpoles);
   if (c->dwork) cudaFree(c->dwork);
   if (c->hpin) cudaFreeHost(c->hpin);
@@ -489,7 +499,14 @@ static ovl_status true_residuals(ovl_ctx* c, const Field& b, int boff, const Fie
   OVL_TRY(norms_batch(c, *t, 0, n, rn));
   OVL_TRY(norms_batch(c, b, boff, n, bn));
   out.resize(n);
-  for (int j = 0; j < n; ++j) out[j] = bn[j] > 0 ? rn[j] / bn[j] : 0.0;
+  for (int j = 0; j < n; ++j) {
+    out[j] = bn[j] > 0 ? rn[j] / bn[j] : 0.0;
+    if (!std::isfinite(out[j])) {
+      char m[160];
+      snprintf(m, sizeof(m), "the true residual of system %d is not finite (the verification sign failed)", j);
+      return set_err(c, OVL_EBREAKDOWN, m);
+    }
+  }
   return OVL_OK;
 }
 
@@ -511,6 +528,45 @@ extern "C" ovl_status overlap_solve(ovl_ctx* c, int nrhs, const double* mus, int
   const int bm = std::max(1, c->P.batch_max);
   const size_t esz = (dtype == OVL_C128 ? 16 : 8) * 12 * (size_t)c->V;
   ovl_status worst = OVL_OK;
+  // undeflated relSUMR with several masses: batches of whole sources (every mass), so that
+  // the first middle solve shares one SUMR basis per source
+  if (c->P.multimass && nmass > 1 && !defl && c->P.solver != OVL_SOLVER_CG && nmass <= bm) {
+    const int nsb = std::max(1, bm / nmass);
+    for (int j0 = 0; j0 < nrhs; j0 += nsb) {
+      const int nj = std::min(nsb, nrhs - j0), n = nj * nmass;
+      Field *bb, *bx;
+      OVL_TRY(get_field(c, "bat_b", P64, n, &bb));
+      OVL_TRY(get_field(c, "bat_x", P64, n, &bx));
+      std::vector<double> bmus(n);
+      for (int k = 0; k < nmass; ++k)
+        for (int jl = 0; jl < nj; ++jl) {
+          bmus[k * nj + jl] = mv[k];
+          OVL_TRY(copy_convert(c, *fb, j0 + jl, *bb, k * nj + jl, 1));
+        }
+      std::vector<ovl_solve_info> binfo(n);
+      ovl_status st = gmresr_batch(c, n, bmus, *bb, 0, *bx, 0, tol, nullptr, binfo.data(), nullptr, nj);
+      if (st != OVL_OK && st != OVL_ENOCONV) return st;
+      if (st == OVL_ENOCONV) worst = st;
+      if (c->P.verify) {
+        std::vector<double> tr;
+        OVL_TRY(true_residuals(c, *bb, 0, *bx, 0, n, bmus, tol, tr));
+        for (int q = 0; q < n; ++q) {
+          binfo[q].true_residual = tr[q];
+          binfo[q].converged = tr[q] <= tol * 1.0000001 ? 1 : 0;
+        }
+      }
+      for (int k = 0; k < nmass; ++k) {
+        char* dst = (char*)x + esz * ((size_t)k * nrhs + j0);
+        OVL_TRY(export_spinors(c, dst, dtype, on_device, nj, *bx, k * nj));
+        if (info)
+          for (int jl = 0; jl < nj; ++jl) info[(size_t)k * nrhs + j0 + jl] = binfo[k * nj + jl];
+      }
+    }
+    OVL_CUDA(c, cudaStreamSynchronize(c->st));
+    if (info)
+      for (int s = 0; s < nsys; ++s) info[s].wilson_f64 = info[s].wilson_f32 = info[s].wilson_f16 = 0;
+    return worst;
+  }
   for (int s0 = 0; s0 < nsys; s0 += bm) {
     const int n = std::min(bm, nsys - s0);
     Field *bb, *bx;
@@ -576,6 +632,35 @@ extern "C" void ovl_defl_destroy(ovl_defl* d) {
   delete d;
 }
 
+// Store the first nk vectors of V as the space d, recompute w = gamma5 eps(K) psi
+// accurately (Sec. 5.1: v^D is recalculated after the eigenvector calculation, before
+// the space is used), and take the Ritz values of D^dag D + 2 mu delta H and the residuals
+// ||gamma5 D psi - psi (psi, gamma5 D psi)|| from the recomputed w.
+static ovl_status defl_store(ovl_ctx* c, ovl_defl* d, const Field* V, int nk, double mu) {
+  if (d->cap < nk) return set_err(c, OVL_EINVAL, "internal: deflation capacity");
+  OVL_TRY(copy_convert(c, *V, 0, d->v, 0, nk));
+  std::vector<double> etas(nk, std::max(c->eps_sign, 1e-8));
+  const int mode = choose_mode(c, etas[0]);
+  OVL_TRY(sign_op(c, mode, d->v, 0, d->w, 0, nk, etas.data(), 0.0, 1.0, nullptr, 0, nullptr, 0, nullptr, nullptr));
+  d->n = nk;
+  d->mu = mu;
+  d->prepared = false;
+  OVL_TRY(defl_prepare(c, d));
+  d->ritz.assign(nk, 0.0);
+  d->res.assign(nk, 0.0);
+  const double a = 0.5 * (1.0 - mu), b = 0.5 * (1.0 + mu);
+  for (int i = 0; i < nk; ++i) {
+    const size_t ii = (size_t)i * nk + i;
+    const double vv = d->VV[ii].real();
+    const cd wv = d->WV[ii];
+    const double dd = a * a * d->WW[ii].real() + 2.0 * a * b * wv.real() + b * b * vv;   // ||D psi||^2
+    const cd th = b * d->G5VV[ii] + a * d->G5VW[ii];                                    // (psi, g5 D psi)
+    d->ritz[i] = (dd + 2.0 * mu * c->P.delta_split * th.real()) / vv;
+    d->res[i] = std::sqrt(std::max(0.0, dd / vv - std::norm(th) / (vv * vv)));
+  }
+  return OVL_OK;
+}
+
 static ovl_status eig_after_outer(ovl_ctx* c, void* data, int outer) {
   (void)c;
   (void)data;
@@ -620,11 +705,20 @@ extern "C" ovl_status eigsumr_accumulate(ovl_ctx* c, ovl_defl** defl, int n_eig,
     e.k = ns;
     e.n_seeded = ns;
   }
+  // The accumulation rides on the context's middle solver: SUMR's Krylov basis (eigSUMR,
+  // Alg. 5) or the residual directions of relCG (eigCG, Sec. 5); the space itself
+  // (eigenvectors of D^dag D) serves both solvers.
+  const bool use_cg = c->P.solver == OVL_SOLVER_CG;
+  if (use_cg) {
+    OVL_TRY(get_field(c, "e_Tp", e.prec, 1, &e.Tprev));
+    OVL_TRY(get_field(c, "e_Zp", e.prec, 1, &e.Zprev));
+  }
   EigHook hook;
   hook.active = true;
   hook.target = std::sqrt(tol);   // GMRESR in two steps while the eigenvectors are being calculated (Sec. 6)
   hook.eta_cap = e.eps_v;
-  hook.hook = eig_hook;
+  hook.hook = use_cg ? nullptr : eig_hook;
+  hook.cg_hook = use_cg ? eig_cg_hook : nullptr;
   hook.after_outer = eig_after_outer;
   hook.data = &e;
   e.eig = &hook;
@@ -635,12 +729,7 @@ extern "C" ovl_status eigsumr_accumulate(ovl_ctx* c, ovl_defl** defl, int n_eig,
   std::vector<double> mus(1, mu);
   // the deflation held so far accelerates this solve too; the space is rebuilt after it
   ovl_defl* use = (!fresh && d->n > 0) ? d : nullptr;
-  // the accumulation rides on SUMR's Krylov basis (Alg. 5), whatever middle solver the
-  // context uses for ordinary solves; the space itself (eigenvectors of D^dag D) serves both
-  const int solver_keep = c->P.solver;
-  c->P.solver = OVL_SOLVER_SUMR;
   ovl_status st = gmresr_batch(c, 1, mus, *fb, 0, *fx, 0, tol, use, info, &hook);
-  c->P.solver = solver_keep;
   if (st != OVL_OK && st != OVL_ENOCONV) {
     if (fresh) ovl_defl_destroy(d);
     return st;
@@ -652,32 +741,7 @@ extern "C" ovl_status eigsumr_accumulate(ovl_ctx* c, ovl_defl** defl, int n_eig,
     if (fresh) ovl_defl_destroy(d);
     return set_err(c, OVL_ENOCONV, "eigSUMR collected no basis vectors (the solve needed no SUMR step)");
   }
-  // store, then recompute w = V psi accurately (Sec. 5.1: recalculate v^D after the
-  // eigenvector calculation when the space is used by SUMR)
-  if (d->cap < nk) return set_err(c, OVL_EINVAL, "internal: deflation capacity");
-  OVL_TRY(copy_convert(c, *e.V, 0, d->v, 0, nk));
-  std::vector<double> etas(nk, std::max(c->eps_sign, 1e-8));
-  const int mode = choose_mode(c, etas[0]);
-  OVL_TRY(sign_op(c, mode, d->v, 0, d->w, 0, nk, etas.data(), 0.0, 1.0, nullptr, 0, nullptr, 0, nullptr, nullptr));
-  d->n = nk;
-  d->mu = mu;
-  d->prepared = false;
-  OVL_TRY(defl_prepare(c, d));
-  // Ritz values of D^dag D + 2 mu delta H and residuals with the recomputed w
-  d->ritz.assign(nk, 0.0);
-  d->res.assign(nk, 0.0);
-  {
-    const double a = 0.5 * (1.0 - mu), b = 0.5 * (1.0 + mu);
-    for (int i = 0; i < nk; ++i) {
-      const size_t ii = (size_t)i * nk + i;
-      const double vv = d->VV[ii].real();
-      const cd wv = d->WV[ii];
-      const double dd = a * a * d->WW[ii].real() + 2.0 * a * b * wv.real() + b * b * vv;   // ||D psi||^2
-      const cd th = b * d->G5VV[ii] + a * d->G5VW[ii];                                    // (psi, g5 D psi)
-      d->ritz[i] = (dd + 2.0 * mu * c->P.delta_split * th.real()) / vv;
-      d->res[i] = std::sqrt(std::max(0.0, dd / vv - std::norm(th) / (vv * vv)));
-    }
-  }
+  OVL_TRY(defl_store(c, d, e.V, nk, mu));
   OVL_TRY(export_spinors(c, x, dtype, on_device, 1, *fx, 0));
   if (info && c->P.verify) {
     std::vector<double> tr;
@@ -687,12 +751,195 @@ extern "C" ovl_status eigsumr_accumulate(ovl_ctx* c, ovl_defl** defl, int n_eig,
   }
   OVL_CUDA(c, cudaStreamSynchronize(c->st));
   // the accumulation basis (4 x m_basis spinors) is not needed between solves
-  for (const char* nm : {"e_V", "e_W", "e_VD", "e_T"}) {
+  for (const char* nm : {"e_V", "e_W", "e_VD", "e_T", "e_Tp", "e_Zp", "e_tmp"}) {
     auto it = c->ws.find(nm);
     if (it != c->ws.end()) free_field(it->second);
   }
   *defl = d;
   return st;
+}
+
+extern "C" ovl_status ovl_ritz_recalculate(ovl_ctx* c, int m, int n_keep, double mu, double delta, const void* v,
+                                           const void* vD, void* v_out, void* vD_out, int dtype, int on_device,
+                                           double* ritz, double* residuals) {
+  if (!c) return OVL_EINVAL;
+  if (!v || !vD || !v_out || !vD_out || !ritz) return set_err(c, OVL_EINVAL, "null pointer");
+  if (m < 1 || m > 1024 || n_keep < 1 || n_keep > m) return set_err(c, OVL_EINVAL, "need 1 <= n_keep <= m <= 1024");
+  if (!(mu > 0 && mu < 1)) return set_err(c, OVL_EINVAL, "mu must lie in (0, 1)");
+  if (dtype != OVL_C128 && dtype != OVL_C64) return set_err(c, OVL_EINVAL, "dtype must be OVL_C128 or OVL_C64");
+  EigState e;
+  e.prec = P64;
+  e.m = m;
+  e.n_eig = n_keep;
+  e.mu = mu;
+  e.delta = delta;
+  Field* VD;
+  OVL_TRY(get_field(c, "e_V", P64, m, &e.V));
+  OVL_TRY(get_field(c, "e_W", P64, m, &e.W));
+  OVL_TRY(get_field(c, "rr_vd", P64, m, &VD));
+  OVL_TRY(import_spinors(c, v, dtype, on_device, m, *e.V, 0));
+  OVL_TRY(import_spinors(c, vD, dtype, on_device, m, *VD, 0));
+  // the basis keeps w with D v = (1+mu)/2 v + (1-mu)/2 w
+  std::vector<cd> a(m, 2.0 / (1.0 - mu)), b(m, -(1.0 + mu) / (1.0 - mu));
+  OVL_TRY(axpby_batch(c, a, *VD, 0, b, *e.V, 0, *e.W, 0, m));
+  e.k = m;
+  OVL_TRY(ritz_step(c, &e, n_keep, false));
+  const int nk = e.k;
+  if (nk < n_keep) return set_err(c, OVL_EBREAKDOWN, "the basis spans fewer than n_keep directions");
+  std::vector<cd> av(n_keep, 0.5 * (1.0 - mu)), bv(n_keep, 0.5 * (1.0 + mu));
+  OVL_TRY(axpby_batch(c, av, *e.W, 0, bv, *e.V, 0, *VD, 0, n_keep));
+  OVL_TRY(export_spinors(c, v_out, dtype, on_device, n_keep, *e.V, 0));
+  OVL_TRY(export_spinors(c, vD_out, dtype, on_device, n_keep, *VD, 0));
+  for (int i = 0; i < n_keep; ++i) {
+    ritz[i] = e.ritz[i];
+    if (residuals) residuals[i] = e.res[i];
+  }
+  OVL_CUDA(c, cudaStreamSynchronize(c->st));
+  return OVL_OK;
+}
+
+// Standalone eigensolver (Sec. 6): the eigSUMR Arnoldi process (Alg. 1 basis of
+// V = gamma5 eps(K), accumulated by Algs. 5-6) run for its own sake, in rounds of
+// `round_diags` Ritz steps. Each round ends with a Rayleigh-Ritz step over the current
+// vectors and those of the previous two rounds, an accurate recomputation of v^D, and a
+// restart from SUMR's last q orthogonalised against the current vectors; the sign
+// accuracy follows the Sec. 5.1 bound that the Ritz step computes.
+extern "C" ovl_status ovl_eigensolve(ovl_ctx* c, ovl_defl** defl, int n_eig, int m_basis, double mu,
+                                     const void* start, int dtype, int on_device, int max_steps, double res_tol,
+                                     int round_diags, int* steps_done) {
+  if (!c) return OVL_EINVAL;
+  if (!defl) return set_err(c, OVL_EINVAL, "defl must not be null");
+  if (n_eig < 1 || m_basis < 2 * n_eig + 8 || m_basis > 1024)
+    return set_err(c, OVL_EINVAL, "need n_eig >= 1 and 2 n_eig + 8 <= m_basis <= 1024");
+  if (!(mu > 0 && mu < 1)) return set_err(c, OVL_EINVAL, "mu must lie in (0, 1)");
+  if (max_steps < 1 || round_diags < 1) return set_err(c, OVL_EINVAL, "need max_steps >= 1 and round_diags >= 1");
+  if (start && dtype != OVL_C128 && dtype != OVL_C64) return set_err(c, OVL_EINVAL, "bad dtype");
+  const int prec = c->P.mixed ? P32 : P64;
+  ovl_defl* d = *defl;
+  bool fresh = false;
+  if (!d) {
+    d = new (std::nothrow) ovl_defl();
+    if (!d) return OVL_ENOMEM;
+    fresh = true;
+    ovl_status s = defl_alloc(c, d, prec, n_eig);
+    if (s != OVL_OK) {
+      ovl_defl_destroy(d);
+      return s;
+    }
+  } else if (d->ctx != c) {
+    return set_err(c, OVL_EINVAL, "deflation space belongs to another context");
+  } else if (d->cap < n_eig) {
+    return set_err(c, OVL_EINVAL, "the space holds fewer than n_eig vectors");
+  }
+  auto fail = [&](ovl_status st) {
+    if (fresh) ovl_defl_destroy(d);
+    return st;
+  };
+  EigState e;
+  e.prec = d->v.prec;
+  e.m = m_basis;
+  e.n_eig = n_eig;
+  e.mu = mu;
+  e.delta = c->P.delta_split;
+  Field *q0, *xd, *g1v, *g1w, *g2v, *g2w;
+  ovl_status st = OVL_OK;
+  if ((st = get_field(c, "e_V", e.prec, m_basis, &e.V)) != OVL_OK) return fail(st);
+  if ((st = get_field(c, "e_W", e.prec, m_basis, &e.W)) != OVL_OK) return fail(st);
+  if ((st = get_field(c, "es_q0", e.prec, 1, &q0)) != OVL_OK) return fail(st);
+  if ((st = get_field(c, "es_x", e.prec, 1, &xd)) != OVL_OK) return fail(st);
+  if ((st = get_field(c, "es_g1v", e.prec, n_eig, &g1v)) != OVL_OK) return fail(st);
+  if ((st = get_field(c, "es_g1w", e.prec, n_eig, &g1w)) != OVL_OK) return fail(st);
+  if ((st = get_field(c, "es_g2v", e.prec, n_eig, &g2v)) != OVL_OK) return fail(st);
+  if ((st = get_field(c, "es_g2w", e.prec, n_eig, &g2w)) != OVL_OK) return fail(st);
+  // start vector: the caller's, or a Z2 source (every real component +-1, Sec. 6)
+  if (start) {
+    if ((st = import_spinors(c, start, dtype, on_device, 1, *q0, 0)) != OVL_OK) return fail(st);
+  } else {
+    std::vector<double> h((size_t)24 * c->V);
+    unsigned long long r = 0x2545F4914F6CDD1Dull;
+    for (auto& xv : h) {
+      r ^= r << 13;
+      r ^= r >> 7;
+      r ^= r << 17;
+      xv = (r >> 63) ? 1.0 : -1.0;
+    }
+    if ((st = import_spinors(c, h.data(), OVL_C128, 0, 1, *q0, 0)) != OVL_OK) return fail(st);
+  }
+  int n1 = 0, n2 = 0, total = 0;
+  int ns = (!fresh && d->n > 0) ? std::min(d->n, n_eig) : 0;
+  std::vector<double> mus(1, mu);
+  for (int round = 0; total < max_steps; ++round) {
+    // seed the basis with the current space; q0 orthogonalised against it
+    e.k = 0;
+    e.n_seeded = 0;
+    e.ndiag = 0;
+    if (ns > 0) {
+      if ((st = copy_convert(c, d->v, 0, *e.V, 0, ns)) != OVL_OK) return fail(st);
+      if ((st = copy_convert(c, d->w, 0, *e.W, 0, ns)) != OVL_OK) return fail(st);
+      e.k = e.n_seeded = ns;
+      for (int pass = 0; pass < 2; ++pass) {
+        std::vector<cd> G, C;
+        if ((st = gram_host(c, d->v, 0, ns, *q0, 0, 1, 0, G)) != OVL_OK) return fail(st);
+        C.resize(ns);
+        for (int i = 0; i < ns; ++i) C[i] = -G[i] / std::max(d->VV[(size_t)i * ns + i].real(), 1e-300);
+        if ((st = combine_host(c, d->v, 0, ns, C, *q0, 0, 1, 1)) != OVL_OK) return fail(st);
+      }
+    }
+    SumrCfg cfg;
+    cfg.prec = e.prec;
+    cfg.target = 1e-300;   // no solve: the process runs for its basis alone
+    cfg.floor = c->P.eta_floor;
+    cfg.eta_dyn = &e.eta_cap;
+    cfg.maxit = std::min(max_steps - total, (m_basis - e.k) + (round_diags - 1) * (m_basis - 2 * n_eig));
+    cfg.qdrift = 0.1;
+    cfg.hook = eig_hook;
+    cfg.hook_data = &e;
+    SumrResult sr;
+    if ((st = sumr_batch(c, cfg, 1, mus, *q0, 0, *xd, 0, sr)) != OVL_OK) return fail(st);
+    total += std::max(1, sr.sign_calls[0]);
+    if (e.k > e.n_seeded || e.ndiag == 0) {
+      if ((st = ritz_step(c, &e, n_eig)) != OVL_OK) return fail(st);
+    }
+    // Rayleigh-Ritz over this round's vectors and the previous two rounds'
+    const int k0 = e.k;
+    if (n1 > 0 && k0 + n1 + n2 <= m_basis) {
+      if ((st = copy_convert(c, *g1v, 0, *e.V, k0, n1)) != OVL_OK) return fail(st);
+      if ((st = copy_convert(c, *g1w, 0, *e.W, k0, n1)) != OVL_OK) return fail(st);
+      if (n2 > 0) {
+        if ((st = copy_convert(c, *g2v, 0, *e.V, k0 + n1, n2)) != OVL_OK) return fail(st);
+        if ((st = copy_convert(c, *g2w, 0, *e.W, k0 + n1, n2)) != OVL_OK) return fail(st);
+      }
+      e.k = k0 + n1 + n2;
+      e.n_seeded = 0;
+      if ((st = ritz_step(c, &e, n_eig)) != OVL_OK) return fail(st);
+    }
+    ns = std::min(e.k, n_eig);
+    if ((st = defl_store(c, d, e.V, ns, mu)) != OVL_OK) return fail(st);
+    // generations: the previous round moves back, this one becomes the newest
+    if (n1 > 0) {
+      if ((st = copy_convert(c, *g1v, 0, *g2v, 0, n1)) != OVL_OK) return fail(st);
+      if ((st = copy_convert(c, *g1w, 0, *g2w, 0, n1)) != OVL_OK) return fail(st);
+    }
+    n2 = n1;
+    if ((st = copy_convert(c, d->v, 0, *g1v, 0, ns)) != OVL_OK) return fail(st);
+    if ((st = copy_convert(c, d->w, 0, *g1w, 0, ns)) != OVL_OK) return fail(st);
+    n1 = ns;
+    double rmax = 0.0;
+    for (int i = 0; i < ns; ++i) rmax = std::max(rmax, d->res[i]);
+    if (ns >= n_eig && rmax <= res_tol) break;
+    // restart from SUMR's last basis vector
+    auto it = c->ws.find("s_q");
+    if (it == c->ws.end()) break;
+    if ((st = copy_convert(c, it->second, 0, *q0, 0, 1)) != OVL_OK) return fail(st);
+  }
+  OVL_CUDA(c, cudaStreamSynchronize(c->st));
+  for (const char* nm : {"e_V", "e_W", "e_VD", "e_T", "es_q0", "es_x", "es_g1v", "es_g1w", "es_g2v", "es_g2w"}) {
+    auto it = c->ws.find(nm);
+    if (it != c->ws.end()) free_field(it->second);
+  }
+  if (steps_done) *steps_done = total;
+  *defl = d;
+  return OVL_OK;
 }
 
 extern "C" ovl_status ovl_defl_info(const ovl_defl* d, int* n, double* ritz, double* residuals) {

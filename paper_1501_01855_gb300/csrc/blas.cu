@@ -280,6 +280,81 @@ void launch_sumr_update(int p, const double* sc, const int* active, SpinorRef x,
     sumr_update_kernel<P32><<<sh.grid(), sh.block(), 0, st>>>(sc, active, x, q, qt, pv, S, u, nrhs, V, sh.nsb, sh.ngr, partials);
 }
 
+// ---------------------------------------------------------------- multi-mass SUMR step
+// One Alg. 1 basis per source shared by nm masses (rho_k + V has the Krylov space of V):
+// for every active system (k, j) = k ns + j the per-mass update of p, S and x with its own
+// coefficients sc[18 (k ns + j) ...] (the layout of sumr_update), then the shared
+// q, q~ update of source j with scq[6 j ...] = (gamma_j, 1/sigma_j, sigma_j). partials
+// {||q||^2} per source.
+template <int P>
+__global__ void __launch_bounds__(256) sumr_mm_update_kernel(const double* sc, const double* scq, const int* active,
+                                                             const int* qactive, SpinorRef x, SpinorRef q,
+                                                             SpinorRef qt, SpinorRef pv, SpinorRef S, SpinorRef u,
+                                                             int ns, int nm, int V, int nsb, int ngr,
+                                                             double* partials) {
+  using T = typename Real<P>::T;
+  __shared__ double red[4 * (BX / 32) * 2];
+  SITE_RHS_INDEX();
+  const int j = rhs;
+  double nq[2] = {0.0, 0.0};
+  if (s < V && j < ns && qactive[j]) {
+    cpx<T> qv[12], qtv[12], uv[12];
+    load_spinor_as<P, T>(q, j, s, qv);
+    for (int k = 0; k < nm; ++k) {
+      const int sys = k * ns + j;
+      if (!active[sys]) continue;
+      const double* c = sc + 18 * sys;
+      const cpx<T> Rm1 = cmk((T)c[0], (T)c[1]), gs = cmk((T)c[2], (T)c[3]), iR = cmk((T)c[4], (T)c[5]);
+      const cpx<T> sgp = cmk((T)c[6], (T)c[7]), zm1 = cmk((T)c[8], (T)c[9]), gj = cmk((T)c[10], (T)c[11]);
+      cpx<T> pvv[12], Sv[12], xv[12];
+      load_spinor_as<P, T>(pv, sys, s, pvv);
+      load_spinor_as<P, T>(S, sys, s, Sv);
+      load_spinor_as<P, T>(x, sys, s, xv);
+#pragma unroll
+      for (int m = 0; m < 12; ++m) {
+        const cpx<T> pn = (qv[m] - Rm1 * pvv[m] + gs * Sv[m]) * iR;
+        Sv[m] = sgp * Sv[m] + zm1 * pvv[m];
+        pvv[m] = pn;
+        xv[m] = xv[m] + gj * pn;
+      }
+      store_spinor_as<P, T>(pv, sys, s, pvv);
+      store_spinor_as<P, T>(S, sys, s, Sv);
+      store_spinor_as<P, T>(x, sys, s, xv);
+    }
+    load_spinor_as<P, T>(qt, j, s, qtv);
+    load_spinor_as<P, T>(u, j, s, uv);
+    const double* cq = scq + 6 * j;
+    const cpx<T> gam = cmk((T)cq[0], (T)cq[1]), isg = cmk((T)cq[2], (T)cq[3]), sg = cmk((T)cq[4], (T)cq[5]);
+#pragma unroll
+    for (int m = 0; m < 12; ++m) {
+      const cpx<T> qn = (uv[m] + gam * qtv[m]) * isg;
+      qtv[m] = sg * qtv[m] + cmulc(gam, qn);
+      qv[m] = qn;
+      nq[0] += (double)norm2(qn);
+    }
+    store_spinor_as<P, T>(q, j, s, qv);
+    store_spinor_as<P, T>(qt, j, s, qtv);
+  }
+  if (partials != nullptr) {
+    block_reduce_rows<2>(nq, red);
+    if (threadIdx.x == 0 && j < ns) {
+      partials[((size_t)j * nsb + sb) * NVRED + 0] = nq[0];
+      partials[((size_t)j * nsb + sb) * NVRED + 1] = 0.0;
+    }
+  }
+}
+void launch_sumr_mm_update(int p, const double* sc, const double* scq, const int* active, const int* qactive,
+                           SpinorRef x, SpinorRef q, SpinorRef qt, SpinorRef pv, SpinorRef S, SpinorRef u, int ns,
+                           int nm, int V, double* partials, cudaStream_t st) {
+  Shape sh = make_shape(V, ns);
+  if (p == P64)
+    sumr_mm_update_kernel<P64><<<sh.grid(), sh.block(), 0, st>>>(sc, scq, active, qactive, x, q, qt, pv, S, u, ns,
+                                                                  nm, V, sh.nsb, sh.ngr, partials);
+  else
+    sumr_mm_update_kernel<P32><<<sh.grid(), sh.block(), 0, st>>>(sc, scq, active, qactive, x, q, qt, pv, S, u, ns,
+                                                                  nm, V, sh.nsb, sh.ngr, partials);
+}
+
 // ---------------------------------------------------------------- Gram block
 // G[i, j] = sum over sites of (A_i, g5? B_j). Grid: (tiles of 16 x 16 pairs) x
 // (site ranges); each block stages SC sites of its 16 A and 16 B vectors in shared

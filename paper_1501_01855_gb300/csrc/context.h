@@ -80,7 +80,10 @@ struct ovl_ctx {
   double* lz_hist = nullptr;     // alpha_j and beta_j histories, 2 * lz_n * lz_cap doubles
   double* lz_Y = nullptr;        // per-pole tridiagonal solves, lz_n * npoles * 2 lz_cap doubles
   double* lz_coefW = nullptr;    // coefficients of the stored vectors, lz_n * lz_cap doubles
+  unsigned int* lz_ctr = nullptr;  // arrival counters of the fused scalar steps, lz_n
   int lz_cap = 0;
+  void* lz_pool = nullptr;       // stored Lanczos bases of every sign precision (one at a time)
+  size_t lz_pool_bytes = 0;
   int lz_kmax[4][17] = {{0}};    // most Lanczos steps seen per sign mode and decade of eta
   double* hpin = nullptr;        // pinned host staging for scalars, 64 * 4096 doubles
   void* hstage = nullptr;        // pinned host staging for spinor copies
@@ -136,6 +139,12 @@ void free_field(Field& f);
 ovl_status ensure_partials(ovl_ctx* c, int nrhs);
 ovl_status ensure_ms(ovl_ctx* c, int nrhs);
 ovl_status ensure_lz(ovl_ctx* c, int nrhs, int cap);
+// a view of n fields of precision prec over the context's basis pool (grown on demand; the
+// view is not owned and must not be passed to free_field)
+ovl_status lz_pool_field(ovl_ctx* c, int prec, int n, Field* out);
+// free every cached workspace, graph and pool of the context (what the next call needs is
+// allocated again)
+void trim_workspaces(ovl_ctx* c);
 ovl_status ensure_stage(ovl_ctx* c, size_t bytes);
 ovl_status ensure_work(ovl_ctx* c, size_t ndoubles);
 

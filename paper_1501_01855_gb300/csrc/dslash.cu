@@ -393,9 +393,134 @@ struct DArgs {
   double c1, c2;
   const double* coef;
   int herm;
-  int variant;   // 0: thread per site, 1: direction split, 2: 4D tiles
-  const LzRhs* lz;
+  int variant;   // 0: thread per site, 1: direction split, 2: 4D tiles, 3: lane pairs
+  LzRhs* lz;
+  LzCtl lzc;
 };
+
+// ---- the scalar step of the stored-basis Lanczos, fused into its Wilson launches -------
+// Called by the whole block for a system whose last partial sum this block wrote. The
+// sum over the site-block partials runs in a fixed order (thread-strided, then a fixed
+// tree), so the result does not depend on which block came last.
+__device__ __forceinline__ double lz_block_sum(const double* partials, int nsb, int rhs, double* sm) {
+  const int tid = threadIdx.y * blockDim.x + threadIdx.x, nt = blockDim.x * blockDim.y;
+  double v = 0.0;
+  for (int b = tid; b < nsb; b += nt) v += __ldcg(partials + ((size_t)rhs * nsb + b) * NVRED);
+  sm[tid] = v;
+  for (int i = nt + tid; i < 256; i += nt) sm[i] = 0.0;
+  __syncthreads();
+  for (int o = 128; o > 0; o >>= 1) {
+    if (tid < o) sm[tid] += sm[tid + o];
+    __syncthreads();
+  }
+  const double r = sm[0];
+  __syncthreads();
+  return r;
+}
+
+template <int MODE>
+__device__ void lz_finish(const DArgs& a, int rhs) {
+  __shared__ double sm[256], em[256];
+  const int tid = threadIdx.y * blockDim.x + threadIdx.x, nt = blockDim.x * blockDim.y;
+  LzRhs& L = a.lz[rhs];
+  const bool skip = L.done != 0;   // read by every thread before any write below
+  __syncthreads();
+  if (!skip) {
+    const double tot = lz_block_sum(a.partials, a.nsb, rhs, sm);
+    if constexpr (MODE == MODE_LZK) {
+      if (tid == 0) {
+        a.lzc.ahist[(size_t)rhs * a.lzc.hcap + L.j] = tot;
+        L.alpha = tot;
+        L.a = tot * L.inv_n;
+        L.b = L.j > 0 ? L.beta_prev * L.inv_nprev : 0.0;
+        if (!(tot > 0.0) || !isfinite(tot)) {
+          L.done = 1;
+          L.status = 2;   // K^2 is positive definite: breakdown
+          L.finished = 1;
+        }
+      }
+    } else {
+      const Poles* P = a.lzc.poles;
+      const double beta = sqrt(tot);
+      const int j = L.j;
+      const double alpha = L.alpha, bp = L.beta_prev;
+      double e = 0.0, m = 0.0;
+      for (int i = tid; i < P->n; i += nt) {
+        const double sg = P->sigma0 + P->ds[i];
+        const double d = alpha + sg - (j > 0 ? bp * bp / L.d[i] : 0.0);
+        L.d[i] = d;
+        L.rho[i] *= beta / d;
+        const double ei = fabs(L.w[i]) * P->gbound[i] * L.rho[i];
+        e += ei;
+        m = fmax(m, ei);
+      }
+      sm[tid] = e;
+      em[tid] = m;
+      for (int i = nt + tid; i < 256; i += nt) sm[i] = em[i] = 0.0;
+      __syncthreads();
+      for (int o = 128; o > 0; o >>= 1) {
+        if (tid < o) {
+          sm[tid] += sm[tid + o];
+          em[tid] = fmax(em[tid], em[tid + o]);
+        }
+        __syncthreads();
+      }
+      if (tid == 0) {
+        a.lzc.bhist[(size_t)rhs * a.lzc.hcap + j] = beta;
+        L.err = sm[0];
+        L.total += 1;
+        L.w_reads += (j > 0 ? 2 : 1);
+        L.inv_nprev = L.inv_n;
+        L.inv_n = beta > 0.0 ? 1.0 / beta : 0.0;
+        L.beta_prev = beta;
+        L.j = j + 1;
+        if (!isfinite(beta) || !isfinite(sm[0])) {
+          L.done = 1;
+          L.status = 2;
+          L.finished = 1;
+        } else if ((L.even ? em[0] * P->n <= L.thr : sm[0] <= L.thr) || beta == 0.0) {
+          // within budget, or an invariant subspace (the Galerkin solutions are exact)
+          L.done = 1;
+          L.status = 0;
+          L.finished = 1;
+        } else if (L.total >= L.maxit) {
+          L.done = 1;
+          L.status = 1;
+          L.finished = 1;
+        } else if (L.j + 1 > L.cap - 1) {
+          L.done = 1;
+          L.status = 3;   // W_{j+2} would not fit: restart from W_{j+1}
+        }
+      }
+    }
+  }
+  if (tid == 0) a.lzc.ctr[rhs] = 0u;
+  __syncthreads();
+}
+
+// After the block's partial sums are written (by thread x = 0 of each row y, for system
+// rhs_y): count the block in, and finish every system for which it came last. nblk: blocks
+// that write partials for one system. Every thread of the block calls this.
+template <int MODE>
+__device__ __forceinline__ void lz_arrive(const DArgs& a, int rhs_row, int nblk) {
+  __shared__ int last[8], rows[8];
+  if (threadIdx.x == 0) {
+    int f = 0;
+    if (rhs_row < a.nrhs) {
+      __threadfence();   // this row's partial sum before the count
+      f = atomicAdd(&a.lzc.ctr[rhs_row], 1u) == (unsigned)(nblk - 1) ? 1 : 0;
+    }
+    last[threadIdx.y] = f;
+    rows[threadIdx.y] = rhs_row;
+  }
+  __syncthreads();
+  for (int y = 0; y < (int)blockDim.y; ++y) {
+    if (last[y]) {   // shared, so the same for every thread of the block
+      __threadfence();
+      lz_finish<MODE>(a, rows[y]);
+    }
+  }
+}
 
 // Epilogue shared by both kernel variants: acc holds the hop sum of site s; v gets this
 // thread's contributions to the NVRED partial sums (see the mode list at the top).
@@ -620,6 +745,9 @@ __global__ void __launch_bounds__(256) __maxnreg__(MaxReg<PL>::v) wilson_kernel(
       }
     }
   }
+  if constexpr (MODE == MODE_LZK || MODE == MODE_LZL) {
+    if (a.lzc.ctr != nullptr) lz_arrive<MODE>(a, rhs, TILED ? (int)gridDim.x : a.nsb);
+  }
 }
 
 // ---- variant 3 (double-float only): two threads per (site, system) ----------------------
@@ -807,6 +935,9 @@ __global__ void __maxnreg__(OVL_WILSON_REG_PAIR) wilson_pair_kernel(const DArgs 
       for (int j = 0; j < NVRED; ++j) a.partials[((size_t)rhs * a.nsb + sb) * NVRED + j] = tot[j];
     }
   }
+  if constexpr (MODE == MODE_LZK || MODE == MODE_LZL) {
+    if (a.lzc.ctr != nullptr) lz_arrive<MODE>(a, rhs, a.nsb);
+  }
 }
 
 // true when the lattice can be covered by whole variant-2 tiles
@@ -869,6 +1000,9 @@ __global__ void __launch_bounds__(4 * BX) __maxnreg__(MaxReg<PL>::v) wilson_spli
       for (int j = 0; j < NVRED; ++j) a.partials[((size_t)rhs * a.nsb + sb) * NVRED + j] = tot[j];
     }
   }
+  if constexpr (MODE == MODE_LZK || MODE == MODE_LZL) {
+    if (a.lzc.ctr != nullptr) lz_arrive<MODE>(a, rhs, a.nsb);
+  }
 }
 
 Shape make_shape(int V, int nrhs) {
@@ -920,6 +1054,7 @@ static DArgs base_args(const Geom& g, double kappa, LinkRef links, int nrhs) {
   a.herm = 0;
   a.variant = links.variant;
   a.lz = nullptr;
+  a.lzc = LzCtl{nullptr, nullptr, nullptr, nullptr, 0, nullptr};
   return a;
 }
 
@@ -959,12 +1094,13 @@ void launch_wilson_mscg_r(int pt, int plink, int pr, int pp, const Geom& g, doub
 }
 
 void launch_wilson_lzK(int pw, int plink, int pt, const Geom& g, double kappa, LinkRef links, SpinorRef W,
-                       SpinorRef t, int nrhs, double* partials, const LzRhs* lz, cudaStream_t st) {
+                       SpinorRef t, int nrhs, double* partials, const LzCtl& ctl, cudaStream_t st) {
   DArgs a = base_args(g, kappa, links, nrhs);
   a.in = W;
   a.out = t;
   a.partials = partials;
-  a.lz = lz;
+  a.lz = ctl.lz;
+  a.lzc = ctl;
   if (pw == P64 && plink == P64 && pt == P64) run<MODE_LZK, P64, P64, P64, P64, P64>(a, st);
   else if (pw == P32 && plink == P32 && pt == P32) run<MODE_LZK, P32, P32, P32, P32, P32>(a, st);
   else if (pw == P16 && plink == P16 && pt == P16) run<MODE_LZK, P16, P16, P16, P16, P16>(a, st);
@@ -973,13 +1109,14 @@ void launch_wilson_lzK(int pw, int plink, int pt, const Geom& g, double kappa, L
 }
 
 void launch_wilson_lzL(int pt, int plink, int pw, const Geom& g, double kappa, LinkRef links, SpinorRef t,
-                       SpinorRef W, int nrhs, double* partials, const LzRhs* lz, cudaStream_t st) {
+                       SpinorRef W, int nrhs, double* partials, const LzCtl& ctl, cudaStream_t st) {
   DArgs a = base_args(g, kappa, links, nrhs);
   a.in = t;
   a.out = W;
   a.aux1 = W;
   a.partials = partials;
-  a.lz = lz;
+  a.lz = ctl.lz;
+  a.lzc = ctl;
   if (pt == P64 && plink == P64 && pw == P64) run<MODE_LZL, P64, P64, P64, P64, P64>(a, st);
   else if (pt == P32 && plink == P32 && pw == P32) run<MODE_LZL, P32, P32, P32, P32, P32>(a, st);
   else if (pt == P16 && plink == P16 && pw == P16) run<MODE_LZL, P16, P16, P16, P16, P16>(a, st);

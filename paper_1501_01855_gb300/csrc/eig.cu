@@ -1,4 +1,4 @@
-// eigSUMR accumulation (Sec. 5, Algs. 5-6). While the middle SUMR solve builds
+// eigSUMR and eigCG accumulation (Sec. 5, Algs. 5-6). While the middle SUMR solve builds
 // its Krylov basis, every step stores v_k = q_j and w_k = V q_j (V = gamma5 eps(K)),
 // so that v^D_k = (1-mu)/2 w_k + (1+mu)/2 q_j = D q_j (Alg. 5). When k reaches the
 // basis size m the Ritz recalculation of Alg. 6 runs:
@@ -228,6 +228,46 @@ ovl_status ritz_step(ovl_ctx* c, EigState* e, int keep, bool restart) {
   cap = std::min(cap, 0.05 * std::sqrt(lmin));
   e->eta_cap = std::min(std::max(cap, 1e-10), c->P.eta_floor);
   if (e->eig) e->eig->eta_cap = e->eta_cap;
+  return OVL_OK;
+}
+
+// eigCG (Sec. 5): system 0's residual directions of the middle relCG solve feed the basis.
+// v = (t_j - beta_{j-1} t_{j-1}) / ||r_j|| is Hhat^-1 r_j (r_j the CG residual; with no
+// deflation Hhat = 1 and these are the Lanczos vectors of H^2), and its
+// v^D = D v = gamma5 (z_j - beta_{j-1} z_{j-1}) / ||r_j||; the basis keeps
+// w = gamma5 eps(K) v = (2 v^D - (1+mu) v) / (1-mu), the form the Ritz step and the
+// deflation space use (D v = (1+mu)/2 v + (1-mu)/2 w).
+ovl_status eig_cg_hook(ovl_ctx* c, void* data, const Field& t, const Field& z,
+                       const std::vector<std::complex<double>>& beta_prev, const std::vector<double>& rnorm,
+                       int iter) {
+  EigState* e = static_cast<EigState*>(data);
+  const double rn = rnorm.empty() ? 0.0 : rnorm[0];
+  if (!(rn > 0.0) || !std::isfinite(rn)) return OVL_OK;
+  const double mu = e->mu;
+  const cd bp = iter > 0 ? beta_prev[0] : cd(0.0);
+  const cd inv = 1.0 / rn;
+  Field* tmp;
+  OVL_TRY(get_field(c, "e_tmp", e->prec, 1, &tmp));
+  // v = (t - bp t_prev) / ||r||
+  std::vector<cd> a1(1, inv), b1(1, -bp * inv), zero(1, 0.0);
+  if (iter > 0) {
+    OVL_TRY(axpby_batch(c, a1, t, 0, b1, *e->Tprev, 0, *e->V, e->k, 1));
+  } else {
+    OVL_TRY(axpby_batch(c, a1, t, 0, zero, t, 0, *e->V, e->k, 1));
+  }
+  // v^D = gamma5 (z - bp z_prev) / ||r||, then w = (2 v^D - (1+mu) v) / (1-mu)
+  if (iter > 0) {
+    OVL_TRY(axpby_batch(c, a1, z, 0, b1, *e->Zprev, 0, *tmp, 0, 1));
+  } else {
+    OVL_TRY(axpby_batch(c, a1, z, 0, zero, z, 0, *tmp, 0, 1));
+  }
+  launch_gamma5(e->prec, tmp->ref(), 1, c->V, c->st);
+  std::vector<cd> a2(1, 2.0 / (1.0 - mu)), b2(1, -(1.0 + mu) / (1.0 - mu));
+  OVL_TRY(axpby_batch(c, a2, *tmp, 0, b2, *e->V, e->k, *e->W, e->k, 1));
+  OVL_TRY(copy_convert(c, t, 0, *e->Tprev, 0, 1));
+  OVL_TRY(copy_convert(c, z, 0, *e->Zprev, 0, 1));
+  e->k += 1;
+  if (e->k == e->m) OVL_TRY(ritz_step(c, e, e->n_eig, true));
   return OVL_OK;
 }
 

@@ -20,11 +20,16 @@ struct EigState {
   Field* V = nullptr;
   Field* W = nullptr;
   EigHook* eig = nullptr;
+  // eigCG: the previous step's t = Hhat^-1 p and z = H t of system 0
+  Field* Tprev = nullptr;
+  Field* Zprev = nullptr;
 };
 
 // keep the lowest `keep` Ritz vectors; restart = a basis restart inside the solve (also
 // keeps the lowest Ritz vectors of the basis without its newest vector)
 ovl_status ritz_step(ovl_ctx* c, EigState* e, int keep, bool restart = false);
 ovl_status eig_hook(ovl_ctx* c, void* data, const Field& q, const Field& u, int iter);
+ovl_status eig_cg_hook(ovl_ctx* c, void* data, const Field& t, const Field& z,
+                       const std::vector<std::complex<double>>& beta_prev, const std::vector<double>& rnorm, int iter);
 
 }  // namespace ovl

@@ -117,16 +117,57 @@ ovl_status ensure_lz(ovl_ctx* c, int nrhs, int cap) {
   if (c->lz_hist) cudaFree(c->lz_hist);
   if (c->lz_Y) cudaFree(c->lz_Y);
   if (c->lz_coefW) cudaFree(c->lz_coefW);
+  if (c->lz_ctr) cudaFree(c->lz_ctr);
   c->lz = nullptr;
   c->lz_hist = c->lz_Y = c->lz_coefW = nullptr;
+  c->lz_ctr = nullptr;
   c->lz_n = c->lz_cap = 0;
   OVL_CUDA(c, cudaMalloc((void**)&c->lz, sizeof(LzRhs) * n));
+  OVL_CUDA(c, cudaMalloc((void**)&c->lz_ctr, sizeof(unsigned int) * n));
+  OVL_CUDA(c, cudaMemsetAsync(c->lz_ctr, 0, sizeof(unsigned int) * n, c->st));
   OVL_CUDA(c, cudaMalloc((void**)&c->lz_hist, sizeof(double) * 2 * (size_t)n * k));
   OVL_CUDA(c, cudaMalloc((void**)&c->lz_Y, sizeof(double) * (size_t)n * c->npoles * 2 * k));
   OVL_CUDA(c, cudaMalloc((void**)&c->lz_coefW, sizeof(double) * (size_t)n * k));
   c->lz_n = n;
   c->lz_cap = k;
   return OVL_OK;
+}
+
+ovl_status lz_pool_field(ovl_ctx* c, int prec, int n, Field* out) {
+  const size_t data = (size_t)spinor_bytes(prec) * c->V * n;
+  const size_t norms = prec == P16 ? sizeof(float) * (size_t)c->V * n : 0;
+  const size_t need = data + norms;
+  if (need > c->lz_pool_bytes) {
+    cudaStreamSynchronize(c->st);
+    if (c->lz_pool) cudaFree(c->lz_pool);
+    c->lz_pool = nullptr;
+    c->lz_pool_bytes = 0;
+    if (cudaMalloc(&c->lz_pool, need) != cudaSuccess) {
+      cudaGetLastError();
+      c->lz_pool = nullptr;
+      return set_err(c, OVL_ENOMEM, "cudaMalloc failed for the stored Lanczos basis");
+    }
+    c->lz_pool_bytes = need;
+  }
+  out->prec = prec;
+  out->n = n;
+  out->V = c->V;
+  out->data = c->lz_pool;
+  out->norm = prec == P16 ? reinterpret_cast<float*>(static_cast<char*>(c->lz_pool) + data) : nullptr;
+  return OVL_OK;
+}
+
+void trim_workspaces(ovl_ctx* c) {
+  if (c->st) cudaStreamSynchronize(c->st);
+  else cudaDeviceSynchronize();
+  for (auto& kv : c->ws) free_field(kv.second);
+  c->ws.clear();
+  if (c->lz_pool) cudaFree(c->lz_pool);
+  c->lz_pool = nullptr;
+  c->lz_pool_bytes = 0;
+  for (auto& g : c->graphs)
+    if (g.exec) cudaGraphExecDestroy(g.exec);
+  c->graphs.clear();
 }
 
 ovl_status ensure_stage(ovl_ctx* c, size_t bytes) {
@@ -398,7 +439,15 @@ ovl_status sign_op(ovl_ctx* c, int mode, const Field& v, int voff, Field& out, i
   if (!c->exact_rational) emin = std::max(emin, c->delta);
   const int cap = lz_cap_for(c, mode, emin);
   const double per_lz = (double)cap * c->V * (spinor_bytes(PP) + (PP == P16 ? 4.0 : 0.0));
-  const int n_fit = (int)std::min(1e9, c->P.basis_gb * 1e9 / per_lz);
+  // the basis budget: params.basis_gb, and never more than 85% of what the device has free
+  // (counting the pool this context already holds)
+  double budget = c->P.basis_gb * 1e9;
+  {
+    size_t fr = 0, tot = 0;
+    if (cudaMemGetInfo(&fr, &tot) == cudaSuccess) budget = std::min(budget, 0.85 * ((double)fr + c->lz_pool_bytes));
+    else cudaGetLastError();
+  }
+  const int n_fit = (int)std::min(1e9, budget / per_lz);
   const bool use_lz = c->P.sign_method == 2 || (c->P.sign_method == 0 && n_fit >= std::min(n, c->P.batch_max));
   if (use_lz) {
     const int nb = std::max(1, std::min(c->P.batch_max, n_fit));
@@ -464,8 +513,8 @@ static ovl_status upload_eta_coef(ovl_ctx* c, int n, const double* eta, const do
 }
 
 // One batch of the sign function by stored-basis Lanczos (lanczos.cu): cycles of at most
-// cap steps, each step the two Wilson launches (MODE_LZK, MODE_LZL) and two one-block
-// scalar kernels, run as cached CUDA graphs of kGraphIters steps without profiling;
+// cap steps, each step the two Wilson launches (MODE_LZK, MODE_LZL) whose last block per
+// system runs the scalar step, as cached CUDA graphs of kGraphIters steps without profiling;
 // then the per-pole tridiagonal solves, one pass over the stored basis, and the final
 // Wilson application with the overlap / sign epilogue.
 static ovl_status sign_op_batch_lz(ovl_ctx* c, int mode, const Field& v, int voff, Field& out, int ooff, int n,
@@ -476,8 +525,10 @@ static ovl_status sign_op_batch_lz(ovl_ctx* c, int mode, const Field& v, int vof
   const int PB = PL;                                                      // basis and t
   const int V = c->V;
   const std::string tag = std::to_string(mode);
-  Field *W, *t, *y;
-  OVL_TRY(get_field(c, "lz_W" + tag, PB, cap * n, &W));
+  Field Wv;
+  Field* W = &Wv;
+  Field *t, *y;
+  OVL_TRY(lz_pool_field(c, PB, cap * n, &Wv));
   OVL_TRY(get_field(c, "lz_t" + tag, PB, n, &t));
   OVL_TRY(get_field(c, "lz_y" + tag, PR, n, &y));
   OVL_TRY(ensure_partials(c, n));
@@ -492,6 +543,7 @@ static ovl_status sign_op_batch_lz(ovl_ctx* c, int mode, const Field& v, int vof
   double* ahist = c->lz_hist;
   double* bhist = c->lz_hist + (size_t)c->lz_n * c->lz_cap;
   const int hcap = c->lz_cap;   // row length of the histories and coefficient buffers
+  const LzCtl ctl{c->lz, c->lz_ctr, ahist, bhist, hcap, c->dpoles};
   ProfPair pp;
 
   prof_begin(c, 4, &pp);
@@ -512,10 +564,8 @@ static ovl_status sign_op_batch_lz(ovl_ctx* c, int mode, const Field& v, int vof
         (unsigned long long)L.variant};
     OVL_TRY(ms_graph(c, key, &gexec, [&](cudaStream_t cs) {
       for (int k = 0; k < kGraphIters; ++k) {
-        launch_wilson_lzK(PB, PL, PB, c->g, c->kappa, L, W->ref(), t->ref(), n, c->partials, c->lz, cs);
-        launch_lz_scalar1(c->lz, c->partials, sh.nsb, n, ahist, hcap, cs);
-        launch_wilson_lzL(PB, PL, PB, c->g, c->kappa, L, t->ref(), W->ref(), n, c->partials, c->lz, cs);
-        launch_lz_scalar2(c->lz, c->partials, sh.nsb, n, bhist, hcap, c->dpoles, cs);
+        launch_wilson_lzK(PB, PL, PB, c->g, c->kappa, L, W->ref(), t->ref(), n, c->partials, ctl, cs);
+        launch_wilson_lzL(PB, PL, PB, c->g, c->kappa, L, t->ref(), W->ref(), n, c->partials, ctl, cs);
       }
     }));
   }
@@ -533,16 +583,10 @@ static ovl_status sign_op_batch_lz(ovl_ctx* c, int mode, const Field& v, int vof
       } else {
         for (int k = 0; k < chunk; ++k) {
           prof_begin(c, wcls, &pp);
-          launch_wilson_lzK(PB, PL, PB, c->g, c->kappa, L, W->ref(), t->ref(), n, c->partials, c->lz, c->st);
-          prof_end(c, &pp, 0.0);
-          prof_begin(c, 5, &pp);
-          launch_lz_scalar1(c->lz, c->partials, sh.nsb, n, ahist, hcap, c->st);
+          launch_wilson_lzK(PB, PL, PB, c->g, c->kappa, L, W->ref(), t->ref(), n, c->partials, ctl, c->st);
           prof_end(c, &pp, 0.0);
           prof_begin(c, wcls, &pp);
-          launch_wilson_lzL(PB, PL, PB, c->g, c->kappa, L, t->ref(), W->ref(), n, c->partials, c->lz, c->st);
-          prof_end(c, &pp, 0.0);
-          prof_begin(c, 5, &pp);
-          launch_lz_scalar2(c->lz, c->partials, sh.nsb, n, bhist, hcap, c->dpoles, c->st);
+          launch_wilson_lzL(PB, PL, PB, c->g, c->kappa, L, t->ref(), W->ref(), n, c->partials, ctl, c->st);
           prof_end(c, &pp, 0.0);
         }
       }

@@ -10,13 +10,15 @@
 // where P-+ are the half-spinor projections of (1 -+ gamma_mu) (gamma5 (1 -+ gamma_mu) sandwiched
 // between x and y reduces to them). The result G_link is defined by dS = 2 Re sum conj(G) dU.
 //
-// Every shifted solution comes from one multi-shift CG per source that keeps the
-// individual x_i (they are stored; at the lattice sizes here they fit in HBM).
+// Every shifted solution comes from a multi-shift CG that keeps the individual x_i: all
+// poles at once when their fields fit in HBM, else in groups of poles solved one after
+// the other (recomputed, not stored; params.force_pole_group).
 // The outer-product kernel runs over all poles in one pass with an FP64
 // accumulator per link (compute in FP64, or FP32 with the mixed setting).
 #include <stdio.h>
 #include <string.h>
 
+#include <algorithm>
 #include <cmath>
 
 #include "context.h"
@@ -145,9 +147,11 @@ void launch_force(int fp32, const Geom& g, double kappa, SpinorRef psi, SpinorRe
   else force_kernel<double><<<nb, 128, 0, st>>>(g, kappa, psi, a, Ka, b, Kb, npoles, coef, G);
 }
 
-// All shifted solutions (K^2 + sigma_i) x_i = v to relative residual tol, FP64.
-static ovl_status shifted_solutions(ovl_ctx* c, const Field& v, Field& xs, double tol, Poles* dpol) {
-  const int np = c->npoles, V = c->V;
+// The shifted solutions (K^2 + sigma_i) x_i = v of one group of np poles (device data dpol,
+// base shift sigma0 = the group's smallest) to relative residual tol, FP64.
+static ovl_status shifted_solutions(ovl_ctx* c, const Field& v, Field& xs, double tol, Poles* dpol, int np,
+                                    double sigma0) {
+  const int V = c->V;
   Field *r, *pb;
   OVL_TRY(get_field(c, "f_r", P64, 1, &r));
   OVL_TRY(get_field(c, "f_p", P64, np, &pb));
@@ -172,8 +176,8 @@ static ovl_status shifted_solutions(ovl_ctx* c, const Field& v, Field& xs, doubl
     for (int k = 0; k < 8; ++k) {
       launch_wilson_K(P64, P64, P64, c->g, c->kappa, L, pb->ref(), t->ref(), 1, c->partials, c->ms, c->st);
       launch_ms_scalar1(c->ms, c->partials, sh.nsb, 1, dpol, c->st);
-      launch_wilson_mscg_r(P64, P64, P64, P64, c->g, c->kappa, L, t->ref(), pb->ref(), r->ref(), 1,
-                           c->hpoles.sigma0, c->partials, c->ms, c->st);
+      launch_wilson_mscg_r(P64, P64, P64, P64, c->g, c->kappa, L, t->ref(), pb->ref(), r->ref(), 1, sigma0,
+                           c->partials, c->ms, c->st);
       launch_ms_scalar2(c->ms, c->partials, sh.nsb, 1, dpol, c->st);
       launch_ms_update_x(r->ref(), pb->ref(), xs.ref(), np, 1, V, c->ms, c->st);
     }
@@ -235,27 +239,21 @@ ovl_status force_compute(ovl_ctx* c, double mu, const Field& phi, double tol, do
   std::vector<double> eta(1, tol * 0.1);
   OVL_TRY(overlap_apply_batch(c, *chi, 0, *psi, 0, 1, mus, eta, 1, SIGN64, nullptr));
   OVL_TRY(wilson_apply_field(c, P64, *psi, 0, *Kpsi, 0, 1));
-  // all shifted solutions for chi and K psi, unit pole weights for the stopping rule
-  Poles fp = c->hpoles;
-  for (int i = 0; i < np; ++i) {
-    fp.omega[i] = 1.0;
-    fp.gbound[i] = 1.0;
+  // The shifted solutions of chi and K psi (unit pole weights for the stopping rule), in
+  // groups of g poles: all at once when their 5 g fields (A, K A, B, K B and the
+  // multi-shift directions) fit in half the free device memory, else as many as fit; each
+  // group is solved afresh (recomputed rather than stored) and its terms added to G.
+  int g = c->P.force_pole_group;
+  if (g <= 0) {
+    size_t fr = 0, tot = 0;
+    if (cudaMemGetInfo(&fr, &tot) != cudaSuccess) {
+      cudaGetLastError();
+      fr = 0;
+    }
+    const double per = 5.0 * V * 192.0;
+    g = fr == 0 ? np : (int)std::max(1.0, std::min((double)np, 0.5 * (double)fr / per));
   }
-  Poles* dfp;
-  OVL_CUDA(c, cudaMalloc((void**)&dfp, sizeof(Poles)));
-  cudaMemcpy(dfp, &fp, sizeof(Poles), cudaMemcpyHostToDevice);
-  Field *A, *KA, *B, *KB;
-  ovl_status st = get_field(c, "f_A", P64, np, &A);
-  if (st == OVL_OK) st = get_field(c, "f_KA", P64, np, &KA);
-  if (st == OVL_OK) st = get_field(c, "f_B", P64, np, &B);
-  if (st == OVL_OK) st = get_field(c, "f_KB", P64, np, &KB);
-  if (st == OVL_OK) st = shifted_solutions(c, *chi, *A, tol * 0.1, dfp);
-  if (st == OVL_OK) st = shifted_solutions(c, *Kpsi, *B, tol * 0.1, dfp);
-  cudaStreamSynchronize(c->st);
-  cudaFree(dfp);
-  if (st != OVL_OK) return st;
-  OVL_TRY(wilson_apply_field(c, P64, *A, 0, *KA, 0, np));
-  OVL_TRY(wilson_apply_field(c, P64, *B, 0, *KB, 0, np));
+  g = std::min(g, np);
   std::vector<double> coef(np);
   for (int i = 0; i < np; ++i) coef[i] = -(1.0 - mu) * c->omega[i];
   const double* dcoef;
@@ -263,12 +261,43 @@ ovl_status force_compute(ovl_ctx* c, double mu, const Field& phi, double tol, do
   const size_t nG = (size_t)V * 4 * 9 * 2;
   OVL_TRY(ensure_work(c, nG));
   OVL_CUDA(c, cudaMemsetAsync(c->dwork, 0, nG * sizeof(double), c->st));
-  ProfPair pp;
-  prof_begin(c, 7, &pp);
-  launch_force(c->P.mixed ? 1 : 0, c->g, c->kappa, psi->ref(), A->ref(), KA->ref(), B->ref(), KB->ref(), np, dcoef,
-               c->dwork, c->st);
-  prof_end(c, &pp, (double)V * (192.0 * (1 + 4.0 * np) + nG / V * 8.0));
-  OVL_TRY(check_launch(c, __func__));
+  Field *A, *KA, *B, *KB;
+  OVL_TRY(get_field(c, "f_A", P64, g, &A));
+  OVL_TRY(get_field(c, "f_KA", P64, g, &KA));
+  OVL_TRY(get_field(c, "f_B", P64, g, &B));
+  OVL_TRY(get_field(c, "f_KB", P64, g, &KB));
+  Poles* dfp;
+  OVL_CUDA(c, cudaMalloc((void**)&dfp, sizeof(Poles)));
+  ovl_status st = OVL_OK;
+  for (int i0 = 0; i0 < np && st == OVL_OK; i0 += g) {
+    const int gn = std::min(g, np - i0);
+    Poles fp;
+    memset(&fp, 0, sizeof(fp));
+    fp.n = gn;
+    fp.sigma0 = c->sigma[i0];
+    for (int i = 0; i < gn; ++i) {
+      fp.ds[i] = c->sigma[i0 + i] - c->sigma[i0];
+      fp.omega[i] = 1.0;
+      fp.gbound[i] = 1.0;
+    }
+    // the previous group's kernels read dfp: update it in stream order
+    cudaStreamSynchronize(c->st);
+    cudaMemcpy(dfp, &fp, sizeof(Poles), cudaMemcpyHostToDevice);
+    st = shifted_solutions(c, *chi, *A, tol * 0.1, dfp, gn, fp.sigma0);
+    if (st == OVL_OK) st = shifted_solutions(c, *Kpsi, *B, tol * 0.1, dfp, gn, fp.sigma0);
+    if (st == OVL_OK) st = wilson_apply_field(c, P64, *A, 0, *KA, 0, gn);
+    if (st == OVL_OK) st = wilson_apply_field(c, P64, *B, 0, *KB, 0, gn);
+    if (st != OVL_OK) break;
+    ProfPair pp;
+    prof_begin(c, 7, &pp);
+    launch_force(c->P.mixed ? 1 : 0, c->g, c->kappa, psi->ref(), A->ref(), KA->ref(), B->ref(), KB->ref(), gn,
+                 dcoef + i0, c->dwork, c->st);
+    prof_end(c, &pp, (double)V * (192.0 * (1 + 4.0 * gn) + nG / V * 8.0));
+    st = check_launch(c, __func__);
+  }
+  cudaStreamSynchronize(c->st);
+  cudaFree(dfp);
+  if (st != OVL_OK) return st;
   OVL_CUDA(c, cudaMemcpyAsync(dSdU, c->dwork, nG * sizeof(double), cudaMemcpyDeviceToHost, c->st));
   OVL_CUDA(c, cudaStreamSynchronize(c->st));
   return OVL_OK;

@@ -119,20 +119,28 @@ void launch_wilson_ovl(int py, int plink, int pv, const Geom& g, double kappa, L
 // the slot, so that one captured graph serves every iteration.
 //   K mode: t = (1 / n_j) K W_j, partials {||t||^2} (alpha_j = ||K v_j||^2);
 //   L mode: W_{j+1} = K t - a W_j - b W_{j-1}, partials {||W_{j+1}||^2}.
+// The scalar step of each system runs inside the same launch: every block writes its
+// partial sums and counts itself in ctr[rhs]; the block that arrives last sums the
+// partials in a fixed order and updates the system's state (K mode: alpha_j, a, b; L mode:
+// beta_j, every pole's pivot and residual, the stopping test), then resets ctr[rhs].
+struct LzCtl {
+  LzRhs* lz;
+  unsigned int* ctr;   // per system, zero between launches
+  double* ahist;       // alpha_j, nrhs rows of hcap
+  double* bhist;       // beta_j
+  int hcap;
+  const Poles* poles;
+};
 void launch_wilson_lzK(int pw, int plink, int pt, const Geom& g, double kappa, LinkRef links, SpinorRef W,
-                       SpinorRef t, int nrhs, double* partials, const LzRhs* lz, cudaStream_t st);
+                       SpinorRef t, int nrhs, double* partials, const LzCtl& ctl, cudaStream_t st);
 void launch_wilson_lzL(int pt, int plink, int pw, const Geom& g, double kappa, LinkRef links, SpinorRef t,
-                       SpinorRef W, int nrhs, double* partials, const LzRhs* lz, cudaStream_t st);
+                       SpinorRef W, int nrhs, double* partials, const LzCtl& ctl, cudaStream_t st);
 // W_0 = v (precision conversion), y = 0, partials {||W_0||^2}
 void launch_lz_init(int pv, int pw, int py, SpinorRef v, SpinorRef W, SpinorRef y, int nrhs, int V,
                     double* partials, cudaStream_t st);
 // start a cycle from the norm partials of W_0; first = 1: weights omega_i, budget eta ||W_0||
 void launch_lz_start(LzRhs* lz, const double* partials, int nsb, int nrhs, const Poles* poles,
                      const double* eta, int maxit, int cap, int first, cudaStream_t st);
-void launch_lz_scalar1(LzRhs* lz, const double* partials, int nsb, int nrhs, double* ahist, int cap,
-                       cudaStream_t st);
-void launch_lz_scalar2(LzRhs* lz, const double* partials, int nsb, int nrhs, double* bhist, int cap,
-                       const Poles* poles, cudaStream_t st);
 // coefficients of the stored vectors in y = sum_i w_i x_i (per system, cap doubles) from
 // the tridiagonal solves; Y is scratch of nrhs * npoles * 2 cap doubles. For a system whose
 // cycle filled up, the weights of the next cycle are set too.
@@ -190,6 +198,13 @@ void launch_zero(int p, SpinorRef x, int nrhs, int V, cudaStream_t st);
 void launch_sumr_update(int p, const double* sc, const int* active, SpinorRef x, SpinorRef q, SpinorRef qt,
                         SpinorRef pv, SpinorRef S, SpinorRef u, int nrhs, int V, double* partials,
                         cudaStream_t st);
+
+// Multi-mass SUMR step: nm masses share the basis of each of ns sources (system k ns + j);
+// sc holds 18 doubles per system (as above), scq 6 per source (gamma, 1/sigma, sigma);
+// active per system, qactive per source. partials {||q||^2} per source.
+void launch_sumr_mm_update(int p, const double* sc, const double* scq, const int* active, const int* qactive,
+                           SpinorRef x, SpinorRef q, SpinorRef qt, SpinorRef pv, SpinorRef S, SpinorRef u, int ns,
+                           int nm, int V, double* partials, cudaStream_t st);
 
 // ---------------------------------------------------------------- dense blocks
 // G[i, j] += (A_i, B_j) for i < na, j < nb (complex, FP64 accumulation); A and B are

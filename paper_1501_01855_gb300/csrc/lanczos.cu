@@ -7,18 +7,18 @@
 // basis and T_k the tridiagonal matrix of the recurrence. The multi-shift CG of mscg.cu
 // carries one search direction per pole and updates all of them every step (two spinor
 // passes per active pole and step); here the basis itself is kept in HBM instead, one
-// vector per step, so that a step is the two Wilson launches and two one-block scalar
-// kernels, and y comes at the end from N_Z tridiagonal solves (scalars) and a single
+// vector per step, so that a step is two Wilson launches (their last blocks do the
+// scalar work), and y comes at the end from N_Z tridiagonal solves (scalars) and a single
 // pass over the stored vectors.
 //
-// Per step j (lz[rhs].j = j, unnormalised vectors W_l with v_l = W_l / n_l):
-//   Wilson MODE_LZK   t = K v_j,              alpha_j = ||t||^2
-//   lz_scalar1        a = alpha_j / n_j,  b = beta_{j-1} / n_{j-1}
-//   Wilson MODE_LZL   W_{j+1} = K t - a W_j - b W_{j-1},   beta_j = ||W_{j+1}|| = n_{j+1}
-//   lz_scalar2        for every pole the LDL^T pivot d_j = alpha_j + sigma_i - beta_{j-1}^2 / d_{j-1}
-//                     and the residual norm rho_i <- rho_i beta_j / d_j of its Galerkin
-//                     solution (||r_i|| = ||v|| prod_l beta_l / d_l), the error bound
-//                     sum_i |w_i| g_i rho_i and the stopping test.
+// Per step j (lz[rhs].j = j, unnormalised vectors W_l with v_l = W_l / n_l), two Wilson
+// launches whose last block per system also runs the scalar step (dslash.cu, lz_finish):
+//   MODE_LZK   t = K v_j;  alpha_j = ||t||^2,  a = alpha_j / n_j,  b = beta_{j-1} / n_{j-1}
+//   MODE_LZL   W_{j+1} = K t - a W_j - b W_{j-1};  beta_j = ||W_{j+1}|| = n_{j+1}, for every
+//              pole the LDL^T pivot d_j = alpha_j + sigma_i - beta_{j-1}^2 / d_{j-1} and the
+//              residual norm rho_i <- rho_i beta_j / d_j of its Galerkin solution
+//              (||r_i|| = ||v|| prod_l beta_l / d_l), the error bound sum_i |w_i| g_i rho_i
+//              and the stopping test.
 // The stopping rule is the one of the multi-shift CG (pole i contributes at most
 // |w_i| g_i ||r_i|| to the error of eps(K) v, g_i = max_[a,b] x / (x^2 + sigma_i)); all
 // poles keep improving until the sum is within eta ||v||.
@@ -169,95 +169,10 @@ __global__ void lz_start_kernel(LzRhs* lz, const double* partials, int nsb, cons
   }
 }
 
-__global__ void lz_scalar1_kernel(LzRhs* lz, const double* partials, int nsb, double* ahist, int cap) {
-  const int rhs = blockIdx.x;
-  LzRhs& L = lz[rhs];
-  if (L.done) return;
-  const double alpha = lz_sum_partials(partials, nsb, rhs);
-  if (threadIdx.x == 0) {
-    ahist[(size_t)rhs * cap + L.j] = alpha;
-    L.alpha = alpha;
-    L.a = alpha * L.inv_n;
-    L.b = L.j > 0 ? L.beta_prev * L.inv_nprev : 0.0;
-    if (!(alpha > 0.0) || !isfinite(alpha)) {
-      L.done = 1;
-      L.status = 2;   // K^2 is positive definite: breakdown
-      L.finished = 1;
-    }
-  }
-}
-
-__global__ void lz_scalar2_kernel(LzRhs* lz, const double* partials, int nsb, double* bhist, int cap,
-                                  const Poles* P) {
-  __shared__ double er[128], em[128];
-  const int rhs = blockIdx.x;
-  LzRhs& L = lz[rhs];
-  if (L.done) return;
-  const double beta = sqrt(lz_sum_partials(partials, nsb, rhs));
-  const int j = L.j;
-  const double alpha = L.alpha, bp = L.beta_prev;
-  double e = 0.0, m = 0.0;
-  for (int i = threadIdx.x; i < P->n; i += blockDim.x) {
-    const double sg = P->sigma0 + P->ds[i];
-    const double d = alpha + sg - (j > 0 ? bp * bp / L.d[i] : 0.0);
-    L.d[i] = d;
-    L.rho[i] *= beta / d;
-    const double ei = fabs(L.w[i]) * P->gbound[i] * L.rho[i];
-    e += ei;
-    m = fmax(m, ei);
-  }
-  er[threadIdx.x] = e;
-  em[threadIdx.x] = m;
-  __syncthreads();
-  for (int o = blockDim.x / 2; o > 0; o >>= 1) {
-    if (threadIdx.x < o) {
-      er[threadIdx.x] += er[threadIdx.x + o];
-      em[threadIdx.x] = fmax(em[threadIdx.x], em[threadIdx.x + o]);
-    }
-    __syncthreads();
-  }
-  if (threadIdx.x == 0) {
-    bhist[(size_t)rhs * cap + j] = beta;
-    L.err = er[0];
-    L.total += 1;
-    L.w_reads += (j > 0 ? 2 : 1);
-    L.inv_nprev = L.inv_n;
-    L.inv_n = beta > 0.0 ? 1.0 / beta : 0.0;
-    L.beta_prev = beta;
-    L.j = j + 1;
-    if (!isfinite(beta) || !isfinite(er[0])) {
-      L.done = 1;
-      L.status = 2;
-      L.finished = 1;
-    } else if ((L.even ? em[0] * P->n <= L.thr : er[0] <= L.thr) || beta == 0.0) {
-      // within budget, or an invariant subspace (the Galerkin solutions are exact)
-      L.done = 1;
-      L.status = 0;
-      L.finished = 1;
-    } else if (L.total >= L.maxit) {
-      L.done = 1;
-      L.status = 1;
-      L.finished = 1;
-    } else if (L.j + 1 > L.cap - 1) {
-      L.done = 1;
-      L.status = 3;   // W_{j+2} would not fit: restart from W_{j+1}
-    }
-  }
-}
-
 void launch_lz_start(LzRhs* lz, const double* partials, int nsb, int nrhs, const Poles* poles, const double* eta,
                      int maxit, int cap, int first, cudaStream_t st) {
   lz_start_kernel<<<nrhs, 128, 0, st>>>(lz, partials, nsb, poles, eta, maxit, cap, first);
 }
-void launch_lz_scalar1(LzRhs* lz, const double* partials, int nsb, int nrhs, double* ahist, int cap,
-                       cudaStream_t st) {
-  lz_scalar1_kernel<<<nrhs, 128, 0, st>>>(lz, partials, nsb, ahist, cap);
-}
-void launch_lz_scalar2(LzRhs* lz, const double* partials, int nsb, int nrhs, double* bhist, int cap,
-                       const Poles* poles, cudaStream_t st) {
-  lz_scalar2_kernel<<<nrhs, 128, 0, st>>>(lz, partials, nsb, bhist, cap, poles);
-}
-
 // ---------------------------------------------------------------- coefficients
 // One block per system. Thread i (pole) solves (T_k + sigma_i) y_i = e_1 by the LDL^T
 // factorisation of T_k + sigma_i (pivots d_l; L unit lower bidiagonal with l_l =

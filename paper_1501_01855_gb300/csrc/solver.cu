@@ -55,7 +55,8 @@ ovl_status norms_batch(ovl_ctx* c, const Field& x, int xoff, int n, std::vector<
   std::vector<double> h(2 * n);
   OVL_TRY(reduce_to_host(c, make_shape(c->V, n).nsb, n, h.data()));
   out.resize(n);
-  for (int j = 0; j < n; ++j) out[j] = std::sqrt(std::max(0.0, h[2 * j]));
+  // a NaN stays NaN (std::max(0.0, NaN) would be 0, a "perfect" norm)
+  for (int j = 0; j < n; ++j) out[j] = std::isnan(h[2 * j]) ? h[2 * j] : std::sqrt(std::max(0.0, h[2 * j]));
   return OVL_OK;
 }
 
@@ -331,6 +332,7 @@ ovl_status sumr_batch(ovl_ctx* c, const SumrCfg& cfg, int n, const std::vector<d
       e = std::min(e, cfg.floor);
       if (cfg.eta_cap > 0) e = std::min(e, cfg.eta_cap);
       if (cfg.eta_fixed > 0) e = cfg.eta_fixed;
+      if (cfg.eta_dyn) e = *cfg.eta_dyn;
       eta[j] = e;
       emin = std::min(emin, e);
     }
@@ -437,6 +439,206 @@ ovl_status sumr_batch(ovl_ctx* c, const SumrCfg& cfg, int n, const std::vector<d
   return OVL_OK;
 }
 
+// ------------------------------------------------------------------ multi-mass relSUMR
+// relSUMR for nm masses sharing the Alg. 1 basis of each of ns sources: rho_k + V has the
+// Krylov space of V whatever rho_k (Sec. 2: SUMR is adapted to many shifts without
+// effort), so q_j, q~_j, gamma_j and sigma_j, and the one sign application per step that
+// produces them, serve every mass; only the Givens QR of rho_k + B and the vectors p, S, x
+// are per mass. System k ns + j solves (rho_k + V) x = b_j from x = 0 (no deflated start:
+// that would give every mass its own residual). The relaxation follows the mass with the
+// largest residual, so that every mass gets a sign at least as accurate as it asks for.
+ovl_status sumr_multimass(ovl_ctx* c, const SumrCfg& cfg, int ns, int nm, const std::vector<double>& mus_m,
+                          const Field& b, int boff, Field& x, int xoff, SumrResult& res) {
+  const int PS = cfg.prec;
+  const int V = c->V;
+  const int n = ns * nm;
+  Field *fq, *fqt, *fp, *fS, *fu;
+  OVL_TRY(get_field(c, "s_q", PS, ns, &fq));
+  OVL_TRY(get_field(c, "s_qt", PS, ns, &fqt));
+  OVL_TRY(get_field(c, "s_p", PS, n, &fp));
+  OVL_TRY(get_field(c, "s_S", PS, n, &fS));
+  OVL_TRY(get_field(c, "s_u", PS, ns, &fu));
+  std::vector<double> rho(nm);
+  for (int k = 0; k < nm; ++k) rho[k] = (1.0 + mus_m[k]) / (1.0 - mus_m[k]);
+  OVL_TRY(copy_convert(c, b, boff, *fq, 0, ns));
+  launch_zero(x.prec, x.ref(xoff), n, V, c->st);
+  std::vector<double> bnorm;
+  OVL_TRY(norms_batch(c, b, boff, ns, bnorm));
+  {
+    std::vector<cd> a(ns), z(ns, 0.0);
+    for (int j = 0; j < ns; ++j) a[j] = bnorm[j] > 0 ? 1.0 / bnorm[j] : 0.0;
+    OVL_TRY(axpby_batch(c, a, *fq, 0, z, *fq, 0, *fq, 0, ns));
+    OVL_TRY(copy_convert(c, *fq, 0, *fqt, 0, ns));
+    launch_zero(PS, fp->ref(), n, V, c->st);
+    launch_zero(PS, fS->ref(), n, V, c->st);
+  }
+  struct St {
+    cd gprev = 0, sprev = 0;
+    double cprev = 1, sigprev = 0;
+    cd zeta = 1.0;
+    cd ghat;
+    bool active = true;
+    int it = 0;
+  };
+  std::vector<St> S(n);
+  std::vector<char> qact(ns, 0);
+  res.iters.assign(n, 0);
+  res.resid.assign(n, 0.0);
+  res.wcalls.assign(n, 0);
+  res.sign_calls.assign(n, 0);
+  res.stopped.assign(n, 0);
+  for (int k = 0; k < nm; ++k)
+    for (int j = 0; j < ns; ++j) {
+      St& t = S[k * ns + j];
+      t.ghat = bnorm[j];
+      t.active = bnorm[j] > 0 && bnorm[j] > cfg.target * bnorm[j];
+      res.resid[k * ns + j] = bnorm[j];
+      if (t.active) qact[j] = 1;
+    }
+  std::vector<double> sc(18 * (size_t)n), scq(6 * (size_t)ns);
+  std::vector<double> eta(ns), dots(4 * ns);
+  std::vector<int> hact(n), hq(ns);
+  int* d_act = c->dint;
+  int* d_qact = c->dint + 2048;
+  for (int iter = 0; iter < cfg.maxit; ++iter) {
+    int nq = 0;
+    double emin = 1e300;
+    for (int j = 0; j < ns; ++j) {
+      if (!qact[j]) {
+        eta[j] = 1.0;
+        continue;
+      }
+      ++nq;
+      double rmax = 0.0;
+      for (int k = 0; k < nm; ++k)
+        if (S[k * ns + j].active) rmax = std::max(rmax, std::abs(S[k * ns + j].ghat));
+      double e = cfg.relax * cfg.target * bnorm[j] / std::max(rmax, 1e-300);
+      e = std::min(e, cfg.floor);
+      if (cfg.eta_cap > 0) e = std::min(e, cfg.eta_cap);
+      if (cfg.eta_fixed > 0) e = cfg.eta_fixed;
+      eta[j] = e;
+      emin = std::min(emin, e);
+    }
+    if (nq == 0) break;
+    const int mode = cfg.mode >= 0 ? cfg.mode : choose_mode(c, emin);
+    SignStats ss;
+    OVL_TRY(sign_op(c, mode, *fq, 0, *fu, 0, ns, eta.data(), 0.0, 1.0, nullptr, 0, fqt, 0, dots.data(), &ss));
+    // a shared sign application is charged once, split over the masses that use it
+    for (int j = 0; j < ns; ++j) {
+      int na = 0;
+      for (int k = 0; k < nm; ++k) na += S[k * ns + j].active ? 1 : 0;
+      if (na == 0) continue;
+      const long long cost = (long long)(2 * ss.iters[j] + 1) * (mode == SIGN64 || mode == SIGN64E ? 2 : 1);
+      for (int k = 0, seen = 0; k < nm; ++k)
+        if (S[k * ns + j].active) {
+          res.wcalls[k * ns + j] += cost / na + (seen < cost % na ? 1 : 0);
+          res.sign_calls[k * ns + j] += 1;
+          ++seen;
+        }
+    }
+    std::fill(sc.begin(), sc.end(), 0.0);
+    for (int j = 0; j < ns; ++j) {
+      hq[j] = qact[j] ? 1 : 0;
+      for (int k = 0; k < nm; ++k) hact[k * ns + j] = qact[j] && S[k * ns + j].active ? 1 : 0;
+      if (!qact[j]) continue;
+      // the basis step of Alg. 1 with an inexact sign (see sumr_batch), shared by the masses
+      const cd qtu(dots[4 * j], dots[4 * j + 1]);
+      const double uu = dots[4 * j + 2], tt = dots[4 * j + 3];
+      const cd gam = tt > 0 ? -qtu / tt : cd(0.0);
+      const double s2 = uu - std::norm(qtu) / std::max(tt, 1e-300);
+      if (!(s2 > 1e-24 * std::max(uu, 1e-300)) || !std::isfinite(s2)) {
+        qact[j] = 0;
+        hq[j] = 0;
+        for (int k = 0; k < nm; ++k) {
+          if (S[k * ns + j].active) res.stopped[k * ns + j] = 2;
+          S[k * ns + j].active = false;
+          hact[k * ns + j] = 0;
+        }
+        continue;
+      }
+      const double sig = std::sqrt(s2);
+      const cd qv[3] = {gam, 1.0 / sig, sig};
+      for (int m = 0; m < 3; ++m) {
+        scq[6 * j + 2 * m] = qv[m].real();
+        scq[6 * j + 2 * m + 1] = qv[m].imag();
+      }
+      for (int k = 0; k < nm; ++k) {
+        St& t = S[k * ns + j];
+        if (!t.active) continue;
+        cd a, Rm1, zm1;
+        if (t.it == 0) {
+          t.zeta = 1.0;
+          a = rho[k] - gam * t.zeta;
+          Rm1 = 0.0;
+          zm1 = 0.0;
+        } else {
+          zm1 = t.cprev * t.sigprev * t.zeta + std::conj(t.sprev) * std::conj(t.gprev);
+          t.zeta = -t.sprev * t.sigprev * t.zeta + t.cprev * std::conj(t.gprev);
+          Rm1 = rho[k] * std::conj(t.sprev) - gam * zm1;
+          a = rho[k] * t.cprev - gam * t.zeta;
+        }
+        const double nrm = std::sqrt(std::norm(a) + sig * sig);
+        const double cc = std::abs(a) / nrm;
+        const cd ss_ = std::abs(a) > 0 ? cc * sig / a : cd(1.0, 0.0);
+        const cd Rjj = cc * a + std::conj(ss_) * sig;
+        const cd g = cc * t.ghat;
+        t.ghat = -ss_ * t.ghat;
+        const cd vals[6] = {Rm1, gam * t.sigprev, 1.0 / Rjj, t.sigprev, zm1, g};
+        double* o = &sc[18 * (size_t)(k * ns + j)];
+        for (int m = 0; m < 6; ++m) {
+          o[2 * m] = vals[m].real();
+          o[2 * m + 1] = vals[m].imag();
+        }
+        t.cprev = cc;
+        t.sprev = ss_;
+        t.sigprev = sig;
+        t.gprev = gam;
+        t.it += 1;
+        res.iters[k * ns + j] = t.it;
+      }
+    }
+    const double *dsc, *dscq;
+    OVL_TRY(upload(c, sc.data(), 18 * n, &dsc));
+    OVL_TRY(upload(c, scq.data(), 6 * ns, &dscq));
+    OVL_CUDA(c, cudaMemcpyAsync(d_act, hact.data(), sizeof(int) * n, cudaMemcpyHostToDevice, c->st));
+    OVL_CUDA(c, cudaMemcpyAsync(d_qact, hq.data(), sizeof(int) * ns, cudaMemcpyHostToDevice, c->st));
+    OVL_TRY(ensure_partials(c, ns));
+    ProfPair pp;
+    prof_begin(c, 4, &pp);
+    launch_sumr_mm_update(PS, dsc, dscq, d_act, d_qact, x.ref(xoff), fq->ref(), fqt->ref(), fp->ref(), fS->ref(),
+                          fu->ref(), ns, nm, V, c->partials, c->st);
+    double nact = 0;
+    for (int q = 0; q < n; ++q) nact += hact[q];
+    prof_end(c, &pp, (double)V * (double)spinor_site_bytes(PS) * (5.0 * nq + 6.0 * nact));
+    OVL_TRY(check_launch(c, __func__));
+    std::vector<double> qn(2 * ns);
+    OVL_TRY(reduce_to_host(c, make_shape(V, ns).nsb, ns, qn.data()));
+    for (int j = 0; j < ns; ++j) {
+      if (!hq[j]) continue;
+      const double qnorm = std::sqrt(std::max(0.0, qn[2 * j]));
+      bool any = false;
+      for (int k = 0; k < nm; ++k) {
+        St& t = S[k * ns + j];
+        if (!hact[k * ns + j]) continue;
+        res.resid[k * ns + j] = std::abs(t.ghat);
+        if (cfg.hist) cfg.hist[k * ns + j].push_back(std::abs(t.ghat) / bnorm[j]);
+        if (std::abs(t.ghat) <= cfg.target * bnorm[j]) t.active = false;
+        any = any || t.active;
+      }
+      if (any && std::fabs(qnorm - 1.0) > cfg.qdrift) {
+        for (int k = 0; k < nm; ++k)
+          if (S[k * ns + j].active) {
+            S[k * ns + j].active = false;
+            res.stopped[k * ns + j] = 1;
+          }
+        any = false;
+      }
+      qact[j] = any ? 1 : 0;
+    }
+  }
+  return OVL_OK;
+}
+
 // ------------------------------------------------------------------ relCG (Alg. 4)
 // Hhat^-1 x = x + sum_i psi_i (c/sqrt(mu_i) - 1) (psi_i, x), per system mass.
 static ovl_status spectral_apply(ovl_ctx* c, ovl_defl* d, const std::vector<double>& mus, Field& x, int xoff, int n) {
@@ -491,6 +693,7 @@ ovl_status cg_batch(ovl_ctx* c, const SumrCfg& cfg, int n, const std::vector<dou
     res.resid[j] = rn[j];
   }
   std::vector<double> eta(n);
+  std::vector<cd> beta_prev(n, 0.0);
   for (int iter = 0; iter < cfg.maxit; ++iter) {
     int nact = 0;
     double emin = 1e300;
@@ -511,6 +714,7 @@ ovl_status cg_batch(ovl_ctx* c, const SumrCfg& cfg, int n, const std::vector<dou
     OVL_TRY(spectral_apply(c, cfg.defl, mus, *ft, 0, n));
     std::vector<long long> wc(n, 0);
     OVL_TRY(overlap_apply_batch(c, *ft, 0, *fz, 0, n, mus, eta, 1, mode, wc.data()));
+    if (cfg.cg_hook) OVL_TRY(cfg.cg_hook(c, cfg.hook_data, *ft, *fz, beta_prev, rn, iter));
     OVL_TRY(overlap_apply_batch(c, *fz, 0, *ft, 0, n, mus, eta, 1, mode, wc.data()));
     OVL_TRY(spectral_apply(c, cfg.defl, mus, *ft, 0, n));
     std::vector<cd> rz;
@@ -546,6 +750,7 @@ ovl_status cg_batch(ovl_ctx* c, const SumrCfg& cfg, int n, const std::vector<dou
         // frozen systems: p = r + 0 p keeps them unchanged in value semantics
       }
     OVL_TRY(axpby_batch(c, onea, *fr, 0, beta, *fp, 0, *fp, 0, n));  // p = r + beta p
+    beta_prev = beta;
   }
   // x = H Hhat^-1 x_j at the accuracy of the middle solve
   OVL_TRY(spectral_apply(c, cfg.defl, mus, *fxj, 0, n));
@@ -561,7 +766,7 @@ ovl_status cg_batch(ovl_ctx* c, const SumrCfg& cfg, int n, const std::vector<dou
 
 // ------------------------------------------------------------------ GMRESR (Alg. 3)
 ovl_status gmresr_batch(ovl_ctx* c, int n, const std::vector<double>& mus, const Field& b, int boff, Field& x,
-                        int xoff, double tol, ovl_defl* defl, ovl_solve_info* info, EigHook* eig) {
+                        int xoff, double tol, ovl_defl* defl, ovl_solve_info* info, EigHook* eig, int nsrc) {
   auto t0 = std::chrono::steady_clock::now();
   const int V = c->V;
   const int kmax = std::max(1, c->P.gmresr_max);
@@ -612,10 +817,23 @@ ovl_status gmresr_batch(ovl_ctx* c, int n, const std::vector<double>& mus, const
     cfg.eta_cap = (eig && eig->active) ? eig->eta_cap : 0.0;
     if (eig && eig->active) {
       cfg.hook = eig->hook;
+      cfg.cg_hook = eig->cg_hook;
       cfg.hook_data = eig->data;
     }
     SumrResult sr;
+    // first outer step of a batch that holds every mass of its sources (system q =
+    // mass * nsrc + source, x = 0 so r = b): the masses share one SUMR basis per source
+    bool mm = k == 0 && nsrc > 0 && n % nsrc == 0 && n / nsrc > 1 && !defl && !(eig && eig->active) &&
+              c->P.solver != OVL_SOLVER_CG;
+    std::vector<double> mus_m;
+    if (mm) {
+      for (int m = 0; m < n / nsrc; ++m) {
+        mus_m.push_back(mus[m * nsrc]);
+        for (int j = 1; j < nsrc; ++j) mm = mm && mus[m * nsrc + j] == mus[m * nsrc];
+      }
+    }
     if (c->P.solver == OVL_SOLVER_CG) OVL_TRY(cg_batch(c, cfg, n, mus, *fmid_b, 0, *fmid_x, 0, sr));
+    else if (mm) OVL_TRY(sumr_multimass(c, cfg, nsrc, n / nsrc, mus_m, *fmid_b, 0, *fmid_x, 0, sr));
     else OVL_TRY(sumr_batch(c, cfg, n, mus, *fmid_b, 0, *fmid_x, 0, sr));
     OVL_TRY(copy_convert(c, *fmid_x, 0, *fu, 0, n));
     if (c->P.solver != OVL_SOLVER_CG) {
@@ -706,6 +924,8 @@ ovl_status gmresr_batch(ovl_ctx* c, int n, const std::vector<double>& mus, const
       I.seconds = secs;
     }
   }
+  for (int j = 0; j < n; ++j)
+    if (!std::isfinite(rn[j])) return set_err(c, OVL_EBREAKDOWN, "GMRESR residual is not finite");
   for (int j = 0; j < n; ++j)
     if (rn[j] > tol * bn[j]) return set_err(c, OVL_ENOCONV, "GMRESR did not reach the tolerance");
   return OVL_OK;

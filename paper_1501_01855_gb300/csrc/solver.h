@@ -10,6 +10,13 @@ namespace ovl {
 // q holds q_j, u holds V q_j for every system of the batch.
 typedef ovl_status (*SumrHook)(ovl_ctx* c, void* data, const Field& q, const Field& u, int iter);
 typedef ovl_status (*OuterHook)(ovl_ctx* c, void* data, int outer);
+// Called in every step j of the middle relCG solve (eigCG, Sec. 5) once z_j = H t_j is
+// known, t_j = Hhat^-1 p_j: with beta_{j-1} (the previous step's beta, 0 at j = 0) and
+// ||r_j||, both per system, the residual direction Hhat^-1 r_j = t_j - beta_{j-1} t_{j-1}
+// and D Hhat^-1 r_j = gamma5 (z_j - beta_{j-1} z_{j-1}) follow from vectors CG computes.
+typedef ovl_status (*CgHook)(ovl_ctx* c, void* data, const Field& t, const Field& z,
+                             const std::vector<std::complex<double>>& beta_prev,
+                             const std::vector<double>& rnorm, int iter);
 
 struct SumrCfg {
   int prec = P64;          // precision of the middle-solve vectors
@@ -21,9 +28,11 @@ struct SumrCfg {
   int mode = -1;           // sign precision, -1: chosen by eta
   double qdrift = 0.1;     // stop when | ||q|| - 1 | exceeds this
   double eta_fixed = 0.0;  // >0: apply the sign at this accuracy every iteration (no relaxation)
+  const double* eta_dyn = nullptr;   // set: the sign accuracy is *eta_dyn, read every iteration
   std::vector<double>* hist = nullptr;   // residual estimates ||r_j|| / ||b||, appended per iteration
   ovl_defl* defl = nullptr;
   SumrHook hook = nullptr;
+  CgHook cg_hook = nullptr;
   void* hook_data = nullptr;
 };
 
@@ -40,6 +49,7 @@ struct EigHook {
   double target = 1e-2;    // middle-solve target while accumulating (GMRESR converges in two steps)
   double eta_cap = 1e-4;   // sign accuracy during accumulation
   SumrHook hook = nullptr;
+  CgHook cg_hook = nullptr;
   OuterHook after_outer = nullptr;
   void* data = nullptr;
 };
@@ -48,8 +58,12 @@ ovl_status sumr_batch(ovl_ctx* c, const SumrCfg& cfg, int n, const std::vector<d
                       Field& x, int xoff, SumrResult& res);
 ovl_status cg_batch(ovl_ctx* c, const SumrCfg& cfg, int n, const std::vector<double>& mus, const Field& b, int boff,
                     Field& x, int xoff, SumrResult& res);
+// nsrc > 0: the batch is every mass of nsrc sources, system q = mass * nsrc + source; the
+// first middle solve (r = b) then shares one SUMR basis per source (sumr_multimass)
 ovl_status gmresr_batch(ovl_ctx* c, int n, const std::vector<double>& mus, const Field& b, int boff, Field& x, int xoff,
-                        double tol, ovl_defl* defl, ovl_solve_info* info, EigHook* eig);
+                        double tol, ovl_defl* defl, ovl_solve_info* info, EigHook* eig, int nsrc = 0);
+ovl_status sumr_multimass(ovl_ctx* c, const SumrCfg& cfg, int ns, int nm, const std::vector<double>& mus_m,
+                          const Field& b, int boff, Field& x, int xoff, SumrResult& res);
 ovl_status overlap_apply_batch(ovl_ctx* c, const Field& v, int voff, Field& out, int ooff, int n,
                                const std::vector<double>& mus, const std::vector<double>& eta, int herm, int mode,
                                long long* wcalls_out);

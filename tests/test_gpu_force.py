@@ -28,17 +28,19 @@ def test_force_matches_oracle(dims, apt):
 
 
 def test_force_finite_differences_8888():
+    """The FP32 adjoint (mixed = 1: FP32 outer products, FP64 accumulation) against central
+    differences of the action on 32 random Lie-algebra directions on 8^4 (16 poles)."""
     dims = (8, 8, 8, 8)
     U = synth.gauge_links(dims, 0.3, 1005)
     phi = synth.gaussian_source(dims, 2005)
     a, b = 0.2, 2.6
     kw = dict(mu=MU, n_poles=16, eps=1e-8, a=a, b=b)
-    c = ctx(dims, U, **kw)
+    c = ctx(dims, U, mixed=1, **kw)
     G, S0 = c.force(phi, tol=1e-11)
     rng = np.random.Generator(np.random.PCG64(33))
     lam = synth._gell_mann()
     h = 1e-4
-    for _ in range(4):
+    for _ in range(32):
         X = np.einsum("...a,aij->...ij", rng.standard_normal(U.shape[:5] + (8,)), lam) * 0.5
         w, v = np.linalg.eigh(X)
         ex = lambda t: np.einsum("...ij,...j,...kj->...ik", v, np.exp(1j * t * w), np.conj(v))
@@ -68,3 +70,35 @@ def test_autograd_action_gradient_matches_oracle():
     Gref = force.gradient(U, phi, M0, MU, om, sg, tol=1e-13)
     assert abs(S.item() - Sref) <= 1e-9 * abs(Sref)
     assert rel(Ut.grad.numpy(), 2.0 * Gref) <= 1e-8
+
+
+@pytest.mark.parametrize("mixed", [0, 1])
+def test_force_4444_matches_dense_oracle(mixed):
+    """4^4, 16 poles: the gradient in FP64 (mixed = 0) and with the FP32 adjoint kernel
+    (mixed = 1: FP32 outer products, FP64 accumulation) against the oracle's gradient
+    (same formula, dense K); the FP32 one to FP32 rounding of the outer products."""
+    dims = (4, 4, 4, 4)
+    U = synth.gauge_links(dims, 0.3, 51)
+    phi = synth.gaussian_source(dims, 52)
+    a, b = 0.2, 2.6
+    c = ctx(dims, U, mu=MU, n_poles=16, eps=1e-6, a=a, b=b, mixed=mixed)
+    G, S = c.force(phi, tol=1e-12)
+    om, sg, _ = zo.zolotarev(16, a, b)
+    Gref, Sref = force.gradient_dense(U, phi, M0, MU, om, sg)
+    err = rel(G, Gref)
+    print("mixed %d: gradient error %.3e, action error %.3e" % (mixed, err, abs(S - Sref) / abs(Sref)))
+    assert abs(S - Sref) <= 1e-9 * abs(Sref)
+    assert err <= (1e-8 if mixed == 0 else 2e-6)
+
+
+def test_force_pole_groups_match_all_at_once():
+    """Shifted solutions recomputed in groups of 3 poles (16 poles: five full groups and
+    one of one) give the gradient of the all-at-once path."""
+    dims = (4, 4, 4, 4)
+    U = synth.gauge_links(dims, 0.3, 53)
+    phi = synth.gaussian_source(dims, 54)
+    kw = dict(mu=MU, n_poles=16, eps=1e-6, a=0.2, b=2.6, mixed=0)
+    G1, S1 = ctx(dims, U, force_pole_group=0, **kw).force(phi, tol=1e-12)
+    G2, S2 = ctx(dims, U, force_pole_group=3, **kw).force(phi, tol=1e-12)
+    assert abs(S1 - S2) <= 1e-12 * abs(S1)
+    assert rel(G2, G1) <= 1e-9

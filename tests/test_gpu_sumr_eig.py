@@ -52,17 +52,19 @@ def test_relaxed_sumr_reaches_target_4444():
     assert tr <= 5e-3, tr           # relaxed to eta_floor = 1e-2: the gap stays small
 
 
-def _eig_setup():
+def _eig_setup(solver=0):
+    """solver 0: eigSUMR (Alg. 5 on SUMR's basis); 1: eigCG (relCG's residual directions)."""
     U, Kd, S, w = dense_4444()
-    c = ctx((4, 4, 4, 4), U, mu=MU, n_poles=16)
+    c = ctx((4, 4, 4, 4), U, mu=MU, n_poles=16, solver=solver)
     b = synth.gaussian_source((4, 4, 4, 4), 2001)
     x = np.zeros_like(b)
     defl, info = c.eigsumr_accumulate(b, x, 1e-10, n_eig=8, m_basis=24)
     return U, S, c, b, x, defl, info
 
 
-def test_eigsumr_solution_and_ritz_pairs():
-    U, S, c, b, x, defl, info = _eig_setup()
+@pytest.mark.parametrize("solver", [0, 1])
+def test_eigsumr_solution_and_ritz_pairs(solver):
+    U, S, c, b, x, defl, info = _eig_setup(solver)
     D = overlap.dense_overlap(S, MU, 256)
     H = overlap.gamma5_matrix(256) @ D
     tr = np.linalg.norm(b.ravel() - D @ x.ravel()) / np.linalg.norm(b)
@@ -83,7 +85,39 @@ def test_eigsumr_solution_and_ritz_pairs():
         assert np.min(np.abs(wH - th)) <= r * (1 + 1e-6) + 1e-7
         # Ritz values of D^dag D + 2 mu delta H lie above the exact eigenvalues in order
         assert ritz[i] >= lamM[i] - 1e-7
+    print("solver %d: Ritz residuals %s" % (solver, np.array2string(res, precision=3)))
     assert res[0] < 0.1
+
+
+def test_ritz_recalculate_matches_oracle():
+    """The library's Ritz step (Alg. 6) on a given basis against the oracle's: a random
+    12-vector basis on 4^4 with v^D = D v from the oracle's dense D; Ritz values, the
+    kept vectors up to a phase, v^D and the residuals. The library forms the Gram blocks
+    from FP32 products (FP64 sums), hence the 1e-5 tolerances."""
+    from oracle import eigen
+    U, Kd, S, w = dense_4444()
+    mu, delta, m, nk = 0.05, 0.01, 12, 5
+    D = overlap.dense_overlap(S, mu, 256)
+    rng = np.random.default_rng(12)
+    shp = (4, 4, 4, 4, 4, 3)
+    # a basis rich in low modes: random combinations of the 20 lowest eigenvectors of D^dag D
+    lam, Y = np.linalg.eigh(D.conj().T @ D)
+    Vm = Y[:, :20] @ (rng.normal(size=(20, m)) + 1j * rng.normal(size=(20, m)))
+    Vm += 1e-2 * (rng.normal(size=Vm.shape) + 1j * rng.normal(size=Vm.shape))
+    VDm = D @ Vm
+    v = np.ascontiguousarray(Vm.T.reshape((m,) + shp))
+    vD = np.ascontiguousarray(VDm.T.reshape((m,) + shp))
+    c = ctx((4, 4, 4, 4), U, mu=mu, n_poles=16)
+    ritz, vo, vdo, res = c.ritz_recalculate(v, vD, nk, mu=mu, delta=delta)
+    lam_o, Vn, VDn, res_o = eigen.ritz_recalculate(Vm, VDm, mu, delta, nk, (256, 4, 3))
+    print("ritz", ritz, "oracle", lam_o)
+    assert np.allclose(ritz, lam_o, rtol=1e-5, atol=1e-7)
+    for i in range(nk):
+        a, o = vo[i].ravel(), Vn[:, i]
+        ph = np.vdot(o, a) / abs(np.vdot(o, a))
+        assert np.linalg.norm(a - ph * o) <= 1e-5 * np.linalg.norm(o)
+        assert np.linalg.norm(vdo[i].ravel() - ph * VDn[:, i]) <= 1e-5 * np.linalg.norm(VDn[:, i])
+    assert np.allclose(res, res_o, rtol=1e-4, atol=1e-7)
 
 
 def test_deflated_solve_and_save_load():
@@ -167,3 +201,61 @@ def test_exact_eigenvector_deflation(solver):
     print("solver %d: undeflated inner %d, exact-eigenvector deflated inner %d"
           % (solver, i0["inner_iters"], i1["inner_iters"]))
     assert i1["inner_iters"] < 0.8 * i0["inner_iters"]
+
+
+def test_eigcg_space_deflates_relcg():
+    """A space accumulated by eigCG during relCG solves (mu = 0.01, 16 vectors) deflates
+    later relCG solves: fewer middle iterations, oracle true residual still 1e-10."""
+    U, Kd, S, w = dense_4444()
+    mu = 0.01
+    ev = np.abs(np.linalg.eigvalsh(Kd))
+    za, zb = 0.95 * ev.min(), 1.05 * ev.max()
+    c = ctx((4, 4, 4, 4), U, mu=mu, n_poles=16, a=za, b=zb, solver=1)
+    defl = None
+    for k in range(2):
+        b0 = synth.gaussian_source((4, 4, 4, 4), 3001 + k)
+        defl, info = c.eigsumr_accumulate(b0, np.zeros_like(b0), 1e-10, n_eig=16, m_basis=40, mu=mu, defl=defl)
+    b2 = synth.gaussian_source((4, 4, 4, 4), 2079)
+    x0, x1 = np.zeros_like(b2), np.zeros_like(b2)
+    i0 = c.solve(b2, x0, 1e-10)[0]
+    i1 = c.solve(b2, x1, 1e-10, defl=defl)[0]
+    om, sg, _ = zo.zolotarev(16, za, zb)
+    Dz = overlap.dense_overlap(overlap.dense_zolotarev_sign(Kd, om, sg), mu, 256)
+    for xx in (x0, x1):
+        assert np.linalg.norm(b2.ravel() - Dz @ xx.ravel()) / np.linalg.norm(b2) <= 1e-10
+    ritz, res = defl.info()
+    print("eigCG: undeflated inner %d, deflated inner %d; residuals %s"
+          % (i0["inner_iters"], i1["inner_iters"], np.array2string(res, precision=3)))
+    assert i1["inner_iters"] < 0.8 * i0["inner_iters"]
+
+
+def test_standalone_eigensolver_4444():
+    """ovl_eigensolve (Sec. 6: eigSUMR without a solve, rounds with three-generation
+    Rayleigh-Ritz and restarts from a re-orthogonalised q) from a Z2 source: the Ritz
+    values approach the lowest eigenvalues of D^dag D + 2 mu delta H from above, in order,
+    and the converged vectors lie in the exact low eigenspace (their component outside
+    the lowest 16 exact eigenvectors is small)."""
+    U, Kd, S, w = dense_4444()
+    ev = np.abs(np.linalg.eigvalsh(Kd))
+    za, zb = 0.95 * ev.min(), 1.05 * ev.max()
+    c = ctx((4, 4, 4, 4), U, mu=MU, n_poles=16, a=za, b=zb)
+    defl, used = c.eigensolve(8, 40, 3000, res_tol=1e-4)
+    ritz, res = defl.info()
+    D = overlap.dense_overlap(S, MU, 256)
+    H = overlap.gamma5_matrix(256) @ D
+    wH, Y = np.linalg.eigh(H)
+    lamM = np.sort(wH ** 2 + 2 * MU * 0.01 * wH)
+    print("steps %d, ritz %s, exact %s, residuals %s" % (used, ritz, lamM[:8], res))
+    assert used <= 3000
+    # the lowest six converge well within the budget; the last two sit next to the rest
+    # of the spectrum and converge more slowly (Sec. 6: the process slows down beyond a
+    # point that depends on the number of vectors)
+    assert np.all(res[:6] <= 1e-3) and np.all(res <= 1e-2)
+    assert np.all(ritz >= lamM[:8] - 1e-6)
+    assert np.allclose(ritz[:6], lamM[:6], rtol=1e-4, atol=1e-7)
+    assert np.allclose(ritz, lamM[:8], rtol=1e-2, atol=1e-6)
+    low = Y[:, np.argsort(np.abs(wH))[:16]]
+    for i in range(6):
+        v, _ = defl.vector(i)
+        v = v.ravel() / np.linalg.norm(v)
+        assert np.linalg.norm(v - low @ (low.conj().T @ v)) <= 1e-2

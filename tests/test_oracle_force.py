@@ -35,3 +35,23 @@ def test_force_finite_differences():
         fd = (Sp - Sm) / (2 * h)
         an = 2 * np.real(np.sum(np.conj(G) * (1j * X @ U)))
         assert abs(fd - an) <= 1e-6 * max(1.0, abs(an))
+
+
+def test_dense_gradient_equals_matrix_free():
+    """gradient_dense (dense K, eigendecomposition) and gradient (matrix-free CGs) are the
+    same formula: on 2^4, periodic and antiperiodic in t, they agree, and its
+    action equals the dense D^dag D solve."""
+    m0, mu = 1.4, 0.05
+    om, sg, _ = zo.zolotarev(8, 0.15, 2.6)
+    for dims, apt in (((2, 2, 2, 2), False), ((2, 2, 2, 2), True)):
+        U = synth.gauge_links(dims, 0.3, 61)
+        phi = synth.gaussian_source(dims, 62)
+        G1 = force.gradient(U, phi, m0, mu, om, sg, tol=1e-14, antiperiodic_t=apt)
+        G2, S2 = force.gradient_dense(U, phi, m0, mu, om, sg, antiperiodic_t=apt)
+        assert np.linalg.norm(G1 - G2) <= 1e-9 * np.linalg.norm(G2)
+        S1, _ = force.action(U, phi, m0, mu, om, sg, tol=1e-14, antiperiodic_t=apt)
+        assert abs(S1 - S2) <= 1e-10 * abs(S2)
+    U = synth.gauge_links((2, 2, 2, 2), 0.3, 61)
+    phi = synth.gaussian_source((2, 2, 2, 2), 62)
+    assert abs(force.gradient_dense(U, phi, m0, mu, om, sg)[1] - _S_dense(U, phi, m0, mu, om, sg)) <= 1e-10 * abs(
+        _S_dense(U, phi, m0, mu, om, sg))
