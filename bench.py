@@ -480,7 +480,7 @@ def extras(args, ctx, dv, dout, ref_out, B, torch, stream, hbm):
 def deflated_batched(B, stream):
     """Deflated, batched right-hand sides (the shape of the paper's use case): eigSUMR
     solves of three Gaussian sources accumulate and refine 32 low modes of D^dag D
-    (basis 96), then the 12 spin-colour point sources at one site are solved in one
+    (basis 2 n + 64 = 128), then the 12 spin-colour point sources at one site are solved in one
     lock-step batch, undeflated and deflated, with relSUMR (deflated start) and relCG
     (spectral preconditioner; the space is handed over through ovl_defl_save/load),
     against one plain-FP64 (no mixed precision, no deflation) solve. mu = 0.02, 1e-10."""
@@ -501,7 +501,7 @@ def deflated_batched(B, stream):
         if k == 2:
             ctx.profile_reset()
             ctx.profile_enable(True)
-        defl, info0 = ctx.eigsumr_accumulate(b0, x0, tol, 32, 96, defl=defl)
+        defl, info0 = ctx.eigsumr_accumulate(b0, x0, tol, 32, 128, defl=defl)
     ctx.profile_enable(False)
     res["eigsumr_3_accumulation_solves_s"] = time.perf_counter() - t0
     prof = ctx.profile_get()
@@ -562,7 +562,7 @@ def config_c4(B, stream):
     """Batched multi-mass deflated solves on 24^3 x 48 (the largest configuration of the
     benchmark set): 12 spin-colour point sources x 3 masses mu in {0.01, 0.02, 0.04} = 36
     systems in one lock-step batch, 64 eigenvectors of D^dag D (accumulated by eigSUMR at
-    mu = 0.01 over three Gaussian-source solves, basis 160) shared by all masses, 24
+    mu = 0.01 over three Gaussian-source solves, basis 2 n + 64 = 192) shared by all masses, 24
     Zolotarev poles, autotuned Wilson kernel, CUDA-graph multi-shift iterations, relative
     residual 1e-10; against one plain-FP64 solve of one source at mu = 0.01."""
     import synth
@@ -582,7 +582,7 @@ def config_c4(B, stream):
     for k in range(3):
         b0 = synth.gaussian_source(dims, 2004 + k)
         x0 = np.zeros_like(b0)
-        defl, _ = ctx.eigsumr_accumulate(b0, x0, tol, 64, 160, defl=defl)
+        defl, _ = ctx.eigsumr_accumulate(b0, x0, tol, 64, 192, defl=defl)
     out["eigsumr_3_solves_s"] = time.perf_counter() - t0
     ritz, rres = defl.info()
     out["ritz_residual_lowest8_max"] = float(np.max(rres[:8]))
@@ -699,6 +699,68 @@ def deflation_gain(B, stream):
     return out
 
 
+def config_c5(B, stream):
+    """Gradient of S = phi^dag (D^dag D)^-1 phi with respect to every gauge link (the fermion
+    force) on 8^4 and 16^3 x 32, mu = 0.05, 16 Zolotarev poles on [0.2, 2.6]: the FP32 adjoint
+    (FP32 outer products, FP64 accumulation) timed against the FP64 one, the recompute path
+    (shifted solutions in groups of 4 poles instead of all stored) against the stored one,
+    and central finite differences of the action along 4 random Lie-algebra directions
+    (2 at 16^3 x 32) against the gradient."""
+    import synth
+    out = {"workload": "fermion force, eps 0.3 links seed 1005, m0 1.4, mu 0.05, 16 poles on [0.2, 2.6], "
+                       "one Gaussian phi, solves to 1e-11"}
+    lam = synth._gell_mann()
+
+    def make(dims, U, **kw):
+        p = B.ovl_params_default()
+        p.stream = stream.cuda_stream
+        p.a_override, p.b_override = 0.2, 2.6
+        for k, v in kw.items():
+            setattr(p, k, v)
+        return B.Overlap(dims, U, M0, 0.05, 16, 1e-8, params=p)
+
+    for dims, ndir in (((8, 8, 8, 8), 4), ((16, 16, 16, 32), 2)):
+        key = "x".join(map(str, dims))
+        U = synth.gauge_links(dims, 0.3, 1005)
+        phi = synth.gaussian_source(dims, 2005)
+        row = {}
+        grads = {}
+        for name, kw in (("fp32_adjoint", {"mixed": 1}), ("fp64_adjoint", {"mixed": 0}),
+                         ("fp32_adjoint_pole_groups_of_4", {"mixed": 1, "force_pole_group": 4})):
+            c = make(dims, U, **kw)
+            c.force(phi, tol=1e-11)                      # warm-up: graphs, workspaces
+            t0 = time.perf_counter()
+            G, S = c.force(phi, tol=1e-11)
+            dt = time.perf_counter() - t0
+            c.close()
+            grads[name] = G
+            row[name] = {"seconds": dt, "action": S, "gradient_norm": float(np.linalg.norm(G))}
+        g0 = grads["fp64_adjoint"]
+        for name in ("fp32_adjoint", "fp32_adjoint_pole_groups_of_4"):
+            row[name]["rel_diff_vs_fp64_adjoint"] = float(np.linalg.norm(grads[name] - g0) / np.linalg.norm(g0))
+        # central finite differences of the action (FP64 path) along random directions
+        rng = np.random.Generator(np.random.PCG64(33))
+        h = 1e-4
+        G = grads["fp32_adjoint"]
+        fd_rows = []
+        for _ in range(ndir):
+            X = np.einsum("...a,aij->...ij", rng.standard_normal(U.shape[:5] + (8,)), lam) * 0.5
+            w, v = np.linalg.eigh(X)
+            ex = lambda t: np.einsum("...ij,...j,...kj->...ik", v, np.exp(1j * t * w), np.conj(v))
+            S2 = []
+            for t in (h, -h):
+                c = make(dims, ex(t) @ U, mixed=1)
+                S2.append(c.force(phi, tol=1e-11)[1])
+                c.close()
+            fd = (S2[0] - S2[1]) / (2 * h)
+            an = float(2 * np.real(np.sum(np.conj(G) * (1j * X @ U))))
+            fd_rows.append({"finite_difference": fd, "gradient": an, "rel_diff": abs(fd - an) / abs(an)})
+        row["finite_differences"] = fd_rows
+        out[key] = row
+        del grads, U
+    return out
+
+
 def run_reference(args, ws, rank):
     """The oracle on this host's cores as the reference arm: every step is a complete
     oracle apply of as many 8^4 vectors as there are cores (a pool of that many
@@ -749,14 +811,16 @@ def main():
                     help="reference arm: 8^4 vectors per step (default: one per core)")
     ap.add_argument("--config-c4", action="store_true",
                     help="run only the 24^3x48 batched multi-mass deflated solves and print their JSON")
+    ap.add_argument("--config-c5", action="store_true",
+                    help="run only the fermion-force measurements (8^4 and 16^3x32) and print their JSON")
     ap.add_argument("--deflation-gain", action="store_true",
                     help="run only the deflation-gain experiment (15/30/45 vectors) and print its JSON")
     args = ap.parse_args()
-    if args.config_c4 or args.deflation_gain:
+    if args.config_c4 or args.config_c5 or args.deflation_gain:
         import torch
         from paper_1501_01855_gb300 import build, binding as B
         build.build()
-        fn = config_c4 if args.config_c4 else deflation_gain
+        fn = config_c4 if args.config_c4 else config_c5 if args.config_c5 else deflation_gain
         print(json.dumps(fn(B, torch.cuda.current_stream())), flush=True)
         return
     if args.warmup < 3:
