@@ -559,6 +559,9 @@ static ovl_status sign_op_batch_lz(ovl_ctx* c, int mode, const Field& v, int vof
     const std::vector<unsigned long long> key = {
         1000ull + (unsigned long long)PB, (unsigned long long)PL, (unsigned long long)n, (unsigned long long)hcap,
         (unsigned long long)(uintptr_t)W->data, (unsigned long long)(uintptr_t)t->data,
+        // FP16 storage: the per-site scales of the pooled basis sit after its data, at an
+        // offset that depends on the cycle length, so they are part of the key
+        (unsigned long long)(uintptr_t)W->norm, (unsigned long long)(uintptr_t)t->norm,
         (unsigned long long)(uintptr_t)c->partials, (unsigned long long)(uintptr_t)c->lz,
         (unsigned long long)(uintptr_t)c->lz_hist, (unsigned long long)(uintptr_t)L.data,
         (unsigned long long)L.variant};
@@ -743,6 +746,8 @@ static ovl_status sign_op_batch(ovl_ctx* c, int mode, const Field& v, int voff, 
         (unsigned long long)PP, (unsigned long long)PL, (unsigned long long)PR, (unsigned long long)n,
         (unsigned long long)np, (unsigned long long)(uintptr_t)pb->data, (unsigned long long)(uintptr_t)t->data,
         (unsigned long long)(uintptr_t)r->data, (unsigned long long)(uintptr_t)y->data,
+        (unsigned long long)(uintptr_t)pb->norm, (unsigned long long)(uintptr_t)t->norm,
+        (unsigned long long)(uintptr_t)r->norm, (unsigned long long)(uintptr_t)y->norm,
         (unsigned long long)(uintptr_t)c->partials, (unsigned long long)(uintptr_t)c->ms,
         (unsigned long long)(uintptr_t)L.data, (unsigned long long)L.variant};
     OVL_TRY(ms_graph(c, key, &gexec, [&](cudaStream_t cs) {

@@ -50,6 +50,25 @@ def test_sign_relaxed_accuracy(prec, eta, bound, method):
     assert err <= bound
 
 
+def test_sign_fp16_repeated_calls_keep_accuracy():
+    """FP16 storage, stored-basis Lanczos, several calls on one context: the cycle length
+    changes between calls (the first is sized from the CG bound, later ones from the steps
+    seen), and with it the offset of the per-site scales inside the pooled basis; every
+    call must still meet its accuracy (cached step graphs included)."""
+    U, Kd, S, w = dense_4444()
+    a, b = _ab(w)
+    c = ctx((4, 4, 4, 4), U, a=a, b=b, n_poles=16, sign_method=0)
+    v = synth.gaussian_source((4, 4, 4, 4), 7, nvec=2)
+    exact = np.stack([(S @ v[j].ravel()).reshape(v[j].shape) for j in range(2)])
+    for eta in (1e-2, 1e-2, 3e-3, 1e-2, 3e-3):
+        out = np.zeros_like(v)
+        c.sign_apply(v, out, eta=eta, prec=2)
+        err = rel(out, exact)
+        print("FP16 eta %g: error %.3e" % (eta, err))
+        assert err <= 2 * eta
+    c.close()
+
+
 @pytest.mark.parametrize("mu,prec", [(0.05, 0), (0.3, 0), (0.05, 3)])
 def test_overlap_apply_matches_dense(mu, prec):
     U, Kd, S, w = dense_4444()
