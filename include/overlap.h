@@ -115,6 +115,12 @@ typedef struct {
                            restarts from its last vector, to which every pole's residual is
                            parallel); 0 (default): sized from the steps this context has
                            needed at that accuracy, else from the CG bound of the base shift */
+  int    gram_method;   /* dense blocks (Gram matrices of the Ritz step, Alg. 6, and the
+                           projections of the deflated starts, Sec. 4): 0 (default) on the
+                           tensor cores with FP64-level accuracy (operands split into six
+                           7-bit digits, exact BF16 products, exact FP32 sums over 512 reals,
+                           double-float and FP64 above) for FP64 and FP32 fields, else as 1;
+                           1 CUDA-core kernel with FP32 products and FP64 sums              */
   void*  stream;        /* cudaStream_t for all work; NULL = legacy default stream              */
 } ovl_params;
 
@@ -313,6 +319,25 @@ void ovl_defl_destroy(ovl_defl* defl);
  * With respect to the links the context was created from. */
 ovl_status overlap_force(ovl_ctx* ctx, double mu, const void* phi, int dtype, int on_device, double tol,
                          double* dSdU, double* S);
+
+/* Gram block G[i][j] = (A_i, [gamma5] B_j) = sum over sites and components of
+ * conj(A_i) [gamma5] B_j: the dense contraction of the Ritz step (Alg. 6: E = V^dag V,
+ * (V^D)^dag V^D, V^dag gamma5 V^D) and of the deflated starts (Sec. 4: Psi^dag b).
+ * A: na spinors, B: nb spinors (1 <= na, nb <= 1024) in the canonical layout of dtype
+ * (host or device per on_device, read only); they are stored in the library as prec
+ * (OVL_PREC_F64 or OVL_PREC_F32) before the contraction. method 0: tensor cores at
+ * FP64-level accuracy (the default path of the library's own Gram blocks), 1: CUDA-core
+ * kernel with FP32 products and FP64 sums. G: host, na x nb complex128 row-major,
+ * overwritten. OVL_ETIMEOUT if a bounded wait inside the tensor-core kernel gave up
+ * (the context stays usable). Synchronises the context stream. */
+ovl_status ovl_gram(ovl_ctx* ctx, const void* A, int na, const void* B, int nb, int dtype, int on_device,
+                    int prec, int g5, int method, double* G);
+
+/* Time `iters` Gram blocks of na x nb random spinors of precision prec held by the
+ * library (method as in ovl_gram), back to back on the context stream with CUDA
+ * events: *ms_per_call receives the mean milliseconds of one block (its kernels and the
+ * memset of its output; no host copy). */
+ovl_status ovl_bench_gram(ovl_ctx* ctx, int prec, int na, int nb, int method, int iters, double* ms_per_call);
 
 /* Kernel-level timing collected with CUDA events on the context stream while
  * enabled: per kernel class, launches, total milliseconds and algorithmic bytes.

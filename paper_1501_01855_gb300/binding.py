@@ -44,6 +44,7 @@ class ovl_params(ctypes.Structure):
                 ("use_graphs", ctypes.c_int),
                 ("verify", ctypes.c_int), ("sign_method", ctypes.c_int), ("basis_gb", ctypes.c_double),
                 ("multimass", ctypes.c_int), ("force_pole_group", ctypes.c_int), ("lanczos_cap", ctypes.c_int),
+                ("gram_method", ctypes.c_int),
                 ("stream", ctypes.c_void_p)]
 
 
@@ -95,6 +96,8 @@ _SIGS = {
     "ovl_bench_wilson": (I, [P, I, I, I, DP, DP]),
     "ovl_wilson_tuning": (I, [P, I, ctypes.POINTER(I), DP, DP, DP, DP]),
     "ovl_bench_fp32": (I, [P, DP]),
+    "ovl_gram": (I, [P, P, I, P, I, I, I, I, I, I, DP]),
+    "ovl_bench_gram": (I, [P, I, I, I, I, I, DP]),
 }
 
 
@@ -415,6 +418,27 @@ class Overlap:
         r = ctypes.c_double()
         _check(load().ovl_bench_fp32(self.h, ctypes.byref(r)), self.h)
         return r.value
+
+    def gram(self, A, B, g5=0, prec=OVL_PREC_F64, method=0):
+        """G[i, j] = (A_i, [gamma5] B_j) for spinor batches A (na) and B (nb), same dtype
+        and device; returns an na x nb complex128 NumPy array."""
+        pa, code, dev, cnta, da = _spinor_arg(A)
+        pb, codeb, devb, cntb, db = _spinor_arg(B)
+        if code != codeb or dev != devb or (dev and da != db):
+            raise ValueError("A and B must share dtype and device")
+        if dev and self.device is not None and da != self.device:
+            raise ValueError("A and B must be on cuda:%d, the context's device" % self.device)
+        na, nb = self._n(cnta), self._n(cntb)
+        G = np.zeros(na * nb * 2)
+        _check(load().ovl_gram(self.h, pa, na, pb, nb, code, dev, int(prec), int(g5), int(method), _dptr(G)), self.h)
+        return G.view(np.complex128).reshape(na, nb)
+
+    def bench_gram(self, prec, na, nb, method=0, iters=3):
+        """Mean milliseconds of one na x nb Gram block on library-held random fields."""
+        ms = ctypes.c_double()
+        _check(load().ovl_bench_gram(self.h, int(prec), int(na), int(nb), int(method), int(iters),
+                                     ctypes.byref(ms)), self.h)
+        return ms.value
 
     def bench_wilson(self, prec, n, iters):
         ms, by = ctypes.c_double(), ctypes.c_double()

@@ -51,6 +51,7 @@ extern "C" ovl_status ovl_params_default(ovl_params* p) {
   p->multimass = 1;
   p->force_pole_group = 0;
   p->lanczos_cap = 0;
+  p->gram_method = 0;
   p->stream = nullptr;
   return OVL_OK;
 }
@@ -284,6 +285,7 @@ static ovl_status create_impl(ovl_ctx* c, const int dims[4], const double* links
   if (!(c->P.basis_gb > 0)) c->P.basis_gb = 96.0;
   if (c->P.lanczos_cap != 0 && (c->P.lanczos_cap < 4 || c->P.lanczos_cap > 1024))
     return set_err(c, OVL_EINVAL, "lanczos_cap must be 0 or lie in 4..1024");
+  if (c->P.gram_method != 0 && c->P.gram_method != 1) return set_err(c, OVL_EINVAL, "gram_method must be 0 or 1");
   if (c->P.batch_max < 1) c->P.batch_max = 1;
   if (c->P.batch_max > 256) c->P.batch_max = 256;
   c->m0 = m0;
@@ -1114,6 +1116,76 @@ extern "C" ovl_status ovl_bench_wilson(ovl_ctx* c, int prec, int n, int iters, d
   const double lb = prec == P64E ? 576 : prec == P64 ? 384 : prec == P32 ? 192 : 96;   // algorithmic
   if (ms_per_launch) *ms_per_launch = ms / iters;
   if (bytes_per_launch) *bytes_per_launch = (double)c->V * (2.0 * sb * n + lb);
+  return OVL_OK;
+}
+
+// ---------------------------------------------------------------- dense Gram block
+extern "C" ovl_status ovl_gram(ovl_ctx* c, const void* A, int na, const void* B, int nb, int dtype, int on_device,
+                               int prec, int g5, int method, double* G) {
+  if (!c) return OVL_EINVAL;
+  if (!A || !B || !G) return set_err(c, OVL_EINVAL, "null pointer");
+  if (na < 1 || na > 1024 || nb < 1 || nb > 1024) return set_err(c, OVL_EINVAL, "na and nb must lie in 1..1024");
+  if (dtype != OVL_C128 && dtype != OVL_C64) return set_err(c, OVL_EINVAL, "dtype must be OVL_C128 or OVL_C64");
+  if (prec != P64 && prec != P32) return set_err(c, OVL_EINVAL, "prec must be OVL_PREC_F64 or OVL_PREC_F32");
+  if (method != 0 && method != 1) return set_err(c, OVL_EINVAL, "method must be 0 or 1");
+  Field *fa, *fb;
+  OVL_TRY(get_field(c, "gr_a", prec, na, &fa));
+  OVL_TRY(get_field(c, "gr_b", prec, nb, &fb));
+  OVL_TRY(import_spinors(c, A, dtype, on_device, na, *fa, 0));
+  OVL_TRY(import_spinors(c, B, dtype, on_device, nb, *fb, 0));
+  const int saved = c->P.gram_method;
+  c->P.gram_method = method;
+  std::vector<cd> Gh;
+  const ovl_status st = gram_host(c, *fa, 0, na, *fb, 0, nb, g5 ? 1 : 0, Gh);
+  c->P.gram_method = saved;
+  if (st != OVL_OK) return st;
+  for (size_t k = 0; k < Gh.size(); ++k) {
+    G[2 * k] = Gh[k].real();
+    G[2 * k + 1] = Gh[k].imag();
+  }
+  return OVL_OK;
+}
+
+extern "C" ovl_status ovl_bench_gram(ovl_ctx* c, int prec, int na, int nb, int method, int iters, double* ms_per_call) {
+  if (!c || (prec != P64 && prec != P32) || na < 1 || na > 1024 || nb < 1 || nb > 1024 || iters < 1 ||
+      (method != 0 && method != 1) || !ms_per_call)
+    return OVL_EINVAL;
+  Field *fa, *fb;
+  OVL_TRY(get_field(c, "bg_a", prec, na, &fa));
+  OVL_TRY(get_field(c, "bg_b", prec, nb, &fb));
+  {
+    std::vector<double> h((size_t)24 * c->V);
+    unsigned long long st = 6789;
+    for (int j = 0; j < na + nb; ++j) {
+      for (auto& x : h) {
+        st = st * 6364136223846793005ull + 1442695040888963407ull;
+        x = ((double)(st >> 11) / 9007199254740992.0) - 0.5;
+      }
+      OVL_TRY(import_spinors(c, h.data(), OVL_C128, 0, 1, j < na ? *fa : *fb, j < na ? j : j - na));
+    }
+  }
+  const int saved = c->P.gram_method;
+  c->P.gram_method = method;
+  double* dG = nullptr;
+  int* derr = nullptr;
+  ovl_status s = gram_device(c, *fa, 0, na, *fb, 0, nb, 0, &dG, &derr);   // sizes the work buffer
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  if (s == OVL_OK && cudaEventCreate(&e0) == cudaSuccess && cudaEventCreate(&e1) == cudaSuccess) {
+    cudaEventRecord(e0, c->st);
+    for (int k = 0; k < iters && s == OVL_OK; ++k) s = gram_device(c, *fa, 0, na, *fb, 0, nb, 0, &dG, &derr);
+    cudaEventRecord(e1, c->st);
+    cudaEventSynchronize(e1);
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, e0, e1);
+    *ms_per_call = ms / iters;
+  }
+  if (e0) cudaEventDestroy(e0);
+  if (e1) cudaEventDestroy(e1);
+  c->P.gram_method = saved;
+  OVL_TRY(s);
+  int herr = 0;
+  if (derr) OVL_CUDA(c, cudaMemcpy(&herr, derr, sizeof(int), cudaMemcpyDeviceToHost));
+  if (herr) return set_err(c, OVL_ETIMEOUT, "tensor-core Gram block: a bounded wait on the MMA pipeline gave up");
   return OVL_OK;
 }
 

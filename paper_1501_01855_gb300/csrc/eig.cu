@@ -5,8 +5,8 @@
 //   E = (v_i, v_j), Cholesky E = U^dag U, M = (v^D_i, v^D_j) + 2 mu delta (v_i, gamma5 v^D_j),
 //   eigenvectors Y of L^-1 M U^-1 (ascending), new v = V U^-1 Y, new v^D likewise,
 //   keep the lowest n; residuals ||gamma5 v^D_i - v_i (v_i, gamma5 v^D_i)||.
-// The Gram blocks run on the GPU (FP32 products, FP64 sums); the m x m algebra is
-// FP64 on the host. If the basis has lost linear independence (Sec. 5 notes that
+// The Gram blocks run on the GPU (tensor cores with FP64-level accuracy by default, see
+// tcgram.cu); the m x m algebra is FP64 on the host. If the basis has lost linear independence (Sec. 5 notes that
 // orthogonality of the SUMR vectors is quickly lost with an inexact sign) and the
 // Cholesky factor does not exist, the basis is orthonormalised through the
 // eigendecomposition of E instead, dropping directions below 1e-10 of its largest

@@ -212,6 +212,15 @@ void launch_sumr_mm_update(int p, const double* sc, const double* scq, const int
 // per block are reduced in a fixed order.
 void launch_gram(int pa, SpinorRef A, int na, int pb, SpinorRef B, int nb, int V, double* G,
                  double* work, size_t work_doubles, int g5, cudaStream_t st);
+// The same block on the tensor cores, FP64-accurate (operands split into 7-bit digits with
+// exact BF16 products and exact FP32 sums; P64 and P32 fields only). ex: na + nb ints;
+// partial: tc_gram_work_doubles(na, nb, nsplit) doubles; err set to 1 on a bounded wait that
+// gave up.
+bool tc_gram_supported(int pa, int pb);
+int tc_gram_splits(int na, int nb, int V, int nsm);
+size_t tc_gram_work_doubles(int na, int nb, int nsplit);
+void launch_tc_gram(int pa, const void* A, int na, int pb, const void* B, int nb, int V, int g5, int nsplit,
+                    double* G, double* partial, int* ex, int* err, cudaStream_t st);
 // Y_j (+)= sum_i A_i C[i, j] for j < ny (C na x ny row-major complex, device); Y distinct
 // from A. add = 1 accumulates into Y.
 void launch_combine(int pa, SpinorRef A, int na, const double* C, int py, SpinorRef Y, int ny, int V, int add,

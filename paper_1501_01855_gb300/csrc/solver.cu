@@ -92,23 +92,57 @@ ovl_status copy_convert(ovl_ctx* c, const Field& in, int ioff, Field& out, int o
   return OVL_OK;
 }
 
+// Gram block G = (A_i, [g5] B_j), na x nb complex row-major, into dG (the last 2 na nb
+// doubles of the work buffer, returned): launched on the context stream, not waited for.
+// *derr is the tensor-core path's device error flag (nullptr on the CUDA-core path).
+ovl_status gram_device(ovl_ctx* c, const Field& A, int aoff, int na, const Field& B, int boff, int nb, int g5,
+                       double** dGout, int** derr) {
+  const size_t gsz = (size_t)na * nb * 2;
+  const bool tc = c->P.gram_method == 0 && tc_gram_supported(A.prec, B.prec);
+  int nsplit = 0;
+  size_t need = gsz * 1300 + gsz;
+  if (tc) {
+    int nsm = 0;
+    OVL_CUDA(c, cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, c->device));
+    nsplit = tc_gram_splits(na, nb, c->V, nsm);
+    // partials, then na + nb exponents and the error flag (as ints), then G
+    need = tc_gram_work_doubles(na, nb, nsplit) + (size_t)(na + nb + 2) / 2 + 1 + gsz;
+  }
+  OVL_TRY(ensure_work(c, need));
+  double* dG = c->dwork + c->dwork_n - gsz;
+  OVL_CUDA(c, cudaMemsetAsync(dG, 0, gsz * sizeof(double), c->st));
+  *derr = nullptr;
+  ProfPair pp;
+  prof_begin(c, 6, &pp);
+  if (tc) {
+    const size_t nw = tc_gram_work_doubles(na, nb, nsplit);
+    int* ex = reinterpret_cast<int*>(c->dwork + nw);
+    *derr = ex + na + nb;
+    OVL_CUDA(c, cudaMemsetAsync(*derr, 0, sizeof(int), c->st));
+    launch_tc_gram(A.prec, A.ref(aoff).data, na, B.prec, B.ref(boff).data, nb, c->V, g5, nsplit, dG, c->dwork, ex,
+                   *derr, c->st);
+  } else {
+    launch_gram(A.prec, A.ref(aoff), na, B.prec, B.ref(boff), nb, c->V, dG, c->dwork, c->dwork_n - gsz, g5, c->st);
+  }
+  prof_end(c, &pp, (double)c->V * ((double)na * spinor_site_bytes(A.prec) + (double)nb * spinor_site_bytes(B.prec)));
+  OVL_TRY(check_launch(c, __func__));
+  *dGout = dG;
+  return OVL_OK;
+}
+
 // Gram block G = (A_i, [g5] B_j), na x nb, to the host (complex row-major).
 ovl_status gram_host(ovl_ctx* c, const Field& A, int aoff, int na, const Field& B, int boff, int nb, int g5,
                      std::vector<cd>& G) {
-  Field* dummy;
-  (void)dummy;
   const size_t gsz = (size_t)na * nb * 2;
-  OVL_TRY(ensure_work(c, gsz * 1300 + gsz));
-  double* dG = c->dwork + c->dwork_n - gsz;
-  OVL_CUDA(c, cudaMemsetAsync(dG, 0, gsz * sizeof(double), c->st));
-  ProfPair pp;
-  prof_begin(c, 6, &pp);
-  launch_gram(A.prec, A.ref(aoff), na, B.prec, B.ref(boff), nb, c->V, dG, c->dwork, c->dwork_n - gsz, g5, c->st);
-  prof_end(c, &pp, (double)c->V * ((double)na * spinor_site_bytes(A.prec) + (double)nb * spinor_site_bytes(B.prec)));
-  OVL_TRY(check_launch(c, __func__));
+  double* dG = nullptr;
+  int* derr = nullptr;
+  OVL_TRY(gram_device(c, A, aoff, na, B, boff, nb, g5, &dG, &derr));
+  int herr = 0;
   std::vector<double> h(gsz);
   OVL_CUDA(c, cudaMemcpyAsync(h.data(), dG, gsz * sizeof(double), cudaMemcpyDeviceToHost, c->st));
+  if (derr) OVL_CUDA(c, cudaMemcpyAsync(&herr, derr, sizeof(int), cudaMemcpyDeviceToHost, c->st));
   OVL_CUDA(c, cudaStreamSynchronize(c->st));
+  if (herr) return set_err(c, OVL_ETIMEOUT, "tensor-core Gram block: a bounded wait on the MMA pipeline gave up");
   G.resize((size_t)na * nb);
   for (size_t k = 0; k < G.size(); ++k) G[k] = cd(h[2 * k], h[2 * k + 1]);
   return OVL_OK;

@@ -72,6 +72,8 @@ ovl_status norms_batch(ovl_ctx* c, const Field& x, int xoff, int n, std::vector<
 ovl_status axpby_batch(ovl_ctx* c, const std::vector<cd>& a, const Field& x, int xoff, const std::vector<cd>& b,
                        const Field& y, int yoff, Field& z, int zoff, int n);
 ovl_status copy_convert(ovl_ctx* c, const Field& in, int ioff, Field& out, int ooff, int n);
+ovl_status gram_device(ovl_ctx* c, const Field& A, int aoff, int na, const Field& B, int boff, int nb, int g5,
+                       double** dG, int** derr);
 ovl_status gram_host(ovl_ctx* c, const Field& A, int aoff, int na, const Field& B, int boff, int nb, int g5,
                      std::vector<cd>& G);
 ovl_status combine_host(ovl_ctx* c, const Field& A, int aoff, int na, const std::vector<cd>& C, Field& Y, int yoff,
