@@ -9,7 +9,9 @@ lattices only) or from the Zolotarev rational of Sec. 3,
   epsilon(K) v = sum_i omega_i K (K^2 + sigma_i)^-1 v,
 
 each shifted system solved by its own plain conjugate gradient (no multi-shift,
-no pole dropping). Test infrastructure only.
+no pole dropping), optionally with the lowest eigenvectors of K taken out and
+their sign applied exactly (Sec. 1: deflation of the smallest eigenvectors of K,
+the approximation covering the rest of the spectrum). Test infrastructure only.
 """
 import numpy as np
 
@@ -162,6 +164,24 @@ def zolotarev_sign_apply(U, v, m0, omega, sigma, tol=1e-13, antiperiodic_t=False
     if return_solutions:
         return out, sols
     return out
+
+
+def deflated_sign_apply(U, v, m0, psi, lam, omega, sigma, tol=1e-13, antiperiodic_t=False):
+    """Sec. 1: sign(K) = sum_i psi_i psi_i^dag sign(lambda_i) over the eigenpairs of K, with
+    the smallest eigenvectors deflated and the Zolotarev rational applied to the rest:
+
+      sign(K) v ~ sum_i sign(lambda_i) psi_i (psi_i, v) + epsilon(K) (v - sum_i psi_i (psi_i, v))
+
+    psi: (n, ...) orthonormal eigenvectors of K, lam their eigenvalues; omega, sigma the
+    rational for the interval left after deflation."""
+    v = np.asarray(v)
+    proj = v.copy()
+    low = np.zeros_like(v)
+    for p, l in zip(psi, lam):
+        c = vdot(p, v)
+        proj = proj - c * p
+        low = low + np.sign(l) * c * p
+    return low + zolotarev_sign_apply(U, proj, m0, omega, sigma, tol, antiperiodic_t)
 
 
 def overlap_apply(U, v, m0, mu, omega, sigma, tol=1e-13, antiperiodic_t=False):

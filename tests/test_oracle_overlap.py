@@ -110,3 +110,35 @@ def test_pooled_per_pole_solves_match():
     for j, mu in enumerate((0.05, 0.3)):
         ref = 0.5 * (1 + mu) * v2[j].ravel() + 0.5 * (1 - mu) * (G5 @ (R @ v2[j].ravel()))
         assert np.linalg.norm(D[j].ravel() - ref) <= 1e-11 * np.linalg.norm(ref)
+
+
+def test_deflated_sign_pins():
+    """Sec. 1: sign(K) with the smallest eigenvectors of K deflated and the Zolotarev
+    rational on the interval left over. With the exact low eigenvectors the result is
+    within Delta(n, a', b) of the spectral sign, although the same rational without the
+    deflation is far off (its interval no longer covers the low modes); no deflated vectors
+    reduces to the plain rational; deflating every eigenvector gives the spectral sign."""
+    U, Kd, S, w = dense_setup(DIMS)
+    wv, Q = np.linalg.eigh(Kd)
+    order = np.argsort(np.abs(wv))
+    v = synth.gaussian_source(DIMS, 5)
+    ref = (S @ v.ravel()).reshape(v.shape)
+    nd = 12
+    lam = wv[order[:nd]]
+    psi = np.stack([Q[:, k].reshape(v.shape) for k in order[:nd]])
+    a2 = 0.99 * np.abs(wv[order[nd]])
+    b = 1.01 * np.max(np.abs(wv))
+    om, sg, delta = zo.zolotarev(6, a2, b)
+    got = overlap.deflated_sign_apply(U, v, 1.4, psi, lam, om, sg, tol=1e-14)
+    err = np.linalg.norm(got - ref) / np.linalg.norm(v)
+    plain = overlap.zolotarev_sign_apply(U, v, 1.4, om, sg, tol=1e-14)
+    err_plain = np.linalg.norm(plain - ref) / np.linalg.norm(v)
+    assert err <= delta * (1 + 1e-6) + 1e-12
+    assert err_plain > 100 * delta
+    # no deflated vectors: the plain rational
+    none = overlap.deflated_sign_apply(U, v, 1.4, psi[:0], lam[:0], om, sg, tol=1e-14)
+    assert np.linalg.norm(none - plain) <= 1e-13 * np.linalg.norm(plain)
+    # every eigenvector deflated: the spectral sign exactly, whatever the rational
+    allpsi = np.stack([Q[:, k].reshape(v.shape) for k in range(Q.shape[1])])
+    full = overlap.deflated_sign_apply(U, v, 1.4, allpsi, wv, om, sg, tol=1e-14)
+    assert np.linalg.norm(full - ref) <= 1e-11 * np.linalg.norm(ref)
