@@ -761,6 +761,65 @@ def config_c5(B, stream):
     return out
 
 
+def kernel_deflation(B, stream):
+    """Kernel low-mode deflation of the sign function (Sec. 1) on rough synthetic links
+    (eps 0.7, where the smallest |lambda(K)| are small and spread, so b/a is large) at
+    8^4: the overlap apply of 16 Gaussian vectors at eta = 1e-10 (double-float,
+    stored-basis Lanczos), undeflated with the fewest poles that reach Delta <= 1e-10 on the
+    library's [a, b], and with 8, 16 and 32 eigenvectors of K deflated (the rational
+    rebuilt on the narrowed interval with the fewest poles); the cost of finding the
+    eigenvectors, the Lanczos steps per apply, and the difference between the results."""
+    import torch
+    import synth
+    dims = (8, 8, 8, 8)
+    U = synth.gauge_links(dims, 0.7, 1006)
+    vecs = synth.gaussian_source(dims, 2006, nvec=NVEC)
+    out = {"workload": "8^4, eps 0.7 links seed 1006, m0 1.4, mu 0.05, 16 Gaussian vectors, eta 1e-10"}
+    p = B.ovl_params_default()
+    p.stream = stream.cuda_stream
+    probe = B.Overlap(dims, U, M0, MU, 64, 1.0, params=p)     # spectral bounds only
+    _, _, _, a, b = probe.zolotarev()
+    probe.close()
+    npoles = next(n for n in range(4, 65) if B.ovl_zolotarev_coeffs(n, a, b)[2] <= EPS)
+    p.a_override, p.b_override = a, b
+    ctx = B.Overlap(dims, U, M0, MU, npoles, EPS, params=p)
+    dv = torch.from_numpy(vecs).cuda()
+    ref = torch.empty_like(dv)
+    out_t = torch.empty_like(dv)
+
+    def timed(dst):
+        ctx.apply(dv, dst, eta=EPS, prec=B.OVL_PREC_F64E)        # warm-up (caps, graphs)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(2):
+            ctx.apply(dv, dst, eta=EPS, prec=B.OVL_PREC_F64E)
+        torch.cuda.synchronize()
+        dt = (time.perf_counter() - t0) / 2
+        ctx.profile_reset()
+        ctx.profile_enable(True)
+        ctx.apply(dv, dst, eta=EPS, prec=B.OVL_PREC_F64E)
+        ctx.profile_enable(False)
+        launches = ctx.profile_get()["wilson_f64e"]["launches"]
+        return {"applies_per_s": NVEC / dt, "ms_per_apply_of_16": dt * 1e3, "wilson_launches_per_apply": launches}
+
+    out["undeflated"] = dict(timed(ref), a=a, b=b, n_poles=npoles)
+    r = ref.cpu().numpy()
+    for n_ev in (8, 16, 32):
+        t0 = time.perf_counter()
+        lam, res, a2, np2, its = ctx.kernel_deflate(n_ev, tol=1e-10, max_iter=400)
+        tk = time.perf_counter() - t0
+        row = dict(timed(out_t), find_eigenvectors_s=tk, filter_steps=its, a=a2, n_poles=np2,
+                   lambda_abs_range=[float(np.min(np.abs(lam))), float(np.max(np.abs(lam)))],
+                   max_residual=float(np.max(res)))
+        g = out_t.cpu().numpy()
+        row["max_rel_diff_vs_undeflated"] = float(max(np.linalg.norm(g[j] - r[j]) / np.linalg.norm(r[j])
+                                                      for j in range(NVEC)))
+        out["deflated_%d" % n_ev] = row
+    ctx.kernel_deflate(0)
+    ctx.close()
+    return out
+
+
 def run_reference(args, ws, rank):
     """The oracle on this host's cores as the reference arm: every step is a complete
     oracle apply of as many 8^4 vectors as there are cores (a pool of that many
@@ -813,14 +872,17 @@ def main():
                     help="run only the 24^3x48 batched multi-mass deflated solves and print their JSON")
     ap.add_argument("--config-c5", action="store_true",
                     help="run only the fermion-force measurements (8^4 and 16^3x32) and print their JSON")
+    ap.add_argument("--kernel-deflation", action="store_true",
+                    help="run only the kernel low-mode deflation measurements (rough links) and print their JSON")
     ap.add_argument("--deflation-gain", action="store_true",
                     help="run only the deflation-gain experiment (15/30/45 vectors) and print its JSON")
     args = ap.parse_args()
-    if args.config_c4 or args.config_c5 or args.deflation_gain:
+    if args.config_c4 or args.config_c5 or args.deflation_gain or args.kernel_deflation:
         import torch
         from paper_1501_01855_gb300 import build, binding as B
         build.build()
-        fn = config_c4 if args.config_c4 else config_c5 if args.config_c5 else deflation_gain
+        fn = (config_c4 if args.config_c4 else config_c5 if args.config_c5 else
+              kernel_deflation if args.kernel_deflation else deflation_gain)
         print(json.dumps(fn(B, torch.cuda.current_stream())), flush=True)
         return
     if args.warmup < 3:

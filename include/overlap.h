@@ -179,7 +179,8 @@ ovl_status ovl_trim(ovl_ctx* ctx);
  * maximum error delta, from Jacobi elliptic functions (AGM / descending Landen). */
 ovl_status ovl_zolotarev_coeffs(int n, double a, double b, double* omega, double* sigma, double* delta);
 
-/* Zolotarev data of the context: omega[n_poles], sigma[n_poles] (may be NULL),
+/* Zolotarev data of the context: omega[n], sigma[n] (may be NULL; n the pole count in use:
+ * n_poles at create, or the count ovl_kernel_deflate chose),
  * the error Delta and the bounds a, b actually used (Sec. 3). */
 ovl_status overlap_zolotarev(const ovl_ctx* ctx, double* omega, double* sigma, double* delta,
                              double* a, double* b);
@@ -319,6 +320,27 @@ void ovl_defl_destroy(ovl_defl* defl);
  * With respect to the links the context was created from. */
 ovl_status overlap_force(ovl_ctx* ctx, double mu, const void* phi, int dtype, int on_device, double tol,
                          double* dSdU, double* S);
+
+/* Kernel low-mode deflation of the sign function (Sec. 1: sign(K) = sum_i psi_i psi_i^dag
+ * sign(lambda_i); the smallest eigenvectors of K are deflated and the approximation covers
+ * the rest of the spectrum). Finds the n_ev eigenpairs of the Hermitian kernel K with the
+ * smallest |lambda| to ||K psi - lambda psi|| <= tol (unit psi) by Chebyshev-filtered
+ * subspace iteration (at most max_iter filter steps of degree up to 24 on a block of n_ev +
+ * max(8, n_ev) FP64 vectors), keeps them in the context, and rebuilds the Zolotarev rational
+ * on [a', b] with a' = 0.95 |lambda_min| of K on the complement (300 Lanczos steps on K^2 with
+ * the eigenvectors projected out at every step; never below the original a): with
+ * n_poles = 0 the fewest poles that keep Delta <= eps_sign, else n_poles (OVL_EAPPROX if
+ * that is not enough). From then on every sign application of the context computes
+ * sign(K) v = sum_i sign(lambda_i) psi_i (psi_i, v) + eps(K) P v, P = 1 - Psi Psi^dag.
+ * n_ev = 0 removes the deflation and restores the context's original interval and poles.
+ * overlap_force refuses to run while a deflation is active (it differentiates the rational
+ * itself). Outputs (may be NULL): lambda[n_ev] (ascending |lambda|), residual[n_ev], the new
+ * lower bound a', the pole count now in use (overlap_zolotarev then reports that many
+ * poles), the filter steps taken. OVL_ENOCONV if the eigenpairs did not reach tol within
+ * max_iter steps (the context is left undeflated). Allocates 7 (n_ev + guard) FP64 spinor
+ * fields of workspace (freed by ovl_trim) and n_ev kept vectors. Synchronises the stream. */
+ovl_status ovl_kernel_deflate(ovl_ctx* ctx, int n_ev, double tol, int max_iter, int n_poles, double* lambda,
+                              double* residual, double* a_new, int* n_poles_used, int* iters_done);
 
 /* Gram block G[i][j] = (A_i, [gamma5] B_j) = sum over sites and components of
  * conj(A_i) [gamma5] B_j: the dense contraction of the Ritz step (Alg. 6: E = V^dag V,

@@ -98,6 +98,7 @@ _SIGS = {
     "ovl_bench_fp32": (I, [P, DP]),
     "ovl_gram": (I, [P, P, I, P, I, I, I, I, I, I, DP]),
     "ovl_bench_gram": (I, [P, I, I, I, I, I, DP]),
+    "ovl_kernel_deflate": (I, [P, I, D, I, I, DP, DP, DP, ctypes.POINTER(I), ctypes.POINTER(I)]),
 }
 
 
@@ -266,11 +267,24 @@ class Overlap:
         return n
 
     def zolotarev(self):
-        om = np.zeros(self.n_poles)
-        sg = np.zeros(self.n_poles)
+        om = np.zeros(64)
+        sg = np.zeros(64)
         de, a, b = np.zeros(1), np.zeros(1), np.zeros(1)
         _check(load().overlap_zolotarev(self.h, _dptr(om), _dptr(sg), _dptr(de), _dptr(a), _dptr(b)), self.h)
-        return om, sg, float(de[0]), float(a[0]), float(b[0])
+        return om[:self.n_poles].copy(), sg[:self.n_poles].copy(), float(de[0]), float(a[0]), float(b[0])
+
+    def kernel_deflate(self, n_ev, tol=1e-10, max_iter=100, n_poles=0):
+        """Deflate the n_ev lowest-|lambda| eigenvectors of K from the sign function and
+        narrow the rational to the rest of the spectrum (n_ev = 0 undoes it). Returns
+        (lambda, residuals, a', poles in use, filter steps)."""
+        lam = np.zeros(max(n_ev, 1))
+        res = np.zeros(max(n_ev, 1))
+        a = ctypes.c_double()
+        npu, its = ctypes.c_int(), ctypes.c_int()
+        _check(load().ovl_kernel_deflate(self.h, int(n_ev), float(tol), int(max_iter), int(n_poles), _dptr(lam),
+                                         _dptr(res), ctypes.byref(a), ctypes.byref(npu), ctypes.byref(its)), self.h)
+        self.n_poles = npu.value
+        return lam[:n_ev].copy(), res[:n_ev].copy(), a.value, npu.value, its.value
 
     def wilson_apply(self, x, out, prec=OVL_PREC_F64):
         pi, po, code, dev, cnt = _io(self.device, x, out)

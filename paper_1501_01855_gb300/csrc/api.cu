@@ -177,7 +177,7 @@ static ovl_status autotune_wilson(ovl_ctx* c) {
 
 // Extreme eigenvalues of K^2 by FP64 Lanczos (no reorthogonalisation; only the
 // ends of the spectrum are used).
-static ovl_status lanczos_bounds(ovl_ctx* c, int steps, double* lmin, double* lmax) {
+ovl_status ovl::lanczos_bounds(ovl_ctx* c, int steps, double* lmin, double* lmax, const Field* proj, int nproj) {
   Field *v0, *v1, *w, *t;
   OVL_TRY(get_field(c, "lz_v0", P64, 1, &v0));
   OVL_TRY(get_field(c, "lz_v1", P64, 1, &v1));
@@ -190,6 +190,15 @@ static ovl_status lanczos_bounds(ovl_ctx* c, int steps, double* lmin, double* lm
     x = ((double)(st >> 11) / 9007199254740992.0) - 0.5;
   }
   OVL_TRY(import_spinors(c, h.data(), OVL_C128, 0, 1, *v1, 0));
+  // v <- v - Psi (Psi^dag v): the Krylov space of K^2 on the complement of proj
+  auto project = [&](Field& f) -> ovl_status {
+    if (!proj || nproj <= 0) return OVL_OK;
+    std::vector<cd> G;
+    OVL_TRY(gram_host(c, *proj, 0, nproj, f, 0, 1, 0, G));
+    for (auto& g : G) g = -g;
+    return combine_host(c, *proj, 0, nproj, G, f, 0, 1, 1);
+  };
+  OVL_TRY(project(*v1));
   std::vector<double> nrm;
   OVL_TRY(norms_batch(c, *v1, 0, 1, nrm));
   std::vector<cd> a1(1, 1.0 / nrm[0]), z1(1, 0.0), one(1, 1.0);
@@ -200,6 +209,7 @@ static ovl_status lanczos_bounds(ovl_ctx* c, int steps, double* lmin, double* lm
   for (int j = 0; j < steps; ++j) {
     OVL_TRY(wilson_apply_field(c, P64, *v1, 0, *t, 0, 1));
     OVL_TRY(wilson_apply_field(c, P64, *t, 0, *w, 0, 1));
+    OVL_TRY(project(*w));
     std::vector<cd> d;
     OVL_TRY(dots_batch(c, *v1, 0, *w, 0, 1, d));
     const double alpha = d[0].real();
@@ -216,6 +226,9 @@ static ovl_status lanczos_bounds(ovl_ctx* c, int steps, double* lmin, double* lm
     v1 = &c->ws["lz_v1"];
     std::vector<cd> ib(1, 1.0 / beta);
     OVL_TRY(axpby_batch(c, ib, *w, 0, z1, *w, 0, *v1, 0, 1));
+    // the three-term recurrence would amplify what is left of the projected directions
+    // (their coefficients follow a recurrence of their own): project every new vector
+    OVL_TRY(project(*v1));
   }
   const int n = (int)al.size();
   be.resize(std::max(0, n - 1));
@@ -228,6 +241,7 @@ extern "C" void overlap_destroy(ovl_ctx* c) {
   if (c->st) cudaStreamSynchronize(c->st);
   else cudaDeviceSynchronize();
   for (auto& kv : c->ws) free_field(kv.second);
+  free_field(c->kd);
   if (c->lz_pool) cudaFree(c->lz_pool);
   for (int p = 0; p < 4; ++p)
     if (c->link[p]) cudaFree(c->link[p]);
@@ -291,7 +305,6 @@ static ovl_status create_impl(ovl_ctx* c, const int dims[4], const double* links
   c->m0 = m0;
   c->kappa = 1.0 / (8.0 - 2.0 * m0);
   c->mu = mu;
-  c->npoles = n_poles;
   c->eps_sign = eps_sign;
   c->st = (cudaStream_t)c->P.stream;
   OVL_CUDA(c, cudaGetDevice(&c->device));
@@ -328,18 +341,29 @@ static ovl_status create_impl(ovl_ctx* c, const int dims[4], const double* links
     if (!(b > 0)) b = 1.05 * std::sqrt(lmax);
   }
   if (!(b > a)) return set_err(c, OVL_EINVAL, "spectral bounds need 0 < a < b");
-  c->za = a;
-  c->zb = b;
-  c->omega.resize(n_poles);
-  c->sigma.resize(n_poles);
-  if (zolotarev_coeffs(n_poles, a, b, c->omega.data(), c->sigma.data(), &c->delta) != 0)
+  OVL_TRY(set_poles(c, n_poles, a, b));
+  c->za0 = a;
+  c->npoles0 = n_poles;
+  return OVL_OK;
+}
+
+ovl_status ovl::set_poles(ovl_ctx* c, int n_poles, double a, double b) {
+  std::vector<double> om(n_poles), sg(n_poles);
+  double delta = 0.0;
+  if (zolotarev_coeffs(n_poles, a, b, om.data(), sg.data(), &delta) != 0)
     return set_err(c, OVL_EINVAL, "Zolotarev coefficients failed");
-  if (c->delta > eps_sign) {
+  if (delta > c->eps_sign) {
     char m[200];
-    snprintf(m, sizeof(m), "Zolotarev Delta %.3e with %d poles on [%.4g, %.4g] exceeds eps_sign %.3e", c->delta,
-             n_poles, a, b, eps_sign);
+    snprintf(m, sizeof(m), "Zolotarev Delta %.3e with %d poles on [%.4g, %.4g] exceeds eps_sign %.3e", delta,
+             n_poles, a, b, c->eps_sign);
     return set_err(c, OVL_EAPPROX, m);
   }
+  c->npoles = n_poles;
+  c->za = a;
+  c->zb = b;
+  c->omega = om;
+  c->sigma = sg;
+  c->delta = delta;
   Poles& P = c->hpoles;
   memset(&P, 0, sizeof(P));
   P.n = n_poles;
@@ -349,7 +373,10 @@ static ovl_status create_impl(ovl_ctx* c, const int dims[4], const double* links
     P.omega[i] = c->omega[i];
     P.gbound[i] = pole_gbound(c->sigma[i], a, b);
   }
+  if (c->st) cudaStreamSynchronize(c->st);
   OVL_CUDA(c, cudaMemcpy(c->dpoles, &P, sizeof(Poles), cudaMemcpyHostToDevice));
+  // step counts seen so far belong to the old rational
+  memset(c->lz_kmax, 0, sizeof(c->lz_kmax));
   return OVL_OK;
 }
 
@@ -1032,6 +1059,10 @@ extern "C" ovl_status overlap_force(ovl_ctx* c, double mu, const void* phi, int 
                                     double* dSdU, double* S) {
   if (!c || !phi || !dSdU) return OVL_EINVAL;
   if (!(mu > 0 && mu < 1)) return set_err(c, OVL_EINVAL, "mu must lie in (0, 1)");
+  if (c->kd_n > 0)
+    return set_err(c, OVL_EINVAL,
+                   "overlap_force differentiates the Zolotarev rational itself: remove the kernel low-mode "
+                   "deflation first (ovl_kernel_deflate with n_ev = 0)");
   Field* fp;
   OVL_TRY(get_field(c, "f_phi", P64, 1, &fp));
   OVL_TRY(import_spinors(c, phi, dtype, on_device, 1, *fp, 0));

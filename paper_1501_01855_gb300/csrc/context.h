@@ -84,6 +84,7 @@ struct ovl_ctx {
   int lz_cap = 0;
   void* lz_pool = nullptr;       // stored Lanczos bases of every sign precision (one at a time)
   size_t lz_pool_bytes = 0;
+  bool lz_pool_busy = false;     // a sign application holds a view of the pool
   int lz_kmax[4][17] = {{0}};    // most Lanczos steps seen per sign mode and decade of eta
   double* hpin = nullptr;        // pinned host staging for scalars, 64 * 4096 doubles
   void* hstage = nullptr;        // pinned host staging for spinor copies
@@ -96,6 +97,14 @@ struct ovl_ctx {
   std::vector<ovl::MsGraph> graphs;  // cached multi-shift CG iteration graphs
   long long graph_clock = 0;
   bool exact_rational = false;   // solve shifted systems past Delta (gradient of the rational)
+  // kernel low-mode deflation of the sign function (Sec. 1): eigenvectors of K with the
+  // smallest |lambda| (FP64), their eigenvalues, and the interval and pole count the rational
+  // had before it was narrowed to the rest of the spectrum
+  ovl::Field kd;
+  int kd_n = 0;
+  std::vector<double> kd_lambda;
+  double za0 = 0.0;
+  int npoles0 = 0;
   std::string err;
   ovl::Profiler prof;
   long long wcalls[4] = {0, 0, 0, 0};  // Wilson applications by precision
@@ -172,6 +181,14 @@ ovl_status sign_op(ovl_ctx* c, int mode, const Field& v, int voff, Field& out, i
                    double c1, double c2, const double* coef, int herm, const Field* dot_w, int woff, double* dots,
                    SignStats* stats);
 int choose_mode(const ovl_ctx* c, double eta);
+
+// Zolotarev rational with n_poles poles on [a, b] (ascending sigma), its error bound and the
+// per-pole bounds, to the context and the device; OVL_EAPPROX when Delta exceeds eps_sign.
+ovl_status set_poles(ovl_ctx* c, int n_poles, double a, double b);
+// Extreme eigenvalues of K^2 by `steps` Lanczos steps from a fixed random vector; with nproj
+// > 0 on the complement of the first nproj (orthonormal) vectors of *proj.
+ovl_status lanczos_bounds(ovl_ctx* c, int steps, double* lmin, double* lmax, const Field* proj = nullptr,
+                          int nproj = 0);
 
 // Upload count doubles of per-system scalars through the pinned ring; returns the
 // device copy (valid for kernels issued later on the context stream).

@@ -12,6 +12,7 @@
 
 #include "context.h"
 #include "hostmath.h"
+#include "solver.h"
 
 namespace ovl {
 
@@ -72,6 +73,23 @@ ovl_status get_field(ovl_ctx* c, const std::string& name, int prec, int n, Field
   if (cudaMalloc(&f.data, bytes) != cudaSuccess) {
     cudaGetLastError();
     f.data = nullptr;
+    // the stored Lanczos basis is a cache sized from the free memory: give it back (and
+    // the graphs that point into it) unless a sign application is using it right now
+    if (c->lz_pool && !c->lz_pool_busy) {
+      cudaStreamSynchronize(c->st);
+      cudaFree(c->lz_pool);
+      c->lz_pool = nullptr;
+      c->lz_pool_bytes = 0;
+      for (auto& g : c->graphs)
+        if (g.exec) cudaGraphExecDestroy(g.exec);
+      c->graphs.clear();
+      if (cudaMalloc(&f.data, bytes) != cudaSuccess) {
+        cudaGetLastError();
+        f.data = nullptr;
+      }
+    }
+  }
+  if (f.data == nullptr) {
     f.n = 0;
     return set_err(c, OVL_ENOMEM, "cudaMalloc failed for workspace " + name);
   }
@@ -126,7 +144,8 @@ ovl_status ensure_lz(ovl_ctx* c, int nrhs, int cap) {
   OVL_CUDA(c, cudaMalloc((void**)&c->lz_ctr, sizeof(unsigned int) * n));
   OVL_CUDA(c, cudaMemsetAsync(c->lz_ctr, 0, sizeof(unsigned int) * n, c->st));
   OVL_CUDA(c, cudaMalloc((void**)&c->lz_hist, sizeof(double) * 2 * (size_t)n * k));
-  OVL_CUDA(c, cudaMalloc((void**)&c->lz_Y, sizeof(double) * (size_t)n * c->npoles * 2 * k));
+  // sized for the largest pole count (kernel deflation can change the count later)
+  OVL_CUDA(c, cudaMalloc((void**)&c->lz_Y, sizeof(double) * (size_t)n * NPMAX * 2 * k));
   OVL_CUDA(c, cudaMalloc((void**)&c->lz_coefW, sizeof(double) * (size_t)n * k));
   c->lz_n = n;
   c->lz_cap = k;
@@ -439,12 +458,13 @@ ovl_status sign_op(ovl_ctx* c, int mode, const Field& v, int voff, Field& out, i
   if (!c->exact_rational) emin = std::max(emin, c->delta);
   const int cap = lz_cap_for(c, mode, emin);
   const double per_lz = (double)cap * c->V * (spinor_bytes(PP) + (PP == P16 ? 4.0 : 0.0));
-  // the basis budget: params.basis_gb, and never more than 85% of what the device has free
-  // (counting the pool this context already holds)
+  // the basis budget: params.basis_gb, and never more than 70% of what the device has free
+  // (counting the pool this context already holds); the rest is left to the workspaces of
+  // the solvers around the sign, and a workspace that still does not fit takes the pool back
   double budget = c->P.basis_gb * 1e9;
   {
     size_t fr = 0, tot = 0;
-    if (cudaMemGetInfo(&fr, &tot) == cudaSuccess) budget = std::min(budget, 0.85 * ((double)fr + c->lz_pool_bytes));
+    if (cudaMemGetInfo(&fr, &tot) == cudaSuccess) budget = std::min(budget, 0.7 * ((double)fr + c->lz_pool_bytes));
     else cudaGetLastError();
   }
   const int n_fit = (int)std::min(1e9, budget / per_lz);
@@ -488,6 +508,63 @@ ovl_status sign_op(ovl_ctx* c, int mode, const Field& v, int voff, Field& out, i
   return OVL_OK;
 }
 
+// Kernel low-mode deflation (Sec. 1: the smallest eigenvectors of K deflated, the rational
+// covering the rest of the spectrum). With Psi the stored eigenvectors (K psi_i = lambda_i
+// psi_i) and P = 1 - Psi Psi^dag,
+//   sign(K) v = K [ R(K^2) P v + sum_i psi_i (psi_i, v) / |lambda_i| ],
+// R the rational on the narrowed interval, so the sign's core runs on P v and the low
+// modes enter y (cleaned of rounding-level components along the psi_i) before the final K
+// application, whose fused epilogue stays as it is.
+// kd_project: C = Psi^dag v (host, n_k x n) and *vin = P v (a P64 workspace), or v itself
+// when no deflation is active (or the rational itself is differentiated).
+static ovl_status kd_project(ovl_ctx* c, const Field& v, int voff, int n, const Field** vin, int* vinoff,
+                             std::vector<cd>& C) {
+  *vin = &v;
+  *vinoff = voff;
+  C.clear();
+  if (c->kd_n <= 0 || c->exact_rational) return OVL_OK;
+  Field* vp;
+  OVL_TRY(get_field(c, "kd_vp", P64, n, &vp));
+  OVL_TRY(copy_convert(c, v, voff, *vp, 0, n));
+  OVL_TRY(gram_host(c, c->kd, 0, c->kd_n, *vp, 0, n, 0, C));
+  std::vector<cd> m(C.size());
+  for (size_t k = 0; k < C.size(); ++k) m[k] = -C[k];
+  OVL_TRY(combine_host(c, c->kd, 0, c->kd_n, m, *vp, 0, n, 1));
+  *vin = vp;
+  *vinoff = 0;
+  return OVL_OK;
+}
+
+// y <- P y + sum_i psi_i (psi_i, v) / |lambda_i| for the C of kd_project. R(K^2) P v has no
+// component along the psi_i in exact arithmetic; in floating point the Krylov recurrences
+// let rounding-level components along them grow (like the Lanczos polynomials outside the
+// narrowed interval), so they are removed from y before the exact low-mode part is added.
+static ovl_status kd_add_low(ovl_ctx* c, Field& y, int n, const std::vector<cd>& C) {
+  if (C.empty()) return OVL_OK;
+  const int nk = c->kd_n;
+  const Field* y64 = &y;
+  if (y.prec != P64 && y.prec != P32) {
+    Field* t;
+    OVL_TRY(get_field(c, "kd_ty", P64, n, &t));
+    OVL_TRY(copy_convert(c, y, 0, *t, 0, n));
+    y64 = t;
+  }
+  std::vector<cd> C2;
+  OVL_TRY(gram_host(c, c->kd, 0, nk, *y64, 0, n, 0, C2));
+  std::vector<cd> L(C.size());
+  for (int i = 0; i < nk; ++i)
+    for (int j = 0; j < n; ++j)
+      L[(size_t)i * n + j] = C[(size_t)i * n + j] / std::fabs(c->kd_lambda[i]) - C2[(size_t)i * n + j];
+  if (y.prec == P64 || y.prec == P32) return combine_host(c, c->kd, 0, nk, L, y, 0, n, 1);
+  Field *t, *te;
+  OVL_TRY(get_field(c, "kd_t", P64, n, &t));
+  OVL_TRY(get_field(c, "kd_te", y.prec, n, &te));
+  OVL_TRY(combine_host(c, c->kd, 0, nk, L, *t, 0, n, 0));
+  OVL_TRY(copy_convert(c, *t, 0, *te, 0, n));
+  std::vector<cd> one(n, 1.0);
+  return axpby_batch(c, one, y, 0, one, *te, 0, y, 0, n);
+}
+
 // Per-system sign accuracies to the device (c->dscal), with the stopping-rule convention
 // of the multi-shift CG: never past Delta (unless the rational itself is differentiated);
 // positive, one error budget shared by the poles; negative, an even share per pole (the
@@ -529,6 +606,11 @@ static ovl_status sign_op_batch_lz(ovl_ctx* c, int mode, const Field& v, int vof
   Field* W = &Wv;
   Field *t, *y;
   OVL_TRY(lz_pool_field(c, PB, cap * n, &Wv));
+  struct PoolBusy {
+    ovl_ctx* c;
+    ~PoolBusy() { c->lz_pool_busy = false; }
+  } busy{c};
+  c->lz_pool_busy = true;
   OVL_TRY(get_field(c, "lz_t" + tag, PB, n, &t));
   OVL_TRY(get_field(c, "lz_y" + tag, PR, n, &y));
   OVL_TRY(ensure_partials(c, n));
@@ -546,9 +628,13 @@ static ovl_status sign_op_batch_lz(ovl_ctx* c, int mode, const Field& v, int vof
   const LzCtl ctl{c->lz, c->lz_ctr, ahist, bhist, hcap, c->dpoles};
   ProfPair pp;
 
+  const Field* vin;
+  int vinoff;
+  std::vector<cd> kdC;
+  OVL_TRY(kd_project(c, v, voff, n, &vin, &vinoff, kdC));
   prof_begin(c, 4, &pp);
-  launch_lz_init(v.prec, PB, PR, v.ref(voff), W->ref(), y->ref(), n, V, c->partials, c->st);
-  prof_end(c, &pp, (double)n * V * (spinor_bytes(v.prec) + spinor_bytes(PB) + spinor_bytes(PR)));
+  launch_lz_init(vin->prec, PB, PR, vin->ref(vinoff), W->ref(), y->ref(), n, V, c->partials, c->st);
+  prof_end(c, &pp, (double)n * V * (spinor_bytes(vin->prec) + spinor_bytes(PB) + spinor_bytes(PR)));
   prof_begin(c, 5, &pp);
   launch_lz_start(c->lz, c->partials, sh.nsb, n, c->dpoles, d_eta, c->P.mscg_max, cap, 1, c->st);
   prof_end(c, &pp, 0.0);
@@ -635,6 +721,7 @@ static ovl_status sign_op_batch_lz(ovl_ctx* c, int mode, const Field& v, int vof
     launch_lz_start(c->lz, c->partials, sh.nsb, n, c->dpoles, d_eta, c->P.mscg_max, cap, 0, c->st);
     OVL_TRY(check_launch(c, __func__));
   }
+  OVL_TRY(kd_add_low(c, *y, n, kdC));
   // final Wilson application with the overlap / sign epilogue
   double* d_part = dot_w ? c->partials : nullptr;
   prof_begin(c, wcls, &pp);
@@ -725,9 +812,13 @@ static ovl_status sign_op_batch(ovl_ctx* c, int mode, const Field& v, int voff, 
   const double sbytes = (double)spinor_bytes(PP) * V, rbytes = (double)spinor_bytes(PR) * V;
   ProfPair pp;
 
+  const Field* vin;
+  int vinoff;
+  std::vector<cd> kdC;
+  OVL_TRY(kd_project(c, v, voff, n, &vin, &vinoff, kdC));
   prof_begin(c, 4, &pp);
-  launch_ms_init(v.prec, PR, PP, v.ref(voff), r->ref(), pb->ref(), y->ref(), np, n, V, c->partials, c->st);
-  prof_end(c, &pp, (double)n * V * (spinor_bytes(v.prec) + 2 * spinor_bytes(PR) + np * spinor_bytes(PP)));
+  launch_ms_init(vin->prec, PR, PP, vin->ref(vinoff), r->ref(), pb->ref(), y->ref(), np, n, V, c->partials, c->st);
+  prof_end(c, &pp, (double)n * V * (spinor_bytes(vin->prec) + 2 * spinor_bytes(PR) + np * spinor_bytes(PP)));
   prof_begin(c, 5, &pp);
   launch_ms_scalar0(c->ms, c->partials, sh.nsb, n, c->dpoles, d_eta, c->P.mscg_max, c->st);
   prof_end(c, &pp, 0.0);
@@ -793,6 +884,7 @@ static ovl_status sign_op_batch(ovl_ctx* c, int mode, const Field& v, int voff, 
     if (total > c->P.mscg_max + 16) break;
     chunk = std::min(32, chunk * 2);
   }
+  OVL_TRY(kd_add_low(c, *y, n, kdC));
   // final Wilson application with the overlap / sign epilogue
   double* d_part = dot_w ? c->partials : nullptr;
   prof_begin(c, wcls, &pp);

@@ -160,16 +160,21 @@ struct TgLoad<P32> {
   }
 };
 
-// balanced base-128 digit s (0-based) of F <= 2^42, as BF16 bits with the sign of x applied
-__device__ __forceinline__ uint32_t digit_bf16(unsigned long long g, int s, uint32_t neg) {
-  // g = F + 64 (2^28 + 2^21 + 2^14 + 2^7 + 1): digit 0 is g >> 35 (0 .. 128), digit s >= 1
-  // is ((g >> (35 - 7 s)) & 127) - 64 (-64 .. 63)
-  int d;
-  if (s == 0) d = (int)(g >> 35);
-  else d = (int)((g >> (35 - 7 * s)) & 127ull) - 64;
-  // exact float of a small integer: bits of 1.5 x 2^23 plus d, minus 1.5 x 2^23
-  const float f = __int_as_float(0x4B400000 + d) - 12582912.0f;
-  return (__float_as_uint(f) >> 16) ^ (neg ? 0x8000u : 0u);
+// Balanced base-128 digit s (0-based) of the real and the imaginary part, as a BF16 pair
+// (real in the low half) with the signs of x applied. g = F + 64 (2^28 + 2^21 + 2^14 + 2^7 +
+// 1), F <= 2^42: digit 0 is g >> 35 (0 .. 128), digit s >= 1 is ((g >> (35 - 7 s)) & 127) - 64.
+// A digit is placed in the mantissa of 128.0f (bits 16..22; 128 carries into the exponent and
+// gives 256), the offset is subtracted exactly, and the upper halves of the two floats are
+// the BF16 values (at most 8 significant bits).
+__device__ __forceinline__ float tg_digit_f(uint32_t lo, uint32_t hi, int s) {
+  if (s == 0) return __uint_as_float(0x43000000u + ((hi >> 3) << 16)) - 128.0f;
+  const uint32_t raw = s == 1 ? (__funnelshift_r(lo, hi, 28) & 127u) : ((lo >> (35 - 7 * s)) & 127u);
+  return __uint_as_float(0x43000000u | (raw << 16)) - 192.0f;
+}
+__device__ __forceinline__ uint32_t tg_digit_pair(uint32_t rlo, uint32_t rhi, uint32_t ilo, uint32_t ihi, int s,
+                                                  uint32_t negmask) {
+  const float fr = tg_digit_f(rlo, rhi, s), fi = tg_digit_f(ilo, ihi, s);
+  return __byte_perm(__float_as_uint(fr), __float_as_uint(fi), 0x7632) ^ negmask;
 }
 
 constexpr unsigned long long TG_BIAS = 64ull * ((1ull << 28) + (1ull << 21) + (1ull << 14) + (1ull << 7) + 1ull);
@@ -316,22 +321,22 @@ __global__ void __launch_bounds__(TG_THREADS, 1)
         if (g5q && q0 + j >= (size_t)g5q) neg ^= 3u;
       }
       const unsigned long long gr = fr + TG_BIAS, gi = fi + TG_BIAS;
+      const uint32_t rlo = (uint32_t)gr, rhi = (uint32_t)(gr >> 32), ilo = (uint32_t)gi, ihi = (uint32_t)(gi >> 32);
+      const uint32_t negmask = ((neg & 1u) ? 0x8000u : 0u) | ((neg & 2u) ? 0x80000000u : 0u);
       if (isA) {
         // A row r and A' row 64 + r: (re, im) and (-im, re)
         const uint32_t off = (uint32_t)((kc * 16 + rg) * 128 + rl * 16 + kp * 4);
 #pragma unroll
         for (int d = 0; d < TG_S; ++d) {
-          const uint32_t br = digit_bf16(gr, d, neg & 1u), bi = digit_bf16(gi, d, neg & 2u);
-          *reinterpret_cast<uint32_t*>(stA + d * TG_TILE_A + off) = br | (bi << 16);
-          *reinterpret_cast<uint32_t*>(stA + d * TG_TILE_A + off + 8 * 128) = (bi ^ 0x8000u) | (br << 16);
+          const uint32_t pr = tg_digit_pair(rlo, rhi, ilo, ihi, d, negmask);
+          *reinterpret_cast<uint32_t*>(stA + d * TG_TILE_A + off) = pr;
+          *reinterpret_cast<uint32_t*>(stA + d * TG_TILE_A + off + 8 * 128) = __byte_perm(pr, 0u, 0x1032) ^ 0x8000u;
         }
       } else {
         const uint32_t off = (uint32_t)((kc * 8 + rg) * 128 + rl * 16 + kp * 4);
 #pragma unroll
-        for (int d = 0; d < TG_S; ++d) {
-          const uint32_t br = digit_bf16(gr, d, neg & 1u), bi = digit_bf16(gi, d, neg & 2u);
-          *reinterpret_cast<uint32_t*>(stB + d * TG_TILE_B + off) = br | (bi << 16);
-        }
+        for (int d = 0; d < TG_S; ++d)
+          *reinterpret_cast<uint32_t*>(stB + d * TG_TILE_B + off) = tg_digit_pair(rlo, rhi, ilo, ihi, d, negmask);
       }
     }
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
