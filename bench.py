@@ -62,10 +62,11 @@ FP64_NOMINAL_TFLOPS = 1.25            # GB300 FP64 (nominal; the ALU roofline of
 # 1056; x 8 neighbours, plus the diagonal term in - kappa hop (24 x (7 + 11)). Loads,
 # index arithmetic, phase selects and the epilogue reductions are not counted.
 DF64_FP32_OPS_PER_SITE = 8 * (12 * 8 + 12 * (4 + 5 * 12) + 24 * 8) + 24 * (7 + 11)
-# DRAM bytes (read + write) per launch of the double-float Wilson kernel in this step,
-# from an ncu capture of this command (the summary under profiles/ gives it); None
-# until captured for the current kernel.
-TRAFFIC_WILSON_DF64 = None
+# DRAM bytes (read + write) per launch of the double-float Wilson kernel in this step: the
+# mean of the first six timed launches (three of each Lanczos mode) in one ncu capture of
+# this command (profiles/launches_overlap_apply_lanczos_df64_16x16x16x32.md); each mode moves
+# 1.18-1.19 x its algorithmic bytes.
+TRAFFIC_WILSON_DF64 = 1.44e9
 # Algorithmic bytes of one Wilson launch, per site: every system reads its input spinor
 # and writes its output (K mode) or also reads p and r and writes r (r-update mode); the
 # four 18-real FP64 links of the site (576 B) are read once per launch.

@@ -117,10 +117,11 @@ static void convert_links(const double* links, const int L[4], int bc_t, std::ve
   }
 }
 
-// Autotuner: time the Wilson-kernel variants (thread per site, direction split, 4D tiles
-// when the lattice divides into them, and for double-float the lane-pair form) for every
-// storage precision on this lattice (random input; one system, four for double-float,
-// whose sign launches carry several) and keep the fastest.
+// Create-time autotuner: the Wilson-kernel launch shapes (thread per site, direction split,
+// 4D tiles when the lattice divides into them, and for double-float the lane-pair form)
+// timed for every storage precision on this lattice (random input), once with one system
+// and once with a batch (min(12, batch_max) systems; 4 in double-float), and the fastest
+// kept for each (another shape must beat the thread-per-site one by 5%).
 static ovl_status autotune_wilson(ovl_ctx* c) {
   const int forced = c->P.wilson_variant;
   std::vector<double> h((size_t)24 * c->V);
@@ -135,38 +136,46 @@ static ovl_status autotune_wilson(ovl_ctx* c) {
   for (int p = 0; p < 4; ++p) {
     if (forced >= 0 && forced <= 3) {
       c->wvar[p] = (forced == 2 && !wilson_tiles_fit(c->g)) || (forced == 3 && p != P64E) ? 0 : forced;
+      c->wvar_multi[p] = c->wvar[p];
       continue;
     }
-    const int ns = p == P64E ? std::min(4, c->P.batch_max) : 1;
+    const int nmulti = p == P64E ? std::min(4, c->P.batch_max) : std::min(12, c->P.batch_max);
     Field *fi, *fo;
-    OVL_TRY(get_field(c, "at_in", p, ns, &fi));
-    OVL_TRY(get_field(c, "at_out", p, ns, &fo));
-    for (int j = 0; j < ns; ++j) OVL_TRY(import_spinors(c, h.data(), OVL_C128, 0, 1, *fi, j));
+    OVL_TRY(get_field(c, "at_in", p, std::max(1, nmulti), &fi));
+    OVL_TRY(get_field(c, "at_out", p, std::max(1, nmulti), &fo));
+    for (int j = 0; j < std::max(1, nmulti); ++j) OVL_TRY(import_spinors(c, h.data(), OVL_C128, 0, 1, *fi, j));
     const int nv = p == P64E ? 4 : wilson_tiles_fit(c->g) ? 3 : 2;
-    for (int v = 0; v < nv; ++v) {
-      if (v == 2 && !wilson_tiles_fit(c->g)) continue;
-      LinkRef L = links_of(c, p);
-      L.variant = v;
-      const int reps = p == P64 ? 3 : 8;
-      for (int w = 0; w < 2; ++w)
-        launch_wilson_K(p, p, p, c->g, c->kappa, L, fi->ref(), fo->ref(), ns, nullptr, nullptr, c->st);
-      OVL_CUDA(c, cudaEventRecord(e0, c->st));
-      for (int w = 0; w < reps; ++w)
-        launch_wilson_K(p, p, p, c->g, c->kappa, L, fi->ref(), fo->ref(), ns, nullptr, nullptr, c->st);
-      OVL_CUDA(c, cudaEventRecord(e1, c->st));
-      OVL_CUDA(c, cudaEventSynchronize(e1));
-      OVL_TRY(check_launch(c, __func__));
-      float ms = 0.f;
-      cudaEventElapsedTime(&ms, e0, e1);
-      c->wtime[p][v] = ms / reps;
+    for (int bucket = 0; bucket < 2; ++bucket) {
+      const int ns = bucket == 0 ? 1 : nmulti;
+      float* wt = bucket == 0 ? c->wtime[p] : c->wtime_multi[p];
+      if (bucket == 1 && ns < 4) {
+        c->wvar_multi[p] = c->wvar[p];
+        break;
+      }
+      for (int v = 0; v < nv; ++v) {
+        if (v == 2 && !wilson_tiles_fit(c->g)) continue;
+        LinkRef L = links_of(c, p);
+        L.variant = L.variant_multi = v;
+        const int reps = p == P64 ? 3 : bucket == 0 ? 8 : 4;
+        for (int w = 0; w < 2; ++w)
+          launch_wilson_K(p, p, p, c->g, c->kappa, L, fi->ref(), fo->ref(), ns, nullptr, nullptr, c->st);
+        OVL_CUDA(c, cudaEventRecord(e0, c->st));
+        for (int w = 0; w < reps; ++w)
+          launch_wilson_K(p, p, p, c->g, c->kappa, L, fi->ref(), fo->ref(), ns, nullptr, nullptr, c->st);
+        OVL_CUDA(c, cudaEventRecord(e1, c->st));
+        OVL_CUDA(c, cudaEventSynchronize(e1));
+        OVL_TRY(check_launch(c, __func__));
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, e0, e1);
+        wt[v] = ms / reps;
+      }
+      // another shape must beat the thread-per-site one by 5%: closer timings are within
+      // run-to-run noise, and the choice should not flip between runs
+      int best = 0;
+      for (int v = 1; v < nv; ++v)
+        if (wt[v] > 0.f && wt[v] < 0.95f * wt[0] && wt[v] < wt[best]) best = v;
+      (bucket == 0 ? c->wvar[p] : c->wvar_multi[p]) = best;
     }
-    // another shape must beat the thread-per-site one by 5%: closer timings are within
-    // run-to-run noise, and the choice should not flip between runs
-    int best = 0;
-    for (int v = 1; v < nv; ++v)
-      if (c->wtime[p][v] > 0.f && c->wtime[p][v] < 0.95f * c->wtime[p][0] && c->wtime[p][v] < c->wtime[p][best])
-        best = v;
-    c->wvar[p] = best;
     free_field(c->ws["at_in"]);
     free_field(c->ws["at_out"]);
   }

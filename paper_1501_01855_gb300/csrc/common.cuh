@@ -279,6 +279,7 @@ struct LinkRef {
   const void* data;  // [mu][chunk][V]
   int V;
   int variant;       // Wilson-kernel variant chosen for this field (0 thread per site, 1 split)
+  int variant_multi; // the variant chosen for launches of 4 or more systems
 };
 
 template <typename T>

@@ -65,6 +65,8 @@ struct ovl_ctx {
   void* link[4] = {nullptr, nullptr, nullptr, nullptr};  // P64, P32, P16, P64E 12-real layouts
   int wvar[4] = {0, 0, 0, 0};                            // Wilson-kernel variant per precision
   float wtime[4][4] = {{0}};                             // autotuner timings (ms per launch)
+  int wvar_multi[4] = {0, 0, 0, 0};                      // the same for launches of >= 4 systems
+  float wtime_multi[4][4] = {{0}};
   ovl::Poles hpoles;
   ovl::Poles* dpoles = nullptr;
   std::map<std::string, ovl::Field> ws;

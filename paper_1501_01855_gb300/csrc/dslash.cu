@@ -1052,7 +1052,7 @@ static DArgs base_args(const Geom& g, double kappa, LinkRef links, int nrhs) {
   a.c1 = a.c2 = 0;
   a.coef = nullptr;
   a.herm = 0;
-  a.variant = links.variant;
+  a.variant = nrhs >= 4 ? links.variant_multi : links.variant;
   a.lz = nullptr;
   a.lzc = LzCtl{nullptr, nullptr, nullptr, nullptr, 0, nullptr};
   return a;

@@ -214,6 +214,7 @@ LinkRef links_of(const ovl_ctx* c, int prec) {
   r.data = c->link[prec];
   r.V = c->V;
   r.variant = c->wvar[prec];
+  r.variant_multi = c->wvar_multi[prec];
   return r;
 }
 
