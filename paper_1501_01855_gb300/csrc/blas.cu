@@ -173,13 +173,25 @@ void launch_norm2(int px, SpinorRef x, int nrhs, int V, double* partials, cudaSt
 __global__ void reduce_partials_kernel(const double* partials, int nsb, double* out) {
   __shared__ double sh[NVRED][128];
   const int rhs = blockIdx.x;
+  // four site blocks in flight per thread, their sums combined in a fixed order
+  double a4[4][NVRED];
+#pragma unroll
+  for (int u = 0; u < 4; ++u)
+#pragma unroll
+    for (int j = 0; j < NVRED; ++j) a4[u][j] = 0.0;
+  int b = threadIdx.x;
+  for (; b + 3 * (int)blockDim.x < nsb; b += 4 * blockDim.x) {
+#pragma unroll
+    for (int u = 0; u < 4; ++u)
+#pragma unroll
+      for (int j = 0; j < NVRED; ++j) a4[u][j] += partials[((size_t)rhs * nsb + b + u * blockDim.x) * NVRED + j];
+  }
+  for (int u = 0; b < nsb; b += blockDim.x, ++u)
+#pragma unroll
+    for (int j = 0; j < NVRED; ++j) a4[u & 3][j] += partials[((size_t)rhs * nsb + b) * NVRED + j];
   double a[NVRED];
 #pragma unroll
-  for (int j = 0; j < NVRED; ++j) a[j] = 0.0;
-  for (int b = threadIdx.x; b < nsb; b += blockDim.x) {
-#pragma unroll
-    for (int j = 0; j < NVRED; ++j) a[j] += partials[((size_t)rhs * nsb + b) * NVRED + j];
-  }
+  for (int j = 0; j < NVRED; ++j) a[j] = (a4[0][j] + a4[1][j]) + (a4[2][j] + a4[3][j]);
 #pragma unroll
   for (int j = 0; j < NVRED; ++j) sh[j][threadIdx.x] = a[j];
   __syncthreads();

@@ -404,8 +404,18 @@ struct DArgs {
 // tree), so the result does not depend on which block came last.
 __device__ __forceinline__ double lz_block_sum(const double* partials, int nsb, int rhs, double* sm) {
   const int tid = threadIdx.y * blockDim.x + threadIdx.x, nt = blockDim.x * blockDim.y;
-  double v = 0.0;
-  for (int b = tid; b < nsb; b += nt) v += __ldcg(partials + ((size_t)rhs * nsb + b) * NVRED);
+  // eight loads in flight per thread (a block of 64 threads sums 2048 partials of a 16^3 x 32
+  // lattice: one dependent L2 load after another would hold the launch for microseconds);
+  // the eight running sums are combined in a fixed order
+  const double* base = partials + (size_t)rhs * nsb * NVRED;
+  double acc8[8] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
+  int b = tid;
+  for (; b + 7 * nt < nsb; b += 8 * nt) {
+#pragma unroll
+    for (int u = 0; u < 8; ++u) acc8[u] += __ldcg(base + (size_t)(b + u * nt) * NVRED);
+  }
+  for (int u = 0; b < nsb; b += nt, ++u) acc8[u & 7] += __ldcg(base + (size_t)b * NVRED);
+  const double v = ((acc8[0] + acc8[1]) + (acc8[2] + acc8[3])) + ((acc8[4] + acc8[5]) + (acc8[6] + acc8[7]));
   sm[tid] = v;
   for (int i = nt + tid; i < 256; i += nt) sm[i] = 0.0;
   __syncthreads();

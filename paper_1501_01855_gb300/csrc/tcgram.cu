@@ -344,7 +344,10 @@ __global__ void __launch_bounds__(TG_THREADS, 1)
     const bool chunk_end = (cs == TG_CHUNK - 1) || (it == nst - 1);
     if (tid == 0) {
       asm volatile("tcgen05.fence::after_thread_sync;");
-      const uint32_t sa = smem_u32(stA), sb = smem_u32(stB);
+      // descriptors of digit 0, K-step 0 of this stage; the others differ only in the start
+      // address (field in the low bits, in units of 16 bytes; no carry out of it below 256 KB)
+      const uint64_t da0 = smem_desc(smem_u32(stA), 2048, 128), db0 = smem_desc(smem_u32(stB), 1024, 128);
+      const uint32_t acc_chunk = cs > 0 ? 1u : 0u;
 #pragma unroll
       for (int kk = 0; kk < 2; ++kk) {   // two K-steps of 16 reals (2 core-matrix columns each)
 #pragma unroll
@@ -352,10 +355,10 @@ __global__ void __launch_bounds__(TG_THREADS, 1)
 #pragma unroll
           for (int ds = (g > TG_S - 1 ? g - TG_S + 1 : 0); ds <= (g < TG_S - 1 ? g : TG_S - 1); ++ds) {
             // digit ds of A, g - ds of B (0-based); the first pair of a group starts its sum
-            const uint64_t da = smem_desc(sa + ds * TG_TILE_A + kk * 2 * 2048, 2048, 128);
-            const uint64_t db = smem_desc(sb + (g - ds) * TG_TILE_B + kk * 2 * 1024, 1024, 128);
+            const uint64_t da = da0 + (uint64_t)((ds * TG_TILE_A + kk * 2 * 2048) >> 4);
+            const uint64_t db = db0 + (uint64_t)(((g - ds) * TG_TILE_B + kk * 2 * 1024) >> 4);
             const int first = g > TG_S - 1 ? g - TG_S + 1 : 0;
-            mma_bf16(tmem + (uint32_t)(g * TG_NB), da, db, idesc, (cs > 0 || kk > 0 || ds > first) ? 1u : 0u);
+            mma_bf16(tmem + (uint32_t)(g * TG_NB), da, db, idesc, (kk > 0 || ds > first) ? 1u : acc_chunk);
           }
         }
       }

@@ -1,5 +1,5 @@
-"""Time the Wilson kernel K alone through the C ABI (ovl_bench_wilson), or one
-sign-function application (--sign ETA).
+"""Time the Wilson kernel K alone through the C ABI (ovl_bench_wilson), one sign-function
+application (--sign ETA), or mixed-precision solves (--solve TOL).
 
     python -m paper_1501_01855_gb300.wilson_bench --dims 24 24 24 48 --prec f32 --nrhs 1
 
@@ -34,11 +34,16 @@ def main(argv=None):
     ap.add_argument("--iters", type=int, default=3)
     ap.add_argument("--variant", type=int, default=-1, choices=[-1, 0, 1, 2, 3])
     ap.add_argument("--sign", type=float, default=0.0, metavar="ETA",
-                    help="instead: one sign-function application (multi-shift CG) to accuracy ETA "
-                         "on nrhs random vectors, 20 poles")
+                    help="instead: one sign-function application to accuracy ETA on nrhs random "
+                         "vectors, 20 poles")
+    ap.add_argument("--solve", type=float, default=0.0, metavar="TOL",
+                    help="instead: mixed-precision GMRESR(relSUMR) solves of nrhs Gaussian sources to "
+                         "relative residual TOL (mu = 0.05, 20 poles, eps 0.3 links, seed 1002)")
     args = ap.parse_args(argv)
     if args.sign > 0:
         return sign_main(args)
+    if args.solve > 0:
+        return solve_main(args)
     p = B.ovl_params_default()
     p.a_override, p.b_override = 0.2, 2.6     # skip the Lanczos bound estimate
     p.wilson_variant = args.variant
@@ -69,6 +74,26 @@ def sign_main(args):
     dt = (time.perf_counter() - t0) / args.iters
     print("sign %s, %s, nrhs %d, eta %g: %.1f ms per application (host buffers)"
           % (args.prec, "x".join(map(str, args.dims)), args.nrhs, args.sign, dt * 1e3))
+    ctx.close()
+
+
+def solve_main(args):
+    import time
+    import synth
+    dims = tuple(args.dims)
+    U = synth.gauge_links(dims, 0.3, 1002)
+    b = synth.gaussian_source(dims, 3002, nvec=args.nrhs)
+    ctx = B.Overlap(dims, U, 1.4, 0.05, 20, 1e-10)
+    x = np.zeros_like(b)
+    ctx.solve(b, x, args.solve)            # warm-up: workspaces, graphs, step caps
+    for _ in range(args.iters):
+        x[...] = 0
+        t0 = time.perf_counter()
+        infos = ctx.solve(b, x, args.solve)
+        dt = time.perf_counter() - t0
+        print("solve %s, nrhs %d, tol %g: %.1f ms, true residual %.2e, inner iterations %d"
+              % ("x".join(map(str, dims)), args.nrhs, args.solve, dt * 1e3,
+                 max(i["true_residual"] for i in infos), infos[0]["inner_iters"]), flush=True)
     ctx.close()
 
 
