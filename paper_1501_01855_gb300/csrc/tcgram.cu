@@ -179,6 +179,51 @@ __device__ __forceinline__ uint32_t tg_digit_pair(uint32_t rlo, uint32_t rhi, ui
 
 constexpr unsigned long long TG_BIAS = 64ull * ((1ull << 28) + (1ull << 21) + (1ull << 14) + (1ull << 7) + 1ull);
 
+// The six digits of one complex element (from the raw staging buffer) as BF16 pairs,
+// negated when neg (gamma5 on B). FP64 operands: the integer splitting above. FP32 operands:
+// the same digits by FP32 arithmetic on the FMA pipe, which the integer splitting leaves
+// idle: r = x 2^-e (exact, two power-of-two factors), then six times d = round(128 r) by the
+// 1.5 x 2^23 addition (exact for |128 r| < 2^22) and r <- 128 r - d (exact: the remainder of
+// a float after its nearest integer), so d_0 is in [-128, 128], the others in [-64, 64], and
+// |x| 2^-e = sum_s d_s 2^(-7 (s + 1)) up to 2^-43, as for the integer digits (balanced by
+// rounding instead of by the bias). A digit is an integer of at most 8 bits, so the upper
+// half of its float is its exact BF16.
+__device__ __forceinline__ float tg_pow2(int k) { return __int_as_float((127 + k) << 23); }
+template <int P>
+__device__ __forceinline__ void tg_digits(const unsigned char* p, int e, bool neg, uint32_t pd[TG_S]) {
+  if constexpr (P == P32) {
+    const float2 w = *reinterpret_cast<const float2*>(p);
+    if (e == TG_EXP_ZERO) {
+#pragma unroll
+      for (int d = 0; d < TG_S; ++d) pd[d] = 0u;
+      return;
+    }
+    const int e1 = e / 2, e2 = e - e1;   // 2^-e as two factors inside the FP32 range
+    float rr = __fmul_rn(__fmul_rn(w.x, tg_pow2(-e1)), tg_pow2(-e2));
+    float ri = __fmul_rn(__fmul_rn(w.y, tg_pow2(-e1)), tg_pow2(-e2));
+    const float M = 12582912.0f;
+    const uint32_t nm = neg ? 0x80008000u : 0u;
+#pragma unroll
+    for (int d = 0; d < TG_S; ++d) {
+      const float dr = __fsub_rn(__fmaf_rn(rr, 128.0f, M), M);
+      const float di = __fsub_rn(__fmaf_rn(ri, 128.0f, M), M);
+      rr = __fmaf_rn(rr, 128.0f, -dr);
+      ri = __fmaf_rn(ri, 128.0f, -di);
+      pd[d] = __byte_perm(__float_as_uint(dr), __float_as_uint(di), 0x7632) ^ nm;
+    }
+  } else {
+    unsigned long long fr, fi;
+    uint32_t sg;
+    TgLoad<P>::get_s(p, e, fr, fi, sg);
+    if (neg) sg ^= 3u;
+    const unsigned long long gr = fr + TG_BIAS, gi = fi + TG_BIAS;
+    const uint32_t rlo = (uint32_t)gr, rhi = (uint32_t)(gr >> 32), ilo = (uint32_t)gi, ihi = (uint32_t)(gi >> 32);
+    const uint32_t negmask = ((sg & 1u) ? 0x8000u : 0u) | ((sg & 2u) ? 0x80000000u : 0u);
+#pragma unroll
+    for (int d = 0; d < TG_S; ++d) pd[d] = tg_digit_pair(rlo, rhi, ilo, ihi, d, negmask);
+  }
+}
+
 // Issue the asynchronous copies of one stage (16 complex elements from q0 of the tile's 64 A
 // and 64 B vectors) into a raw staging buffer, 16 bytes per copy, zero-filled past the last
 // vector or element; one commit group per call.
@@ -312,31 +357,21 @@ __global__ void __launch_bounds__(TG_THREADS, 1)
       const int tt = task & 31, rg = tt >> 2, kc = tt & 3;
       const int r = rg * 8 + rl;
       const int j = kc * 4 + kp;
-      unsigned long long fr, fi;
-      uint32_t neg;
+      uint32_t pd[TG_S];   // digit s of (re, im) as a BF16 pair
       if (isA) {
-        TgLoad<PA>::get_s(rawA + r * tg_rstride(PA) + j * tg_esize(PA), ea_s[r], fr, fi, neg);
-      } else {
-        TgLoad<PB>::get_s(rawB + r * tg_rstride(PB) + j * tg_esize(PB), eb_s[r], fr, fi, neg);
-        if (g5q && q0 + j >= (size_t)g5q) neg ^= 3u;
-      }
-      const unsigned long long gr = fr + TG_BIAS, gi = fi + TG_BIAS;
-      const uint32_t rlo = (uint32_t)gr, rhi = (uint32_t)(gr >> 32), ilo = (uint32_t)gi, ihi = (uint32_t)(gi >> 32);
-      const uint32_t negmask = ((neg & 1u) ? 0x8000u : 0u) | ((neg & 2u) ? 0x80000000u : 0u);
-      if (isA) {
+        tg_digits<PA>(rawA + r * tg_rstride(PA) + j * tg_esize(PA), ea_s[r], false, pd);
         // A row r and A' row 64 + r: (re, im) and (-im, re)
         const uint32_t off = (uint32_t)((kc * 16 + rg) * 128 + rl * 16 + kp * 4);
 #pragma unroll
         for (int d = 0; d < TG_S; ++d) {
-          const uint32_t pr = tg_digit_pair(rlo, rhi, ilo, ihi, d, negmask);
-          *reinterpret_cast<uint32_t*>(stA + d * TG_TILE_A + off) = pr;
-          *reinterpret_cast<uint32_t*>(stA + d * TG_TILE_A + off + 8 * 128) = __byte_perm(pr, 0u, 0x1032) ^ 0x8000u;
+          *reinterpret_cast<uint32_t*>(stA + d * TG_TILE_A + off) = pd[d];
+          *reinterpret_cast<uint32_t*>(stA + d * TG_TILE_A + off + 8 * 128) = __byte_perm(pd[d], 0u, 0x1032) ^ 0x8000u;
         }
       } else {
+        tg_digits<PB>(rawB + r * tg_rstride(PB) + j * tg_esize(PB), eb_s[r], g5q && q0 + j >= (size_t)g5q, pd);
         const uint32_t off = (uint32_t)((kc * 8 + rg) * 128 + rl * 16 + kp * 4);
 #pragma unroll
-        for (int d = 0; d < TG_S; ++d)
-          *reinterpret_cast<uint32_t*>(stB + d * TG_TILE_B + off) = tg_digit_pair(rlo, rhi, ilo, ihi, d, negmask);
+        for (int d = 0; d < TG_S; ++d) *reinterpret_cast<uint32_t*>(stB + d * TG_TILE_B + off) = pd[d];
       }
     }
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
