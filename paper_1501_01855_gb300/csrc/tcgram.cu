@@ -9,7 +9,8 @@
 // Every vector i gets a power-of-two scale 2^e_i above its largest element; each real
 // element x becomes the 42-bit fixed-point integer F = trunc(|x| 2^(42 - e_i)), written in
 // six balanced base-128 digits a_1 .. a_6 (a_1 in [0, 128], the others in [-64, 63]), so
-// x = sign(x) 2^e_i sum_s a_s 2^(-7 s) up to 2^(e_i - 42). Digits are exact in BF16 and
+// x = sign(x) 2^e_i sum_s a_s 2^(-7 s) up to 2^(e_i - 43) (FP32 operands get the same digits,
+// signed, from FP32 arithmetic: tg_digits). Digits are exact in BF16 and
 // their products exact in the tensor core; for each group g = s + t (2 .. 8) the products
 // a_s b_t summed over 512 reals stay below 2^24 in magnitude, so the FP32 accumulator holds
 // that sum exactly. Every 512 reals the seven group sums are read from tensor memory and
