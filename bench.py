@@ -475,6 +475,26 @@ def extras(args, ctx, dv, dout, ref_out, B, torch, stream, hbm):
         cs.close()
     out["solve_16x16x16x32_mu0.05"] = sol
     out["deflated_batched_16x16x16x32_mu0.02"] = deflated_batched(B, stream)
+    # Gram block of the Ritz step (128 x 128 spinors on 16^3 x 32): tensor cores at FP64 level
+    # against the CUDA-core kernel with FP32 products
+    try:
+        p = B.ovl_params_default()
+        p.a_override, p.b_override = 0.2, 2.6
+        p.stream = stream.cuda_stream
+        cg = B.Overlap(DIMS, synth.unit_links(DIMS), M0, MU, 8, 1e-3, params=p)
+        v = int(np.prod(DIMS))
+        g = {}
+        for name, prec, method in (("f64_tensor_cores", B.OVL_PREC_F64, 0), ("f32_tensor_cores", B.OVL_PREC_F32, 0),
+                                   ("f64_cuda_cores_fp32_products", B.OVL_PREC_F64, 1)):
+            ms = cg.bench_gram(prec, 128, 128, method, 3)
+            g[name] = {"ms": ms, "T_complex_mac_per_s": 128.0 * 128 * 12 * v / (ms * 1e-3) / 1e12}
+            if method == 0:
+                # 2 K-steps x 26 digit-pair MMAs of 128 x 64 x 16 per 16 complex elements and tile
+                g[name]["bf16_TFLOP_per_s_tensor_pipe"] = 4 * (12.0 * v / 16) * 2 * 26 * (128 * 64 * 16) * 2 / (ms * 1e-3) / 1e12
+        cg.close()
+        out["gram_128x128_16x16x16x32"] = g
+    except Exception as e:   # the extras must not cost the benchmark line
+        out["gram_128x128_16x16x16x32"] = {"error": str(e)}
     return out
 
 
