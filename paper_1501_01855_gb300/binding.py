@@ -370,9 +370,11 @@ class Overlap:
         """Standalone eigSUMR eigensolver (ovl_eigensolve): returns (space, steps used)."""
         mu = self.mu if mu is None else mu
         if start is not None:
-            ps, code, dev, cnt, _ = _spinor_arg(start)
+            ps, code, dev, cnt, ds = _spinor_arg(start)
             if self._n(cnt) != 1:
                 raise ValueError("start must be one spinor")
+            if dev and self.device is not None and ds != self.device:
+                raise ValueError("start must be on cuda:%d, the context's device" % self.device)
         else:
             ps, code, dev = None, OVL_C128, 0
         h = ctypes.c_void_p(defl.h.value if defl is not None else None)
