@@ -32,22 +32,32 @@ namespace ovl {
 
 enum { MODE_K = 0, MODE_R = 1, MODE_OVL = 2, MODE_LZK = 3, MODE_LZL = 4 };
 
-// Register cap per thread, by link precision. Uncapped, the compiler hoists all
-// neighbour loads and takes ~255 registers (8 warps per SM): the FP32/FP16 kernels
-// are then latency-bound, and the double-float kernel has too few warps to hide its
-// dependent FP32 chains. Swept on 24^3x48 (one system, ms per launch):
-//   FP32 K   64: 0.0619 (spills 148 B; the multi-shift r-update form 440 B)
-//            72: 0.0555   80: 0.0557 (best for 12 systems and for a whole FP32 sign)
-//            96: 0.0594
+// Register cap per thread, by link precision (and, for FP16 storage, spinor precision).
+// Uncapped, the compiler hoists all neighbour loads and takes ~255 registers (8 warps
+// per SM): the FP32/FP16 kernels are then latency-bound, and the double-float kernel has
+// too few warps to hide its dependent FP32 chains. Swept on 24^3x48 (ms per launch):
+//   FP32 K, one system   64: 0.0619 (spills 148 B; the multi-shift r-update form 440 B)
+//                        72: 0.0555   80: 0.0557 (best for 12 systems and for a whole FP32 sign)
+//                        96: 0.0594
+//   FP16 K, one system / 12 systems   72: 0.0575 / 0.5936   80: 0.0578 / 0.5798
+//                                     96: 0.0574 / 0.6444  128: 0.0554 / 0.5816
 //   double-float K  104: 0.375  112: 0.365  120: 0.438  128: 0.329
+// The FP16 cap moves its K launch by 4% at most, and at its best the launch takes as long
+// as the FP32 one (0.0553 ms) with half the bytes: the bound is the latency of each site's
+// chain of dependent loads, not HBM. FP16 keeps the FP32 cap.
 #ifndef OVL_WILSON_REG_DF
 #define OVL_WILSON_REG_DF 128
 #endif
 #ifndef OVL_WILSON_REG_SP
 #define OVL_WILSON_REG_SP 80
 #endif
-template <int PL> struct MaxReg {
-  static constexpr int v = PL == P64E ? OVL_WILSON_REG_DF : PL == P64 ? 255 : OVL_WILSON_REG_SP;
+#ifndef OVL_WILSON_REG_HP
+#define OVL_WILSON_REG_HP OVL_WILSON_REG_SP
+#endif
+template <int PL, int PIN> struct MaxReg {
+  static constexpr int v = PL == P64E ? OVL_WILSON_REG_DF
+                         : PL == P64  ? 255
+                         : (PL == P16 && PIN == P16) ? OVL_WILSON_REG_HP : OVL_WILSON_REG_SP;
 };
 
 // Sums inside the hop term. For double-float operands the sum is "lazy": TwoSum on the
@@ -697,7 +707,7 @@ __device__ __forceinline__ void block_reduce_partials(R v[NVRED], double* smem, 
 // get zero), so the partial layout (system, BX-site block) is the same for all variants.
 constexpr int TX = 8, TY = 4, TZ = 4, TT = 2;
 template <int MODE, int PIN, int PL, int POUT, int PA1, int PA2, bool TILED>
-__global__ void __launch_bounds__(256) __maxnreg__(MaxReg<PL>::v) wilson_kernel(const DArgs a) {
+__global__ void __launch_bounds__(256) __maxnreg__((MaxReg<PL, PIN>::v)) wilson_kernel(const DArgs a) {
   using T = typename Real<PL>::T;
   __shared__ double red[4 * (BX / 32) * NVRED];
   int sb, rhs, s;
@@ -961,7 +971,7 @@ bool wilson_tiles_fit(const Geom& g) {
 // uniform within a warp. The four partial sums meet in shared memory and the
 // direction-0 warps finish the site.
 template <int MODE, int PIN, int PL, int POUT, int PA1, int PA2>
-__global__ void __launch_bounds__(4 * BX) __maxnreg__(MaxReg<PL>::v) wilson_split_kernel(const DArgs a) {
+__global__ void __launch_bounds__(4 * BX) __maxnreg__((MaxReg<PL, PIN>::v)) wilson_split_kernel(const DArgs a) {
   using T = typename Real<PL>::T;
   __shared__ cpx<T> part[3][BX][12];
   __shared__ double red[(4 * BX / 32) * NVRED];
