@@ -31,9 +31,9 @@
 // current one into the canonical no-swizzle K-major layout (core matrices of 8 rows x 16
 // bytes), double buffered; thread 0 issues the stage's 52 MMAs (2 K-steps x 26 digit pairs)
 // and commits them to the stage's mbarrier, which the slicing of the stage after next waits
-// on. Waits are bounded by a 2 s deadline: one that
-// gives up sets the error flag, the CTA skips the rest, frees its tensor memory and
-// returns, and the host reports OVL_ETIMEOUT.
+// on. Waits are bounded by a 2 s deadline: one that gives up sets the error flag, the CTA
+// skips the rest, waits once more (again bounded) for the MMAs it has committed, frees its
+// tensor memory and returns, and the host reports OVL_ETIMEOUT.
 #include <stdint.h>
 
 #include "kernels.h"
@@ -341,9 +341,12 @@ __global__ void __launch_bounds__(TG_THREADS, 1)
       asm volatile("cp.async.commit_group;" ::: "memory");
     asm volatile("cp.async.wait_group 1;" ::: "memory");
     if ((pend >> s) & 1u) {
-      if (!mbar_wait(smem_u32(&bar[s]), (ph >> s) & 1u)) abort_flag = 1;
-      ph ^= 1u << s;
-      pend &= ~(1u << s);
+      if (mbar_wait(smem_u32(&bar[s]), (ph >> s) & 1u)) {
+        ph ^= 1u << s;
+        pend &= ~(1u << s);
+      } else {
+        abort_flag = 1;   // the stage stays pending: the exit waits for it once more
+      }
     }
     __syncthreads();
     if (abort_flag) break;
@@ -437,12 +440,13 @@ __global__ void __launch_bounds__(TG_THREADS, 1)
       asm volatile("tcgen05.fence::before_thread_sync;");
     }
   }
-  // wait for the last commits of each stage barrier before the CTA lets go of its memory
+  // wait for the last commits of each stage barrier before the CTA lets go of its memory,
+  // also after an abort (MMAs still in flight must not outlive the tensor memory); each
+  // wait again has its own deadline. A commit of a stage also covers every earlier MMA.
   asm volatile("cp.async.wait_all;" ::: "memory");
   __syncthreads();
-  const int aborted = abort_flag;
   for (int s = 0; s < 2; ++s)
-    if (((pend >> s) & 1u) && !aborted)
+    if ((pend >> s) & 1u)
       if (!mbar_wait(smem_u32(&bar[s]), (ph >> s) & 1u)) abort_flag = 1;
   __syncthreads();
   if (abort_flag && tid == 0) atomicExch(err, 1);
