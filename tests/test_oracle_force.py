@@ -1,14 +1,15 @@
-"""Pin of the oracle's gauge-link gradient: central finite differences of S along
+"""Pins of the oracle's gauge-link gradient: central finite differences of S along
 random Lie-algebra directions U -> exp(i h X) U, with S evaluated by dense
-linear algebra on the frozen Zolotarev rational (2^4 lattice)."""
+linear algebra on the frozen Zolotarev rational (2^4 lattice), for the matrix-free
+gradient and for its dense form; and the two forms against each other."""
 import numpy as np
 
 import synth
 from oracle import wilson, overlap, zolotarev as zo, force
 
 
-def _S_dense(U, phi, m0, mu, om, sg):
-    Kd = wilson.dense_K(U, m0)
+def _S_dense(U, phi, m0, mu, om, sg, apt=False):
+    Kd = wilson.dense_K(U, m0, apt)
     E = overlap.dense_zolotarev_sign(Kd, om, sg)
     ns = int(np.prod(U.shape[:4]))
     D = overlap.dense_overlap(E, mu, ns)
@@ -35,6 +36,35 @@ def test_force_finite_differences():
         fd = (Sp - Sm) / (2 * h)
         an = 2 * np.real(np.sum(np.conj(G) * (1j * X @ U)))
         assert abs(fd - an) <= 1e-6 * max(1.0, abs(an))
+
+
+def _fd_check(G, U, phi, m0, mu, om, sg, seed, ndir, apt=False):
+    """Central differences of the dense action along ndir random su(3) directions
+    against 2 Re <G, i X U>."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    lam = synth._gell_mann()
+    h = 1e-5
+    for _ in range(ndir):
+        X = np.einsum("...a,aij->...ij", rng.standard_normal(U.shape[:5] + (8,)), lam) * 0.5
+        w, v = np.linalg.eigh(X)
+        expo = lambda t: np.einsum("...ij,...j,...kj->...ik", v, np.exp(1j * t * w), np.conj(v))
+        Sp = _S_dense(expo(h) @ U, phi, m0, mu, om, sg, apt)
+        Sm = _S_dense(expo(-h) @ U, phi, m0, mu, om, sg, apt)
+        fd = (Sp - Sm) / (2 * h)
+        an = 2 * np.real(np.sum(np.conj(G) * (1j * X @ U)))
+        assert abs(fd - an) <= 1e-6 * max(1.0, abs(an)), (fd, an)
+
+
+def test_dense_gradient_finite_differences():
+    """gradient_dense on its own against central differences of the dense action (2^4,
+    periodic and antiperiodic in t, two masses)."""
+    m0 = 1.4
+    om, sg, _ = zo.zolotarev(8, 0.15, 2.6)
+    for mu, apt, seed in ((0.05, False, 41), (0.3, True, 42)):
+        U = synth.gauge_links((2, 2, 2, 2), 0.3, seed)
+        phi = synth.gaussian_source((2, 2, 2, 2), seed + 1)
+        G, _ = force.gradient_dense(U, phi, m0, mu, om, sg, antiperiodic_t=apt)
+        _fd_check(G, U, phi, m0, mu, om, sg, seed + 2, 4, apt)
 
 
 def test_dense_gradient_equals_matrix_free():
