@@ -179,6 +179,38 @@ ovl_status ovl_trim(ovl_ctx* ctx);
  * maximum error delta, from Jacobi elliptic functions (AGM / descending Landen). */
 ovl_status ovl_zolotarev_coeffs(int n, double a, double b, double* omega, double* sigma, double* delta);
 
+/* Host-only (no GPU, no context): the small dense FP64 numerics that the solvers run on
+ * the host between kernel launches, exported so that they can be checked on their own.
+ * Complex matrices are n x n, row-major, interleaved (re, im) doubles; inputs are read
+ * only, outputs are caller buffers of the same size; 1 <= n <= 4096, else OVL_EINVAL.
+ *   ovl_host_eigh             Hermitian eigendecomposition by cyclic complex Jacobi
+ *                             rotations: w ascending, z the orthonormal eigenvectors as
+ *                             columns (a = z diag(w) z^dag). The diagonalisation of
+ *                             L^-1 M U^-1 in the Ritz step (Alg. 6), of the projected
+ *                             gamma5 D in the least-squares start (Sec. 4) and of the
+ *                             Rayleigh quotient in the kernel low-mode deflation (Sec. 1).
+ *                             The full matrix is read; a non-finite entry gives OVL_EINVAL.
+ *   ovl_host_cholesky         a = l l^dag with l lower triangular, positive real diagonal
+ *                             (the E = U^dag U of Alg. 6); OVL_EBREAKDOWN unless a is
+ *                             numerically positive definite.
+ *   ovl_host_lower_inverse    li = l^-1 for lower-triangular l (zero entries above the
+ *                             diagonal are not read); OVL_EBREAKDOWN on a zero pivot.
+ *   ovl_host_lu_solve         x = a^-1 b for nb right-hand sides (b, x: n x nb row-major)
+ *                             by partially pivoted LU (the least-squares normal equations
+ *                             of the deflated start, Sec. 4); OVL_EBREAKDOWN when a pivot
+ *                             column is exactly zero.
+ *   ovl_host_tridiag_extremes smallest and largest eigenvalue of the real symmetric
+ *                             tridiagonal matrix (diagonal d[n], off-diagonal e[n-1]; e
+ *                             unused for n = 1) by Sturm-sequence bisection from the
+ *                             Gershgorin interval: the extremes of the Lanczos tridiagonal
+ *                             of K^2, whose square roots estimate the interval [a, b] of
+ *                             |K| that the rational of Sec. 3 covers. */
+ovl_status ovl_host_eigh(int n, const double* a, double* w, double* z);
+ovl_status ovl_host_cholesky(int n, const double* a, double* l);
+ovl_status ovl_host_lower_inverse(int n, const double* l, double* li);
+ovl_status ovl_host_lu_solve(int n, const double* a, const double* b, int nb, double* x);
+ovl_status ovl_host_tridiag_extremes(int n, const double* d, const double* e, double* lmin, double* lmax);
+
 /* Zolotarev data of the context: omega[n], sigma[n] (may be NULL; n the pole count in use:
  * n_poles at create, or the count ovl_kernel_deflate chose),
  * the error Delta and the bounds a, b actually used (Sec. 3). */

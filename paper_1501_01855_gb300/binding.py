@@ -69,6 +69,11 @@ _SIGS = {
     "ovl_version": (ctypes.c_char_p, []),
     "ovl_params_default": (I, [ctypes.POINTER(ovl_params)]),
     "ovl_zolotarev_coeffs": (I, [I, D, D, DP, DP, DP]),
+    "ovl_host_eigh": (I, [I, DP, DP, DP]),
+    "ovl_host_cholesky": (I, [I, DP, DP]),
+    "ovl_host_lower_inverse": (I, [I, DP, DP]),
+    "ovl_host_lu_solve": (I, [I, DP, DP, I, DP]),
+    "ovl_host_tridiag_extremes": (I, [I, DP, DP, DP, DP]),
     "overlap_create": (I, [ctypes.POINTER(P), ctypes.POINTER(I), DP, D, D, I, D, ctypes.POINTER(ovl_params)]),
     "overlap_destroy": (None, [P]),
     "overlap_last_error": (ctypes.c_char_p, [P]),
@@ -201,6 +206,68 @@ def ovl_zolotarev_coeffs(n, a, b):
     de = np.zeros(1)
     _check(load().ovl_zolotarev_coeffs(int(n), float(a), float(b), _dptr(om), _dptr(sg), _dptr(de)))
     return om, sg, float(de[0])
+
+
+def _square_c128(a):
+    a = np.ascontiguousarray(np.asarray(a, dtype=np.complex128))
+    if a.ndim != 2 or a.shape[0] != a.shape[1]:
+        raise ValueError("expected a square matrix")
+    return a
+
+
+def _cptr(a):
+    return a.ctypes.data_as(DP)
+
+
+def ovl_host_eigh(a):
+    """Host Jacobi eigendecomposition of a Hermitian matrix: (w ascending, Z columns)."""
+    a = _square_c128(a)
+    n = a.shape[0]
+    w = np.zeros(n)
+    z = np.zeros((n, n), dtype=np.complex128)
+    _check(load().ovl_host_eigh(n, _cptr(a), _dptr(w), _cptr(z)))
+    return w, z
+
+
+def ovl_host_cholesky(a):
+    """Host Cholesky a = L L^dag (L lower)."""
+    a = _square_c128(a)
+    l = np.zeros_like(a)
+    _check(load().ovl_host_cholesky(a.shape[0], _cptr(a), _cptr(l)))
+    return l
+
+
+def ovl_host_lower_inverse(l):
+    l = _square_c128(l)
+    li = np.zeros_like(l)
+    _check(load().ovl_host_lower_inverse(l.shape[0], _cptr(l), _cptr(li)))
+    return li
+
+
+def ovl_host_lu_solve(a, b):
+    """Host pivoted LU solve of a x = b (b: n or n x nb)."""
+    a = _square_c128(a)
+    b = np.ascontiguousarray(np.asarray(b, dtype=np.complex128))
+    vec = b.ndim == 1
+    b2 = b.reshape(a.shape[0], -1) if vec else b
+    if b2.shape[0] != a.shape[0]:
+        raise ValueError("b must have as many rows as a")
+    b2 = np.ascontiguousarray(b2)
+    x = np.zeros_like(b2)
+    _check(load().ovl_host_lu_solve(a.shape[0], _cptr(a), _cptr(b2), b2.shape[1], _cptr(x)))
+    return x.ravel() if vec else x
+
+
+def ovl_host_tridiag_extremes(d, e):
+    """Smallest and largest eigenvalue of the symmetric tridiagonal (d, e)."""
+    d = np.ascontiguousarray(np.asarray(d, dtype=np.float64))
+    e = np.ascontiguousarray(np.asarray(e, dtype=np.float64))
+    if e.size != max(0, d.size - 1):
+        raise ValueError("e must hold len(d) - 1 entries")
+    lo, hi = np.zeros(1), np.zeros(1)
+    ep = _dptr(e) if e.size else None
+    _check(load().ovl_host_tridiag_extremes(d.size, _dptr(d), ep, _dptr(lo), _dptr(hi)))
+    return float(lo[0]), float(hi[0])
 
 
 def _current_device():

@@ -413,6 +413,59 @@ extern "C" ovl_status ovl_zolotarev_coeffs(int n, double a, double b, double* om
   return zolotarev_coeffs(n, a, b, omega, sigma, delta) == 0 ? OVL_OK : OVL_EINVAL;
 }
 
+// The host numerics the solvers run between launches, on caller copies (the helpers
+// work in place); complex matrices are row-major interleaved (re, im) doubles, which is
+// the layout of std::complex<double>.
+static const int HOST_NMAX = 4096;
+
+extern "C" ovl_status ovl_host_eigh(int n, const double* a, double* w, double* z) {
+  if (n < 1 || n > HOST_NMAX || !a || !w || !z) return OVL_EINVAL;
+  std::vector<cd> A((size_t)n * n);
+  memcpy(A.data(), a, sizeof(cd) * (size_t)n * n);
+  for (int i = 0; i < n; ++i)
+    for (int j = 0; j < n; ++j)
+      if (!std::isfinite(A[(size_t)i * n + j].real()) || !std::isfinite(A[(size_t)i * n + j].imag())) return OVL_EINVAL;
+  eigh_jacobi(n, A.data(), w, reinterpret_cast<cd*>(z));
+  return OVL_OK;
+}
+
+extern "C" ovl_status ovl_host_cholesky(int n, const double* a, double* l) {
+  if (n < 1 || n > HOST_NMAX || !a || !l) return OVL_EINVAL;
+  std::vector<cd> L((size_t)n * n);
+  memcpy(L.data(), a, sizeof(cd) * (size_t)n * n);
+  if (cholesky_lower(n, L.data()) != 0) return OVL_EBREAKDOWN;
+  memcpy(l, L.data(), sizeof(cd) * (size_t)n * n);
+  return OVL_OK;
+}
+
+extern "C" ovl_status ovl_host_lower_inverse(int n, const double* l, double* li) {
+  if (n < 1 || n > HOST_NMAX || !l || !li) return OVL_EINVAL;
+  const cd* L = reinterpret_cast<const cd*>(l);
+  for (int i = 0; i < n; ++i)
+    if (std::abs(L[(size_t)i * n + i]) == 0.0) return OVL_EBREAKDOWN;
+  std::vector<cd> Li((size_t)n * n);
+  lower_inverse(n, L, Li.data());
+  memcpy(li, Li.data(), sizeof(cd) * (size_t)n * n);
+  return OVL_OK;
+}
+
+extern "C" ovl_status ovl_host_lu_solve(int n, const double* a, const double* b, int nb, double* x) {
+  if (n < 1 || n > HOST_NMAX || nb < 1 || nb > HOST_NMAX || !a || !b || !x) return OVL_EINVAL;
+  std::vector<cd> A((size_t)n * n), B((size_t)n * nb);
+  memcpy(A.data(), a, sizeof(cd) * (size_t)n * n);
+  memcpy(B.data(), b, sizeof(cd) * (size_t)n * nb);
+  if (lu_solve(n, A.data(), B.data(), nb) != 0) return OVL_EBREAKDOWN;
+  memcpy(x, B.data(), sizeof(cd) * (size_t)n * nb);
+  return OVL_OK;
+}
+
+extern "C" ovl_status ovl_host_tridiag_extremes(int n, const double* d, const double* e, double* lmin,
+                                                double* lmax) {
+  if (n < 1 || !d || (n > 1 && !e) || !lmin || !lmax) return OVL_EINVAL;
+  tridiag_extremes(n, d, e, lmin, lmax);
+  return OVL_OK;
+}
+
 extern "C" ovl_status overlap_zolotarev(const ovl_ctx* c, double* omega, double* sigma, double* delta, double* a,
                                         double* b) {
   if (!c) return OVL_EINVAL;

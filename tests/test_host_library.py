@@ -1,6 +1,9 @@
 """CPU-side checks of liboverlap: the library loads, exports every symbol that
-include/overlap.h declares, and its host-only numerics (Zolotarev coefficients
-from its own elliptic-function code) agree with the oracle. No GPU calls."""
+include/overlap.h declares, and its host-only numerics agree with the oracle or with
+NumPy: the Zolotarev coefficients from its own elliptic-function code, and the small
+dense linear algebra the solvers run between launches (Jacobi eigendecomposition,
+Cholesky, triangular inverse, pivoted LU, Sturm bisection of a tridiagonal). No GPU
+calls."""
 import os
 import re
 
@@ -66,3 +69,113 @@ def test_binding_checks_output_buffers():
     import torch
     with pytest.raises(ValueError):
         binding._io(None, torch.zeros((2, 3), dtype=torch.complex128), torch.zeros((2, 2), dtype=torch.complex128))
+
+
+# ---- the host numerics the solvers run between launches (Alg. 6, Sec. 4, Sec. 3 bounds)
+def _herm(n, rng, spread=1.0):
+    Z = rng.normal(size=(n, n)) + 1j * rng.normal(size=(n, n))
+    Q, _ = np.linalg.qr(Z)
+    w = np.sort(rng.uniform(-1, 1, n)) * spread
+    return (Q * w) @ Q.conj().T, w
+
+
+@pytest.mark.parametrize("n", [1, 2, 7, 48, 130])
+def test_host_eigh_against_numpy(n):
+    binding = _lib()
+    rng = np.random.default_rng(n)
+    A, _ = _herm(n, rng)
+    w, Z = binding.ovl_host_eigh(A)
+    assert np.all(np.diff(w) >= 0)
+    assert np.allclose(w, np.linalg.eigvalsh(A), rtol=0, atol=1e-13 * max(1, n))
+    assert np.allclose(Z.conj().T @ Z, np.eye(n), atol=1e-12)
+    assert np.allclose(A @ Z, Z * w, atol=1e-12)
+
+
+def test_host_eigh_degenerate_graded_and_diagonal():
+    """Repeated eigenvalues (an invariant subspace, any basis of it), a spectrum spread
+    over ten decades as in a Ritz step on D^dag D, and an input that is already diagonal."""
+    binding = _lib()
+    rng = np.random.default_rng(3)
+    Q, _ = np.linalg.qr(rng.normal(size=(9, 9)) + 1j * rng.normal(size=(9, 9)))
+    lam = np.array([1, 1, 1, 2, 2, 3, 3, 3, 3], dtype=float)
+    A = (Q * lam) @ Q.conj().T
+    w, Z = binding.ovl_host_eigh(A)
+    assert np.allclose(w, lam, atol=1e-13)
+    assert np.allclose(Z.conj().T @ Z, np.eye(9), atol=1e-12)
+    assert np.allclose(A @ Z, Z * w, atol=1e-12)
+    lam = np.logspace(-8, 2, 24)
+    Q, _ = np.linalg.qr(rng.normal(size=(24, 24)) + 1j * rng.normal(size=(24, 24)))
+    A = (Q * lam) @ Q.conj().T
+    w, Z = binding.ovl_host_eigh(A)
+    assert np.allclose(w, lam, rtol=0, atol=1e-12 * lam[-1])
+    assert np.allclose(A @ Z, Z * w, atol=1e-12 * lam[-1])
+    d = np.array([3.0, -1.0, 2.0, 0.5])
+    w, Z = binding.ovl_host_eigh(np.diag(d).astype(complex))
+    assert np.array_equal(w, np.sort(d))
+    assert np.allclose(np.abs(Z), np.eye(4)[:, np.argsort(d)])
+
+
+def test_host_cholesky_and_lower_inverse():
+    binding = _lib()
+    rng = np.random.default_rng(4)
+    for n in (1, 5, 64):
+        X = rng.normal(size=(n + 3, n)) + 1j * rng.normal(size=(n + 3, n))
+        E = X.conj().T @ X                       # a Gram matrix, as in Alg. 6
+        L = binding.ovl_host_cholesky(E)
+        assert np.allclose(np.triu(L, 1), 0)
+        assert np.all(np.real(np.diag(L)) > 0) and np.allclose(np.imag(np.diag(L)), 0)
+        assert np.allclose(L @ L.conj().T, E, atol=1e-12 * np.abs(E).max())
+        assert np.allclose(L, np.linalg.cholesky(E), atol=1e-11 * np.abs(L).max())
+        Li = binding.ovl_host_lower_inverse(L)
+        assert np.allclose(Li @ L, np.eye(n), atol=1e-11)
+    A, _ = _herm(6, rng)                         # indefinite
+    with pytest.raises(binding.OvlError) as e:
+        binding.ovl_host_cholesky(A)
+    assert e.value.status == binding.OVL_EBREAKDOWN
+    with pytest.raises(binding.OvlError) as e:
+        binding.ovl_host_lower_inverse(np.zeros((3, 3), dtype=complex))
+    assert e.value.status == binding.OVL_EBREAKDOWN
+
+
+def test_host_lu_solve():
+    binding = _lib()
+    rng = np.random.default_rng(5)
+    for n, nb in ((1, 1), (6, 1), (40, 3)):
+        A = rng.normal(size=(n, n)) + 1j * rng.normal(size=(n, n))
+        B = rng.normal(size=(n, nb)) + 1j * rng.normal(size=(n, nb))
+        X = binding.ovl_host_lu_solve(A, B)
+        assert np.allclose(X, np.linalg.solve(A, B), atol=1e-10 * np.abs(X).max())
+    # a zero leading entry needs the row exchange
+    A = np.array([[0, 1, 2], [3, 0, 1], [1, 1, 0]], dtype=complex)
+    b = np.array([1, 2, 3], dtype=complex)
+    assert np.allclose(binding.ovl_host_lu_solve(A, b), np.linalg.solve(A, b), atol=1e-14)
+    A[:, 1] = 0                                  # a zero pivot column
+    with pytest.raises(binding.OvlError) as e:
+        binding.ovl_host_lu_solve(A, b)
+    assert e.value.status == binding.OVL_EBREAKDOWN
+
+
+@pytest.mark.parametrize("n", [1, 2, 50, 300])
+def test_host_tridiag_extremes(n):
+    binding = _lib()
+    rng = np.random.default_rng(6 + n)
+    d = rng.uniform(0.05, 7.0, n)               # K^2-like: positive diagonal
+    e = rng.uniform(0.0, 2.0, n - 1)
+    lo, hi = binding.ovl_host_tridiag_extremes(d, e)
+    T = np.diag(d) + np.diag(e, 1) + np.diag(e, -1)
+    ev = np.linalg.eigvalsh(T)
+    assert abs(lo - ev[0]) <= 1e-12 * max(1, abs(ev[-1]))
+    assert abs(hi - ev[-1]) <= 1e-12 * max(1, abs(ev[-1]))
+
+
+def test_host_numerics_reject_bad_arguments():
+    binding = _lib()
+    lib = binding.load()
+    assert lib.ovl_host_eigh(0, None, None, None) == binding.OVL_EINVAL
+    assert lib.ovl_host_lu_solve(2, None, None, 1, None) == binding.OVL_EINVAL
+    assert lib.ovl_host_tridiag_extremes(3, None, None, None, None) == binding.OVL_EINVAL
+    A = np.eye(3, dtype=complex)
+    A[1, 2] = np.nan
+    with pytest.raises(binding.OvlError) as e:
+        binding.ovl_host_eigh(A)
+    assert e.value.status == binding.OVL_EINVAL
