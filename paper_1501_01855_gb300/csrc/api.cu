@@ -781,6 +781,14 @@ extern "C" ovl_status eigsumr_accumulate(ovl_ctx* c, ovl_defl** defl, int n_eig,
   } else if (d->ctx != c) {
     return set_err(c, OVL_EINVAL, "deflation space belongs to another context");
   }
+  // a space created here goes back on every error exit; only the last line hands it over
+  struct FreshSpace {
+    ovl_defl* d;
+    bool own;
+    ~FreshSpace() {
+      if (own) ovl_defl_destroy(d);
+    }
+  } guard{d, fresh};
   EigState e;
   e.prec = d->v.prec;
   e.m = m_basis;
@@ -821,17 +829,11 @@ extern "C" ovl_status eigsumr_accumulate(ovl_ctx* c, ovl_defl** defl, int n_eig,
   // the deflation held so far accelerates this solve too; the space is rebuilt after it
   ovl_defl* use = (!fresh && d->n > 0) ? d : nullptr;
   ovl_status st = gmresr_batch(c, 1, mus, *fb, 0, *fx, 0, tol, use, info, &hook);
-  if (st != OVL_OK && st != OVL_ENOCONV) {
-    if (fresh) ovl_defl_destroy(d);
-    return st;
-  }
+  if (st != OVL_OK && st != OVL_ENOCONV) return st;
   // final Ritz step over whatever the basis holds
   if (e.k > e.n_seeded || e.ndiag == 0 || e.k > n_eig) OVL_TRY(ritz_step(c, &e, n_eig));
   const int nk = e.k;
-  if (nk < 1) {
-    if (fresh) ovl_defl_destroy(d);
-    return set_err(c, OVL_ENOCONV, "eigSUMR collected no basis vectors (the solve needed no SUMR step)");
-  }
+  if (nk < 1) return set_err(c, OVL_ENOCONV, "eigSUMR collected no basis vectors (the solve needed no SUMR step)");
   OVL_TRY(defl_store(c, d, e.V, nk, mu));
   OVL_TRY(export_spinors(c, x, dtype, on_device, 1, *fx, 0));
   if (info && c->P.verify) {
@@ -846,6 +848,7 @@ extern "C" ovl_status eigsumr_accumulate(ovl_ctx* c, ovl_defl** defl, int n_eig,
     auto it = c->ws.find(nm);
     if (it != c->ws.end()) free_field(it->second);
   }
+  guard.own = false;
   *defl = d;
   return st;
 }
@@ -1023,7 +1026,10 @@ extern "C" ovl_status ovl_eigensolve(ovl_ctx* c, ovl_defl** defl, int n_eig, int
     if (it == c->ws.end()) break;
     if ((st = copy_convert(c, it->second, 0, *q0, 0, 1)) != OVL_OK) return fail(st);
   }
-  OVL_CUDA(c, cudaStreamSynchronize(c->st));
+  {
+    const cudaError_t ce = cudaStreamSynchronize(c->st);
+    if (ce != cudaSuccess) return fail(cuda_check(c, ce, "cudaStreamSynchronize(c->st)"));
+  }
   for (const char* nm : {"e_V", "e_W", "e_VD", "e_T", "es_q0", "es_x", "es_g1v", "es_g1w", "es_g2v", "es_g2w"}) {
     auto it = c->ws.find(nm);
     if (it != c->ws.end()) free_field(it->second);
