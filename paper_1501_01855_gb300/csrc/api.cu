@@ -968,6 +968,9 @@ extern "C" ovl_status ovl_eigensolve(ovl_ctx* c, ovl_defl** defl, int n_eig, int
     e.n_seeded = 0;
     e.ndiag = 0;
     if (ns > 0) {
+      // the Gram blocks of the space (absent after ovl_defl_load until first use; n x n with
+      // n = d->n, which exceeds ns when the caller's space holds more than n_eig vectors)
+      if ((st = defl_prepare(c, d)) != OVL_OK) return fail(st);
       if ((st = copy_convert(c, d->v, 0, *e.V, 0, ns)) != OVL_OK) return fail(st);
       if ((st = copy_convert(c, d->w, 0, *e.W, 0, ns)) != OVL_OK) return fail(st);
       e.k = e.n_seeded = ns;
@@ -975,7 +978,7 @@ extern "C" ovl_status ovl_eigensolve(ovl_ctx* c, ovl_defl** defl, int n_eig, int
         std::vector<cd> G, C;
         if ((st = gram_host(c, d->v, 0, ns, *q0, 0, 1, 0, G)) != OVL_OK) return fail(st);
         C.resize(ns);
-        for (int i = 0; i < ns; ++i) C[i] = -G[i] / std::max(d->VV[(size_t)i * ns + i].real(), 1e-300);
+        for (int i = 0; i < ns; ++i) C[i] = -G[i] / std::max(d->VV[(size_t)i * d->n + i].real(), 1e-300);
         if ((st = combine_host(c, d->v, 0, ns, C, *q0, 0, 1, 1)) != OVL_OK) return fail(st);
       }
     }
