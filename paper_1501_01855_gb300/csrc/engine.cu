@@ -191,6 +191,8 @@ void trim_workspaces(ovl_ctx* c) {
 
 ovl_status ensure_stage(ovl_ctx* c, size_t bytes) {
   if (bytes <= c->hstage_bytes) return OVL_OK;
+  // the last copy out of the old buffer must be done before it goes back
+  if (c->hstage) OVL_CUDA(c, cudaEventSynchronize(c->stage_ev));
   if (c->hstage) cudaFreeHost(c->hstage);
   c->hstage = nullptr;
   OVL_CUDA(c, cudaMallocHost(&c->hstage, bytes));
