@@ -36,6 +36,7 @@ Under torchrun each rank runs an independent replica on its own GPU (the path
 shards by right-hand sides; weak scaling, no collective on the data path).
 """
 import argparse
+import contextlib
 import json
 import os
 import statistics
@@ -404,77 +405,95 @@ def run_ours(args, ws, rank, local):
     ctx.trim()     # the extras create contexts of their own
 
     if rank == 0 and not args.no_extras:
-        line["extras"] = extras(args, ctx, dv, dout, ref_out, B, torch, stream, hbm)
+        with _section(line, "extras"):
+            line["extras"] = extras(args, ctx, dv, dout, ref_out, B, torch, stream, hbm)
     ctx.close()
     if rank == 0 and ws == 1 and not args.no_cpu:
-        line["cpu_baseline"] = oracle_baseline()
+        try:
+            line["cpu_baseline"] = oracle_baseline()
+        except Exception as e:   # the oracle's timing must not cost the GPU line
+            line["cpu_baseline"] = {"kind": "oracle", "error": "%s: %s" % (type(e).__name__, e)}
     return line
+
+
+@contextlib.contextmanager
+def _section(out, key):
+    """One block of the extras: an exception is recorded under key instead of costing the
+    benchmark line."""
+    try:
+        yield
+    except Exception as e:
+        out[key] = {"error": "%s: %s" % (type(e).__name__, e)}
 
 
 def extras(args, ctx, dv, dout, ref_out, B, torch, stream, hbm):
     import synth
     out = {}
-    # the same apply in native FP64 (the plain path), and the mixed-precision applies:
-    # FP32 sign at eta=1e-6, FP16 storage at eta=1e-2; errors against the double-float result
-    for name, prec, eta in (("native_fp64_eta1e-10", B.OVL_PREC_F64, 1e-10), ("fp32_eta1e-6", B.OVL_PREC_F32, 1e-6),
-                            ("fp16_eta1e-2", B.OVL_PREC_F16, 1e-2)):
-        ctx.apply(dv, dout, eta=eta, prec=prec)
-        torch.cuda.synchronize()
-        e0 = torch.cuda.Event(enable_timing=True)
-        e1 = torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        reps = 3
-        for _ in range(reps):
+    with _section(out, "precision_applies"):
+        # the same apply in native FP64 (the plain path), and the mixed-precision applies:
+        # FP32 sign at eta=1e-6, FP16 storage at eta=1e-2; errors against the double-float result
+        for name, prec, eta in (("native_fp64_eta1e-10", B.OVL_PREC_F64, 1e-10), ("fp32_eta1e-6", B.OVL_PREC_F32, 1e-6),
+                                ("fp16_eta1e-2", B.OVL_PREC_F16, 1e-2)):
             ctx.apply(dv, dout, eta=eta, prec=prec)
-        e1.record(stream)
-        torch.cuda.synchronize()
-        ms = e0.elapsed_time(e1) / reps
-        got = dout.cpu().numpy()
-        err = max(np.linalg.norm(got[j] - ref_out[j]) / np.linalg.norm(ref_out[j]) for j in range(NVEC))
-        out[name] = {"applies_per_s": NVEC / (ms * 1e-3), "max_rel_error_vs_df64": err}
+            torch.cuda.synchronize()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            reps = 3
+            for _ in range(reps):
+                ctx.apply(dv, dout, eta=eta, prec=prec)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ms = e0.elapsed_time(e1) / reps
+            got = dout.cpu().numpy()
+            err = max(np.linalg.norm(got[j] - ref_out[j]) / np.linalg.norm(ref_out[j]) for j in range(NVEC))
+            out[name] = {"applies_per_s": NVEC / (ms * 1e-3), "max_rel_error_vs_df64": err}
     ctx.trim()
-    # Wilson kernel bandwidth on 24^3x48 (working set larger than L2)
-    dims = (24, 24, 24, 48)
-    p = B.ovl_params_default()
-    p.a_override, p.b_override = 0.2, 2.6
-    p.stream = stream.cuda_stream
-    cw = B.Overlap(dims, synth.unit_links(dims), M0, MU, 8, 1e-3, params=p)
-    ds = {}
-    for prec, nm in ((0, "f64"), (3, "df64"), (1, "f32"), (2, "f16")):
-        for n in (1, 12):
-            ms, by = cw.bench_wilson(prec, n, 40 if n == 1 else 8)
-            gbs = by / (ms * 1e-3) / 1e9
-            ds["%s_n%d" % (nm, n)] = {"ms": ms, "GB/s": gbs, "frac_hbm": gbs / hbm,
-                                     "Gsites/s": 663552 * n / (ms * 1e-3) / 1e9}
-    cw.close()
-    out["wilson_24x24x24x48"] = ds
-    # one RHS solve to 1e-10: mixed GMRESR(relSUMR) vs plain FP64
-    U = synth.gauge_links(DIMS, 0.3, LINK_SEED)
-    b = synth.gaussian_source(DIMS, 3002)
-    sol = {}
-    for nm, mixed, emul in (("mixed_relSUMR", 1, 1), ("mixed_relSUMR_native_fp64_outer", 1, 0),
-                            ("plain_fp64_relSUMR", 0, 0)):
+    with _section(out, "wilson_24x24x24x48"):
+        # Wilson kernel bandwidth on 24^3x48 (working set larger than L2)
+        dims = (24, 24, 24, 48)
         p = B.ovl_params_default()
-        p.mixed = mixed
-        p.emulate_fp64 = emul
+        p.a_override, p.b_override = 0.2, 2.6
         p.stream = stream.cuda_stream
-        cs = B.Overlap(DIMS, U, M0, MU, NPOLES, EPS, params=p)
-        x = np.zeros_like(b)
-        cs.solve(b, x, 1e-10)             # warm-up (allocations)
-        t0 = time.perf_counter()
-        info = cs.solve(b, x, 1e-10)[0]
-        dt = time.perf_counter() - t0
-        cs.profile_reset()
-        cs.profile_enable(True)
-        cs.solve(b, x, 1e-10)
-        cs.profile_enable(False)
-        prof = {k: round(v["ms"], 2) for k, v in cs.profile_get().items() if v["launches"]}
-        sol[nm] = {"seconds": dt, "solves_per_s": 1.0 / dt, "true_residual": info["true_residual"],
-                   "outer": info["outer_iters"], "inner": info["inner_iters"],
-                   "wilson_calls_dp2": info["wilson_calls"], "profile_ms": prof}
-        cs.close()
-    out["solve_16x16x16x32_mu0.05"] = sol
-    out["deflated_batched_16x16x16x32_mu0.02"] = deflated_batched(B, stream)
+        cw = B.Overlap(dims, synth.unit_links(dims), M0, MU, 8, 1e-3, params=p)
+        ds = {}
+        for prec, nm in ((0, "f64"), (3, "df64"), (1, "f32"), (2, "f16")):
+            for n in (1, 12):
+                ms, by = cw.bench_wilson(prec, n, 40 if n == 1 else 8)
+                gbs = by / (ms * 1e-3) / 1e9
+                ds["%s_n%d" % (nm, n)] = {"ms": ms, "GB/s": gbs, "frac_hbm": gbs / hbm,
+                                         "Gsites/s": 663552 * n / (ms * 1e-3) / 1e9}
+        cw.close()
+        out["wilson_24x24x24x48"] = ds
+    with _section(out, "solve_16x16x16x32_mu0.05"):
+        # one RHS solve to 1e-10: mixed GMRESR(relSUMR) vs plain FP64
+        U = synth.gauge_links(DIMS, 0.3, LINK_SEED)
+        b = synth.gaussian_source(DIMS, 3002)
+        sol = {}
+        for nm, mixed, emul in (("mixed_relSUMR", 1, 1), ("mixed_relSUMR_native_fp64_outer", 1, 0),
+                                ("plain_fp64_relSUMR", 0, 0)):
+            p = B.ovl_params_default()
+            p.mixed = mixed
+            p.emulate_fp64 = emul
+            p.stream = stream.cuda_stream
+            cs = B.Overlap(DIMS, U, M0, MU, NPOLES, EPS, params=p)
+            x = np.zeros_like(b)
+            cs.solve(b, x, 1e-10)             # warm-up (allocations)
+            t0 = time.perf_counter()
+            info = cs.solve(b, x, 1e-10)[0]
+            dt = time.perf_counter() - t0
+            cs.profile_reset()
+            cs.profile_enable(True)
+            cs.solve(b, x, 1e-10)
+            cs.profile_enable(False)
+            prof = {k: round(v["ms"], 2) for k, v in cs.profile_get().items() if v["launches"]}
+            sol[nm] = {"seconds": dt, "solves_per_s": 1.0 / dt, "true_residual": info["true_residual"],
+                       "outer": info["outer_iters"], "inner": info["inner_iters"],
+                       "wilson_calls_dp2": info["wilson_calls"], "profile_ms": prof}
+            cs.close()
+        out["solve_16x16x16x32_mu0.05"] = sol
+    with _section(out, "deflated_batched_16x16x16x32_mu0.02"):
+        out["deflated_batched_16x16x16x32_mu0.02"] = deflated_batched(B, stream)
     # Gram block of the Ritz step (128 x 128 spinors on 16^3 x 32): tensor cores at FP64 level
     # against the CUDA-core kernel with FP32 products
     try:

@@ -29,3 +29,14 @@ def test_clock_parser_median_max_and_reasons():
 def test_peak_lookup_returns_a_bandwidth():
     gbs, src = bench.peaks()
     assert gbs > 1000 and src in ("measured", "fallback")
+
+
+def test_extras_section_records_an_error_and_goes_on():
+    """A failing block of the extras leaves its error under its key; the line is kept."""
+    import bench
+    out = {}
+    with bench._section(out, "a"):
+        raise RuntimeError("boom")
+    with bench._section(out, "b"):
+        out["b"] = 1
+    assert out == {"a": {"error": "RuntimeError: boom"}, "b": 1}
