@@ -237,7 +237,8 @@ ovl_status ovl_wilson_apply(ovl_ctx* ctx, const void* in, void* out, int n, int 
  * (48 bytes of spinor plus a 4-byte scale per site), each buffer rounded up to 256
  * bytes, so n V <= 131072 in FP64; a larger call returns OVL_EINVAL. No cudaMalloc,
  * cudaFree or other allocating routine is called. The first call on a device looks up
- * the array's device address (cudaGetSymbolAddress) once. Like every entry point here,
+ * the array's device address (cudaGetSymbolAddress) once; make that first call before
+ * any stream capture begins. Like every entry point here,
  * the call returns after its work on the context stream has completed. All calls share
  * the array: calls that overlap on the GPU race on it, and it keeps the last call's
  * intermediate data (nothing in it has to start at zero). */

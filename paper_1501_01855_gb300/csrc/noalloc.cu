@@ -11,7 +11,7 @@
 // stays allocated until the process exits. Host code cannot use its name as an
 // address (on the host the symbol is only a stand-in); its device address is looked up
 // once per device with cudaGetSymbolAddress on the first call made on that device
-// and cached. Every call shares the array: calls that overlap on the GPU (other
+// and cached; that first call belongs before any stream capture begins. Every call shares the array: calls that overlap on the GPU (other
 // streams, other host threads) race on it, and after a call it holds that call's
 // intermediate fields. Nothing in it needs to start at zero, because each call writes
 // every byte it later reads.
