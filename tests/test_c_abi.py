@@ -1,0 +1,78 @@
+"""The boundary is a C ABI: a C99 program (gcc, -pedantic -Werror) includes
+include/overlap.h, links liboverlap.so and calls the host-only entry points; its output
+agrees with the oracle (Zolotarev coefficients, Sec. 3) and with NumPy (the host
+numerics), and a bad argument comes back as OVL_EINVAL. No GPU calls."""
+import os
+import shutil
+import subprocess
+
+import numpy as np
+import pytest
+
+from oracle import zolotarev as zo
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+C_SRC = r"""
+#include <stdio.h>
+#include <string.h>
+#include "overlap.h"
+
+int main(void) {
+  double om[8], sg[8], de, lo, hi, w[3], z[18], a[18];
+  const double d[4] = {2.0, 3.0, 4.0, 5.0}, e[3] = {1.0, 0.5, 0.25};
+  int i;
+  if (ovl_zolotarev_coeffs(8, 0.15, 2.6, om, sg, &de) != OVL_OK) return 1;
+  for (i = 0; i < 8; ++i) printf("%.17g %.17g\n", om[i], sg[i]);
+  printf("%.17g\n", de);
+  if (ovl_host_tridiag_extremes(4, d, e, &lo, &hi) != OVL_OK) return 2;
+  printf("%.17g %.17g\n", lo, hi);
+  /* [[2, i, 0], [-i, 2, 0], [0, 0, 5]] as interleaved (re, im), row-major */
+  memset(a, 0, sizeof(a));
+  a[0] = 2.0; a[3] = 1.0; a[7] = -1.0; a[8] = 2.0; a[16] = 5.0;
+  if (ovl_host_eigh(3, a, w, z) != OVL_OK) return 3;
+  printf("%.17g %.17g %.17g\n", w[0], w[1], w[2]);
+  printf("%d\n", (int)ovl_zolotarev_coeffs(0, 0.15, 2.6, om, sg, &de));
+  printf("%s\n", ovl_version());
+  return 0;
+}
+"""
+
+
+@pytest.fixture(scope="module")
+def c_program(tmp_path_factory):
+    gcc = shutil.which("gcc") or shutil.which("cc")
+    if gcc is None:
+        pytest.skip("no C compiler")
+    from paper_1501_01855_gb300 import build
+    lib = build.build()
+    d = tmp_path_factory.mktemp("cabi")
+    src = d / "t.c"
+    src.write_text(C_SRC)
+    exe = d / "t"
+    libdir = os.path.dirname(lib)
+    cmd = [gcc, "-std=c99", "-Wall", "-Wextra", "-Werror", "-pedantic", "-I", os.path.join(ROOT, "include"),
+           str(src), "-L", libdir, "-loverlap", "-Wl,-rpath," + libdir, "-o", str(exe)]
+    r = subprocess.run(cmd, capture_output=True, text=True)
+    assert r.returncode == 0, r.stderr
+    return str(exe)
+
+
+def test_c_program_calls_the_library(c_program):
+    r = subprocess.run([c_program], capture_output=True, text=True, timeout=120)
+    assert r.returncode == 0, (r.returncode, r.stderr)
+    lines = r.stdout.strip().splitlines()
+    om = np.array([float(l.split()[0]) for l in lines[:8]])
+    sg = np.array([float(l.split()[1]) for l in lines[:8]])
+    de = float(lines[8])
+    o2, s2, d2 = zo.zolotarev(8, 0.15, 2.6)
+    assert np.allclose(om, o2, rtol=1e-11, atol=0) and np.allclose(sg, s2, rtol=1e-11, atol=0)
+    assert abs(de - d2) <= 1e-6 * d2 + 5e-15
+    lo, hi = map(float, lines[9].split())
+    T = np.diag([2.0, 3.0, 4.0, 5.0]) + np.diag([1.0, 0.5, 0.25], 1) + np.diag([1.0, 0.5, 0.25], -1)
+    ev = np.linalg.eigvalsh(T)
+    assert abs(lo - ev[0]) <= 1e-13 and abs(hi - ev[-1]) <= 1e-13
+    w = np.array(list(map(float, lines[10].split())))
+    assert np.allclose(w, [1.0, 3.0, 5.0], atol=1e-14)
+    assert int(lines[11]) == -1                      # OVL_EINVAL
+    assert lines[12].startswith("liboverlap")
