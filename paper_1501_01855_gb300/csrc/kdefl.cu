@@ -205,7 +205,13 @@ extern "C" ovl_status ovl_kernel_deflate(ovl_ctx* c, int n_ev, double tol, int m
   kd.V = c->V;
   OVL_CUDA(c, cudaMalloc(&kd.data, kd.chunk_bytes()));
   c->kd = kd;
-  OVL_TRY(copy_convert(c, *X, 0, c->kd, 0, n_ev));
+  {
+    const ovl_status cs = copy_convert(c, *X, 0, c->kd, 0, n_ev);
+    if (cs != OVL_OK) {
+      free_field(c->kd);
+      return cs;
+    }
+  }
   c->kd_lambda.assign(theta.begin(), theta.begin() + n_ev);
   c->kd_n = n_ev;
   // the interval left: lambda_min of K^2 on the complement
