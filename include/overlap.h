@@ -337,7 +337,9 @@ ovl_status ovl_defl_vector(const ovl_defl* defl, int i, double* v, double* vD);
  * header line "OVLDEFL 1 n=<n> V=<V> mu=<mu>", then per vector v_i and
  * w_i = gamma5 eps(K) v_i as complex128 canonical spinors, then the n Ritz values
  * and n residuals as float64. Load creates a new space on ctx (OVL_EINVAL if the file
- * is malformed or V differs from the context's); save and load round-trip bit-exactly. */
+ * is malformed or V differs from the context's); save returns OVL_EINVAL when the file
+ * cannot be opened or a write fails (the file is then incomplete). Save and load
+ * round-trip bit-exactly. */
 ovl_status ovl_defl_save(const ovl_defl* defl, const char* path);
 ovl_status ovl_defl_load(ovl_ctx* ctx, ovl_defl** defl, const char* path);
 /* Free a deflation space (NULL is allowed). */

@@ -1070,19 +1070,21 @@ extern "C" ovl_status ovl_defl_save(const ovl_defl* d, const char* path) {
   ovl_ctx* c = d->ctx;
   FILE* f = fopen(path, "wb");
   if (!f) return set_err(c, OVL_EINVAL, std::string("cannot open ") + path);
-  fprintf(f, "OVLDEFL 1 n=%d V=%d mu=%.17g\n", d->n, c->V, d->mu);
+  // every write is checked: a full disk must not leave a truncated file reported as saved
+  bool ok = fprintf(f, "OVLDEFL 1 n=%d V=%d mu=%.17g\n", d->n, c->V, d->mu) > 0;
   std::vector<double> h((size_t)24 * c->V);
-  for (int i = 0; i < d->n; ++i) {
+  for (int i = 0; i < d->n && ok; ++i) {
     ovl_status s = export_spinors(c, h.data(), OVL_C128, 0, 1, d->v, i);
     if (s != OVL_OK) { fclose(f); return s; }
-    fwrite(h.data(), sizeof(double), h.size(), f);
+    ok = fwrite(h.data(), sizeof(double), h.size(), f) == h.size();
     s = export_spinors(c, h.data(), OVL_C128, 0, 1, d->w, i);
     if (s != OVL_OK) { fclose(f); return s; }
-    fwrite(h.data(), sizeof(double), h.size(), f);
+    ok = ok && fwrite(h.data(), sizeof(double), h.size(), f) == h.size();
   }
-  fwrite(d->ritz.data(), sizeof(double), d->n, f);
-  fwrite(d->res.data(), sizeof(double), d->n, f);
-  fclose(f);
+  ok = ok && fwrite(d->ritz.data(), sizeof(double), d->n, f) == (size_t)d->n;
+  ok = ok && fwrite(d->res.data(), sizeof(double), d->n, f) == (size_t)d->n;
+  ok = (fclose(f) == 0) && ok;
+  if (!ok) return set_err(c, OVL_EINVAL, std::string("writing ") + path + " failed");
   return OVL_OK;
 }
 
