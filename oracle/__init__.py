@@ -13,6 +13,7 @@ Modules
   wilson     gamma matrices, Wilson kernel K (Sec. 1, Eq. for aK_xy), dense K
   zolotarev  Zolotarev coefficients omega_i, sigma_i and Delta (Sec. 3)
   overlap    sign(K) (spectral definition, Sec. 1), epsilon(K) by per-pole CG,
+             the sign with the smallest eigenvectors of K deflated (Sec. 1),
              D(mu), H = gamma5 D, D^dagger D (Sec. 1)
   solvers    Alg. 1 basis, minimal-residual (GMRES) iterates, GMRESR (Alg. 3),
              preconditioned CGNE (Alg. 4), dense solves
@@ -22,5 +23,6 @@ Modules
              approximation (not in the paper; derivation in force.py)
 
 Parity unpinned: none of the functions above is left without a pin; the pins
-live in tests/test_oracle_*.py.
+live in tests/test_oracle_*.py, and tests/test_oracle_planted_mistakes.py checks
+that they fail when a plausible mistake is planted in any of these functions.
 """
