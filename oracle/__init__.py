@@ -24,5 +24,6 @@ Modules
 
 Parity unpinned: none of the functions above is left without a pin; the pins
 live in tests/test_oracle_*.py, and tests/test_oracle_planted_mistakes.py checks
-that they fail when a plausible mistake is planted in any of these functions.
+that they fail when plausible mistakes are planted in these modules (one expression
+of one function at a time).
 """
