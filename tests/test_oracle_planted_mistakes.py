@@ -14,9 +14,9 @@ dropping the conjugate in the q-tilde update of eigsumr_build changes the basis 
 but not their span (each new one still adds U q_j), so the Rayleigh-Ritz result of
 Alg. 6 is the same; the same rewrite in sumr_basis, whose basis is an output, is a
 case. Pins that run the oracle in a spawn process pool (the workers import the
-unmodified oracle) and the minute-long matrix-free force pins are not used here; the
-matrix-free gradient is pinned by its equality with the dense form
-(test_dense_gradient_equals_matrix_free), whose own mistakes are planted below.
+unmodified oracle) and the minute-long matrix-free force pins are not used here: the
+matrix-free gradient is checked by the quick form of its equality with the dense
+gradient, whose own mistakes are caught by finite differences.
 """
 import inspect
 import textwrap
@@ -73,6 +73,7 @@ PINS = {
     "spectral preconditioner c^2": te.test_spectral_preconditioner_maps_to_c2,
     # force
     "dense gradient, finite differences": tf.test_dense_gradient_finite_differences,
+    "matrix-free gradient = dense gradient": tf.test_matrix_free_gradient_quick,
 }
 
 # (module, function, expression, planted form, pins that may catch it)
@@ -210,6 +211,12 @@ CASES = [
      "+ link_outer(r(Kd @ b), r(a), m0, antiperiodic_t))", ["dense gradient, finite differences"]),
     (force, "gradient_dense", "c = -(1.0 - mu) * om", "c = -(1.0 + mu) * om", ["dense gradient, finite differences"]),
     (force, "gradient_dense", "Ri @ Kpsi", "Ri @ psi", ["dense gradient, finite differences"]),
+    (force, "gradient", "- link_outer(b, Ka, m0, antiperiodic_t)", "+ link_outer(b, Ka, m0, antiperiodic_t)",
+     ["matrix-free gradient = dense gradient"]),
+    (force, "gradient", "b, _ = overlap.cg(A, Kpsi, tol)", "b, _ = overlap.cg(A, psi, tol)",
+     ["matrix-free gradient = dense gradient"]),
+    (force, "gradient", "psi = apply_H(U, chi, m0, mu, omega, sigma, tol, antiperiodic_t)", "psi = chi",
+     ["matrix-free gradient = dense gradient"]),
 ]
 
 
