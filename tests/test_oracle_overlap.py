@@ -142,3 +142,25 @@ def test_deflated_sign_pins():
     allpsi = np.stack([Q[:, k].reshape(v.shape) for k in range(Q.shape[1])])
     full = overlap.deflated_sign_apply(U, v, 1.4, allpsi, wv, om, sg, tol=1e-14)
     assert np.linalg.norm(full - ref) <= 1e-11 * np.linalg.norm(ref)
+
+
+def test_batched_forms_in_process_match_dense():
+    """The batched per-pole forms run in this process (workers = 1): every (vector, pole)
+    pair by its own CG, each vector's solutions summed with its own weights, then K and
+    D(mu) per vector with its own mass, against the dense rational on 2^4."""
+    from oracle import zolotarev as zo
+    d2 = (2, 2, 2, 2)
+    U2, Kd, S, w = dense_setup(d2)
+    om, sg, _ = zo.zolotarev(6, 0.2, 2.6)
+    vs = synth.gaussian_source(d2, 16, nvec=3)
+    R = overlap.dense_zolotarev_sign(Kd, om, sg)
+    G5 = overlap.gamma5_matrix(16)
+    s, its = overlap.zolotarev_sign_apply_many(U2, vs, 1.4, om, sg, tol=1e-14, workers=1)
+    mus = [0.05, 0.3, 0.6]
+    D = overlap.overlap_apply_many(U2, vs, 1.4, mus, om, sg, tol=1e-14, workers=1)
+    for j, mu in enumerate(mus):
+        v = vs[j].ravel()
+        assert np.linalg.norm(s[j].ravel() - R @ v) <= 1e-11 * np.linalg.norm(v)
+        ref = 0.5 * (1 + mu) * v + 0.5 * (1 - mu) * (G5 @ (R @ v))
+        assert np.linalg.norm(D[j].ravel() - ref) <= 1e-11 * np.linalg.norm(ref)
+    assert len(its) == 3 and all(len(i) == 6 for i in its)

@@ -60,6 +60,7 @@ PINS = {
     "free-field overlap spectrum 2^4": lambda: to.test_free_field_overlap_spectrum((2, 2, 2, 2), False),
     "matrix-free D = dense D": to.test_matrix_free_overlap_matches_dense,
     "deflated sign": to.test_deflated_sign_pins,
+    "batched forms = dense rational": to.test_batched_forms_in_process_match_dense,
     # solvers, Algs. 1-4
     "Alg. 1 basis": ts.test_alg1_basis,
     "minimal residual = brute force": ts.test_minres_iterates_brute_force,
@@ -156,6 +157,15 @@ CASES = [
     (overlap, "overlap_apply", "wilson.apply_gamma5(s)", "s", ["matrix-free D = dense D"]),
     (overlap, "overlap_apply_dagger", "g5(overlap_apply(U, g5(v),", "(overlap_apply(U, (v),",
      ["matrix-free D = dense D"]),
+    (overlap, "_worker_pole_solve", "K @ (K @ p) + s * p", "K @ p + s * p", ["batched forms = dense rational"]),
+    (overlap, "shifted_solves", "xs = [[res[j * npol + i][0]", "xs = [[res[i * nv + j][0]",
+     ["batched forms = dense rational"]),
+    (overlap, "zolotarev_sign_apply_many", "out[j] = (K @ y).reshape(vs.shape[1:])", "out[j] = y.reshape(vs.shape[1:])",
+     ["batched forms = dense rational"]),
+    (overlap, "zolotarev_sign_apply_many", "y = sum(om * x for om, x in zip(omega, xs[j]))",
+     "y = sum(om * x for om, x in zip(omega, xs[0]))", ["batched forms = dense rational"]),
+    (overlap, "overlap_apply_many", "0.5 * (1.0 + mus[j]) * vs[j] + 0.5 * (1.0 - mus[j])",
+     "0.5 * (1.0 + mus[0]) * vs[j] + 0.5 * (1.0 - mus[0])", ["batched forms = dense rational"]),
     (overlap, "deflated_sign_apply", "c = vdot(p, v)", "c = vdot(v, p)", ["deflated sign"]),
     (overlap, "deflated_sign_apply", "proj = proj - c * p", "proj = proj", ["deflated sign"]),
     (overlap, "deflated_sign_apply", "low = low + np.sign(l) * c * p", "low = low + c * p", ["deflated sign"]),
