@@ -117,6 +117,8 @@ CASES = [
     (wilson, "sparse_K", "sb[tco == 0] = -1.0", "sb[tco == lt - 1] = -1.0",
      ["sparse K = dense K, 4x2x2x4 antiperiodic", "sparse K = apply_K, 8x4x4x6"]),
     (wilson, "sparse_K", "np.kron(GAMMA5, np.eye(3))", "np.kron(I4, np.eye(3))", ["sparse K = dense K, 2^4"]),
+    (wilson, "dense_operator", "return cols.reshape(n, n).T.copy()", "return cols.reshape(n, n).copy()",
+     ["sparse K = dense K, 2^4", "free-field |lambda(K)| 2^4"]),
     (wilson, "free_field_K_abs_spectrum", "lam = 2 * kap * np.sqrt(b ** 2 + s2)", "lam = kap * np.sqrt(b ** 2 + s2)",
      ["free-field |lambda(K)| 2^4"]),
     # ---- zolotarev: elliptic coefficients, product form, partial fractions
@@ -136,6 +138,8 @@ CASES = [
      ["equioscillation n = 2", "Delta monotone, epsilon odd"]),
     (zolotarev, "zolotarev", "np.prod(ceven - codd[i])", "np.prod(codd[i] - ceven)",
      ["equioscillation n = 2", "Delta monotone, epsilon odd"]),
+    (zolotarev, "zolotarev", "delta = (hi - lo) / (hi + lo)", "delta = (hi - lo) / hi",
+     ["n = 1 closed form", "equioscillation n = 3"]),
     (zolotarev, "epsilon", "w * x / (x * x + s)", "w / (x * x + s)", ["equioscillation n = 3"]),
     # ---- overlap: spectral sign, D(mu), matrix-free rational
     (overlap, "dense_sign", "(Q * np.sign(w)) @ np.conj(Q.T)", "(Q * np.sign(w)) @ Q.T", ["sign^2 = 1"]),
@@ -172,6 +176,8 @@ CASES = [
     (overlap, "free_field_overlap_spectrum", "(b + sg * 1j * s) / r", "(b + sg * 1j * s)",
      ["free-field overlap spectrum 2^4"]),
     # ---- solvers: Alg. 1 recurrence, minimal residual, GMRESR, CGNE
+    (solvers, "vdot", "np.vdot(np.asarray(a).ravel(), np.asarray(b).ravel())",
+     "np.dot(np.asarray(a).ravel(), np.asarray(b).ravel())", ["Alg. 1 basis", "minimal residual = brute force"]),
     (solvers, "sumr_basis", "qt = s * qt + np.conj(g) * qn", "qt = s * qt + g * qn", ["Alg. 1 basis"]),
     (solvers, "sumr_basis", "g = -vdot(qt, u)", "g = vdot(qt, u)", ["Alg. 1 basis"]),
     (solvers, "sumr_basis", "qn = (u + g * qt) / s", "qn = (u - g * qt) / s", ["Alg. 1 basis"]),
@@ -204,6 +210,8 @@ CASES = [
     (deflation, "sumr_ls_start", "np.linalg.solve(G, np.conj(DP.T) @ bb)", "np.linalg.solve(G, DP.T @ bb)",
      ["Galerkin and LS starts"]),
     (deflation, "sumr_ls_start", "DP = DVm @ Y", "DP = DVm", ["Galerkin and LS starts"]),
+    (deflation, "sumr_ls_start", "np.vdot(DP[:, j], bb) / np.vdot", "np.vdot(bb, DP[:, j]) / np.vdot",
+     ["Galerkin and LS starts"]),
     (deflation, "spectral_precond", "c / np.sqrt(np.asarray(mus, dtype=np.float64)) - 1.0",
      "c / np.asarray(mus, dtype=np.float64) - 1.0",
      ["spectral preconditioner c^2", "CGNE, spectral preconditioner"]),
