@@ -32,16 +32,16 @@ def c_coefficients(n, a, b):
 
 
 def r0(y, c, n):
-    """R0(y) = y prod (y^2 + c_{2l}) / prod (y^2 + c_{2l-1}) without the scale d."""
+    """R0(y) = y prod (y^2 + c_{2l}) / prod (y^2 + c_{2l-1}) without the scale d, taken as
+    y / (y^2 + c_{2n-1}) times the n-1 ratios (y^2 + c_{2l}) / (y^2 + c_{2l-1}): the two
+    products alone leave the double range for large n and b/a (n = 64 at b/a = 2600),
+    each ratio lies between 1 and c_{2l} / c_{2l-1}."""
     y = np.asarray(y, dtype=np.float64)
     y2 = y * y
-    num = np.ones_like(y)
-    den = np.ones_like(y)
+    r = y / (y2 + c[2 * n - 2])                        # c_{2n-1}
     for l in range(1, n):
-        num = num * (y2 + c[2 * l - 1])   # c_{2l}
-    for l in range(1, n + 1):
-        den = den * (y2 + c[2 * l - 2])   # c_{2l-1}
-    return y * num / den
+        r = r * (y2 + c[2 * l - 1]) / (y2 + c[2 * l - 2])   # c_{2l} / c_{2l-1}
+    return r
 
 
 def extrema(n, a, b, c=None, ngrid=20001):
@@ -77,9 +77,14 @@ def zolotarev(n, a, b):
     ceven = c[1::2]                        # c_2, ..., c_{2n-2}
     omega = np.empty(n)
     for i in range(n):
-        num = np.prod(ceven - codd[i])
-        den = np.prod(np.delete(codd, i) - codd[i])
-        omega[i] = a * d * num / den
+        # prod_l (c_{2l} - c_{2i-1}) / prod_{l != i} (c_{2l-1} - c_{2i-1}), the n-1 factors of
+        # each product paired in index order: c is increasing, so every ratio lies in
+        # (0, 1) and neither product overflows (both do for n near 50)
+        others = np.delete(codd, i)
+        ratio = 1.0
+        for num_t, den_t in zip(ceven - codd[i], others - codd[i]):
+            ratio *= num_t / den_t
+        omega[i] = a * d * ratio
     sigma = a * a * codd
     return omega, sigma, delta
 

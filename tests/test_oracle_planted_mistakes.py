@@ -127,16 +127,17 @@ CASES = [
     (zolotarev, "c_coefficients", "l * Kp / (2 * n)", "l * Kp / n", ["n = 1 closed form", "equioscillation n = 3"]),
     (zolotarev, "c_coefficients", "sn ** 2 / cn ** 2", "cn ** 2 / sn ** 2",
      ["n = 1 closed form", "equioscillation n = 3"]),
-    (zolotarev, "r0", "num = num * (y2 + c[2 * l - 1])", "num = num * (y2 + c[2 * l - 2])",
-     ["equioscillation n = 3"]),
+    (zolotarev, "r0", "r = r * (y2 + c[2 * l - 1]) / (y2 + c[2 * l - 2])",
+     "r = r * (y2 + c[2 * l - 2]) / (y2 + c[2 * l - 2])", ["equioscillation n = 3"]),
+    (zolotarev, "r0", "r = y / (y2 + c[2 * n - 2])", "r = y / (y2 + c[2 * n - 3])", ["equioscillation n = 3"]),
     (zolotarev, "zolotarev", "d = 2.0 / (lo + hi)", "d = 1.0 / hi", ["n = 1 closed form", "equioscillation n = 3"]),
-    (zolotarev, "zolotarev", "omega[i] = a * d * num / den", "omega[i] = d * num / den",
+    (zolotarev, "zolotarev", "omega[i] = a * d * ratio", "omega[i] = d * ratio",
      ["n = 1 closed form", "equioscillation n = 3"]),
     (zolotarev, "zolotarev", "sigma = a * a * codd", "sigma = a * codd",
      ["n = 1 closed form", "equioscillation n = 3"]),
-    (zolotarev, "zolotarev", "np.delete(codd, i) - codd[i]", "codd[i] - np.delete(codd, i)",
+    (zolotarev, "zolotarev", "others - codd[i]", "codd[i] - others",
      ["equioscillation n = 2", "Delta monotone, epsilon odd"]),
-    (zolotarev, "zolotarev", "np.prod(ceven - codd[i])", "np.prod(codd[i] - ceven)",
+    (zolotarev, "zolotarev", "zip(ceven - codd[i]", "zip(codd[i] - ceven",
      ["equioscillation n = 2", "Delta monotone, epsilon odd"]),
     (zolotarev, "zolotarev", "delta = (hi - lo) / (hi + lo)", "delta = (hi - lo) / hi",
      ["n = 1 closed form", "equioscillation n = 3"]),

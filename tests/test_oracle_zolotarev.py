@@ -97,3 +97,16 @@ def test_elliptic_values_against_mpmath():
         sn = mp.ellipfun("sn", l * Kp / (2 * n), m=m1)
         cn = mp.ellipfun("cn", l * Kp / (2 * n), m=m1)
         assert abs(float(sn ** 2 / cn ** 2) - c[l - 1]) <= 1e-12 * c[l - 1]
+
+
+@pytest.mark.parametrize("n,a,b", [(48, 0.002, 2.6), (64, 0.001, 2.6), (64, 0.3, 2.6)])
+def test_large_order_stays_finite_and_attains_delta(n, a, b):
+    """Up to the library's 64 poles and b/a = 2600: every omega_i and sigma_i finite and
+    positive, sigma ascending, and the sampled max |1 - epsilon| on [a, b] equals Delta (the
+    bound holds and is attained) to the rounding of the partial-fraction sum in double."""
+    om, sg, delta = zo.zolotarev(n, a, b)
+    assert np.all(np.isfinite(om)) and np.all(np.isfinite(sg)) and np.isfinite(delta)
+    assert np.all(om > 0) and np.all(sg > 0) and np.all(np.diff(sg) > 0)
+    xs = np.exp(np.linspace(np.log(a), np.log(b), 400001))
+    err = np.max(np.abs(zo.epsilon(xs, om, sg) - 1.0))
+    assert abs(err - delta) <= 1e-3 * delta + 2e-14, (err, delta)
