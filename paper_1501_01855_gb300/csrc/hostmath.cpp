@@ -54,12 +54,15 @@ void ellip_sncn(double u, double m, double* sn, double* cn) {
 }
 
 // ------------------------------------------------------------------ Zolotarev
+// R0(y) = y prod_{l<n} (y^2 + c_{2l}) / prod_{l<=n} (y^2 + c_{2l-1}), evaluated as
+// y / (y^2 + c_{2n-1}) times the n-1 ratios (y^2 + c_{2l}) / (y^2 + c_{2l-1}): the two
+// products on their own leave the double range (n factors up to (b/a)^2 each, e.g.
+// n = 64 at b/a = 2600), the ratios stay between 1 and c_{2l} / c_{2l-1}.
 static double r0(double y, const std::vector<double>& c, int n) {
   const double y2 = y * y;
-  double num = 1.0, den = 1.0;
-  for (int l = 1; l < n; ++l) num *= (y2 + c[2 * l - 1]);
-  for (int l = 1; l <= n; ++l) den *= (y2 + c[2 * l - 2]);
-  return y * num / den;
+  double r = y / (y2 + c[2 * n - 2]);
+  for (int l = 1; l < n; ++l) r *= (y2 + c[2 * l - 1]) / (y2 + c[2 * l - 2]);
+  return r;
 }
 
 int zolotarev_coeffs(int n, double a, double b, double* omega, double* sigma, double* delta) {
@@ -97,13 +100,17 @@ int zolotarev_coeffs(int n, double a, double b, double* omega, double* sigma, do
   }
   const double d = 2.0 / (lo + hi);
   *delta = (hi - lo) / (hi + lo);
+  // omega_i = a d prod_{l<n} (c_{2l} - c_{2i-1}) / prod_{l!=i} (c_{2l-1} - c_{2i-1}) with the
+  // n-1 factors of numerator and denominator paired in index order: c is increasing, so
+  // every ratio lies in (0, 1) and neither product can overflow (they do for n near 50)
   for (int i = 0; i < n; ++i) {
     const double ci = c[2 * i];
-    double num = 1.0, den = 1.0;
-    for (int l = 1; l < n; ++l) num *= (c[2 * l - 1] - ci);
-    for (int l = 0; l < n; ++l)
-      if (l != i) den *= (c[2 * l] - ci);
-    omega[i] = a * d * num / den;
+    double ratio = 1.0;
+    for (int l = 1; l < n; ++l) {
+      const int j = (l - 1 < i) ? l - 1 : l;   // the l-th index of {0 .. n-1} without i
+      ratio *= (c[2 * l - 1] - ci) / (c[2 * j] - ci);
+    }
+    omega[i] = a * d * ratio;
     sigma[i] = a * a * ci;
   }
   return 0;

@@ -43,6 +43,21 @@ def test_library_zolotarev_matches_oracle(n, a, b):
     assert abs(de - d2) <= 1e-6 * d2 + 5e-15
 
 
+@pytest.mark.parametrize("n,a,b", [(48, 0.002, 2.6), (64, 0.001, 2.6), (64, 0.3, 2.6)])
+def test_library_zolotarev_large_order(n, a, b):
+    """Up to 64 poles and b/a = 2600 the library's coefficients stay finite and positive
+    (plain products of n factors would leave the double range), agree with the oracle's,
+    and their sampled error on [a, b] attains the Delta the library reports."""
+    binding = _lib()
+    om, sg, de = binding.ovl_zolotarev_coeffs(n, a, b)
+    assert np.all(np.isfinite(om)) and np.all(om > 0) and np.all(np.diff(sg) > 0)
+    o2, s2, _ = zo.zolotarev(n, a, b)
+    assert np.allclose(om, o2, rtol=1e-10, atol=0) and np.allclose(sg, s2, rtol=1e-10, atol=0)
+    xs = np.exp(np.linspace(np.log(a), np.log(b), 400001))
+    err = np.max(np.abs(zo.epsilon(xs, om, sg) - 1.0))
+    assert abs(err - de) <= 1e-3 * de + 2e-14, (err, de)
+
+
 def test_library_rejects_bad_arguments():
     binding = _lib()
     with pytest.raises(binding.OvlError):
