@@ -4,7 +4,7 @@
 
 with |epsilon| oscillating between 1-Delta and 1+Delta on [a, b]. The paper
 does not print the coefficients; it refers to Jacobi elliptic functions. Written
-out here in the product form: for y = x/a in [1, b/a], k' = sqrt(1 - (a/b)^2),
+out here in the product form: for y = x/a in [1, b/a], k = a/b, k' = sqrt(1 - k^2),
 K' = K(k'),
 
   c_l = sn^2(l K'/(2n); k') / cn^2(l K'/(2n); k'),   l = 1 .. 2n-1
@@ -23,12 +23,23 @@ from scipy import special, optimize
 
 
 def c_coefficients(n, a, b):
-    """c_1 .. c_{2n-1} (index 0 holds c_1)."""
-    m1 = 1.0 - (a / b) ** 2               # parameter m = k'^2 for scipy
-    Kp = special.ellipk(m1)
+    """c_1 .. c_{2n-1} (index 0 holds c_1).
+
+    K' = K(k') from the complementary parameter k^2 = (a/b)^2 (scipy's ellipkm1), since
+    1 - (a/b)^2 formed in double loses it at large b/a; past K'/2, where cn is small,
+    sn/cn at u = K' - delta is cn(delta) / (k sn(delta)) with delta = (2n - l) K'/(2n)
+    (the quarter-period shift sn(u + K') = cd(u), cn(u + K') = -k sd(u))."""
+    k = a / b
+    m1 = 1.0 - k * k                      # parameter m = k'^2 for scipy
+    Kp = special.ellipkm1(k * k)          # K(1 - k^2) = K(k')
     l = np.arange(1, 2 * n)
-    sn, cn, dn, ph = special.ellipj(l * Kp / (2 * n), m1)
-    return sn ** 2 / cn ** 2
+    c = np.empty(2 * n - 1)
+    near = l <= n
+    sn, cn, dn, ph = special.ellipj(l[near] * Kp / (2 * n), m1)
+    c[near] = sn ** 2 / cn ** 2
+    sn, cn, dn, ph = special.ellipj((2 * n - l[~near]) * Kp / (2 * n), m1)
+    c[~near] = (cn / (k * sn)) ** 2
+    return c
 
 
 def r0(y, c, n):

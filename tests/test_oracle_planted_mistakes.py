@@ -122,9 +122,14 @@ CASES = [
     (wilson, "free_field_K_abs_spectrum", "lam = 2 * kap * np.sqrt(b ** 2 + s2)", "lam = kap * np.sqrt(b ** 2 + s2)",
      ["free-field |lambda(K)| 2^4"]),
     # ---- zolotarev: elliptic coefficients, product form, partial fractions
-    (zolotarev, "c_coefficients", "m1 = 1.0 - (a / b) ** 2", "m1 = (a / b) ** 2",
+    (zolotarev, "c_coefficients", "m1 = 1.0 - k * k", "m1 = k * k",
      ["n = 1 closed form", "equioscillation n = 3"]),
-    (zolotarev, "c_coefficients", "l * Kp / (2 * n)", "l * Kp / n", ["n = 1 closed form", "equioscillation n = 3"]),
+    (zolotarev, "c_coefficients", "l[near] * Kp / (2 * n)", "l[near] * Kp / n",
+     ["n = 1 closed form", "equioscillation n = 3"]),
+    (zolotarev, "c_coefficients", "special.ellipkm1(k * k)", "special.ellipkm1(1.0 - k * k)",
+     ["n = 1 closed form", "equioscillation n = 3"]),
+    (zolotarev, "c_coefficients", "(cn / (k * sn)) ** 2", "(cn / sn) ** 2", ["equioscillation n = 3"]),
+    (zolotarev, "c_coefficients", "(2 * n - l[~near])", "(2 * n - l[~near] + 1)", ["equioscillation n = 3"]),
     (zolotarev, "c_coefficients", "sn ** 2 / cn ** 2", "cn ** 2 / sn ** 2",
      ["n = 1 closed form", "equioscillation n = 3"]),
     (zolotarev, "r0", "r = r * (y2 + c[2 * l - 1]) / (y2 + c[2 * l - 2])",
