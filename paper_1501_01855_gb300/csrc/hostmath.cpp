@@ -18,11 +18,13 @@
 namespace ovl {
 
 // ------------------------------------------------------------------ elliptic
-static void agm_phi(double u, double m, double* phi_out, double* K_out) {
+// The complement mc = 1 - m is passed on its own: for m within rounding of 1 (the Zolotarev
+// modulus k' = sqrt(1 - (a/b)^2) at large b/a) 1 - m in double would lose it entirely.
+static void agm_phi(double u, double m, double mc, double* phi_out, double* K_out) {
   // A&S 16.4: a0 = 1, b0 = sqrt(1-m), c0 = sqrt(m)
   double a[64], c[64];
   a[0] = 1.0;
-  double b = std::sqrt(1.0 - m);
+  double b = std::sqrt(mc);
   c[0] = std::sqrt(m);
   int N = 0;
   while (N < 60) {
@@ -40,15 +42,15 @@ static void agm_phi(double u, double m, double* phi_out, double* K_out) {
   if (K_out) *K_out = M_PI / (2.0 * a[N]);
 }
 
-double ellip_K(double m) {
+double ellip_K(double m, double mc) {
   double K;
-  agm_phi(0.0, m, nullptr, &K);
+  agm_phi(0.0, m, mc, nullptr, &K);
   return K;
 }
 
-void ellip_sncn(double u, double m, double* sn, double* cn) {
+void ellip_sncn(double u, double m, double mc, double* sn, double* cn) {
   double phi;
-  agm_phi(u, m, &phi, nullptr);
+  agm_phi(u, m, mc, &phi, nullptr);
   *sn = std::sin(phi);
   *cn = std::cos(phi);
 }
@@ -67,13 +69,25 @@ static double r0(double y, const std::vector<double>& c, int n) {
 
 int zolotarev_coeffs(int n, double a, double b, double* omega, double* sigma, double* delta) {
   if (n < 1 || !(a > 0) || !(b > a)) return -1;
-  const double m1 = 1.0 - (a / b) * (a / b);
-  const double Kp = ellip_K(m1);
+  const double k = a / b;          // the complementary modulus of k'
+  const double mc = k * k;         // 1 - k'^2, exact up to one rounding
+  if (!(mc > 0)) return -1;
+  const double m1 = 1.0 - mc;
+  const double Kp = ellip_K(m1, mc);
   std::vector<double> c(2 * n - 1);
   for (int l = 1; l <= 2 * n - 1; ++l) {
     double sn, cn;
-    ellip_sncn(l * Kp / (2.0 * n), m1, &sn, &cn);
-    c[l - 1] = (sn * sn) / (cn * cn);
+    if (l <= n) {
+      ellip_sncn(l * Kp / (2.0 * n), m1, mc, &sn, &cn);
+      c[l - 1] = (sn * sn) / (cn * cn);
+    } else {
+      // past K'/2 cn(u) is small and cos(am u) loses it: with delta = K' - u,
+      // sn(K' - delta) / cn(K' - delta) = cn(delta) / (k sn(delta)) (the quarter-period shift
+      // sn(u + K') = cd(u), cn(u + K') = -k sd(u))
+      ellip_sncn((2 * n - l) * Kp / (2.0 * n), m1, mc, &sn, &cn);
+      const double t = cn / (k * sn);
+      c[l - 1] = t * t;
+    }
   }
   // extrema of R0 over y in [1, b/a]: endpoints plus golden-section refinement of
   // every interior extremum of a dense logarithmic grid

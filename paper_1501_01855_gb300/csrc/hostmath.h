@@ -5,8 +5,9 @@
 
 namespace ovl {
 
-double ellip_K(double m);
-void ellip_sncn(double u, double m, double* sn, double* cn);
+// complete integral K(m) and sn, cn at parameter m; mc = 1 - m given separately
+double ellip_K(double m, double mc);
+void ellip_sncn(double u, double m, double mc, double* sn, double* cn);
 // omega[n], sigma[n] (ascending sigma) and the maximum error delta; 0 on success
 int zolotarev_coeffs(int n, double a, double b, double* omega, double* sigma, double* delta);
 // max over a <= x <= b of x / (x^2 + sigma)

@@ -58,6 +58,28 @@ def test_library_zolotarev_large_order(n, a, b):
     assert abs(err - de) <= 1e-3 * de + 2e-14, (err, de)
 
 
+@pytest.mark.parametrize("n,a,b,rtol", [(20, 0.2, 2.6, 1e-14), (64, 0.001, 2.6, 1e-12), (64, 1e-8, 2.6, 1e-7)])
+def test_library_zolotarev_sigma_against_mpmath(n, a, b, rtol):
+    """sigma_i = a^2 c_{2i-1} from the library's own AGM against 40-digit mpmath, from the
+    benchmark's b/a = 13 to b/a = 2.6e8, where 1 - (a/b)^2 rounds to 1 in double; the Delta it
+    reports is attained by its own coefficients."""
+    mp = pytest.importorskip("mpmath")
+    mp.mp.dps = 40
+    binding = _lib()
+    om, sg, de = binding.ovl_zolotarev_coeffs(n, a, b)
+    A, Bv = mp.mpf(a), mp.mpf(b)
+    m1 = 1 - (A / Bv) ** 2
+    Kp = mp.ellipk(m1)
+    for i in range(n):
+        u = (2 * i + 1) * Kp / (2 * n)
+        ref = float(A * A * mp.ellipfun("sn", u, m=m1) ** 2 / mp.ellipfun("cn", u, m=m1) ** 2)
+        assert abs(sg[i] - ref) <= rtol * ref, (i, sg[i], ref)
+    assert np.all(np.isfinite(om)) and np.all(om > 0)
+    xs = np.exp(np.linspace(np.log(a), np.log(b), 400001))
+    err = np.max(np.abs(zo.epsilon(xs, om, sg) - 1.0))
+    assert abs(err - de) <= 1e-3 * de + 2e-14, (err, de)
+
+
 def test_library_rejects_bad_arguments():
     binding = _lib()
     with pytest.raises(binding.OvlError):
