@@ -126,8 +126,9 @@ int zolotarev_coeffs(int n, double a, double b, double* omega, double* sigma, do
     }
     omega[i] = a * d * ratio;
     sigma[i] = a * a * ci;
+    if (!std::isfinite(omega[i]) || !std::isfinite(sigma[i])) return -1;
   }
-  return 0;
+  return std::isfinite(*delta) ? 0 : -1;
 }
 
 double pole_gbound(double sigma, double a, double b) {
