@@ -183,8 +183,10 @@ ovl_status ovl_zolotarev_coeffs(int n, double a, double b, double* omega, double
  * the host between kernel launches, exported so that they can be checked on their own.
  * Complex matrices are n x n, row-major, interleaved (re, im) doubles; inputs are read
  * only, outputs are caller buffers of the same size; 1 <= n <= 4096, else OVL_EINVAL.
- *   ovl_host_eigh             Hermitian eigendecomposition by cyclic complex Jacobi
- *                             rotations: w ascending, z the orthonormal eigenvectors as
+ *   ovl_host_eigh             Hermitian eigendecomposition (Householder reduction to a
+ *                             real tridiagonal, implicit QR steps with Wilkinson shifts;
+ *                             cyclic Jacobi rotations should those not converge):
+ *                             w ascending, z the orthonormal eigenvectors as
  *                             columns (a = z diag(w) z^dag). The diagonalisation of
  *                             L^-1 M U^-1 in the Ritz step (Alg. 6), of the projected
  *                             gamma5 D in the least-squares start (Sec. 4) and of the

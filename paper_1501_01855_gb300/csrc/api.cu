@@ -425,7 +425,7 @@ extern "C" ovl_status ovl_host_eigh(int n, const double* a, double* w, double* z
   for (int i = 0; i < n; ++i)
     for (int j = 0; j < n; ++j)
       if (!std::isfinite(A[(size_t)i * n + j].real()) || !std::isfinite(A[(size_t)i * n + j].imag())) return OVL_EINVAL;
-  eigh_jacobi(n, A.data(), w, reinterpret_cast<cd*>(z));
+  eigh_herm(n, A.data(), w, reinterpret_cast<cd*>(z));
   return OVL_OK;
 }
 

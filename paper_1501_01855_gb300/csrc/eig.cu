@@ -73,7 +73,7 @@ ovl_status ritz_step(ovl_ctx* c, EigState* e, int keep, bool restart) {
     } else {
       std::vector<cd> Ec = E, Z((size_t)k * k);
       std::vector<double> w(k);
-      eigh_jacobi(k, Ec.data(), w.data(), Z.data());
+      eigh_herm(k, Ec.data(), w.data(), Z.data());
       const double thr = 1e-10 * std::max(w[k - 1], 1e-300);
       std::vector<int> keepc;
       for (int i = 0; i < k; ++i)
@@ -101,7 +101,7 @@ ovl_status ritz_step(ovl_ctx* c, EigState* e, int keep, bool restart) {
     }
   std::vector<double> lam(r);
   std::vector<cd> T0 = T;
-  eigh_jacobi(r, T.data(), lam.data(), Y.data());
+  eigh_herm(r, T.data(), lam.data(), Y.data());
   keep = std::min(keep, r);
   // Locally optimal restart (the eigCG restart that the accumulation of Sec. 5 adapts):
   // at a basis restart keep the lowest Ritz vectors of the whole basis and those of the
@@ -119,7 +119,7 @@ ovl_status ritz_step(ovl_ctx* c, EigState* e, int keep, bool restart) {
     for (int i = 0; i < k1; ++i)
       for (int j = 0; j < k1; ++j) T1[(size_t)i * k1 + j] = T0[(size_t)i * k + j];
     std::vector<double> lam1(k1);
-    eigh_jacobi(k1, T1.data(), lam1.data(), Y1.data());
+    eigh_herm(k1, T1.data(), lam1.data(), Y1.data());
     // Z = [Y[:, :keep], (Y1[:, :keep]; 0)], orthonormalised (modified Gram-Schmidt)
     std::vector<std::vector<cd>> Z;
     for (int j = 0; j < 2 * keep; ++j) {
@@ -161,7 +161,7 @@ ovl_status ritz_step(ovl_ctx* c, EigState* e, int keep, bool restart) {
         T2[(size_t)b2 * q + a2] = std::conj(h);
       }
     std::vector<double> lam2(q);
-    eigh_jacobi(q, T2.data(), lam2.data(), Y2.data());
+    eigh_herm(q, T2.data(), lam2.data(), Y2.data());
     nout = q;
     Yc.assign((size_t)r * nout, 0.0);
     for (int i = 0; i < k; ++i)

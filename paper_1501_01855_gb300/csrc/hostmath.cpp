@@ -6,13 +6,15 @@
 //    product form d y prod(y^2+c_{2l}) / prod(y^2+c_{2l-1}) in y = x/a, d from
 //    equioscillation, partial fractions in x.
 //  * Small dense complex linear algebra for the Ritz step and the deflation
-//    projections: Cholesky, triangular inverse, cyclic Jacobi Hermitian
-//    eigensolver, LU solve; Sturm bisection for tridiagonal extremes (Lanczos).
+//    projections: Cholesky, triangular inverse, Hermitian eigensolver (Householder
+//    tridiagonalisation and implicit QR; cyclic Jacobi as its fallback), LU solve;
+//    Sturm bisection for tridiagonal extremes (Lanczos).
 #include "hostmath.h"
 
 #include <algorithm>
 #include <cmath>
 #include <complex>
+#include <limits>
 #include <vector>
 
 namespace ovl {
@@ -230,6 +232,138 @@ void eigh_jacobi(int n, cd* A /* Hermitian, destroyed */, double* w, cd* Z /* co
     for (int r = 0; r < n; ++r) Zs[r * n + j] = Z[r * n + idx[j]];
   }
   for (int i = 0; i < n * n; ++i) Z[i] = Zs[i];
+}
+
+// Real symmetric tridiagonal eigenproblem by implicit symmetric QR steps with Wilkinson
+// shifts (Golub & Van Loan, Matrix Computations, 8.3): on the last unreduced block
+// [p, q] a rotation of rows/columns (p, p+1) made from (a_p - mu, b_p) starts a bulge
+// that further rotations chase to the bottom; off-diagonals below eps (|a_i| + |a_i+1|)
+// are set to zero. a: diagonal, b: b[i] couples i and i+1. Every rotation is applied to
+// the columns of Z (n x n row-major). false if some block has not converged after
+// 30 n steps in all.
+static bool tridiag_qr(int n, double* a, double* b, cd* Z) {
+  const double eps = std::numeric_limits<double>::epsilon();
+  int q = n - 1, steps = 0;
+  while (q > 0) {
+    if (std::fabs(b[q - 1]) <= eps * (std::fabs(a[q - 1]) + std::fabs(a[q]))) {
+      b[q - 1] = 0.0;
+      --q;
+      continue;
+    }
+    int p = q - 1;
+    while (p > 0 && std::fabs(b[p - 1]) > eps * (std::fabs(a[p - 1]) + std::fabs(a[p]))) --p;
+    if (p > 0) b[p - 1] = 0.0;
+    if (++steps > 30 * n) return false;
+    // Wilkinson shift: the eigenvalue of the trailing 2 x 2 block nearer to a_q
+    const double d = 0.5 * (a[q - 1] - a[q]), bq = b[q - 1];
+    const double mu = a[q] - bq * bq / (d + std::copysign(std::hypot(d, bq), d));
+    double x = a[p] - mu, z = b[p];
+    for (int k = p; k < q; ++k) {
+      // P = [[c, -s], [s, c]] on coordinates (k, k+1), P^T (x, z) = (r, 0)
+      const double r = std::hypot(x, z);
+      const double c = r > 0.0 ? x / r : 1.0, s = r > 0.0 ? z / r : 0.0;
+      if (k > p) b[k - 1] = r;                                  // the bulge is gone
+      const double ak = a[k], ak1 = a[k + 1], bk = b[k];
+      a[k] = c * c * ak + 2.0 * c * s * bk + s * s * ak1;
+      a[k + 1] = s * s * ak - 2.0 * c * s * bk + c * c * ak1;
+      b[k] = c * s * (ak1 - ak) + (c * c - s * s) * bk;
+      double bulge = 0.0;
+      if (k + 1 < q) {
+        bulge = s * b[k + 1];                                   // new entry (k, k+2)
+        b[k + 1] = c * b[k + 1];
+      }
+      for (int i = 0; i < n; ++i) {
+        const cd zk = Z[(size_t)i * n + k], zk1 = Z[(size_t)i * n + k + 1];
+        Z[(size_t)i * n + k] = c * zk + s * zk1;
+        Z[(size_t)i * n + k + 1] = -s * zk + c * zk1;
+      }
+      x = b[k];
+      z = bulge;
+    }
+  }
+  return true;
+}
+
+// Hermitian eigendecomposition: Householder reduction to tridiagonal form (Golub & Van
+// Loan 8.3.1; reflections I - tau v v^dag chosen so that no cancellation occurs in v_0,
+// each applied as the rank-2 update A - v w^dag - w v^dag and accumulated in Q), a diagonal
+// phase D that makes the off-diagonal real and non-negative (T = D T' D^dag), then
+// tridiag_qr on T' with the columns of Q D. Cyclic Jacobi is the fallback should the QR
+// iteration not converge. w ascending, Z the eigenvectors as columns.
+void eigh_herm(int n, cd* A /* Hermitian, destroyed */, double* w, cd* Z /* columns */) {
+  if (n <= 0) return;
+  std::vector<cd> Q((size_t)n * n, 0.0), v(n), pv(n);
+  for (int i = 0; i < n; ++i) Q[(size_t)i * n + i] = 1.0;
+  const std::vector<cd> A0(A, A + (size_t)n * n);
+  for (int k = 0; k + 2 < n; ++k) {
+    const int L = n - k - 1;   // reflect x = A[k+1 .., k]
+    double sig = 0.0;
+    for (int i = 1; i < L; ++i) sig += std::norm(A[(size_t)(k + 1 + i) * n + k]);
+    if (sig == 0.0) continue;
+    const cd x0 = A[(size_t)(k + 1) * n + k];
+    const double ax0 = std::abs(x0), nx = std::sqrt(ax0 * ax0 + sig);
+    const cd ph = ax0 > 0.0 ? x0 / ax0 : cd(1.0);
+    const cd beta = -ph * nx;                       // H x = beta e_1
+    for (int i = 0; i < L; ++i) v[i] = A[(size_t)(k + 1 + i) * n + k];
+    v[0] = x0 - beta;                               // = ph (|x0| + ||x||)
+    double vv = 0.0;
+    for (int i = 0; i < L; ++i) vv += std::norm(v[i]);
+    const double tau = 2.0 / vv;
+    // p = tau A22 v, K = tau/2 v^dag p (real), w = p - K v, A22 -= v w^dag + w v^dag
+    for (int i = 0; i < L; ++i) {
+      cd t = 0.0;
+      const cd* row = A + (size_t)(k + 1 + i) * n + (k + 1);
+      for (int j = 0; j < L; ++j) t += row[j] * v[j];
+      pv[i] = tau * t;
+    }
+    cd K = 0.0;
+    for (int i = 0; i < L; ++i) K += std::conj(v[i]) * pv[i];
+    K *= 0.5 * tau;
+    for (int i = 0; i < L; ++i) pv[i] -= K.real() * v[i];
+    for (int i = 0; i < L; ++i) {
+      cd* row = A + (size_t)(k + 1 + i) * n + (k + 1);
+      for (int j = 0; j < L; ++j) row[j] -= v[i] * std::conj(pv[j]) + pv[i] * std::conj(v[j]);
+    }
+    A[(size_t)(k + 1) * n + k] = beta;
+    A[(size_t)k * n + k + 1] = std::conj(beta);
+    for (int i = 1; i < L; ++i) {
+      A[(size_t)(k + 1 + i) * n + k] = 0.0;
+      A[(size_t)k * n + k + 1 + i] = 0.0;
+    }
+    // Q <- Q H = Q - tau (Q v) v^dag on columns k+1 ..
+    for (int r = 0; r < n; ++r) {
+      cd* row = Q.data() + (size_t)r * n + (k + 1);
+      cd t = 0.0;
+      for (int j = 0; j < L; ++j) t += row[j] * v[j];
+      t *= tau;
+      for (int j = 0; j < L; ++j) row[j] -= t * std::conj(v[j]);
+    }
+  }
+  std::vector<double> a(n), b(std::max(1, n - 1), 0.0);
+  std::vector<cd> ph(n, 1.0);
+  for (int i = 0; i < n; ++i) a[i] = A[(size_t)i * n + i].real();
+  for (int i = 0; i + 1 < n; ++i) {
+    const cd e = A[(size_t)(i + 1) * n + i];
+    const double ae = std::abs(e);
+    b[i] = ae;
+    ph[i + 1] = ae > 0.0 ? ph[i] * (e / ae) : ph[i];
+  }
+  for (int r = 0; r < n; ++r)
+    for (int j = 0; j < n; ++j) Z[(size_t)r * n + j] = Q[(size_t)r * n + j] * ph[j];
+  if (!tridiag_qr(n, a.data(), b.data(), Z)) {
+    std::vector<cd> Ac = A0;
+    eigh_jacobi(n, Ac.data(), w, Z);
+    return;
+  }
+  std::vector<int> idx(n);
+  for (int i = 0; i < n; ++i) idx[i] = i;
+  std::stable_sort(idx.begin(), idx.end(), [&](int x, int y) { return a[x] < a[y]; });
+  std::vector<cd> Zs((size_t)n * n);
+  for (int j = 0; j < n; ++j) {
+    w[j] = a[idx[j]];
+    for (int r = 0; r < n; ++r) Zs[(size_t)r * n + j] = Z[(size_t)r * n + idx[j]];
+  }
+  std::copy(Zs.begin(), Zs.end(), Z);
 }
 
 int lu_solve(int n, cd* A, cd* B, int nb) {

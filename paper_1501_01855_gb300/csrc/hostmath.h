@@ -16,6 +16,9 @@ double pole_gbound(double sigma, double a, double b);
 int cholesky_lower(int n, std::complex<double>* A);
 void lower_inverse(int n, const std::complex<double>* L, std::complex<double>* Li);
 void eigh_jacobi(int n, std::complex<double>* A, double* w, std::complex<double>* Z);
+// Hermitian eigendecomposition (Householder tridiagonalisation + implicit QR; Jacobi as
+// the fallback): w ascending, Z eigenvectors as columns, A destroyed
+void eigh_herm(int n, std::complex<double>* A, double* w, std::complex<double>* Z);
 int lu_solve(int n, std::complex<double>* A, std::complex<double>* B, int nb);
 void tridiag_extremes(int n, const double* d, const double* e, double* lmin, double* lmax);
 

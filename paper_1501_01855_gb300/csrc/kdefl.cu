@@ -67,7 +67,7 @@ ovl_status kd_rayleigh_ritz(ovl_ctx* c, Field& X, Field& KX, Field& Xn, Field& K
       T[(size_t)j * m + i] = std::conj(a);
     }
   std::vector<double> w(m);
-  eigh_jacobi(m, T.data(), w.data(), Z.data());
+  eigh_herm(m, T.data(), w.data(), Z.data());
   std::vector<int> ord(m);
   std::iota(ord.begin(), ord.end(), 0);
   std::stable_sort(ord.begin(), ord.end(), [&](int x, int y) { return std::fabs(w[x]) < std::fabs(w[y]); });

@@ -239,7 +239,7 @@ ovl_status defl_start(ovl_ctx* c, ovl_defl* d, const Field& b, int boff, int nsy
         Hs[(size_t)i * n + k] = h;
         Hs[(size_t)k * n + i] = std::conj(h);
       }
-    eigh_jacobi(n, Hs.data(), w.data(), Y.data());
+    eigh_herm(n, Hs.data(), w.data(), Y.data());
     std::vector<cd> M;
     dd_matrix(d, mu, M);
     // rotated normal equations: (Y^dag M Y) alpha = Y^dag (D psi)^dag b

@@ -152,6 +152,38 @@ def test_host_eigh_degenerate_graded_and_diagonal():
     assert np.allclose(np.abs(Z), np.eye(4)[:, np.argsort(d)])
 
 
+def test_host_eigh_hard_cases():
+    """Clusters of equal eigenvalues, a spectrum over 14 decades, an already tridiagonal
+    complex matrix, a reducible one, Wilkinson's W (close pairs), rank one and zero; and the
+    192 x 192 size of a Ritz step's basis in the deflated 24^3 x 48 solves."""
+    binding = _lib()
+    rng = np.random.default_rng(8)
+
+    def check(A):
+        n = A.shape[0]
+        w, Z = binding.ovl_host_eigh(A)
+        scale = max(1.0, np.abs(np.linalg.eigvalsh(A)).max())
+        assert np.all(np.diff(w) >= 0)
+        assert np.allclose(w, np.linalg.eigvalsh(A), rtol=0, atol=1e-13 * scale)
+        assert np.abs(Z.conj().T @ Z - np.eye(n)).max() <= 1e-13
+        assert np.abs(A @ Z - Z * w).max() <= 1e-13 * scale
+
+    Q, _ = np.linalg.qr(rng.normal(size=(100, 100)) + 1j * rng.normal(size=(100, 100)))
+    check((Q * np.repeat([1.0, 2.0, 3.0, 4.0], 25)) @ Q.conj().T)
+    check((Q * np.logspace(-12, 2, 100)) @ Q.conj().T)
+    T = np.diag(rng.normal(size=50)) + np.diag(rng.normal(size=49) + 1j * rng.normal(size=49), 1)
+    T = T + np.triu(T, 1).conj().T
+    check(T)
+    T[20, 21] = T[21, 20] = 0
+    check(T)
+    W = np.diag(np.abs(np.arange(-15.0, 16.0))) + np.eye(31, k=1) + np.eye(31, k=-1)
+    check(W.astype(complex))
+    check(np.ones((40, 40), dtype=complex))
+    check(np.zeros((7, 7), dtype=complex))
+    Q, _ = np.linalg.qr(rng.normal(size=(192, 192)) + 1j * rng.normal(size=(192, 192)))
+    check((Q * np.sort(rng.uniform(1e-4, 3.0, 192))) @ Q.conj().T)
+
+
 def test_host_cholesky_and_lower_inverse():
     binding = _lib()
     rng = np.random.default_rng(4)
