@@ -226,36 +226,56 @@ ovl_status defl_start(ovl_ctx* c, ovl_defl* d, const Field& b, int boff, int nsy
   OVL_TRY(gram_host(c, d->v, 0, n, b, boff, nsys, 0, VB));
   OVL_TRY(gram_host(c, d->w, 0, n, b, boff, nsys, 0, WB));
   coefs.assign((size_t)n * nsys, 0.0);
+  // the rotation Y and the rotated normal matrix depend on the mass only: built once per
+  // distinct mass of the batch (sources x masses share them)
+  struct PerMass {
+    double mu;
+    std::vector<cd> Y, G;
+  };
+  std::vector<PerMass> per_mass;
   for (int j = 0; j < nsys; ++j) {
     const double mu = mus[j];
     const double a = 0.5 * (1.0 - mu), bb = 0.5 * (1.0 + mu);
-    // Hs = (psi_i, gamma5 D psi_j) = b (psi, g5 psi) + a (psi, g5 w)
-    std::vector<cd> Hs((size_t)n * n), Y((size_t)n * n);
-    std::vector<double> w(n);
-    for (size_t k = 0; k < Hs.size(); ++k) Hs[k] = bb * d->G5VV[k] + a * d->G5VW[k];
-    for (int i = 0; i < n; ++i)
-      for (int k = i + 1; k < n; ++k) {
-        const cd h = 0.5 * (Hs[(size_t)i * n + k] + std::conj(Hs[(size_t)k * n + i]));
-        Hs[(size_t)i * n + k] = h;
-        Hs[(size_t)k * n + i] = std::conj(h);
-      }
-    eigh_herm(n, Hs.data(), w.data(), Y.data());
-    std::vector<cd> M;
-    dd_matrix(d, mu, M);
-    // rotated normal equations: (Y^dag M Y) alpha = Y^dag (D psi)^dag b
-    std::vector<cd> MY((size_t)n * n), G((size_t)n * n), rhs(n);
-    for (int i = 0; i < n; ++i)
-      for (int k = 0; k < n; ++k) {
-        cd s = 0;
-        for (int l = 0; l < n; ++l) s += M[(size_t)i * n + l] * Y[(size_t)l * n + k];
-        MY[(size_t)i * n + k] = s;
-      }
-    for (int i = 0; i < n; ++i)
-      for (int k = 0; k < n; ++k) {
-        cd s = 0;
-        for (int l = 0; l < n; ++l) s += std::conj(Y[(size_t)l * n + i]) * MY[(size_t)l * n + k];
-        G[(size_t)i * n + k] = s;
-      }
+    const PerMass* pm = nullptr;
+    for (const auto& q : per_mass)
+      if (q.mu == mu) pm = &q;
+    if (pm == nullptr) {
+      PerMass q;
+      q.mu = mu;
+      // Hs = (psi_i, gamma5 D psi_j) = b (psi, g5 psi) + a (psi, g5 w)
+      std::vector<cd> Hs((size_t)n * n);
+      std::vector<double> w(n);
+      q.Y.resize((size_t)n * n);
+      for (size_t k = 0; k < Hs.size(); ++k) Hs[k] = bb * d->G5VV[k] + a * d->G5VW[k];
+      for (int i = 0; i < n; ++i)
+        for (int k = i + 1; k < n; ++k) {
+          const cd h = 0.5 * (Hs[(size_t)i * n + k] + std::conj(Hs[(size_t)k * n + i]));
+          Hs[(size_t)i * n + k] = h;
+          Hs[(size_t)k * n + i] = std::conj(h);
+        }
+      eigh_herm(n, Hs.data(), w.data(), q.Y.data());
+      std::vector<cd> M;
+      dd_matrix(d, mu, M);
+      // rotated normal equations: (Y^dag M Y) alpha = Y^dag (D psi)^dag b
+      std::vector<cd> MY((size_t)n * n);
+      q.G.resize((size_t)n * n);
+      for (int i = 0; i < n; ++i)
+        for (int k = 0; k < n; ++k) {
+          cd s = 0;
+          for (int l = 0; l < n; ++l) s += M[(size_t)i * n + l] * q.Y[(size_t)l * n + k];
+          MY[(size_t)i * n + k] = s;
+        }
+      for (int i = 0; i < n; ++i)
+        for (int k = 0; k < n; ++k) {
+          cd s = 0;
+          for (int l = 0; l < n; ++l) s += std::conj(q.Y[(size_t)l * n + i]) * MY[(size_t)l * n + k];
+          q.G[(size_t)i * n + k] = s;
+        }
+      per_mass.push_back(std::move(q));
+      pm = &per_mass.back();
+    }
+    const std::vector<cd>& Y = pm->Y;
+    std::vector<cd> G = pm->G, rhs(n);   // lu_solve overwrites its matrix
     for (int i = 0; i < n; ++i) {
       cd s = 0;
       for (int l = 0; l < n; ++l) {
