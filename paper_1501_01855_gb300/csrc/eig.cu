@@ -142,16 +142,19 @@ ovl_status ritz_step(ovl_ctx* c, EigState* e, int keep, bool restart) {
       Z.push_back(z);
     }
     const int q = (int)Z.size();
-    // Rayleigh-Ritz on span Z: T2 = Z^dag T Z
-    std::vector<cd> T2((size_t)q * q), Y2((size_t)q * q);
+    // Rayleigh-Ritz on span Z: T2 = Z^dag T Z, with T Z formed once (k^2 q + q^2 k
+    // products instead of q^2 k^2; the same sums in the same order)
+    std::vector<cd> T2((size_t)q * q), Y2((size_t)q * q), TZ((size_t)k * q);
+    for (int b2 = 0; b2 < q; ++b2)
+      for (int i = 0; i < k; ++i) {
+        cd ti = 0;
+        for (int l = 0; l < k; ++l) ti += T0[(size_t)i * k + l] * Z[b2][l];
+        TZ[(size_t)i * q + b2] = ti;
+      }
     for (int a2 = 0; a2 < q; ++a2)
       for (int b2 = 0; b2 < q; ++b2) {
         cd sacc = 0;
-        for (int i = 0; i < k; ++i) {
-          cd ti = 0;
-          for (int l = 0; l < k; ++l) ti += T0[(size_t)i * k + l] * Z[b2][l];
-          sacc += std::conj(Z[a2][i]) * ti;
-        }
+        for (int i = 0; i < k; ++i) sacc += std::conj(Z[a2][i]) * TZ[(size_t)i * q + b2];
         T2[(size_t)a2 * q + b2] = sacc;
       }
     for (int a2 = 0; a2 < q; ++a2)
