@@ -494,6 +494,20 @@ def extras(args, ctx, dv, dout, ref_out, B, torch, stream, hbm):
         out["solve_16x16x16x32_mu0.05"] = sol
     with _section(out, "deflated_batched_16x16x16x32_mu0.02"):
         out["deflated_batched_16x16x16x32_mu0.02"] = deflated_batched(B, stream)
+    with _section(out, "host_eigh_ms"):
+        # the m x m Hermitian eigendecomposition of a Ritz step on the host (m = 192: the basis
+        # of the 24^3 x 48 deflated solves; Householder + implicit QR), through the C ABI
+        rng = np.random.default_rng(5)
+        res = {}
+        for m in (64, 192):
+            Qm, _ = np.linalg.qr(rng.normal(size=(m, m)) + 1j * rng.normal(size=(m, m)))
+            A = (Qm * np.sort(rng.uniform(1e-4, 3.0, m))) @ Qm.conj().T
+            B.ovl_host_eigh(A)
+            t0 = time.perf_counter()
+            for _ in range(3):
+                B.ovl_host_eigh(A)
+            res["m%d" % m] = (time.perf_counter() - t0) / 3 * 1e3
+        out["host_eigh_ms"] = res
     # Gram block of the Ritz step (128 x 128 spinors on 16^3 x 32): tensor cores at FP64 level
     # against the CUDA-core kernel with FP32 products
     try:
