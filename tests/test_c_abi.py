@@ -1,7 +1,8 @@
 """The boundary is a C ABI: a C99 program (gcc, -pedantic -Werror) includes
 include/overlap.h, links liboverlap.so and calls the host-only entry points; its output
 agrees with the oracle (Zolotarev coefficients, Sec. 3) and with NumPy (the host
-numerics), and a bad argument comes back as OVL_EINVAL. No GPU calls."""
+numerics), and a bad argument comes back as OVL_EINVAL. The Python binding's ctypes
+structures have the C layout, field by field. No GPU calls."""
 import os
 import shutil
 import subprocess
@@ -76,3 +77,33 @@ def test_c_program_calls_the_library(c_program):
     assert np.allclose(w, [1.0, 3.0, 5.0], atol=1e-14)
     assert int(lines[11]) == -1                      # OVL_EINVAL
     assert lines[12].startswith("liboverlap")
+
+
+def test_ctypes_structs_match_the_c_layout(tmp_path):
+    """The binding's ctypes mirrors of ovl_params and ovl_solve_info have the C compiler's
+    size and every field's offset (a drifted field would pass every later parameter
+    shifted): a C program prints sizeof and offsetof for each field the binding names."""
+    import ctypes
+    gcc = shutil.which("gcc") or shutil.which("cc")
+    if gcc is None:
+        pytest.skip("no C compiler")
+    from paper_1501_01855_gb300 import binding as B
+    lines = ["#include <stdio.h>", "#include <stddef.h>", '#include "overlap.h"', "int main(void) {"]
+    for st in (B.ovl_params, B.ovl_solve_info):
+        cname = st.__name__
+        lines.append('  printf("%s %%zu\\n", sizeof(%s));' % (cname, cname))
+        for f, _ in st._fields_:
+            lines.append('  printf("%s.%s %%zu\\n", offsetof(%s, %s));' % (cname, f, cname, f))
+    lines += ["  return 0;", "}"]
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines) + "\n")
+    exe = tmp_path / "layout"
+    r = subprocess.run([gcc, "-std=c99", "-Wall", "-Werror", "-pedantic", "-I", os.path.join(ROOT, "include"),
+                        str(src), "-o", str(exe)], capture_output=True, text=True)
+    assert r.returncode == 0, r.stderr
+    out = dict(l.split() for l in subprocess.run([str(exe)], capture_output=True, text=True).stdout.splitlines())
+    for st in (B.ovl_params, B.ovl_solve_info):
+        cname = st.__name__
+        assert int(out[cname]) == ctypes.sizeof(st), cname
+        for f, _ in st._fields_:
+            assert int(out["%s.%s" % (cname, f)]) == getattr(st, f).offset, (cname, f)
