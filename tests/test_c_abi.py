@@ -2,8 +2,10 @@
 include/overlap.h, links liboverlap.so and calls the host-only entry points; its output
 agrees with the oracle (Zolotarev coefficients, Sec. 3) and with NumPy (the host
 numerics), and a bad argument comes back as OVL_EINVAL. The Python binding's ctypes
-structures have the C layout, field by field. No GPU calls."""
+structures have the C layout, field by field, and its function signatures the header's
+argument kinds, position by position. No GPU calls."""
 import os
+import re
 import shutil
 import subprocess
 
@@ -107,3 +109,42 @@ def test_ctypes_structs_match_the_c_layout(tmp_path):
         assert int(out[cname]) == ctypes.sizeof(st), cname
         for f, _ in st._fields_:
             assert int(out["%s.%s" % (cname, f)]) == getattr(st, f).offset, (cname, f)
+
+
+def _c_kind(decl):
+    decl = decl.strip()
+    if "*" in decl or "[" in decl:
+        return "ptr"
+    decl = re.sub(r"\b(const|unsigned)\b", "", decl).split()
+    base = " ".join(decl[:-1]) if len(decl) > 1 else decl[0]
+    return {"int": "int", "double": "double", "long long": "longlong", "size_t": "size_t"}.get(base, base)
+
+
+def _ctypes_kind(t):
+    import ctypes
+    if t is None:
+        return "void"
+    if t in (ctypes.c_void_p, ctypes.c_char_p) or (isinstance(t, type) and issubclass(t, ctypes._Pointer)):
+        return "ptr"
+    return {ctypes.c_int: "int", ctypes.c_double: "double", ctypes.c_longlong: "longlong",
+            ctypes.c_size_t: "size_t"}.get(t, repr(t))
+
+
+def test_binding_signatures_match_the_header():
+    """Every function the binding loads has, in include/overlap.h, the same number of
+    arguments and the same kind (int, double, long long, pointer) in each position, and the
+    same kind of result; a mismatch would pass garbage on both x86 and Arm."""
+    from paper_1501_01855_gb300 import binding as B
+    hdr = open(os.path.join(ROOT, "include", "overlap.h")).read()
+    hdr = re.sub(r"/\*.*?\*/", "", hdr, flags=re.S)
+    protos = {}
+    for m in re.finditer(r"([A-Za-z_][A-Za-z_0-9 \*]*?)\b((?:ovl|overlap|eigsumr)_[a-z0-9_]+)\s*\(([^;{]*?)\)\s*;", hdr):
+        ret, name, args = m.group(1), m.group(2), m.group(3)
+        args = [] if args.strip() in ("", "void") else [a for a in args.split(",")]
+        protos[name] = ("ptr" if "*" in ret else _c_kind(ret + " x").replace("ovl_status", "int"), [_c_kind(a) for a in args])
+    for name, (res, argt) in B._SIGS.items():
+        assert name in protos, name
+        cres, cargs = protos[name]
+        assert len(cargs) == len(argt), (name, cargs, argt)
+        assert [_ctypes_kind(t) for t in argt] == cargs, (name, cargs)
+        assert _ctypes_kind(res) == cres, (name, cres, res)
