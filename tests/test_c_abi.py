@@ -148,3 +148,25 @@ def test_binding_signatures_match_the_header():
         assert len(cargs) == len(argt), (name, cargs, argt)
         assert [_ctypes_kind(t) for t in argt] == cargs, (name, cargs)
         assert _ctypes_kind(res) == cres, (name, cres, res)
+
+
+def test_binding_constants_match_the_header(tmp_path):
+    """Status codes, element types, precisions, solvers and the profiler class count that
+    the binding copies from include/overlap.h have the header's values."""
+    gcc = shutil.which("gcc") or shutil.which("cc")
+    if gcc is None:
+        pytest.skip("no C compiler")
+    from paper_1501_01855_gb300 import binding as B
+    names = [n for n in dir(B) if re.fullmatch(r"OVL_[A-Z0-9_]+", n) and isinstance(getattr(B, n), int)]
+    assert len(names) >= 18
+    body = "\n".join('  printf("%s %%d\\n", (int)%s);' % (n, n) for n in names)
+    src = tmp_path / "consts.c"
+    src.write_text('#include <stdio.h>\n#include "overlap.h"\nint main(void) {\n%s\n  return 0;\n}\n' % body)
+    exe = tmp_path / "consts"
+    r = subprocess.run([gcc, "-std=c99", "-Wall", "-Werror", "-pedantic", "-I", os.path.join(ROOT, "include"),
+                        str(src), "-o", str(exe)], capture_output=True, text=True)
+    assert r.returncode == 0, r.stderr
+    out = dict(l.split() for l in subprocess.run([str(exe)], capture_output=True, text=True).stdout.splitlines())
+    for n in names:
+        assert int(out[n]) == getattr(B, n), n
+    assert set(B.STATUS_NAMES) == {getattr(B, n) for n in names if n.startswith("OVL_E") or n == "OVL_OK"}
