@@ -248,3 +248,17 @@ def test_host_numerics_reject_bad_arguments():
     with pytest.raises(binding.OvlError) as e:
         binding.ovl_host_eigh(A)
     assert e.value.status == binding.OVL_EINVAL
+
+
+def test_params_defaults_are_the_documented_ones():
+    """ovl_params_default (no GPU) gives the defaults include/overlap.h documents."""
+    binding = _lib()
+    p = binding.ovl_params_default()
+    doc = {"solver": 0, "emulate_fp64": 1, "eta_floor": 1e-2, "sp_switch": 1e-6, "half_switch": 2e-3,
+           "relax_factor": 1.0, "gmresr_max": 30, "inner_max": 2000, "mscg_max": 5000, "delta_split": 0.01,
+           "c_spec": np.sqrt(3.0) / 2.0, "bc_t": 0, "batch_max": 36, "wilson_variant": -1, "use_graphs": 1,
+           "verify": 1, "sign_method": 0, "basis_gb": 96.0, "multimass": 1, "force_pole_group": 0,
+           "lanczos_cap": 0, "gram_method": 0}
+    for k, v in doc.items():
+        assert getattr(p, k) == pytest.approx(v, rel=1e-15), k
+    assert not p.stream
