@@ -74,6 +74,7 @@ _SIGS = {
     "ovl_host_lower_inverse": (I, [I, DP, DP]),
     "ovl_host_lu_solve": (I, [I, DP, DP, I, DP]),
     "ovl_host_tridiag_extremes": (I, [I, DP, DP, DP, DP]),
+    "ovl_host_ritz": (I, [I, DP, DP, DP, D, D, I, I, DP, DP, DP, ctypes.POINTER(I)]),
     "overlap_create": (I, [ctypes.POINTER(P), ctypes.POINTER(I), DP, D, D, I, D, ctypes.POINTER(ovl_params)]),
     "overlap_destroy": (None, [P]),
     "overlap_last_error": (ctypes.c_char_p, [P]),
@@ -256,6 +257,23 @@ def ovl_host_lu_solve(a, b):
     x = np.zeros_like(b2)
     _check(load().ovl_host_lu_solve(a.shape[0], _cptr(a), _cptr(b2), b2.shape[1], _cptr(x)))
     return x.ravel() if vec else x
+
+
+def ovl_host_ritz(E, MVD, G5, mu, delta, keep, restart=False):
+    """Host algebra of one Ritz step (Alg. 6) on the k x k Gram blocks of a basis:
+    (Ritz values, C (k x kept), residual norms)."""
+    E, MVD, G5 = (_square_c128(x) for x in (E, MVD, G5))
+    k = E.shape[0]
+    if MVD.shape != E.shape or G5.shape != E.shape:
+        raise ValueError("E, MVD and G5 must have the same shape")
+    ritz, res = np.zeros(2 * keep), np.zeros(2 * keep)
+    C = np.zeros((k, 2 * keep), dtype=np.complex128)
+    kept = ctypes.c_int()
+    _check(load().ovl_host_ritz(k, _cptr(E), _cptr(MVD), _cptr(G5), float(mu), float(delta), int(keep),
+                                1 if restart else 0, _dptr(ritz), _cptr(C), _dptr(res), ctypes.byref(kept)))
+    n = kept.value
+    Cn = C.ravel()[:k * n].reshape(k, n).copy()
+    return ritz[:n].copy(), Cn, res[:n].copy()
 
 
 def ovl_host_tridiag_extremes(d, e):

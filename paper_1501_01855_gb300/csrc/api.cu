@@ -466,6 +466,26 @@ extern "C" ovl_status ovl_host_tridiag_extremes(int n, const double* d, const do
   return OVL_OK;
 }
 
+extern "C" ovl_status ovl_host_ritz(int k, const double* E, const double* MVD, const double* G5, double mu,
+                                    double delta, int keep, int restart, double* ritz, double* C, double* res,
+                                    int* kept) {
+  if (k < 1 || k > 1024 || keep < 1 || keep > k || !E || !MVD || !G5 || !ritz || !C || !res || !kept)
+    return OVL_EINVAL;
+  if (!(mu > 0 && mu < 1) || !(delta >= 0)) return OVL_EINVAL;
+  const size_t kk2 = (size_t)2 * k * k;
+  for (const double* p : {E, MVD, G5})
+    for (size_t i = 0; i < kk2; ++i)
+      if (!std::isfinite(p[i])) return OVL_EINVAL;
+  RitzHost rh;
+  ritz_host(k, reinterpret_cast<const cd*>(E), reinterpret_cast<const cd*>(MVD), reinterpret_cast<const cd*>(G5), mu,
+            delta, keep, restart != 0, &rh);
+  *kept = rh.keep;
+  memcpy(ritz, rh.lam.data(), sizeof(double) * rh.keep);
+  memcpy(res, rh.res.data(), sizeof(double) * rh.keep);
+  memcpy(C, rh.C.data(), sizeof(cd) * (size_t)k * rh.keep);
+  return OVL_OK;
+}
+
 extern "C" ovl_status overlap_zolotarev(const ovl_ctx* c, double* omega, double* sigma, double* delta, double* a,
                                         double* b) {
   if (!c) return OVL_EINVAL;

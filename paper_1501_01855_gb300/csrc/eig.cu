@@ -31,22 +31,20 @@
 
 namespace ovl {
 
-ovl_status ritz_step(ovl_ctx* c, EigState* e, int keep, bool restart) {
-  const int k = e->k;
-  if (k == 0) return OVL_OK;
+// The k x k algebra of a Ritz step (Alg. 6), on the host in FP64, from the Gram blocks of a
+// basis v_1 .. v_k with v^D_i = D v_i: E = (v_i, v_j), MVD = (v^D_i, v^D_j) and
+// G5 = (v_i, gamma5 v^D_j), row-major. Gives the Ritz values (ascending), the coefficients C
+// (k x keep, row-major) of the kept Ritz vectors in the basis, their residual norms
+// ||gamma5 v^D - v (v, gamma5 v^D)||, and whether E had no Cholesky factor (the basis is then
+// orthonormalised through the eigendecomposition of E, dropping directions below 1e-10 of
+// its largest eigenvalue). restart: the locally optimal restart described in ritz_step.
+void ritz_host(int k, const cd* E_in, const cd* MVD_in, const cd* G5_in, double mu, double delta, int keep,
+               bool restart, RitzHost* out) {
+  const size_t kk2 = (size_t)k * k;
+  std::vector<cd> E(E_in, E_in + kk2);
+  const std::vector<cd> MVD(MVD_in, MVD_in + kk2), G5(G5_in, G5_in + kk2);
   keep = std::min(keep, k);
-  const double mu = e->mu, delta = e->delta;
-  const double a = 0.5 * (1.0 - mu), b = 0.5 * (1.0 + mu);
-  Field* VD;
-  OVL_TRY(get_field(c, "e_VD", e->prec, e->m, &VD));
-  {
-    std::vector<cd> aa(k, a), bb(k, b);
-    OVL_TRY(axpby_batch(c, aa, *e->W, 0, bb, *e->V, 0, *VD, 0, k));
-  }
-  std::vector<cd> E, MVD, G5;
-  OVL_TRY(gram_host(c, *e->V, 0, k, *e->V, 0, k, 0, E));
-  OVL_TRY(gram_host(c, *VD, 0, k, *VD, 0, k, 0, MVD));
-  OVL_TRY(gram_host(c, *e->V, 0, k, *VD, 0, k, 1, G5));
+  out->cholesky_fallback = false;
   std::vector<cd> M((size_t)k * k);
   for (int i = 0; i < k; ++i)
     for (int j = 0; j < k; ++j) M[(size_t)i * k + j] = MVD[(size_t)i * k + j] + 2.0 * mu * delta * G5[(size_t)i * k + j];
@@ -82,7 +80,7 @@ ovl_status ritz_step(ovl_ctx* c, EigState* e, int keep, bool restart) {
       B.assign((size_t)k * r, 0.0);
       for (int i = 0; i < k; ++i)
         for (int jj = 0; jj < r; ++jj) B[(size_t)i * r + jj] = Z[(size_t)i * k + keepc[jj]] / std::sqrt(w[keepc[jj]]);
-      e->cholesky_fallbacks += 1;
+      out->cholesky_fallback = true;
     }
   }
   // T = B^dag M B (r x r)
@@ -184,16 +182,9 @@ ovl_status ritz_step(ovl_ctx* c, EigState* e, int keep, bool restart) {
       for (int l = 0; l < r; ++l) s += B[(size_t)i * r + l] * Yc[(size_t)l * keep + j];
       C[(size_t)i * keep + j] = s;
     }
-  // rotate v and w
-  Field* Tv;
-  OVL_TRY(get_field(c, "e_T", e->prec, e->m, &Tv));
-  OVL_TRY(combine_host(c, *e->V, 0, k, C, *Tv, 0, keep, 0));
-  OVL_TRY(copy_convert(c, *Tv, 0, *e->V, 0, keep));
-  OVL_TRY(combine_host(c, *e->W, 0, k, C, *Tv, 0, keep, 0));
-  OVL_TRY(copy_convert(c, *Tv, 0, *e->W, 0, keep));
   // Ritz values and residuals from the Gram data: ||r||^2 = ||v^D||^2 - |(v, g5 v^D)|^2
-  e->ritz.assign(lam.begin(), lam.begin() + keep);
-  e->res.assign(keep, 0.0);
+  out->lam.assign(lam.begin(), lam.begin() + keep);
+  out->res.assign(keep, 0.0);
   for (int j = 0; j < keep; ++j) {
     cd nd = 0, th = 0;
     for (int p = 0; p < k; ++p)
@@ -202,8 +193,42 @@ ovl_status ritz_step(ovl_ctx* c, EigState* e, int keep, bool restart) {
         nd += w * MVD[(size_t)p * k + q];
         th += w * G5[(size_t)p * k + q];
       }
-    e->res[j] = std::sqrt(std::max(0.0, nd.real() - std::norm(th)));
+    out->res[j] = std::sqrt(std::max(0.0, nd.real() - std::norm(th)));
   }
+  out->C = C;
+  out->keep = keep;
+}
+
+ovl_status ritz_step(ovl_ctx* c, EigState* e, int keep, bool restart) {
+  const int k = e->k;
+  if (k == 0) return OVL_OK;
+  keep = std::min(keep, k);
+  const double mu = e->mu, delta = e->delta;
+  const double a = 0.5 * (1.0 - mu), b = 0.5 * (1.0 + mu);
+  Field* VD;
+  OVL_TRY(get_field(c, "e_VD", e->prec, e->m, &VD));
+  {
+    std::vector<cd> aa(k, a), bb(k, b);
+    OVL_TRY(axpby_batch(c, aa, *e->W, 0, bb, *e->V, 0, *VD, 0, k));
+  }
+  std::vector<cd> E, MVD, G5;
+  OVL_TRY(gram_host(c, *e->V, 0, k, *e->V, 0, k, 0, E));
+  OVL_TRY(gram_host(c, *VD, 0, k, *VD, 0, k, 0, MVD));
+  OVL_TRY(gram_host(c, *e->V, 0, k, *VD, 0, k, 1, G5));
+  RitzHost rh;
+  ritz_host(k, E.data(), MVD.data(), G5.data(), mu, delta, keep, restart, &rh);
+  if (rh.cholesky_fallback) e->cholesky_fallbacks += 1;
+  keep = rh.keep;
+  const std::vector<cd>& C = rh.C;
+  // rotate v and w
+  Field* Tv;
+  OVL_TRY(get_field(c, "e_T", e->prec, e->m, &Tv));
+  OVL_TRY(combine_host(c, *e->V, 0, k, C, *Tv, 0, keep, 0));
+  OVL_TRY(copy_convert(c, *Tv, 0, *e->V, 0, keep));
+  OVL_TRY(combine_host(c, *e->W, 0, k, C, *Tv, 0, keep, 0));
+  OVL_TRY(copy_convert(c, *Tv, 0, *e->W, 0, keep));
+  e->ritz = rh.lam;
+  e->res = rh.res;
   // largest coefficient of the newly added vectors in the kept eigenvectors
   double mx = 0.0;
   for (int p = e->n_seeded; p < k; ++p)

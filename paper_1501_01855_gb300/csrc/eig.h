@@ -25,6 +25,16 @@ struct EigState {
   Field* Zprev = nullptr;
 };
 
+// the host part of a Ritz step (Alg. 6) on given Gram blocks (see eig.cu)
+struct RitzHost {
+  std::vector<double> lam, res;
+  std::vector<std::complex<double>> C;   // k x keep, row-major
+  int keep = 0;
+  bool cholesky_fallback = false;
+};
+void ritz_host(int k, const std::complex<double>* E, const std::complex<double>* MVD, const std::complex<double>* G5,
+               double mu, double delta, int keep, bool restart, RitzHost* out);
+
 // keep the lowest `keep` Ritz vectors; restart = a basis restart inside the solve (also
 // keeps the lowest Ritz vectors of the basis without its newest vector)
 ovl_status ritz_step(ovl_ctx* c, EigState* e, int keep, bool restart = false);

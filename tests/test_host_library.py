@@ -262,3 +262,76 @@ def test_params_defaults_are_the_documented_ones():
     for k, v in doc.items():
         assert getattr(p, k) == pytest.approx(v, rel=1e-15), k
     assert not p.stream
+
+
+def _ritz_setup(k, seed):
+    """Gram blocks of a random basis of k vectors on the dense 2^4 overlap operator."""
+    from oracle import overlap
+    from tests.oracle_util import dense_setup
+    mu = 0.05
+    _, _, S, _ = dense_setup((2, 2, 2, 2))
+    D = overlap.dense_overlap(S, mu, 16)
+    G5 = overlap.gamma5_matrix(16)
+    rng = np.random.default_rng(seed)
+    V = rng.normal(size=(192, k)) + 1j * rng.normal(size=(192, k))
+    VD = D @ V
+    return mu, D, G5, V, VD, V.conj().T @ V, VD.conj().T @ VD, V.conj().T @ (G5 @ VD)
+
+
+def test_host_ritz_step_matches_oracle():
+    """The library's host algebra of a Ritz step (Alg. 6) on given Gram blocks against the
+    oracle's ritz_recalculate on the vectors themselves: Ritz values, residual norms, and the
+    Ritz vectors V C (orthonormal, each within a phase of the oracle's)."""
+    from oracle import eigen
+    binding = _lib()
+    delta = 0.01
+    for k, keep, seed in ((12, 5, 1), (40, 8, 2)):
+        mu, D, G5, V, VD, E, MVD, G5m = _ritz_setup(k, seed)
+        ritz, C, res = binding.ovl_host_ritz(E, MVD, G5m, mu, delta, keep)
+        lam, Vn, VDn, res_o = eigen.ritz_recalculate(V, VD, mu, delta, keep, (16, 4, 3))
+        assert C.shape == (k, keep)
+        assert np.allclose(ritz, lam, rtol=1e-11, atol=0)
+        assert np.allclose(res, res_o, rtol=1e-8, atol=1e-11)
+        W = V @ C
+        assert np.allclose(W.conj().T @ W, np.eye(keep), atol=1e-10)
+        overlap_ = np.abs(np.sum(W.conj() * Vn, axis=0))
+        assert np.allclose(overlap_, 1.0, atol=1e-9)
+
+
+def test_host_ritz_locally_optimal_restart():
+    """restart = 1: the Rayleigh-Ritz of D^dag D + 2 mu delta gamma5 D on the span of the
+    lowest keep Ritz vectors of the basis and of the basis without its newest vector
+    (2 keep values), against the same construction in NumPy from the oracle's Ritz vectors."""
+    from oracle import eigen
+    binding = _lib()
+    delta, k, keep = 0.01, 30, 6
+    mu, D, G5, V, VD, E, MVD, G5m = _ritz_setup(k, 3)
+    ritz, C, res = binding.ovl_host_ritz(E, MVD, G5m, mu, delta, keep, restart=True)
+    assert len(ritz) == 2 * keep and C.shape == (k, 2 * keep)
+    _, V1, _, _ = eigen.ritz_recalculate(V, VD, mu, delta, keep, (16, 4, 3))
+    _, V2, _, _ = eigen.ritz_recalculate(V[:, :k - 1], VD[:, :k - 1], mu, delta, keep, (16, 4, 3))
+    Qs, _ = np.linalg.qr(np.concatenate([V1, V2], axis=1))
+    Mop = D.conj().T @ D + 2 * mu * delta * (G5 @ D)
+    ref = np.linalg.eigvalsh(Qs.conj().T @ Mop @ Qs)
+    assert np.allclose(ritz, ref, rtol=1e-10, atol=0)
+    W = V @ C
+    assert np.allclose(W.conj().T @ W, np.eye(2 * keep), atol=1e-9)
+
+
+def test_host_ritz_without_cholesky_factor():
+    """A basis with a repeated vector has a singular E: the step orthonormalises through the
+    eigendecomposition of E instead and gives the Ritz values of the span."""
+    from oracle import eigen
+    binding = _lib()
+    delta, keep = 0.01, 5
+    mu, D, G5, V, VD, E, MVD, G5m = _ritz_setup(16, 4)
+    Vr = np.concatenate([V, V[:, 3:4]], axis=1)
+    VDr = D @ Vr
+    ritz, C, res = binding.ovl_host_ritz(Vr.conj().T @ Vr, VDr.conj().T @ VDr, Vr.conj().T @ (G5 @ VDr), mu, delta,
+                                         keep)
+    lam, _, _, _ = eigen.ritz_recalculate(V, VD, mu, delta, keep, (16, 4, 3))
+    assert np.allclose(ritz, lam, rtol=1e-8, atol=0)
+    W = Vr @ C
+    assert np.allclose(W.conj().T @ W, np.eye(keep), atol=1e-8)
+    with pytest.raises(binding.OvlError):
+        binding.ovl_host_ritz(E, MVD, G5m, mu, delta, 0)
