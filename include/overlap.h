@@ -207,6 +207,21 @@ ovl_status ovl_zolotarev_coeffs(int n, double a, double b, double* omega, double
  *                             Gershgorin interval: the extremes of the Lanczos tridiagonal
  *                             of K^2, whose square roots estimate the interval [a, b] of
  *                             |K| that the rational of Sec. 3 covers. */
+/* Host-only: one step of the library's relSUMR recurrence for one system (Algs. 1-2, Sec. 2;
+ * the short recurrence re-derived from App. A: progressive Givens QR of rho I + B^), as the
+ * solver runs it between the sign application u = V q_j with its fused reductions and the
+ * vector update. rho = (1 + mu)/(1 - mu) > 1; dots = {Re (q~_j, u), Im (q~_j, u), ||u||^2,
+ * ||q~_j||^2} with (a, b) = sum conj(a) b. state[11], in and out: {gamma_{j-1} (re, im),
+ * s_{j-1} (re, im), c_{j-1}, sigma_{j-1}, zeta (re, im), g^ (re, im), j}; a solve starts from
+ * {0, 0, 0, 0, 1, 0, 1, 0, ||r_0||, 0, 0} with q_0 = q~_0 = r_0 / ||r_0||, p = S = 0. coef[18]
+ * receives 9 complex numbers (R, gs, iR, sp, z, g, gamma_j, 1/sigma_j, sigma_j) for the update
+ *   p' = (q_j - R p + gs S) iR,  S <- sp S + z p,  p <- p',  x <- x + g p',
+ *   q_{j+1} = (u + gamma_j q~_j) / sigma_j,  q~_{j+1} = sigma_j q~_j + conj(gamma_j) q_{j+1},
+ * after which |g^| is the residual estimate ||b - (rho + V) x||. OVL_EBREAKDOWN, state
+ * untouched, when sigma_j^2 vanishes to rounding (an exhausted Krylov space) or a dot is not
+ * finite; OVL_EINVAL for rho <= 1, a null pointer or a non-finite state. */
+ovl_status ovl_host_sumr_step(double rho, const double* dots, double* state, double* coef);
+
 /* Host-only: the k x k algebra of one Ritz step (Alg. 6) as the eigen accumulation runs it
  * between its Gram blocks and the rotation of the basis, for a basis v_1 .. v_k with
  * v^D_i = D(mu) v_i (Sec. 5). E = (v_i, v_j), MVD = (v^D_i, v^D_j), G5 = (v_i, gamma5 v^D_j):

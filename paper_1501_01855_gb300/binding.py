@@ -75,6 +75,7 @@ _SIGS = {
     "ovl_host_lu_solve": (I, [I, DP, DP, I, DP]),
     "ovl_host_tridiag_extremes": (I, [I, DP, DP, DP, DP]),
     "ovl_host_ritz": (I, [I, DP, DP, DP, D, D, I, I, DP, DP, DP, ctypes.POINTER(I)]),
+    "ovl_host_sumr_step": (I, [D, DP, DP, DP]),
     "overlap_create": (I, [ctypes.POINTER(P), ctypes.POINTER(I), DP, D, D, I, D, ctypes.POINTER(ovl_params)]),
     "overlap_destroy": (None, [P]),
     "overlap_last_error": (ctypes.c_char_p, [P]),
@@ -274,6 +275,17 @@ def ovl_host_ritz(E, MVD, G5, mu, delta, keep, restart=False):
     n = kept.value
     Cn = C.ravel()[:k * n].reshape(k, n).copy()
     return ritz[:n].copy(), Cn, res[:n].copy()
+
+
+def ovl_host_sumr_step(rho, dots, state):
+    """One step of the library's relSUMR recurrence (host): updates state (11 doubles) in
+    place and returns the 9 complex update coefficients."""
+    dots = np.ascontiguousarray(np.asarray(dots, dtype=np.float64))
+    if dots.size != 4 or state.dtype != np.float64 or state.size != 11 or not state.flags["C_CONTIGUOUS"]:
+        raise ValueError("dots: 4 doubles; state: a contiguous float64 array of 11")
+    coef = np.zeros(18)
+    _check(load().ovl_host_sumr_step(float(rho), _dptr(dots), _dptr(state), _dptr(coef)))
+    return coef.view(np.complex128)
 
 
 def ovl_host_tridiag_extremes(d, e):

@@ -466,6 +466,34 @@ extern "C" ovl_status ovl_host_tridiag_extremes(int n, const double* d, const do
   return OVL_OK;
 }
 
+extern "C" ovl_status ovl_host_sumr_step(double rho, const double* dots, double* state, double* coef) {
+  if (!dots || !state || !coef || !(rho > 1.0) || !std::isfinite(rho)) return OVL_EINVAL;
+  for (int i = 0; i < 11; ++i)
+    if (!std::isfinite(state[i])) return OVL_EINVAL;
+  SumrRec r;
+  r.gprev = cd(state[0], state[1]);
+  r.sprev = cd(state[2], state[3]);
+  r.cprev = state[4];
+  r.sigprev = state[5];
+  r.zeta = cd(state[6], state[7]);
+  r.ghat = cd(state[8], state[9]);
+  r.it = (int)state[10];
+  cd gam;
+  double sig;
+  if (!sumr_basis_step(cd(dots[0], dots[1]), dots[2], dots[3], &gam, &sig)) return OVL_EBREAKDOWN;
+  cd v6[6];
+  sumr_rec_step(r, rho, gam, sig, v6);
+  const cd vals[9] = {v6[0], v6[1], v6[2], v6[3], v6[4], v6[5], gam, 1.0 / sig, sig};
+  for (int k = 0; k < 9; ++k) {
+    coef[2 * k] = vals[k].real();
+    coef[2 * k + 1] = vals[k].imag();
+  }
+  const double st[11] = {r.gprev.real(), r.gprev.imag(), r.sprev.real(), r.sprev.imag(), r.cprev, r.sigprev,
+                         r.zeta.real(), r.zeta.imag(), r.ghat.real(), r.ghat.imag(), (double)r.it};
+  memcpy(state, st, sizeof(st));
+  return OVL_OK;
+}
+
 extern "C" ovl_status ovl_host_ritz(int k, const double* E, const double* MVD, const double* G5, double mu,
                                     double delta, int keep, int restart, double* ritz, double* C, double* res,
                                     int* kept) {

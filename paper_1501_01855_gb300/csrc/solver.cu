@@ -298,6 +298,58 @@ ovl_status defl_start(ovl_ctx* c, ovl_defl* d, const Field& b, int boff, int nsy
   return OVL_OK;
 }
 
+// ------------------------------------------------------------------ SUMR recurrence
+// Alg. 1 with the sign applied inexactly: gamma_j is the projection coefficient of u = V q_j
+// on q~_j and sigma_j = ||u + gamma_j q~_j||, so that V q_j = sigma_j q_{j+1} - gamma_j q~_j
+// holds for the computed vectors; with an exact (unitary) sign this is gamma_j = -(q~_j, u)
+// and sigma_j = sqrt(1 - |gamma_j|^2) of Alg. 1. Inputs (q~, u), ||u||^2, ||q~||^2; false
+// when the Krylov space is exhausted or the sign was not finite.
+bool sumr_basis_step(cd qtu, double uu, double tt, cd* gam_out, double* sig_out) {
+  const cd gam = tt > 0 ? -qtu / tt : cd(0.0);
+  const double s2 = uu - std::norm(qtu) / std::max(tt, 1e-300);
+  if (!(s2 > 1e-24 * std::max(uu, 1e-300)) || !std::isfinite(s2)) return false;
+  *gam_out = gam;
+  *sig_out = std::sqrt(s2);
+  return true;
+}
+
+// One step of the short recurrence of one system (reading 7: the progressive Givens QR of
+// rho I + B^, re-derived from App. A; its upper part is gamma_j times the coefficients of
+// q~_j, carried by the two auxiliary vectors p and S). vals = {R_{j-1,j}, gamma_j
+// sigma_{j-1}, 1/R_jj, sigma_{j-1}, zeta_{j-1}, g_j}: the coefficients of the vector update;
+// s.ghat becomes the residual estimate after this step.
+void sumr_rec_step(SumrRec& s, double rho, cd gam, double sig, cd vals[6]) {
+  cd a, Rm1, zm1;
+  if (s.it == 0) {
+    s.zeta = 1.0;
+    a = rho - gam * s.zeta;
+    Rm1 = 0.0;
+    zm1 = 0.0;
+  } else {
+    zm1 = s.cprev * s.sigprev * s.zeta + std::conj(s.sprev) * std::conj(s.gprev);
+    s.zeta = -s.sprev * s.sigprev * s.zeta + s.cprev * std::conj(s.gprev);
+    Rm1 = rho * std::conj(s.sprev) - gam * zm1;
+    a = rho * s.cprev - gam * s.zeta;
+  }
+  const double nrm = std::sqrt(std::norm(a) + sig * sig);
+  const double cc = std::abs(a) / nrm;
+  const cd ss_ = std::abs(a) > 0 ? cc * sig / a : cd(1.0, 0.0);
+  const cd Rjj = cc * a + std::conj(ss_) * sig;
+  const cd g = cc * s.ghat;
+  s.ghat = -ss_ * s.ghat;
+  vals[0] = Rm1;
+  vals[1] = gam * s.sigprev;
+  vals[2] = 1.0 / Rjj;
+  vals[3] = s.sigprev;
+  vals[4] = zm1;
+  vals[5] = g;
+  s.cprev = cc;
+  s.sprev = ss_;
+  s.sigprev = sig;
+  s.gprev = gam;
+  s.it += 1;
+}
+
 // ------------------------------------------------------------------ relSUMR
 ovl_status sumr_batch(ovl_ctx* c, const SumrCfg& cfg, int n, const std::vector<double>& mus, const Field& b, int boff,
                       Field& x, int xoff, SumrResult& res) {
@@ -349,13 +401,8 @@ ovl_status sumr_batch(ovl_ctx* c, const SumrCfg& cfg, int n, const std::vector<d
     launch_zero(PS, fS->ref(), n, V, c->st);
   }
   // per-system recurrence state
-  struct St {
-    cd gprev = 0, sprev = 0;
-    double cprev = 1, sigprev = 0;
-    cd zeta = 1.0;
-    cd ghat;
+  struct St : SumrRec {
     bool active = true;
-    int it = 0;
   };
   std::vector<St> S(n);
   res.iters.assign(n, 0);
@@ -408,55 +455,27 @@ ovl_status sumr_batch(ovl_ctx* c, const SumrCfg& cfg, int n, const std::vector<d
       hact[j] = S[j].active ? 1 : 0;
       if (!S[j].active) continue;
       St& s = S[j];
-      // Alg. 1 with the sign applied inexactly: gamma_j is the projection coefficient of
-      // u on q~_j and sigma_j = ||u + gamma_j q~_j||, so that V q_j = sigma_j q_{j+1} - gamma_j q~_j
-      // holds for the computed vectors; with an exact (unitary) sign this is
-      // gamma_j = -(q~_j, u) and sigma_j = sqrt(1 - |gamma_j|^2) of Alg. 1.
-      const cd qtu(dots[4 * j], dots[4 * j + 1]);
-      const double uu = dots[4 * j + 2], tt = dots[4 * j + 3];
-      const cd gam = tt > 0 ? -qtu / tt : cd(0.0);
-      const double s2 = uu - std::norm(qtu) / std::max(tt, 1e-300);
-      if (!(s2 > 1e-24 * std::max(uu, 1e-300)) || !std::isfinite(s2)) {
+      cd gam;
+      double sig;
+      if (!sumr_basis_step(cd(dots[4 * j], dots[4 * j + 1]), dots[4 * j + 2], dots[4 * j + 3], &gam, &sig)) {
         // Krylov space exhausted or a non-finite sign: stop this system here
         s.active = false;
         hact[j] = 0;
         res.stopped[j] = 2;
         continue;
       }
-      const double sig = std::sqrt(s2);
-      cd a, Rm1, zm1;
-      if (s.it == 0) {
-        s.zeta = 1.0;
-        a = rho[j] - gam * s.zeta;
-        Rm1 = 0.0;
-        zm1 = 0.0;
-      } else {
-        zm1 = s.cprev * s.sigprev * s.zeta + std::conj(s.sprev) * std::conj(s.gprev);
-        s.zeta = -s.sprev * s.sigprev * s.zeta + s.cprev * std::conj(s.gprev);
-        Rm1 = rho[j] * std::conj(s.sprev) - gam * zm1;
-        a = rho[j] * s.cprev - gam * s.zeta;
-      }
-      const double nrm = std::sqrt(std::norm(a) + sig * sig);
-      const double cc = std::abs(a) / nrm;
-      const cd ss_ = std::abs(a) > 0 ? cc * sig / a : cd(1.0, 0.0);
-      const cd Rjj = cc * a + std::conj(ss_) * sig;
-      const cd g = cc * s.ghat;
-      s.ghat = -ss_ * s.ghat;
-      const cd vals[9] = {Rm1, gam * s.sigprev, 1.0 / Rjj, s.sigprev, zm1, g, gam, 1.0 / sig, sig};
+      cd v6[6];
+      sumr_rec_step(s, rho[j], gam, sig, v6);
+      const cd vals[9] = {v6[0], v6[1], v6[2], v6[3], v6[4], v6[5], gam, 1.0 / sig, sig};
       for (int k = 0; k < 9; ++k) {
         o[2 * k] = vals[k].real();
         o[2 * k + 1] = vals[k].imag();
       }
       if (log_level() >= 3) {
-        fprintf(stderr, "  sumr sys %d it %d vals", j, s.it + 1);
+        fprintf(stderr, "  sumr sys %d it %d vals", j, s.it);
         for (int k = 0; k < 9; ++k) fprintf(stderr, " (%.6f,%.6f)", vals[k].real(), vals[k].imag());
         fprintf(stderr, "\n");
       }
-      s.cprev = cc;
-      s.sprev = ss_;
-      s.sigprev = sig;
-      s.gprev = gam;
-      s.it += 1;
       res.iters[j] = s.it;
     }
     const double* dsc;
@@ -526,13 +545,8 @@ ovl_status sumr_multimass(ovl_ctx* c, const SumrCfg& cfg, int ns, int nm, const 
     launch_zero(PS, fp->ref(), n, V, c->st);
     launch_zero(PS, fS->ref(), n, V, c->st);
   }
-  struct St {
-    cd gprev = 0, sprev = 0;
-    double cprev = 1, sigprev = 0;
-    cd zeta = 1.0;
-    cd ghat;
+  struct St : SumrRec {
     bool active = true;
-    int it = 0;
   };
   std::vector<St> S(n);
   std::vector<char> qact(ns, 0);
@@ -595,12 +609,10 @@ ovl_status sumr_multimass(ovl_ctx* c, const SumrCfg& cfg, int ns, int nm, const 
       hq[j] = qact[j] ? 1 : 0;
       for (int k = 0; k < nm; ++k) hact[k * ns + j] = qact[j] && S[k * ns + j].active ? 1 : 0;
       if (!qact[j]) continue;
-      // the basis step of Alg. 1 with an inexact sign (see sumr_batch), shared by the masses
-      const cd qtu(dots[4 * j], dots[4 * j + 1]);
-      const double uu = dots[4 * j + 2], tt = dots[4 * j + 3];
-      const cd gam = tt > 0 ? -qtu / tt : cd(0.0);
-      const double s2 = uu - std::norm(qtu) / std::max(tt, 1e-300);
-      if (!(s2 > 1e-24 * std::max(uu, 1e-300)) || !std::isfinite(s2)) {
+      // the basis step of Alg. 1 with an inexact sign, shared by the masses
+      cd gam;
+      double sig;
+      if (!sumr_basis_step(cd(dots[4 * j], dots[4 * j + 1]), dots[4 * j + 2], dots[4 * j + 3], &gam, &sig)) {
         qact[j] = 0;
         hq[j] = 0;
         for (int k = 0; k < nm; ++k) {
@@ -610,7 +622,6 @@ ovl_status sumr_multimass(ovl_ctx* c, const SumrCfg& cfg, int ns, int nm, const 
         }
         continue;
       }
-      const double sig = std::sqrt(s2);
       const cd qv[3] = {gam, 1.0 / sig, sig};
       for (int m = 0; m < 3; ++m) {
         scq[6 * j + 2 * m] = qv[m].real();
@@ -619,35 +630,13 @@ ovl_status sumr_multimass(ovl_ctx* c, const SumrCfg& cfg, int ns, int nm, const 
       for (int k = 0; k < nm; ++k) {
         St& t = S[k * ns + j];
         if (!t.active) continue;
-        cd a, Rm1, zm1;
-        if (t.it == 0) {
-          t.zeta = 1.0;
-          a = rho[k] - gam * t.zeta;
-          Rm1 = 0.0;
-          zm1 = 0.0;
-        } else {
-          zm1 = t.cprev * t.sigprev * t.zeta + std::conj(t.sprev) * std::conj(t.gprev);
-          t.zeta = -t.sprev * t.sigprev * t.zeta + t.cprev * std::conj(t.gprev);
-          Rm1 = rho[k] * std::conj(t.sprev) - gam * zm1;
-          a = rho[k] * t.cprev - gam * t.zeta;
-        }
-        const double nrm = std::sqrt(std::norm(a) + sig * sig);
-        const double cc = std::abs(a) / nrm;
-        const cd ss_ = std::abs(a) > 0 ? cc * sig / a : cd(1.0, 0.0);
-        const cd Rjj = cc * a + std::conj(ss_) * sig;
-        const cd g = cc * t.ghat;
-        t.ghat = -ss_ * t.ghat;
-        const cd vals[6] = {Rm1, gam * t.sigprev, 1.0 / Rjj, t.sigprev, zm1, g};
+        cd vals[6];
+        sumr_rec_step(t, rho[k], gam, sig, vals);
         double* o = &sc[18 * (size_t)(k * ns + j)];
         for (int m = 0; m < 6; ++m) {
           o[2 * m] = vals[m].real();
           o[2 * m + 1] = vals[m].imag();
         }
-        t.cprev = cc;
-        t.sprev = ss_;
-        t.sigprev = sig;
-        t.gprev = gam;
-        t.it += 1;
         res.iters[k * ns + j] = t.it;
       }
     }

@@ -18,6 +18,17 @@ typedef ovl_status (*CgHook)(ovl_ctx* c, void* data, const Field& t, const Field
                              const std::vector<std::complex<double>>& beta_prev,
                              const std::vector<double>& rnorm, int iter);
 
+// State of the SUMR short recurrence of one system (see sumr_rec_step in solver.cu)
+struct SumrRec {
+  cd gprev = 0, sprev = 0;
+  double cprev = 1, sigprev = 0;
+  cd zeta = 1.0;
+  cd ghat;   // residual estimate (complex; its modulus is ||r_j||)
+  int it = 0;
+};
+bool sumr_basis_step(cd qtu, double uu, double tt, cd* gam, double* sig);
+void sumr_rec_step(SumrRec& s, double rho, cd gam, double sig, cd vals[6]);
+
 struct SumrCfg {
   int prec = P64;          // precision of the middle-solve vectors
   double target = 1e-3;    // relative residual target

@@ -335,3 +335,74 @@ def test_host_ritz_without_cholesky_factor():
     assert np.allclose(W.conj().T @ W, np.eye(keep), atol=1e-8)
     with pytest.raises(binding.OvlError):
         binding.ovl_host_ritz(E, MVD, G5m, mu, delta, 0)
+
+
+def _sumr_dense(binding, U, rho, b, nsteps):
+    """relSUMR on a dense unitary U, A = rho + U: the library's host recurrence for the
+    scalars, the vector update of the device kernel written out in NumPy."""
+    nb = np.linalg.norm(b)
+    q = b / nb
+    qt = q.copy()
+    p = np.zeros_like(b)
+    S = np.zeros_like(b)
+    x = np.zeros_like(b)
+    state = np.array([0, 0, 0, 0, 1, 0, 1, 0, nb, 0, 0], dtype=np.float64)
+    hist = []
+    for _ in range(nsteps):
+        u = U @ q
+        qtu = np.vdot(qt, u)
+        dots = [qtu.real, qtu.imag, np.vdot(u, u).real, np.vdot(qt, qt).real]
+        R, gs, iR, sp, z, g, gam, isg, sg = binding.ovl_host_sumr_step(rho, dots, state)
+        pn = (q - R * p + gs * S) * iR
+        S = sp * S + z * p
+        p = pn
+        x = x + g * pn
+        qn = (u + gam * qt) * isg
+        qt = sg * qt + np.conj(gam) * qn
+        q = qn
+        hist.append(abs(complex(state[8], state[9])))
+    return x, np.array(hist)
+
+
+@pytest.mark.parametrize("case", ["random_unitary_200", "overlap_2x2x2x2"])
+def test_host_sumr_recurrence_equals_gmres(case):
+    """The library's SUMR recurrence (Algs. 1-2 re-derived from App. A) reproduces the
+    minimal-residual iterates: on A = rho + U with U a random 200 x 200 unitary and with
+    U = gamma5 sign(K) of the 2^4 lattice (rho = (1 + mu)/(1 - mu), mu = 0.05), its residual
+    estimate equals the oracle's GMRES residual history and its iterate the GMRES iterate
+    (relative 1e-10 over 40 steps); the estimate is the true residual of the iterate."""
+    from oracle import solvers
+    binding = _lib()
+    mu = 0.05
+    rho = (1 + mu) / (1 - mu)
+    rng = np.random.default_rng(12)
+    if case == "random_unitary_200":
+        Q, R = np.linalg.qr(rng.normal(size=(200, 200)) + 1j * rng.normal(size=(200, 200)))
+        U = Q * (np.diag(R) / np.abs(np.diag(R)))
+    else:
+        from oracle import overlap
+        from tests.oracle_util import dense_setup
+        _, _, S, _ = dense_setup((2, 2, 2, 2))
+        U = overlap.gamma5_matrix(16) @ S
+    N = U.shape[0]
+    b = rng.normal(size=N) + 1j * rng.normal(size=N)
+    A = rho * np.eye(N) + U
+    nsteps = 40
+    x, hist = _sumr_dense(binding, U, rho, b, nsteps)
+    xg, hg = solvers.minres_iterates(lambda v: A @ v, b, nsteps)
+    assert len(hg) == nsteps
+    assert np.allclose(hist, hg, rtol=1e-10, atol=1e-13 * np.linalg.norm(b))
+    assert np.linalg.norm(x - xg) <= 1e-10 * np.linalg.norm(xg)
+    assert abs(np.linalg.norm(b - A @ x) - hist[-1]) <= 1e-10 * np.linalg.norm(b)
+
+
+def test_host_sumr_step_stops_on_an_exhausted_space():
+    """sigma_j = 0 (u in the span of q~_j, an exhausted Krylov space) is OVL_EBREAKDOWN and
+    leaves the state as it was."""
+    binding = _lib()
+    state = np.array([0, 0, 0, 0, 1, 0, 1, 0, 2.0, 0, 0], dtype=np.float64)
+    before = state.copy()
+    with pytest.raises(binding.OvlError) as e:
+        binding.ovl_host_sumr_step(1.1, [1.0, 0.0, 1.0, 1.0], state)   # u = q~: ||u||^2 = |(q~, u)|^2
+    assert e.value.status == binding.OVL_EBREAKDOWN
+    assert np.array_equal(state, before)
