@@ -222,6 +222,21 @@ ovl_status ovl_zolotarev_coeffs(int n, double a, double b, double* omega, double
  * finite; OVL_EINVAL for rho <= 1, a null pointer or a non-finite state. */
 ovl_status ovl_host_sumr_step(double rho, const double* dots, double* state, double* coef);
 
+/* Host-only: the deflated start of relSUMR (Sec. 4) from Gram blocks, as the solver runs it
+ * after computing them on the device: for a space psi_1 .. psi_n with w_i = gamma5 eps(K) psi_i
+ * (so that D(mu) psi = (1+mu)/2 psi + (1-mu)/2 w), VV = (psi_i, psi_j), WW = (w_i, w_j),
+ * WV = (w_i, psi_j), G5VV = (psi_i, gamma5 psi_j), G5VW = (psi_i, gamma5 w_j) (n x n) and, for
+ * nsys right-hand sides b_j at masses mus[j], VB = (psi_l, b_j) and WB = (w_l, b_j) (n x nsys),
+ * all complex, row-major, interleaved. The space is rotated to psi' = psi Y diagonalising
+ * (psi'_i, gamma5 D psi'_j); alpha minimises ||b - D psi' alpha|| (per_vector = 1: the
+ * per-vector alpha_j = (D psi'_j, b) / (D psi'_j, D psi'_j) of Sec. 4 instead). coefs
+ * (n x nsys) receives x0 = psi coefs_j. OVL_EBREAKDOWN for singular normal equations,
+ * OVL_EINVAL for n outside 1..1024, nsys outside 1..4096, a mass outside (0, 1), a null
+ * pointer or a non-finite entry. */
+ovl_status ovl_host_defl_start(int n, const double* VV, const double* WW, const double* WV, const double* G5VV,
+                               const double* G5VW, int nsys, const double* VB, const double* WB, const double* mus,
+                               int per_vector, double* coefs);
+
 /* Host-only: the k x k algebra of one Ritz step (Alg. 6) as the eigen accumulation runs it
  * between its Gram blocks and the rotation of the basis, for a basis v_1 .. v_k with
  * v^D_i = D(mu) v_i (Sec. 5). E = (v_i, v_j), MVD = (v^D_i, v^D_j), G5 = (v_i, gamma5 v^D_j):

@@ -76,6 +76,7 @@ _SIGS = {
     "ovl_host_tridiag_extremes": (I, [I, DP, DP, DP, DP]),
     "ovl_host_ritz": (I, [I, DP, DP, DP, D, D, I, I, DP, DP, DP, ctypes.POINTER(I)]),
     "ovl_host_sumr_step": (I, [D, DP, DP, DP]),
+    "ovl_host_defl_start": (I, [I, DP, DP, DP, DP, DP, I, DP, DP, DP, I, DP]),
     "overlap_create": (I, [ctypes.POINTER(P), ctypes.POINTER(I), DP, D, D, I, D, ctypes.POINTER(ovl_params)]),
     "overlap_destroy": (None, [P]),
     "overlap_last_error": (ctypes.c_char_p, [P]),
@@ -286,6 +287,22 @@ def ovl_host_sumr_step(rho, dots, state):
     coef = np.zeros(18)
     _check(load().ovl_host_sumr_step(float(rho), _dptr(dots), _dptr(state), _dptr(coef)))
     return coef.view(np.complex128)
+
+
+def ovl_host_defl_start(VV, WW, WV, G5VV, G5VW, VB, WB, mus, per_vector=False):
+    """Host deflated start (Sec. 4) from Gram blocks: the n x nsys coefficients of x0 on psi."""
+    VV, WW, WV, G5VV, G5VW = (_square_c128(x) for x in (VV, WW, WV, G5VV, G5VW))
+    n = VV.shape[0]
+    VB = np.ascontiguousarray(np.asarray(VB, dtype=np.complex128)).reshape(n, -1)
+    WB = np.ascontiguousarray(np.asarray(WB, dtype=np.complex128)).reshape(n, -1)
+    nsys = VB.shape[1]
+    mus = np.ascontiguousarray(np.broadcast_to(np.asarray(mus, dtype=np.float64), (nsys,)))
+    if WB.shape != VB.shape or any(x.shape != (n, n) for x in (WW, WV, G5VV, G5VW)):
+        raise ValueError("inconsistent Gram block shapes")
+    co = np.zeros((n, nsys), dtype=np.complex128)
+    _check(load().ovl_host_defl_start(n, _cptr(VV), _cptr(WW), _cptr(WV), _cptr(G5VV), _cptr(G5VW), nsys, _cptr(VB),
+                                      _cptr(WB), _dptr(mus), 1 if per_vector else 0, _cptr(co)))
+    return co
 
 
 def ovl_host_tridiag_extremes(d, e):

@@ -494,6 +494,26 @@ extern "C" ovl_status ovl_host_sumr_step(double rho, const double* dots, double*
   return OVL_OK;
 }
 
+extern "C" ovl_status ovl_host_defl_start(int n, const double* VV, const double* WW, const double* WV,
+                                          const double* G5VV, const double* G5VW, int nsys, const double* VB,
+                                          const double* WB, const double* mus, int per_vector, double* coefs) {
+  if (n < 1 || n > 1024 || nsys < 1 || nsys > 4096 || !VV || !WW || !WV || !G5VV || !G5VW || !VB || !WB || !mus ||
+      !coefs)
+    return OVL_EINVAL;
+  for (int j = 0; j < nsys; ++j)
+    if (!(mus[j] > 0 && mus[j] < 1)) return OVL_EINVAL;
+  const size_t nn = (size_t)2 * n * n, nb = (size_t)2 * n * nsys;
+  for (const double* p : {VV, WW, WV, G5VV, G5VW})
+    for (size_t i = 0; i < nn; ++i)
+      if (!std::isfinite(p[i])) return OVL_EINVAL;
+  for (const double* p : {VB, WB})
+    for (size_t i = 0; i < nb; ++i)
+      if (!std::isfinite(p[i])) return OVL_EINVAL;
+  auto C = [](const double* p) { return reinterpret_cast<const cd*>(p); };
+  return defl_start_host(n, C(VV), C(WW), C(WV), C(G5VV), C(G5VW), nsys, C(VB), C(WB), mus, per_vector != 0,
+                         reinterpret_cast<cd*>(coefs));
+}
+
 extern "C" ovl_status ovl_host_ritz(int k, const double* E, const double* MVD, const double* G5, double mu,
                                     double delta, int keep, int restart, double* ritz, double* C, double* res,
                                     int* kept) {

@@ -201,31 +201,28 @@ ovl_status defl_prepare(ovl_ctx* c, ovl_defl* d) {
   return OVL_OK;
 }
 
-// (D psi)^dag (D psi) at mass mu, n x n
-static void dd_matrix(const ovl_defl* d, double mu, std::vector<cd>& M) {
-  const int n = d->n;
+// (D psi)^dag (D psi) at mass mu, n x n, from the Gram blocks of psi and w
+static void dd_matrix(int n, const cd* VV, const cd* WW, const cd* WV, double mu, std::vector<cd>& M) {
   const double a = 0.5 * (1.0 - mu), b = 0.5 * (1.0 + mu);
   M.assign((size_t)n * n, 0.0);
   for (int i = 0; i < n; ++i)
     for (int j = 0; j < n; ++j) {
-      const cd wv = d->WV[(size_t)i * n + j];
-      const cd vw = std::conj(d->WV[(size_t)j * n + i]);
-      M[(size_t)i * n + j] = a * a * d->WW[(size_t)i * n + j] + a * b * (wv + vw) + b * b * d->VV[(size_t)i * n + j];
+      const cd wv = WV[(size_t)i * n + j];
+      const cd vw = std::conj(WV[(size_t)j * n + i]);
+      M[(size_t)i * n + j] = a * a * WW[(size_t)i * n + j] + a * b * (wv + vw) + b * b * VV[(size_t)i * n + j];
     }
 }
 
-// Sec. 4, SUMR variant: x0 = sum_j alpha_j psi'_j minimising ||b - D x0|| with psi'
-// the rotation that diagonalises (psi_i, gamma5 D psi_j). Returns, per system, the
-// coefficients on psi (after folding in the rotation) in X0 (n_ev x nsys, column j),
-// and fills r0 = b - D x0 on the device when rv is given.
-ovl_status defl_start(ovl_ctx* c, ovl_defl* d, const Field& b, int boff, int nsys, const std::vector<double>& mus,
-                      std::vector<cd>& coefs) {
-  OVL_TRY(defl_prepare(c, d));
-  const int n = d->n;
-  std::vector<cd> VB, WB;
-  OVL_TRY(gram_host(c, d->v, 0, n, b, boff, nsys, 0, VB));
-  OVL_TRY(gram_host(c, d->w, 0, n, b, boff, nsys, 0, WB));
-  coefs.assign((size_t)n * nsys, 0.0);
+// Sec. 4, SUMR variant, on the host: x0 = sum_j alpha_j psi'_j minimising ||b - D x0|| with
+// psi' the rotation that diagonalises (psi_i, gamma5 D psi_j), from the Gram blocks of the
+// space (n x n, row-major: VV = (psi_i, psi_j), WW = (w_i, w_j), WV = (w_i, psi_j),
+// G5VV = (psi_i, gamma5 psi_j), G5VW = (psi_i, gamma5 w_j); D psi = (1+mu)/2 psi + (1-mu)/2 w)
+// and, per system j, VB = (psi_l, b_j), WB = (w_l, b_j) (n x nsys). coefs (n x nsys): x0 on
+// psi with the rotation folded in. per_vector: the per-vector alpha_j of Sec. 4 instead of
+// the least-squares solve. OVL_EBREAKDOWN when the normal equations are singular.
+ovl_status defl_start_host(int n, const cd* VV, const cd* WW, const cd* WV, const cd* G5VV, const cd* G5VW,
+                           int nsys, const cd* VB, const cd* WB, const double* mus, bool per_vector, cd* coefs) {
+  for (size_t i = 0; i < (size_t)n * nsys; ++i) coefs[i] = 0.0;
   // the rotation Y and the rotated normal matrix depend on the mass only: built once per
   // distinct mass of the batch (sources x masses share them)
   struct PerMass {
@@ -246,7 +243,7 @@ ovl_status defl_start(ovl_ctx* c, ovl_defl* d, const Field& b, int boff, int nsy
       std::vector<cd> Hs((size_t)n * n);
       std::vector<double> w(n);
       q.Y.resize((size_t)n * n);
-      for (size_t k = 0; k < Hs.size(); ++k) Hs[k] = bb * d->G5VV[k] + a * d->G5VW[k];
+      for (size_t k = 0; k < Hs.size(); ++k) Hs[k] = bb * G5VV[k] + a * G5VW[k];
       for (int i = 0; i < n; ++i)
         for (int k = i + 1; k < n; ++k) {
           const cd h = 0.5 * (Hs[(size_t)i * n + k] + std::conj(Hs[(size_t)k * n + i]));
@@ -255,7 +252,7 @@ ovl_status defl_start(ovl_ctx* c, ovl_defl* d, const Field& b, int boff, int nsy
         }
       eigh_herm(n, Hs.data(), w.data(), q.Y.data());
       std::vector<cd> M;
-      dd_matrix(d, mu, M);
+      dd_matrix(n, VV, WW, WV, mu, M);
       // rotated normal equations: (Y^dag M Y) alpha = Y^dag (D psi)^dag b
       std::vector<cd> MY((size_t)n * n);
       q.G.resize((size_t)n * n);
@@ -284,10 +281,10 @@ ovl_status defl_start(ovl_ctx* c, ovl_defl* d, const Field& b, int boff, int nsy
       }
       rhs[i] = s;
     }
-    if (d->per_vector) {
+    if (per_vector) {
       for (int i = 0; i < n; ++i) rhs[i] /= G[(size_t)i * n + i];
     } else if (lu_solve(n, G.data(), rhs.data(), 1) != 0) {
-      return set_err(c, OVL_EBREAKDOWN, "singular deflation normal equations");
+      return OVL_EBREAKDOWN;
     }
     for (int i = 0; i < n; ++i) {
       cd s = 0;
@@ -295,6 +292,22 @@ ovl_status defl_start(ovl_ctx* c, ovl_defl* d, const Field& b, int boff, int nsy
       coefs[(size_t)i * nsys + j] = s;
     }
   }
+  return OVL_OK;
+}
+
+// The deflated start of Sec. 4 for nsys systems: Gram blocks on the device, then
+// defl_start_host. coefs (n_ev x nsys, column j) are x0 of system j on psi.
+ovl_status defl_start(ovl_ctx* c, ovl_defl* d, const Field& b, int boff, int nsys, const std::vector<double>& mus,
+                      std::vector<cd>& coefs) {
+  OVL_TRY(defl_prepare(c, d));
+  const int n = d->n;
+  std::vector<cd> VB, WB;
+  OVL_TRY(gram_host(c, d->v, 0, n, b, boff, nsys, 0, VB));
+  OVL_TRY(gram_host(c, d->w, 0, n, b, boff, nsys, 0, WB));
+  coefs.assign((size_t)n * nsys, 0.0);
+  if (defl_start_host(n, d->VV.data(), d->WW.data(), d->WV.data(), d->G5VV.data(), d->G5VW.data(), nsys, VB.data(),
+                      WB.data(), mus.data(), d->per_vector, coefs.data()) != OVL_OK)
+    return set_err(c, OVL_EBREAKDOWN, "singular deflation normal equations");
   return OVL_OK;
 }
 
@@ -693,7 +706,7 @@ static ovl_status spectral_apply(ovl_ctx* c, ovl_defl* d, const std::vector<doub
   std::vector<cd> C((size_t)ne * n);
   for (int j = 0; j < n; ++j) {
     std::vector<cd> M;
-    dd_matrix(d, mus[j], M);
+    dd_matrix(ne, d->VV.data(), d->WW.data(), d->WV.data(), mus[j], M);
     for (int i = 0; i < ne; ++i) {
       const double mui = std::max(M[(size_t)i * ne + i].real() / std::max(d->VV[(size_t)i * ne + i].real(), 1e-300), 1e-300);
       const double f = c->P.c_spec / std::sqrt(mui) - 1.0;

@@ -26,6 +26,8 @@ struct SumrRec {
   cd ghat;   // residual estimate (complex; its modulus is ||r_j||)
   int it = 0;
 };
+ovl_status defl_start_host(int n, const cd* VV, const cd* WW, const cd* WV, const cd* G5VV, const cd* G5VW,
+                           int nsys, const cd* VB, const cd* WB, const double* mus, bool per_vector, cd* coefs);
 bool sumr_basis_step(cd qtu, double uu, double tt, cd* gam, double* sig);
 void sumr_rec_step(SumrRec& s, double rho, cd gam, double sig, cd vals[6]);
 

@@ -406,3 +406,38 @@ def test_host_sumr_step_stops_on_an_exhausted_space():
         binding.ovl_host_sumr_step(1.1, [1.0, 0.0, 1.0, 1.0], state)   # u = q~: ||u||^2 = |(q~, u)|^2
     assert e.value.status == binding.OVL_EBREAKDOWN
     assert np.array_equal(state, before)
+
+
+@pytest.mark.parametrize("space", ["exact_low_modes", "random"])
+def test_host_deflated_start_matches_oracle(space):
+    """The library's deflated start of relSUMR (Sec. 4) from the Gram blocks of a space
+    against the oracle's sumr_ls_start on the vectors themselves (2^4, three right-hand sides
+    at masses 0.05, 0.3, 0.05): the least-squares x0 and the per-vector form."""
+    from oracle import deflation, overlap
+    from tests.oracle_util import dense_setup
+    binding = _lib()
+    _, _, S, _ = dense_setup((2, 2, 2, 2))
+    G5 = overlap.gamma5_matrix(16)
+    rng = np.random.default_rng(21)
+    mus = [0.05, 0.3, 0.05]
+    n = 8
+    if space == "exact_low_modes":
+        H = G5 @ overlap.dense_overlap(S, 0.05, 16)
+        w, Yh = np.linalg.eigh(0.5 * (H + H.conj().T))
+        Psi = Yh[:, np.argsort(np.abs(w))[:n]]
+    else:
+        Psi, _ = np.linalg.qr(rng.normal(size=(192, n)) + 1j * rng.normal(size=(192, n)))
+    W = G5 @ S @ Psi                                   # w = gamma5 sign(K) psi
+    Bs = rng.normal(size=(192, 3)) + 1j * rng.normal(size=(192, 3))
+    h = lambda X, Y: X.conj().T @ Y
+    blocks = (h(Psi, Psi), h(W, W), h(W, Psi), h(Psi, G5 @ Psi), h(Psi, G5 @ W), h(Psi, Bs), h(W, Bs))
+    for per_vector in (False, True):
+        co = binding.ovl_host_defl_start(*blocks, mus, per_vector=per_vector)
+        for j, mu in enumerate(mus):
+            D = overlap.dense_overlap(S, mu, 16)
+            shape = (16, 4, 3)
+            psi = [Psi[:, i].reshape(shape) for i in range(n)]
+            dpsi = [(D @ Psi[:, i]).reshape(shape) for i in range(n)]
+            ref = deflation.sumr_ls_start(psi, dpsi, Bs[:, j].reshape(shape), per_vector=per_vector).ravel()
+            got = Psi @ co[:, j]
+            assert np.linalg.norm(got - ref) <= 1e-11 * np.linalg.norm(ref), (space, per_vector, j)
