@@ -441,3 +441,46 @@ def test_host_deflated_start_matches_oracle(space):
             ref = deflation.sumr_ls_start(psi, dpsi, Bs[:, j].reshape(shape), per_vector=per_vector).ravel()
             got = Psi @ co[:, j]
             assert np.linalg.norm(got - ref) <= 1e-11 * np.linalg.norm(ref), (space, per_vector, j)
+
+
+def test_host_sumr_shared_basis_for_several_masses():
+    """Multi-mass relSUMR (Sec. 2: SUMR carries over to many shifts): one Alg. 1 basis
+    q_j, q~_j of U serves every mass, each mass with its own recurrence state and its own
+    p, S, x; each mass's residual estimate and iterate equal the GMRES iterates of its own
+    rho + U (random 200 x 200 unitary, mu = 0.01, 0.02, 0.04)."""
+    from oracle import solvers
+    binding = _lib()
+    rng = np.random.default_rng(13)
+    Q, R = np.linalg.qr(rng.normal(size=(200, 200)) + 1j * rng.normal(size=(200, 200)))
+    U = Q * (np.diag(R) / np.abs(np.diag(R)))
+    b = rng.normal(size=200) + 1j * rng.normal(size=200)
+    mus = [0.01, 0.02, 0.04]
+    rhos = [(1 + m) / (1 - m) for m in mus]
+    nb = np.linalg.norm(b)
+    q = b / nb
+    qt = q.copy()
+    st = [np.array([0, 0, 0, 0, 1, 0, 1, 0, nb, 0, 0], dtype=np.float64) for _ in mus]
+    p = [np.zeros_like(b) for _ in mus]
+    S = [np.zeros_like(b) for _ in mus]
+    x = [np.zeros_like(b) for _ in mus]
+    hist = [[] for _ in mus]
+    nsteps = 35
+    for _ in range(nsteps):
+        u = U @ q
+        qtu = np.vdot(qt, u)
+        dots = [qtu.real, qtu.imag, np.vdot(u, u).real, np.vdot(qt, qt).real]
+        for k, rho in enumerate(rhos):
+            Rk, gs, iR, sp, z, g, gam, isg, sg = binding.ovl_host_sumr_step(rho, dots, st[k])
+            pn = (q - Rk * p[k] + gs * S[k]) * iR
+            S[k] = sp * S[k] + z * p[k]
+            p[k] = pn
+            x[k] = x[k] + g * pn
+            hist[k].append(abs(complex(st[k][8], st[k][9])))
+        qn = (u + gam * qt) * isg            # the basis step is the same for every mass
+        qt = sg * qt + np.conj(gam) * qn
+        q = qn
+    for k, rho in enumerate(rhos):
+        A = rho * np.eye(200) + U
+        xg, hg = solvers.minres_iterates(lambda v: A @ v, b, nsteps)
+        assert np.allclose(hist[k], hg, rtol=1e-10, atol=1e-13 * nb), k
+        assert np.linalg.norm(x[k] - xg) <= 1e-10 * np.linalg.norm(xg), k
