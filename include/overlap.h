@@ -402,6 +402,14 @@ void ovl_defl_destroy(ovl_defl* defl);
 ovl_status overlap_force(ovl_ctx* ctx, double mu, const void* phi, int dtype, int on_device, double tol,
                          double* dSdU, double* S);
 
+/* Host-only: the Rayleigh-Ritz step of K inside ovl_kernel_deflate (Sec. 1: the eigenpairs
+ * of the Hermitian kernel) on the span of m vectors x_1 .. x_m, from E = (x_i, x_j) and
+ * H = (x_i, K x_j) (m x m complex, row-major, interleaved): theta[m], signed, in the order of
+ * |theta|, and C (m x m complex, row-major) with X C orthonormal and C^dag H C = diag(theta).
+ * OVL_EBREAKDOWN when E has no Cholesky factor; OVL_EINVAL for m outside 1..1024, a null
+ * pointer or a non-finite entry. */
+ovl_status ovl_host_rayleigh_ritz(int m, const double* E, const double* H, double* theta, double* C);
+
 /* Kernel low-mode deflation of the sign function (Sec. 1: sign(K) = sum_i psi_i psi_i^dag
  * sign(lambda_i); the smallest eigenvectors of K are deflated and the approximation covers
  * the rest of the spectrum). Finds the n_ev eigenpairs of the Hermitian kernel K with the

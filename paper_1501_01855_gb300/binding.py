@@ -77,6 +77,7 @@ _SIGS = {
     "ovl_host_ritz": (I, [I, DP, DP, DP, D, D, I, I, DP, DP, DP, ctypes.POINTER(I)]),
     "ovl_host_sumr_step": (I, [D, DP, DP, DP]),
     "ovl_host_defl_start": (I, [I, DP, DP, DP, DP, DP, I, DP, DP, DP, I, DP]),
+    "ovl_host_rayleigh_ritz": (I, [I, DP, DP, DP, DP]),
     "overlap_create": (I, [ctypes.POINTER(P), ctypes.POINTER(I), DP, D, D, I, D, ctypes.POINTER(ovl_params)]),
     "overlap_destroy": (None, [P]),
     "overlap_last_error": (ctypes.c_char_p, [P]),
@@ -303,6 +304,16 @@ def ovl_host_defl_start(VV, WW, WV, G5VV, G5VW, VB, WB, mus, per_vector=False):
     _check(load().ovl_host_defl_start(n, _cptr(VV), _cptr(WW), _cptr(WV), _cptr(G5VV), _cptr(G5VW), nsys, _cptr(VB),
                                       _cptr(WB), _dptr(mus), 1 if per_vector else 0, _cptr(co)))
     return co
+
+
+def ovl_host_rayleigh_ritz(E, H):
+    """Rayleigh-Ritz of K from E = X^dag X and H = X^dag K X (host): (theta by |theta|, C)."""
+    E, H = _square_c128(E), _square_c128(H)
+    m = E.shape[0]
+    th = np.zeros(m)
+    C = np.zeros((m, m), dtype=np.complex128)
+    _check(load().ovl_host_rayleigh_ritz(m, _cptr(E), _cptr(H), _dptr(th), _cptr(C)))
+    return th, C
 
 
 def ovl_host_tridiag_extremes(d, e):

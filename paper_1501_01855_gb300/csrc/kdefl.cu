@@ -29,19 +29,15 @@ namespace ovl {
 
 namespace {
 
-// Rayleigh-Ritz of K on the span of X (m vectors): Xn = X C orthonormal with C^dag (X^dag K X)
-// C = diag(theta) (ascending |theta|), KXn = (K X) C, res_i = ||K xn_i - theta_i xn_i||,
-// q_i = ||K xn_i||^2 (the Rayleigh quotients of K^2).
-ovl_status kd_rayleigh_ritz(ovl_ctx* c, Field& X, Field& KX, Field& Xn, Field& KXn, Field& R, int m,
-                            std::vector<double>& theta, std::vector<double>& res, std::vector<double>& q) {
-  std::vector<cd> E, H;
-  OVL_TRY(gram_host(c, X, 0, m, X, 0, m, 0, E));
-  OVL_TRY(wilson_apply_field(c, P64, X, 0, KX, 0, m));
-  OVL_TRY(gram_host(c, X, 0, m, KX, 0, m, 0, H));
+// The host part of the Rayleigh-Ritz step of K (Sec. 1 eigenpairs) on the span of m vectors
+// X: from E = (x_i, x_j) and H = (x_i, K x_j) (row-major), the coefficients C (m x m) with
+// X C orthonormal and C^dag H C = diag(theta), theta in the order of |theta|. OVL_EBREAKDOWN
+// when E has no Cholesky factor (the block lost linear independence).
+ovl_status kd_rayleigh_ritz_host(int m, std::vector<cd> E, std::vector<cd> H, std::vector<double>& theta,
+                                 std::vector<cd>& C) {
   // B = L^-dag with E = L L^dag, so that B^dag E B = 1
   std::vector<cd> L = E;
-  if (cholesky_lower(m, L.data()) != 0)
-    return set_err(c, OVL_EBREAKDOWN, "kernel deflation: the filtered block lost linear independence");
+  if (cholesky_lower(m, L.data()) != 0) return OVL_EBREAKDOWN;
   std::vector<cd> Li((size_t)m * m), B((size_t)m * m);
   lower_inverse(m, L.data(), Li.data());
   for (int i = 0; i < m; ++i)
@@ -72,7 +68,7 @@ ovl_status kd_rayleigh_ritz(ovl_ctx* c, Field& X, Field& KX, Field& Xn, Field& K
   std::iota(ord.begin(), ord.end(), 0);
   std::stable_sort(ord.begin(), ord.end(), [&](int x, int y) { return std::fabs(w[x]) < std::fabs(w[y]); });
   // C = B Z, columns in the order of |theta|
-  std::vector<cd> C((size_t)m * m);
+  C.assign((size_t)m * m, 0.0);
   theta.resize(m);
   for (int jj = 0; jj < m; ++jj) {
     const int j = ord[jj];
@@ -83,6 +79,21 @@ ovl_status kd_rayleigh_ritz(ovl_ctx* c, Field& X, Field& KX, Field& Xn, Field& K
       C[(size_t)i * m + jj] = s;
     }
   }
+  return OVL_OK;
+}
+
+// Rayleigh-Ritz of K on the span of X (m vectors): Xn = X C orthonormal with C^dag (X^dag K X)
+// C = diag(theta) (ascending |theta|), KXn = (K X) C, res_i = ||K xn_i - theta_i xn_i||,
+// q_i = ||K xn_i||^2 (the Rayleigh quotients of K^2).
+ovl_status kd_rayleigh_ritz(ovl_ctx* c, Field& X, Field& KX, Field& Xn, Field& KXn, Field& R, int m,
+                            std::vector<double>& theta, std::vector<double>& res, std::vector<double>& q) {
+  std::vector<cd> E, H;
+  OVL_TRY(gram_host(c, X, 0, m, X, 0, m, 0, E));
+  OVL_TRY(wilson_apply_field(c, P64, X, 0, KX, 0, m));
+  OVL_TRY(gram_host(c, X, 0, m, KX, 0, m, 0, H));
+  std::vector<cd> C;
+  if (kd_rayleigh_ritz_host(m, E, H, theta, C) != OVL_OK)
+    return set_err(c, OVL_EBREAKDOWN, "kernel deflation: the filtered block lost linear independence");
   OVL_TRY(combine_host(c, X, 0, m, C, Xn, 0, m, 0));
   OVL_TRY(combine_host(c, KX, 0, m, C, KXn, 0, m, 0));
   std::vector<cd> one(m, 1.0), mt(m);
@@ -129,6 +140,22 @@ ovl_status kd_filter(ovl_ctx* c, Field*& X, Field*& Y1, Field*& Y2, Field& T, Fi
 }  // namespace ovl
 
 using namespace ovl;
+
+extern "C" ovl_status ovl_host_rayleigh_ritz(int m, const double* E, const double* H, double* theta, double* C) {
+  if (m < 1 || m > 1024 || !E || !H || !theta || !C) return OVL_EINVAL;
+  const size_t mm = (size_t)m * m;
+  for (size_t i = 0; i < 2 * mm; ++i)
+    if (!std::isfinite(E[i]) || !std::isfinite(H[i])) return OVL_EINVAL;
+  const cd* e = reinterpret_cast<const cd*>(E);
+  const cd* h = reinterpret_cast<const cd*>(H);
+  std::vector<double> th;
+  std::vector<cd> c;
+  const ovl_status st = kd_rayleigh_ritz_host(m, std::vector<cd>(e, e + mm), std::vector<cd>(h, h + mm), th, c);
+  if (st != OVL_OK) return st;
+  std::memcpy(theta, th.data(), sizeof(double) * m);
+  std::memcpy(C, c.data(), sizeof(cd) * mm);
+  return OVL_OK;
+}
 
 extern "C" ovl_status ovl_kernel_deflate(ovl_ctx* c, int n_ev, double tol, int max_iter, int n_poles, double* lambda,
                                          double* residual, double* a_out, int* n_poles_out, int* iters_done) {

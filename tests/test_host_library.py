@@ -484,3 +484,44 @@ def test_host_sumr_shared_basis_for_several_masses():
         xg, hg = solvers.minres_iterates(lambda v: A @ v, b, nsteps)
         assert np.allclose(hist[k], hg, rtol=1e-10, atol=1e-13 * nb), k
         assert np.linalg.norm(x[k] - xg) <= 1e-10 * np.linalg.norm(xg), k
+
+
+def test_host_rayleigh_ritz_of_K():
+    """The Rayleigh-Ritz step of the kernel low-mode deflation (Sec. 1) on given Gram blocks
+    against SciPy's generalized Hermitian eigensolver: theta in the order of |theta| (signed),
+    X C orthonormal, C^dag H C diagonal; exact low eigenvectors of K in the span come out
+    exactly among the Ritz pairs; a block with a zero vector (no Cholesky factor of E) is
+    OVL_EBREAKDOWN."""
+    import scipy.linalg
+    from tests.oracle_util import dense_setup
+    binding = _lib()
+    _, Kd, _, wK = dense_setup((2, 2, 2, 2))
+    rng = np.random.default_rng(31)
+    m = 14
+    X = rng.normal(size=(192, m)) + 1j * rng.normal(size=(192, m))
+    E, H = X.conj().T @ X, X.conj().T @ (Kd @ X)
+    th, C = binding.ovl_host_rayleigh_ritz(E, H)
+    ref = scipy.linalg.eigh(0.5 * (H + H.conj().T), E, eigvals_only=True)
+    assert np.allclose(np.sort(th), np.sort(ref), rtol=1e-10, atol=1e-12)
+    assert np.all(np.diff(np.abs(th)) >= 0)
+    W = X @ C
+    assert np.allclose(W.conj().T @ W, np.eye(m), atol=1e-10)
+    assert np.allclose(C.conj().T @ H @ C, np.diag(th), atol=1e-10)
+    # a block that holds the 4 lowest-|lambda| eigenvectors of K returns them exactly among its
+    # Ritz pairs (K is indefinite: the random directions add Ritz values anywhere inside its
+    # spectrum, so these need not come first)
+    w, Q = np.linalg.eigh(Kd)
+    low = Q[:, np.argsort(np.abs(w))[:4]]
+    Xl = np.concatenate([low, rng.normal(size=(192, 6)) + 1j * rng.normal(size=(192, 6))], axis=1)
+    Xl = Xl @ (rng.normal(size=(10, 10)) + 1j * rng.normal(size=(10, 10)))
+    th2, C2 = binding.ovl_host_rayleigh_ritz(Xl.conj().T @ Xl, Xl.conj().T @ (Kd @ Xl))
+    Wl = Xl @ C2
+    for lam in w[np.argsort(np.abs(w))[:4]]:
+        i = int(np.argmin(np.abs(th2 - lam)))
+        assert abs(th2[i] - lam) <= 1e-10
+        assert np.linalg.norm(Kd @ Wl[:, i] - lam * Wl[:, i]) <= 1e-9
+    Xd = X[:, :5].copy()
+    Xd[:, 2] = 0.0                          # a zero vector: E has a zero pivot
+    with pytest.raises(binding.OvlError) as e:
+        binding.ovl_host_rayleigh_ritz(Xd.conj().T @ Xd, Xd.conj().T @ (Kd @ Xd))
+    assert e.value.status == binding.OVL_EBREAKDOWN
