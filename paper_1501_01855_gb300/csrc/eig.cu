@@ -61,8 +61,17 @@ void ritz_host(int k, const cd* E_in, const cd* MVD_in, const cd* G5_in, double 
   std::vector<cd> B;
   int r = k;
   {
+    // the Cholesky coordinates only while every pivot L_jj^2 stays above 1e-10 of the largest
+    // diagonal of E (the cut the eigendecomposition below applies to E's eigenvalues): a
+    // nearly dependent basis (SUMR vectors lose orthogonality with an inexact sign, Sec. 5)
+    // can pass the factorisation with a pivot at rounding level, and U^-1 ~ 1/pivot then
+    // wrecks the projected matrix
     std::vector<cd> L = E;
-    if (cholesky_lower(k, L.data()) == 0) {
+    double emax = 0.0;
+    for (int i = 0; i < k; ++i) emax = std::max(emax, E[(size_t)i * k + i].real());
+    bool chol = cholesky_lower(k, L.data()) == 0;
+    for (int i = 0; chol && i < k; ++i) chol = std::norm(L[(size_t)i * k + i]) >= 1e-10 * emax;
+    if (chol) {
       std::vector<cd> Li((size_t)k * k);
       lower_inverse(k, L.data(), Li.data());
       B.resize((size_t)k * k);

@@ -525,3 +525,25 @@ def test_host_rayleigh_ritz_of_K():
     with pytest.raises(binding.OvlError) as e:
         binding.ovl_host_rayleigh_ritz(Xd.conj().T @ Xd, Xd.conj().T @ (Kd @ Xd))
     assert e.value.status == binding.OVL_EBREAKDOWN
+
+
+def test_host_ritz_nearly_dependent_basis():
+    """A basis with a vector within 1e-7 or 1e-6 of another (SUMR vectors lose orthogonality
+    with an inexact sign, Sec. 5) factorises with a pivot of 1e-14 to 1e-12 of the largest
+    diagonal of E. The Ritz step must give the Ritz pairs of the well-conditioned span (the
+    orthonormalisation drops the near-null direction); taking U^-1 from such a pivot put
+    errors of 6e-3 to 2e-1 into the Ritz values and 1e-2 into the orthonormality."""
+    from oracle import eigen
+    binding = _lib()
+    for seed in range(6):
+        for eps in (1e-7, 1e-6):
+            mu, D, G5, V, VD, E, MVD, G5m = _ritz_setup(16, 100 + seed)
+            rng = np.random.default_rng(seed)
+            Vr = np.concatenate([V, V[:, :1] + eps * rng.normal(size=(192, 1))], axis=1)
+            VDr = D @ Vr
+            ritz, C, res = binding.ovl_host_ritz(Vr.conj().T @ Vr, VDr.conj().T @ VDr, Vr.conj().T @ (G5 @ VDr),
+                                                 mu, 0.01, 5)
+            lam, _, _, _ = eigen.ritz_recalculate(V, VD, mu, 0.01, 5, (16, 4, 3))
+            assert np.allclose(ritz, lam, rtol=1e-7, atol=0), (seed, eps)
+            W = Vr @ C
+            assert np.allclose(W.conj().T @ W, np.eye(5), atol=1e-9), (seed, eps)
