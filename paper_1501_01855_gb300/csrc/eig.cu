@@ -8,9 +8,9 @@
 // The Gram blocks run on the GPU (tensor cores with FP64-level accuracy by default, see
 // tcgram.cu); the m x m algebra is FP64 on the host. If the basis has lost linear independence (Sec. 5 notes that
 // orthogonality of the SUMR vectors is quickly lost with an inexact sign) and the
-// Cholesky factor does not exist, the basis is orthonormalised through the
-// eigendecomposition of E instead, dropping directions below 1e-10 of its largest
-// eigenvalue.
+// Cholesky factor does not exist, or has a pivot below 1e-10 of the largest diagonal of E,
+// the basis is orthonormalised through the eigendecomposition of E instead, dropping
+// directions below 1e-10 of its largest eigenvalue.
 //
 // Sign accuracy while accumulating: the bound of Sec. 5.1 (the one used for the
 // paper's runs),
