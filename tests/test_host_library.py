@@ -547,3 +547,27 @@ def test_host_ritz_nearly_dependent_basis():
             assert np.allclose(ritz, lam, rtol=1e-7, atol=0), (seed, eps)
             W = Vr @ C
             assert np.allclose(W.conj().T @ W, np.eye(5), atol=1e-9), (seed, eps)
+
+
+def test_host_ritz_restart_properties_over_random_bases():
+    """The locally optimal restart on 20 random bases (k = 14..59, various keep): at least keep
+    pairs (near-duplicates of the two Ritz sets are dropped), the lowest keep values at or
+    below the Ritz values of the whole basis (the restart span contains those vectors) and
+    at or above the true eigenvalues of D^dag D + 2 mu delta gamma5 D, orthonormal vectors,
+    and W^dag M W = diag(ritz) exactly (a Rayleigh-Ritz of M on their span)."""
+    from oracle import eigen
+    binding = _lib()
+    for seed in range(20):
+        k = int(np.random.default_rng(seed).integers(14, 60))
+        keep = int(np.random.default_rng(seed + 99).integers(2, (k - 1) // 2))
+        mu, D, G5, V, VD, E, MVD, G5m = _ritz_setup(k, 500 + seed)
+        ritz, C, res = binding.ovl_host_ritz(E, MVD, G5m, mu, 0.01, keep, restart=True)
+        lam, _, _, _ = eigen.ritz_recalculate(V, VD, mu, 0.01, keep, (16, 4, 3))
+        Mop = D.conj().T @ D + 2 * mu * 0.01 * (G5 @ D)
+        true = np.linalg.eigvalsh(Mop)
+        W = V @ C
+        assert keep <= len(ritz) <= 2 * keep, seed
+        assert np.all(ritz[:keep] <= lam * (1 + 1e-12) + 1e-14), seed
+        assert np.all(ritz >= true[:len(ritz)] - 1e-12), seed
+        assert np.abs(W.conj().T @ W - np.eye(len(ritz))).max() <= 1e-10, seed
+        assert np.allclose(W.conj().T @ Mop @ W, np.diag(ritz), atol=1e-10), seed
