@@ -571,3 +571,25 @@ def test_host_ritz_restart_properties_over_random_bases():
         assert np.all(ritz >= true[:len(ritz)] - 1e-12), seed
         assert np.abs(W.conj().T @ W - np.eye(len(ritz))).max() <= 1e-10, seed
         assert np.allclose(W.conj().T @ Mop @ W, np.diag(ritz), atol=1e-10), seed
+
+
+@pytest.mark.parametrize("seed", [12, 13, 14])
+def test_host_sumr_estimate_with_an_inexact_sign(seed):
+    """With the sign applied inexactly (U + P, ||P|| = eta up to 1e-3: a relaxed sign of Sec. 3),
+    the recurrence takes gamma_j as a projection and sigma_j = ||u + gamma_j q~_j||, so that
+    V q_j = sigma_j q_{j+1} - gamma_j q~_j holds for the vectors computed (reading 8): its
+    residual estimate stays the true residual of the operator it was given, to 1e-2 of itself
+    over 60 steps."""
+    binding = _lib()
+    mu = 0.05
+    rho = (1 + mu) / (1 - mu)
+    rng = np.random.default_rng(seed)
+    Q, R = np.linalg.qr(rng.normal(size=(200, 200)) + 1j * rng.normal(size=(200, 200)))
+    U = Q * (np.diag(R) / np.abs(np.diag(R)))
+    b = rng.normal(size=200) + 1j * rng.normal(size=200)
+    for eta in (1e-6, 1e-4, 1e-3):
+        P = rng.normal(size=(200, 200)) + 1j * rng.normal(size=(200, 200))
+        P *= eta / np.linalg.norm(P, 2)
+        x, hist = _sumr_dense(binding, U + P, rho, b, 60)
+        true = np.linalg.norm(b - (rho * np.eye(200) + U + P) @ x)
+        assert abs(true - hist[-1]) <= 1e-2 * hist[-1], (eta, true, hist[-1])
