@@ -507,6 +507,15 @@ def extras(args, ctx, dv, dout, ref_out, B, torch, stream, hbm):
             for _ in range(3):
                 B.ovl_host_eigh(A)
             res["m%d" % m] = (time.perf_counter() - t0) / 3 * 1e3
+        # a whole Ritz restart on the host (Alg. 6 with the locally optimal restart) at the
+        # 24^3 x 48 accumulation's sizes: basis 192, 64 kept, on Gram blocks of random data
+        V = rng.normal(size=(2048, 192)) + 1j * rng.normal(size=(2048, 192))
+        VD = rng.uniform(0.05, 1.0, size=(2048, 1)) * V
+        E, M, G = V.conj().T @ V, VD.conj().T @ VD, V.conj().T @ VD
+        B.ovl_host_ritz(E, M, G, 0.05, 0.01, 64, restart=True)
+        t0 = time.perf_counter()
+        B.ovl_host_ritz(E, M, G, 0.05, 0.01, 64, restart=True)
+        res["ritz_restart_k192_keep64"] = (time.perf_counter() - t0) * 1e3
         out["host_eigh_ms"] = res
     # Gram block of the Ritz step (128 x 128 spinors on 16^3 x 32): tensor cores at FP64 level
     # against the CUDA-core kernel with FP32 products
