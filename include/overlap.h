@@ -207,6 +207,12 @@ ovl_status ovl_zolotarev_coeffs(int n, double a, double b, double* omega, double
  *                             Gershgorin interval: the extremes of the Lanczos tridiagonal
  *                             of K^2, whose square roots estimate the interval [a, b] of
  *                             |K| that the rational of Sec. 3 covers. */
+ovl_status ovl_host_eigh(int n, const double* a, double* w, double* z);
+ovl_status ovl_host_cholesky(int n, const double* a, double* l);
+ovl_status ovl_host_lower_inverse(int n, const double* l, double* li);
+ovl_status ovl_host_lu_solve(int n, const double* a, const double* b, int nb, double* x);
+ovl_status ovl_host_tridiag_extremes(int n, const double* d, const double* e, double* lmin, double* lmax);
+
 /* Host-only: one step of the library's relSUMR recurrence for one system (Algs. 1-2, Sec. 2;
  * the short recurrence re-derived from App. A: progressive Givens QR of rho I + B^), as the
  * solver runs it between the sign application u = V q_j with its fused reductions and the
@@ -240,23 +246,19 @@ ovl_status ovl_host_defl_start(int n, const double* VV, const double* WW, const 
 /* Host-only: the k x k algebra of one Ritz step (Alg. 6) as the eigen accumulation runs it
  * between its Gram blocks and the rotation of the basis, for a basis v_1 .. v_k with
  * v^D_i = D(mu) v_i (Sec. 5). E = (v_i, v_j), MVD = (v^D_i, v^D_j), G5 = (v_i, gamma5 v^D_j):
- * k x k complex, row-major, interleaved (re, im). Cholesky E = U^dag U (or, without a factor,
- * the eigendecomposition of E with directions below 1e-10 of its largest eigenvalue
- * dropped), eigenvectors Y of U^-dag (MVD + 2 mu delta G5) U^-1, the lowest keep kept.
- * restart = 1 is the locally optimal restart of a full basis: the lowest keep Ritz vectors
- * of the basis and of the basis without v_k, Rayleigh-Ritz on their span (up to 2 keep
- * pairs). Out: *kept, the Ritz values ritz (ascending; D^dag D + 2 mu delta gamma5 D),
+ * k x k complex, row-major, interleaved (re, im). Cholesky E = U^dag U (or, without a factor
+ * or with a pivot below 1e-10 of E's largest diagonal, the eigendecomposition of E with
+ * directions below 1e-10 of its largest eigenvalue dropped), eigenvectors Y of
+ * U^-dag (MVD + 2 mu delta G5) U^-1, the lowest keep kept. restart = 1 is the locally
+ * optimal restart of a full basis (on the Cholesky path): the lowest keep Ritz vectors of
+ * the basis and of the basis without v_k, Rayleigh-Ritz on their span (keep to 2 keep pairs;
+ * near-duplicates of the two sets are dropped). Out: *kept, the Ritz values ritz (ascending; D^dag D + 2 mu delta gamma5 D),
  * the coefficients C (k x *kept complex, row-major) of the Ritz vectors in v_1 .. v_k and
  * the residual norms ||gamma5 v^D - v (v, gamma5 v^D)|| (res); ritz and res hold 2 keep
  * doubles, C 2 k keep complex numbers. OVL_EINVAL for k outside 1..1024, keep outside 1..k,
  * mu outside (0, 1), delta < 0, a null pointer or a non-finite Gram entry. */
 ovl_status ovl_host_ritz(int k, const double* E, const double* MVD, const double* G5, double mu, double delta,
                          int keep, int restart, double* ritz, double* C, double* res, int* kept);
-ovl_status ovl_host_eigh(int n, const double* a, double* w, double* z);
-ovl_status ovl_host_cholesky(int n, const double* a, double* l);
-ovl_status ovl_host_lower_inverse(int n, const double* l, double* li);
-ovl_status ovl_host_lu_solve(int n, const double* a, const double* b, int nb, double* x);
-ovl_status ovl_host_tridiag_extremes(int n, const double* d, const double* e, double* lmin, double* lmax);
 
 /* Zolotarev data of the context: omega[n], sigma[n] (may be NULL; n the pole count in use:
  * n_poles at create, or the count ovl_kernel_deflate chose),
