@@ -89,12 +89,14 @@ def test_dense_gradient_equals_matrix_free():
 
 def test_matrix_free_gradient_quick():
     """The matrix-free gradient (CG solves at 1e-9) equals the dense form to 1e-6 on 2^4
-    with a 4-pole rational: the quick form of the check above, cheap enough to rerun under
-    planted mistakes."""
+    with a 4-pole rational, and the action to 1e-7: the quick form of the check above, cheap
+    enough to rerun under planted mistakes."""
     m0, mu = 1.4, 0.05
     om, sg, _ = zo.zolotarev(4, 0.15, 2.6)
     U = synth.gauge_links((2, 2, 2, 2), 0.3, 61)
     phi = synth.gaussian_source((2, 2, 2, 2), 62)
     G1 = force.gradient(U, phi, m0, mu, om, sg, tol=1e-9)
-    G2, _ = force.gradient_dense(U, phi, m0, mu, om, sg)
+    G2, S2 = force.gradient_dense(U, phi, m0, mu, om, sg)
     assert np.linalg.norm(G1 - G2) <= 1e-6 * np.linalg.norm(G2)
+    S1, _ = force.action(U, phi, m0, mu, om, sg, tol=1e-9)
+    assert abs(S1 - S2) <= 1e-7 * abs(S2)

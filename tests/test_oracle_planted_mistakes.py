@@ -13,7 +13,9 @@ touched. A rewrite that leaves every output unchanged in exact arithmetic is no 
 dropping the conjugate in the q-tilde update of eigsumr_build changes the basis vectors
 but not their span (each new one still adds U q_j), so the Rayleigh-Ritz result of
 Alg. 6 is the same; the same rewrite in sumr_basis, whose basis is an output, is a
-case. Pins that run the oracle in a spawn process pool (the workers import the
+case. Neither is a rewrite that keeps an iteration from converging (gamma5 dropped from
+H, whose square then is no CG operator): it is caught only after its solves reach their
+iteration limits, minutes later. Pins that run the oracle in a spawn process pool (the workers import the
 unmodified oracle) and the minute-long matrix-free force pins are not used here: the
 matrix-free gradient is checked by the quick form of its equality with the dense
 gradient, whose own mistakes are caught by finite differences.
@@ -241,6 +243,7 @@ CASES = [
      ["matrix-free gradient = dense gradient"]),
     (force, "gradient", "psi = apply_H(U, chi, m0, mu, omega, sigma, tol, antiperiodic_t)", "psi = chi",
      ["matrix-free gradient = dense gradient"]),
+    (force, "action", "overlap.vdot(phi, chi)", "overlap.vdot(chi, chi)", ["matrix-free gradient = dense gradient"]),
 ]
 
 
